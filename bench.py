@@ -1,0 +1,398 @@
+#!/usr/bin/env python3
+"""Butterfly apply throughput on GB300: points x RHS per second.
+
+Default workload: the 2-D generalized Radon analogue, N = 1024 (2^20 sources and
+targets), q = 5 (r = 25), one right-hand side, mixed precision (complex64
+weights, FP32 interpolation, double-float phase).  A step is one full apply
+(init, 5 column levels, switch, 5 row levels, final) on inputs resident in HBM.
+
+Printed (one JSON line on rank 0): value (points*RHS/s), the FP64 GPU butterfly
+on the same problem and the speedup over it, relative errors against the FP64
+oracle (restricted butterfly on one level-m target box, and the direct sum on
+sampled targets), the roofline of the dominant kernel pass (timed live with CUDA
+events on the launching stream), the end-to-end rate through the host-buffer C
+ABI call, the CPU oracle baseline, SM clocks sampled during the timed region.
+
+--impl reference times the FP64 CPU oracle (the only reference this method has).
+Under torchrun every rank runs an independent replica (the single-problem path
+has no data-parallel split here); value is the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "butterfly apply points*RHS/s at stated rel-err, mixed/batched vs FP64 GPU; %roof"
+UNIT = "points*RHS/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="genradon2d", choices=["genradon2d", "genradon3d", "dft64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_1305_4650_gb300 import workloads as wl
+    return {"genradon2d": wl.genradon2d, "genradon3d": wl.genradon3d, "dft64": wl.dft64}[name]()
+
+
+# ------------------------------------------------------------------ clocks
+
+class Clocks:
+    """nvidia-smi sampler (200 ms) running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------- algorithmic work
+
+def phase_ops(phase: str, d: int, precision: str) -> int:
+    """FP32-pipe operations of one e^{2 pi i Phi} in the mixed path: the double-float
+    evaluation and mod-1 reduction of Phi (operation count of the formula) plus 20 for
+    the FP32 sincos of the reduced argument (range reduction and two short polynomials)."""
+    df_mul_frac, df_mul, df_add, df_sqrt, df_frac = 7, 7, 11, 10, 5
+    if phase == "dot":
+        core = d * df_mul_frac + d + 2
+    elif phase == "genradon":
+        core = d * df_mul_frac + d * df_mul + (d - 1) * df_add + df_sqrt + df_frac + 4
+    elif phase == "hypradon":
+        core = df_mul + df_add + df_sqrt + df_mul_frac + 2
+    else:
+        core = 2 * d * df_add + df_frac
+    return core + 20
+
+
+def pass_work(spec, ps, nrhs=1):
+    """Algorithmic counts of one kernel pass: phase evaluations, complex x real MACs
+    (interpolation), complex multiplies (modulation) and complex MACs (switch)."""
+    import numpy as np
+    import oracle
+    d, q, r, P = spec.d, spec.q, spec.r, spec.npts
+    z = oracle.cheb_nodes(q, spec.node_kind)
+    nz_src = int(np.count_nonzero([oracle.lagrange1(z, t, spec.src_off - 0.5) for t in range(q)])) ** d
+    nz_tgt = int(np.count_nonzero([oracle.lagrange1(z, t, spec.tgt_off - 0.5) for t in range(q)])) ** d
+    per_level_ph = (2 ** d + 1) * r
+    per_level_mac = (2 ** (d + 1) - 2) * q ** (d + 1)
+    w = dict(phases=0, macs=0, cmuls=0, cmacs=0)
+    w["phases"] += ps["k"] * per_level_ph * P
+    w["cmuls"] += ps["k"] * per_level_ph * P * nrhs
+    w["macs"] += ps["k"] * per_level_mac * P * nrhs
+    if ps["init"]:
+        w["phases"] += (1 + nz_src) * P
+        w["cmuls"] += (1 + nz_src) * P * nrhs
+    if ps["switch"]:
+        w["phases"] += r * r * P
+        w["cmacs"] += r * r * P * nrhs
+    if ps["final"]:
+        w["phases"] += (1 + nz_tgt) * P
+        w["cmuls"] += (1 + nz_tgt) * P * nrhs
+    return w
+
+
+def work_ops(spec, w):
+    return w["phases"] * phase_ops(spec.phase, spec.d, spec.precision) + 2 * w["macs"] + 4 * w["cmuls"] + 4 * w["cmacs"]
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_1305_4650_gb300 import bf, workloads as wl
+    if world > 1:
+        import torch.distributed as dist
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    spec = workload(args.workload)
+    nrhs = 1
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    prec = spec.precision
+    plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec)
+    passes = plan.passes()
+    g_np = wl.source_values(spec, nrhs, plan.cdtype, seed=spec.seed + rank)
+    g = torch.from_numpy(g_np).to(dev)
+    f = torch.empty_like(g)
+
+    # ---- timed region: K applies through the C ABI (device buffers)
+    for _ in range(args.warmup):
+        plan.apply(g, f)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.apply(g, f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
+    clocks = clk.summary()
+    value = spec.npts * nrhs * world / (ms * 1e-3)
+    out_f = f.cpu().numpy()
+
+    # ---- per-pass device times (same passes, events between launches on the same stream)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(passes) + 1)]
+    tpass = [0.0] * len(passes)
+    for _ in range(args.steps):
+        evs[0].record(stream)
+        for i in range(len(passes)):
+            plan.apply_pass(i, g.data_ptr(), f.data_ptr(), nrhs, sptr)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        for i in range(len(passes)):
+            tpass[i] += evs[i].elapsed_time(evs[i + 1]) / args.steps
+    dom = max(range(len(passes)), key=lambda i: tpass[i])
+    wdom = pass_work(spec, passes[dom], nrhs)
+    ops = work_ops(spec, wdom)
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2.07e9 / 1e12       # FP32-pipe Tops/s at the 2070 MHz max clock
+    achieved = ops / (tpass[dom] * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "Tops/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": f"pass{dom}:{passes[dom]['kind']} l0={passes[dom]['l0']} k={passes[dom]['k']}"
+                          + (" +init" if passes[dom]["init"] else "") + (" +switch" if passes[dom]["switch"] else "")
+                          + (" +final" if passes[dom]["final"] else ""),
+                "kernel_ms": round(tpass[dom], 4), "share": round(tpass[dom] / sum(tpass), 4),
+                "peak_basis": "152 SMs x 128 FP32 lanes x 2.07 GHz (derived, one FP32-pipe op per lane per clock)",
+                "pass_ms": [round(t, 4) for t in tpass]}
+    all_ops = sum(work_ops(spec, pass_work(spec, p, nrhs)) for p in passes)
+    roofline["apply_frac"] = round(all_ops / (ms * 1e-3) / 1e12 / peak, 4)
+
+    # ---- FP64 GPU butterfly on the same problem (the baseline of the speedup)
+    fp64 = None
+    if prec != "fp64" and args.fp64_steps > 0:
+        p64 = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="fp64")
+        g64 = g.to(torch.complex128)
+        f64 = torch.empty_like(g64)
+        p64.apply(g64, f64)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.fp64_steps):
+            p64.apply(g64, f64)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = max_over_ranks(a0.elapsed_time(a1) / args.fp64_steps)
+        fp64 = {"value": spec.npts * nrhs * world / (ms64 * 1e-3), "ms_per_step": round(ms64, 3),
+                "speedup_mixed_over_fp64": round(ms64 / ms, 2)}
+        out64 = f64.cpu().numpy()
+        p64.close()
+
+    # ---- end to end through the C ABI with host buffers (H2D + apply + D2H per step)
+    gh = torch.from_numpy(g_np).pin_memory()
+    fh = torch.empty_like(gh).pin_memory()
+    for _ in range(2):
+        plan.apply_host_ptr(gh.data_ptr(), fh.data_ptr(), nrhs, sptr)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        plan.apply_host_ptr(gh.data_ptr(), fh.data_ptr(), nrhs, sptr)
+    t1 = time.perf_counter()
+    barrier()
+    ms_e2e = max_over_ranks((t1 - t0) * 1e3 / args.steps)
+    nbytes = g_np.nbytes
+    e2e = {"value": spec.npts * nrhs * world / (ms_e2e * 1e-3), "unit": UNIT, "ms_per_step": round(ms_e2e, 3),
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+
+    # ---- accuracy against the oracle (rank 0)
+    acc = None
+    if rank == 0 and not args.no_accuracy:
+        import oracle
+        P = oracle.Problem(**spec.oracle_kwargs())
+        box = (1 << (spec.d * spec.switch_level)) // 3
+        g0 = g_np[0].astype(np.complex128)
+        tg = oracle.restricted_targets(P, spec.switch_level, box)
+        t0 = time.perf_counter()
+        ref = oracle.butterfly(P, g0, restrict=(spec.switch_level, box))[tg]
+        t_or = time.perf_counter() - t0
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        samp = tg[:: max(1, len(tg) // 32)]
+        direct = oracle.direct_sum(P, g0, targets=samp)
+        pos = np.searchsorted(tg, samp) if np.all(np.diff(tg) > 0) else [list(tg).index(s) for s in samp]
+        acc = {"rel_l2_vs_oracle_butterfly": rel(out_f[0][tg], ref),
+               "rel_l2_vs_direct_sum": rel(out_f[0][samp], direct),
+               "oracle_butterfly_vs_direct_sum": rel(ref[pos], direct),
+               "sample": f"{len(tg)} targets of level-{spec.switch_level} box {box}; direct sum on {len(samp)}",
+               "oracle_s": round(t_or, 2)}
+        if fp64 is not None:
+            fp64["rel_l2_vs_oracle_butterfly"] = rel(out64[0][tg], ref)
+            fp64["rel_l2_vs_direct_sum"] = rel(out64[0][samp], direct)
+
+    # ---- CPU oracle baseline (rank 0 at N = 1): restricted butterfly on one level-1 target box,
+    # which does 1/2^d of the apply's work and yields 1/2^d of the outputs
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_sample(spec, g_np[0])
+
+    plan.close()
+    if rank != 0:
+        return None
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64" if prec == "mixed" else "c128",
+            "data": "synthetic",
+            "config": {"workload": spec.name, "d": spec.d, "N": spec.N, "q": spec.q, "r": spec.r,
+                       "phase": spec.phase, "precision": prec, "nrhs": nrhs, "switch_level": spec.switch_level,
+                       "passes": len(passes), "fuse_levels": plan_fuse(passes),
+                       "l2": "no flush: each step streams ~1.7 GB of weights through the 129 MB L2",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "fp64_gpu": fp64, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * len(passes), "clocks": clocks}
+    return line
+
+
+def plan_fuse(passes):
+    return max(p["k"] for p in passes)
+
+
+def cpu_sample(spec, g0, level=1):
+    import numpy as np
+    import oracle
+    P = oracle.Problem(**spec.oracle_kwargs())
+    box = 0
+    n_out = spec.npts >> (spec.d * level)
+    t0 = time.perf_counter()
+    oracle.butterfly(P, np.asarray(g0, np.complex128), restrict=(level, box))
+    dt = time.perf_counter() - t0
+    return {"value": n_out / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+            "seconds": round(dt, 2),
+            "sample": f"FP64 oracle butterfly restricted to target box {box} at level {level}: "
+                      f"{n_out} of {spec.npts} outputs, 1/{2 ** (spec.d * level)} of the apply's translations"}
+
+
+# ---------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    import numpy as np
+    import oracle
+    from paper_1305_4650_gb300 import workloads as wl
+    spec = workload(args.workload)
+    g0 = wl.source_values(spec, 1, np.complex64)[0]
+    level = 2 if spec.d == 2 else 1
+    for _ in range(args.warmup):
+        cpu_sample(spec, g0, level)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        s = cpu_sample(spec, g0, level)
+        vals.append(s["value"])
+        secs.append(s["seconds"])
+    value = len(vals) / sum(1.0 / v for v in vals)
+    n_out = spec.npts >> (spec.d * level)
+    ms = n_out / value * 1e3
+    cpu = {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": s["sample"]}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": spec.name, "d": spec.d, "N": spec.N, "q": spec.q, "phase": spec.phase,
+                       "precision": "fp64 (CPU oracle)", "nrhs": 1},
+            "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        line = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

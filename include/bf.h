@@ -1,0 +1,152 @@
+/*
+ * bf.h -- C ABI of the GB300 (sm_103a) Chebyshev-interpolation butterfly.
+ *
+ * The operator (Poulson, Demanet, Maxwell, Ying, "A Parallel Butterfly
+ * Algorithm", Section 1, Eq. 1 and Eq. "phase"):
+ *
+ *     f(x_i) ~= sum_j exp(2 pi i Phi(x_i, y_j)) g(y_j),   i, j = 0 .. N^d - 1,
+ *
+ * applied by the butterfly of Algorithm 1 with the analytic tensor-product
+ * Chebyshev interpolation of Section 1.4 (column space below the switch level
+ * m, an r x r switch at level m, row space above it), r = q^d.
+ *
+ * Points.  Targets x_i and sources y_j sit on uniform grids, one per leaf box:
+ * with the row-major multi-index (i_0, ..., i_{d-1}) of flat index i (last
+ * index fastest),  x_k = x_lo[k] + (i_k + tgt_off) * x_w[k] / N  and likewise
+ * y_k = y_lo[k] + (j_k + src_off) * y_w[k] / N.
+ *
+ * Data.  g and f are contiguous arrays of nrhs x N^d complex numbers
+ * (interleaved real, imaginary; right-hand side slowest, then row-major
+ * points).  The element type is complex128 (two doubles) for BF_PREC_FP64 and
+ * complex64 (two floats) otherwise.  Device pointers must be 16-byte aligned.
+ *
+ * Streams.  Every apply is asynchronous on the given stream (a cudaStream_t
+ * passed as void*; NULL = legacy default stream).  Device-side errors surface
+ * at the caller's next synchronisation; launch errors are returned as
+ * BF_ERR_CUDA and the CUDA error code is kept in the plan (bf_last_cuda_error).
+ *
+ * Threads.  A plan owns one workspace; applies on one plan must be ordered on
+ * the same stream (or otherwise serialised).  Different plans are independent.
+ *
+ * Errors.  Invalid arguments return BF_ERR_INVALID_ARG and write nothing.
+ */
+#ifndef BF_GB300_H
+#define BF_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bf_plan_s *bf_plan;
+
+typedef enum {
+    BF_OK = 0,
+    BF_ERR_INVALID_ARG = 1,
+    BF_ERR_UNSUPPORTED = 2,
+    BF_ERR_NOMEM = 3,
+    BF_ERR_CUDA = 4,
+    BF_ERR_TIMEOUT = 5,
+    BF_ERR_INTERNAL = 6
+} bf_status;
+
+/* Phase functions Phi (cycles; the kernel is exp(2 pi i Phi)), Section 3:
+ *   BF_PHASE_DOT        Phi = s x.y                                  (Fourier, d = 1..3)
+ *   BF_PHASE_GENRADON   Phi = s (x.y + sqrt(sum_k a_k(x)^2 y_k^2)),  generalized Radon analogue;
+ *                       d=2: a_0 = (2 + sin2pi x0 sin2pi x1)/3, a_1 = (2 + cos2pi x0 cos2pi x1)/3;
+ *                       d=3: a_k = (2 + sin2pi x_k cos2pi x_{k+1 mod 3})/3
+ *   BF_PHASE_HYPRADON   Phi = s x_0 sqrt(y_0^2 + y_1^2 x_1^2),       hyperbolic Radon (d = 2 only)
+ *   BF_PHASE_SEPARABLE  Phi = s (sum_k sin 2pi(x_k + (k+1)/7) + sum_k y_k^2/(k+2)), a test phase
+ *                       for which the butterfly is exact (s = 0 gives Phi = 0). */
+typedef enum {
+    BF_PHASE_DOT = 0,
+    BF_PHASE_GENRADON = 1,
+    BF_PHASE_HYPRADON = 2,
+    BF_PHASE_SEPARABLE = 3
+} bf_phase_kind;
+
+/* Arithmetic of an apply.
+ *   BF_PREC_FP64   complex128 weights, FP64 interpolation, FP64 phase, FP64 sincos.
+ *   BF_PREC_MIXED  complex64 weights, FP32 interpolation and sincos; Phi is evaluated
+ *                  and reduced mod 1 in double-float (pairs of FP32 numbers, >= 44
+ *                  significant bits) before the FP32 sincos. */
+typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1 } bf_precision;
+
+typedef struct {
+    double x_lo[3], x_w[3];   /* target domain: prod_k [x_lo[k], x_lo[k] + x_w[k]), x_w > 0  */
+    double y_lo[3], y_w[3];   /* source domain, y_w > 0                                     */
+    double phase_scale;       /* s in the phase formulas above                              */
+    double tgt_off, src_off;  /* point offset inside its leaf box, in [0, 1)               */
+    int32_t precision;        /* bf_precision                                               */
+    int32_t switch_level;     /* m in [0, L-1]; -1 selects floor(L/2)                       */
+    int32_t node_kind;        /* 0 Chebyshev-Lobatto cos(j pi/(q-1))/2, 1 first kind        */
+    int32_t max_nrhs;         /* largest nrhs an apply may use (>= 1)                       */
+    int32_t fuse_levels;      /* levels fused per kernel pass; 0 selects the default        */
+    int32_t reserved[7];      /* must be zero                                               */
+} bf_params;
+
+/* Defaults for the problem classes of Section 3: X = [0,1)^d, Y = [-N/2, N/2)^d
+ * (integer frequencies), s = 1, points at the lower corner of their leaf boxes,
+ * BF_PREC_MIXED, m = floor(L/2), Lobatto nodes, max_nrhs = 1. */
+bf_status bf_params_default(int d, int64_t N, bf_params *out);
+
+/* Build a plan for d in {2,3} (d = 1 is not compiled), N = 2^L with 1 <= L and
+ * N^d <= 2^30, q nodes per dimension (q in {2,3,4,5,6,8} for d = 2, q in {2,3,4}
+ * for d = 3; other q return BF_ERR_UNSUPPORTED),
+ * phase kind `phase` (HYPRADON needs d = 2).  Allocates device workspace of
+ * 2 * max_nrhs * N^d * q^d complex numbers plus small geometry tables on the
+ * current CUDA device.  On success *out owns that memory until bf_destroy. */
+bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_params *p,
+                         bf_plan *out);
+
+/* f = B g: g and f are device arrays of nrhs x N^d complex numbers (see Data).
+ * 0 <= nrhs <= max_nrhs; nrhs = 0 does nothing.  g is read only; f is overwritten.
+ * g and f must not overlap. */
+bf_status bf_apply(bf_plan plan, const void *g_dev, void *f_dev, int nrhs, void *stream);
+
+/* g = B^H f, the exact conjugate transpose of the approximate operator applied by
+ * bf_apply (every step conjugate-transposed, levels in reverse). */
+bf_status bf_apply_adjoint(bf_plan plan, const void *f_dev, void *g_dev, int nrhs, void *stream);
+
+/* Host-buffer variant of bf_apply: copies g_host to plan-owned device memory,
+ * applies, copies f back to f_host, and synchronises the stream before returning.
+ * Host buffers should be pinned for full copy bandwidth. */
+bf_status bf_apply_host(bf_plan plan, const void *g_host, void *f_host, int nrhs, void *stream);
+
+/* count independent problems, in order, on one stream: f[i] = B_i g[i] with nrhs[i]
+ * right-hand sides.  Each plan's workspace is used by its own problem only. */
+bf_status bf_apply_batched(const bf_plan *plans, const void *const *g_dev, void *const *f_dev,
+                           const int *nrhs, int count, void *stream);
+
+/* Release the plan and its device memory.  bf_destroy(NULL) is a no-op.  The caller
+ * must ensure no apply on this plan is still running. */
+bf_status bf_destroy(bf_plan plan);
+
+/* Static, human-readable name of a status code. */
+const char *bf_status_string(bf_status s);
+
+/* The CUDA error code behind the last BF_ERR_CUDA of this plan (0 if none). */
+bf_status bf_last_cuda_error(bf_plan plan, int *cuda_err);
+
+/* Introspection used by tests and the benchmark.
+ *   bf_plan_info: d, N, q, switch level m, levels fused per pass, number of kernel
+ *   launches per apply (per right-hand-side batch), bytes of device workspace. */
+bf_status bf_plan_info(bf_plan plan, int *d, int64_t *N, int *q, int *m, int *fuse_levels,
+                       int *launches_per_apply, int64_t *workspace_bytes);
+
+/* Instrumentation.  An apply is a fixed schedule of kernel passes (see
+ * bf_plan_info: launches_per_apply).  bf_apply_pass runs pass i of that schedule
+ * only, with the same arguments as bf_apply; running passes 0 .. n-1 in order on
+ * one stream is exactly bf_apply.  Used to time individual kernels with events
+ * recorded between passes.  bf_pass_info describes pass i: kind (0 column pass
+ * with optional init/switch, 1 row pass with optional final), first level l0,
+ * number of fused levels k, flags (1 init, 2 switch, 4 final). */
+bf_status bf_apply_pass(bf_plan plan, int i, const void *g_dev, void *f_dev, int nrhs, void *stream);
+bf_status bf_pass_info(bf_plan plan, int i, int *kind, int *l0, int *k, int *flags);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BF_GB300_H */

@@ -1,0 +1,237 @@
+"""Python binding of the C ABI in include/bf.h (argument marshalling only).
+
+Every step of the butterfly runs in the sm_103a kernels of ``libbf_gb300.so``;
+this module only converts arguments.  PyTorch supplies device memory and the
+current stream.  If the library has not been built, every entry point raises
+instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libbf_gb300.so")
+
+PHASE = {"dot": 0, "genradon": 1, "hypradon": 2, "separable": 3}
+PREC = {"fp64": 0, "mixed": 1}
+STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_ERR_NOMEM",
+          4: "BF_ERR_CUDA", 5: "BF_ERR_TIMEOUT", 6: "BF_ERR_INTERNAL"}
+
+EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_apply_host",
+           "bf_apply_batched", "bf_destroy", "bf_status_string", "bf_last_cuda_error", "bf_plan_info",
+           "bf_apply_pass", "bf_pass_info"]
+
+
+class BfError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(code, code)}")
+        self.code = code
+
+
+class BfParams(ctypes.Structure):
+    _fields_ = [("x_lo", ctypes.c_double * 3), ("x_w", ctypes.c_double * 3),
+                ("y_lo", ctypes.c_double * 3), ("y_w", ctypes.c_double * 3),
+                ("phase_scale", ctypes.c_double), ("tgt_off", ctypes.c_double), ("src_off", ctypes.c_double),
+                ("precision", ctypes.c_int32), ("switch_level", ctypes.c_int32), ("node_kind", ctypes.c_int32),
+                ("max_nrhs", ctypes.c_int32), ("fuse_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+
+
+_lib = None
+
+
+def load():
+    """Load the CUDA library (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"butterfly CUDA library not built: {LIB_PATH} missing "
+                               "(run __graft_entry__.build() or python -m paper_1305_4650_gb300.build)")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        lib.bf_params_default.argtypes = [i32, i64, ctypes.POINTER(BfParams)]
+        lib.bf_plan_create.argtypes = [i32, i64, i32, i32, ctypes.POINTER(BfParams), ctypes.POINTER(vp)]
+        lib.bf_apply.argtypes = [vp, vp, vp, i32, vp]
+        lib.bf_apply_adjoint.argtypes = [vp, vp, vp, i32, vp]
+        lib.bf_apply_host.argtypes = [vp, vp, vp, i32, vp]
+        lib.bf_apply_batched.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                         ctypes.POINTER(i32), i32, vp]
+        lib.bf_destroy.argtypes = [vp]
+        lib.bf_status_string.argtypes = [i32]
+        lib.bf_status_string.restype = ctypes.c_char_p
+        lib.bf_last_cuda_error.argtypes = [vp, ctypes.POINTER(i32)]
+        lib.bf_plan_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i64)]
+        lib.bf_apply_pass.argtypes = [vp, i32, vp, vp, i32, vp]
+        lib.bf_pass_info.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                     ctypes.POINTER(i32)]
+        for name in EXPORTS:
+            getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
+        lib.bf_status_string.restype = ctypes.c_char_p
+        _lib = lib
+    return _lib
+
+
+def _check(code: int, what: str, plan=None):
+    if code != 0:
+        if code == 4 and plan is not None and plan.value:
+            e = ctypes.c_int()
+            load().bf_last_cuda_error(plan, ctypes.byref(e))
+            what = f"{what} (cudaError {e.value})"
+        raise BfError(code, what)
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream) if hasattr(stream, "cuda_stream") else int(stream)
+
+
+class Plan:
+    """A butterfly plan: owns device workspace and geometry tables."""
+
+    def __init__(self, d: int, N: int, q: int, phase: str, precision: str = "mixed", scale: float = 1.0,
+                 x_lo=None, x_w=None, y_lo=None, y_w=None, tgt_off: float = 0.0, src_off: float = 0.0,
+                 switch_level: int = -1, node_kind: int = 0, max_nrhs: int = 1, fuse_levels: int = 0):
+        lib = load()
+        p = BfParams()
+        _check(lib.bf_params_default(d, N, ctypes.byref(p)), "bf_params_default")
+        for name, val in (("x_lo", x_lo), ("x_w", x_w), ("y_lo", y_lo), ("y_w", y_w)):
+            if val is not None:
+                arr = getattr(p, name)
+                for k, v in enumerate(list(val)[:3]):
+                    arr[k] = float(v)
+        p.phase_scale = scale
+        p.tgt_off, p.src_off = tgt_off, src_off
+        p.precision = PREC[precision]
+        p.switch_level = switch_level
+        p.node_kind = node_kind
+        p.max_nrhs = max_nrhs
+        p.fuse_levels = fuse_levels
+        h = ctypes.c_void_p()
+        _check(lib.bf_plan_create(d, N, q, PHASE[phase], ctypes.byref(p), ctypes.byref(h)), "bf_plan_create")
+        self._h = h
+        self.d, self.N, self.q, self.precision, self.max_nrhs = d, N, q, precision, max_nrhs
+        self.npts = N ** d
+        self.cdtype = np.complex128 if precision == "fp64" else np.complex64
+
+    @classmethod
+    def from_spec(cls, spec, max_nrhs: int = 1, precision: str | None = None, fuse_levels: int = 0) -> "Plan":
+        x_lo, x_w, y_lo, y_w = spec.domain()
+        return cls(spec.d, spec.N, spec.q, spec.phase, precision or spec.precision, spec.scale,
+                   x_lo, x_w, y_lo, y_w, spec.tgt_off, spec.src_off, spec.switch_level, spec.node_kind,
+                   max_nrhs, fuse_levels)
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def torch_dtype(self):
+        import torch
+        return torch.complex128 if self.precision == "fp64" else torch.complex64
+
+    def _nrhs(self, t) -> int:
+        import torch
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError("expected a CUDA tensor")
+        if t.dtype != self.torch_dtype():
+            raise TypeError(f"expected dtype {self.torch_dtype()}, got {t.dtype}")
+        if not t.is_contiguous() or t.numel() % self.npts:
+            raise ValueError("expected a contiguous tensor of nrhs x N^d elements")
+        return t.numel() // self.npts
+
+    def apply(self, g, f=None, stream=None):
+        """f = B g for CUDA tensors of shape (N^d,) or (nrhs, N^d)."""
+        import torch
+        n = self._nrhs(g)
+        if f is None:
+            f = torch.empty_like(g)
+        elif self._nrhs(f) != n:
+            raise ValueError("g and f differ in size")
+        _check(load().bf_apply(self._h, g.data_ptr(), f.data_ptr(), n, _stream_ptr(stream)), "bf_apply", self._h)
+        return f
+
+    def apply_adjoint(self, f, g=None, stream=None):
+        """g = B^H f."""
+        import torch
+        n = self._nrhs(f)
+        if g is None:
+            g = torch.empty_like(f)
+        elif self._nrhs(g) != n:
+            raise ValueError("f and g differ in size")
+        _check(load().bf_apply_adjoint(self._h, f.data_ptr(), g.data_ptr(), n, _stream_ptr(stream)),
+               "bf_apply_adjoint", self._h)
+        return g
+
+    def apply_host(self, g: np.ndarray, f: np.ndarray | None = None, stream=None) -> np.ndarray:
+        """Host-buffer apply: H2D copy, butterfly, D2H copy, stream synchronised."""
+        g = np.ascontiguousarray(g, dtype=self.cdtype)
+        if g.size % self.npts:
+            raise ValueError("g must hold nrhs x N^d values")
+        if f is None:
+            f = np.empty_like(g)
+        n = g.size // self.npts
+        st = 0 if stream is None else _stream_ptr(stream)
+        _check(load().bf_apply_host(self._h, g.ctypes.data, f.ctypes.data, n, st), "bf_apply_host", self._h)
+        return f
+
+    def apply_ptr(self, g_ptr: int, f_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
+        _check(load().bf_apply(self._h, g_ptr, f_ptr, nrhs, stream_ptr), "bf_apply", self._h)
+
+    def apply_host_ptr(self, g_ptr: int, f_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
+        _check(load().bf_apply_host(self._h, g_ptr, f_ptr, nrhs, stream_ptr), "bf_apply_host", self._h)
+
+    def apply_pass(self, i: int, g_ptr: int, f_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
+        """Run pass i of the apply schedule only (instrumentation)."""
+        _check(load().bf_apply_pass(self._h, i, g_ptr, f_ptr, nrhs, stream_ptr), "bf_apply_pass", self._h)
+
+    def passes(self) -> list[dict]:
+        i32 = ctypes.c_int
+        out = []
+        for i in range(self.info()["launches"]):
+            kind, l0, k, fl = i32(), i32(), i32(), i32()
+            _check(load().bf_pass_info(self._h, i, ctypes.byref(kind), ctypes.byref(l0), ctypes.byref(k),
+                                       ctypes.byref(fl)), "bf_pass_info")
+            out.append(dict(kind="row" if kind.value else "col", l0=l0.value, k=k.value,
+                            init=bool(fl.value & 1), switch=bool(fl.value & 2), final=bool(fl.value & 4)))
+        return out
+
+    def info(self) -> dict:
+        i32, i64 = ctypes.c_int, ctypes.c_int64
+        d, q, m, k, nl = i32(), i32(), i32(), i32(), i32()
+        N, ws = i64(), i64()
+        _check(load().bf_plan_info(self._h, ctypes.byref(d), ctypes.byref(N), ctypes.byref(q), ctypes.byref(m),
+                                   ctypes.byref(k), ctypes.byref(nl), ctypes.byref(ws)), "bf_plan_info")
+        return dict(d=d.value, N=N.value, q=q.value, m=m.value, fuse_levels=k.value, launches=nl.value,
+                    workspace_bytes=ws.value)
+
+    def last_cuda_error(self) -> int:
+        e = ctypes.c_int()
+        _check(load().bf_last_cuda_error(self._h, ctypes.byref(e)), "bf_last_cuda_error")
+        return e.value
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().bf_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def apply_batched(plans, gs, fs, nrhs, stream=None) -> None:
+    """Independent problems in order on one stream (device tensors)."""
+    n = len(plans)
+    vp = ctypes.c_void_p
+    P = (vp * n)(*[p.handle for p in plans])
+    G = (vp * n)(*[g.data_ptr() for g in gs])
+    F = (vp * n)(*[f.data_ptr() for f in fs])
+    R = (ctypes.c_int * n)(*nrhs)
+    _check(load().bf_apply_batched(P, G, F, R, n, _stream_ptr(stream)), "bf_apply_batched")

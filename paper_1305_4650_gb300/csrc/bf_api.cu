@@ -1,0 +1,503 @@
+// Host side of the C ABI declared in include/bf.h: validation, plan
+// construction (Chebyshev nodes, Lagrange child->parent matrices, per-level
+// feature tables, fusion schedule), device workspace and kernel launches.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/bf.h"
+#include "bf_device.cuh"
+#include "bf_launch.h"
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+
+struct Pass {
+    int row;     // 0: init/column/switch pass, 1: row/final pass
+    int l0, k, flags;
+    int T;       // tiles of 2^{dk} pairs per CTA
+};
+
+}  // namespace
+
+struct bf_plan_s {
+    int d = 0, L = 0, q = 0, r = 0, m = 0, kind = 0, prec = 0, node_kind = 0, max_nrhs = 1;
+    int kc = 0, kr = 0;        // fused levels per column / row pass
+    int64_t N = 0, npts = 0;   // N, N^d (= pairs per level)
+    bf_params prm{};
+    double z[bfk::QMAX] = {};
+    double M[2][bfk::QMAX][bfk::QMAX] = {};
+    double lsrc[bfk::QMAX] = {}, ltgt[bfk::QMAX] = {};
+    void *tt[3] = {}, *st[3] = {};
+    void *w0 = nullptr, *w1 = nullptr;
+    void *gstage = nullptr, *fstage = nullptr;
+    size_t csize = 8;          // bytes per complex number
+    int64_t ws_bytes = 0;
+    std::vector<Pass> passes;
+    const bfl::PassFns *fns = nullptr;
+    int last_cuda = 0;
+};
+
+namespace bfl {
+const PassFns *get_fns(int d, int q, int prec)
+{
+    if (d == 2) return prec == 0 ? fns_d2_f64(q) : fns_d2_mix(q);
+    if (d == 3) return prec == 0 ? fns_d3_f64(q) : fns_d3_mix(q);
+    return nullptr;
+}
+}  // namespace bfl
+
+namespace {
+
+double lagrange1(int q, const double *z, int t, double xi)
+{
+    double v = 1.0;
+    for (int k = 0; k < q; ++k)
+        if (k != t) v *= (xi - z[k]) / (z[t] - z[k]);
+    return v;
+}
+
+bf_status cuda_fail(bf_plan p, cudaError_t e)
+{
+    if (p) p->last_cuda = (int)e;
+    return e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA;
+}
+
+// per-dimension feature values of a target (x) or source (y) coordinate, see bf_device.cuh
+void tfeat(int kind, double s, int k, double x, double f[3])
+{
+    f[0] = f[1] = f[2] = 0.0;
+    switch (kind) {
+    case BF_PHASE_DOT: f[0] = s * x; break;
+    case BF_PHASE_GENRADON: f[0] = s * x; f[1] = std::sin(2 * kPi * x); f[2] = std::cos(2 * kPi * x); break;
+    case BF_PHASE_HYPRADON: f[0] = s * x; f[1] = x * x; break;
+    default: f[0] = s * std::sin(2 * kPi * (x + (k + 1) / 7.0)); break;
+    }
+}
+
+void sfeat(int kind, double s, int k, double y, double f[2])
+{
+    if (kind == BF_PHASE_SEPARABLE) {
+        f[0] = s * y * y / (k + 2.0);
+        f[1] = 0.0;
+    } else {
+        f[0] = y;
+        f[1] = y * y;
+    }
+}
+
+inline void split(double v, float &hi, float &lo)
+{
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+}
+
+template <class T>
+bf_status upload(bf_plan p, const std::vector<T> &h, void **dptr)
+{
+    cudaError_t e = cudaMalloc(dptr, h.size() * sizeof(T));
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    e = cudaMemcpy(*dptr, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    return BF_OK;
+}
+
+// Feature tables: level l, box i, slot j (j < q: node z_j, j = q: centre, j = q+1: grid point).
+bf_status build_tables(bf_plan p)
+{
+    const int q = p->q, L = p->L, d = p->d;
+    const double s = p->prm.phase_scale;
+    const int64_t nent = ((2LL << L) - 1) * (q + 2);
+    for (int k = 0; k < d; ++k) {
+        std::vector<double> T(nent * 3), S(nent * 2);
+        for (int l = 0; l <= L; ++l) {
+            const int64_t nb = 1LL << l;
+            const double w = p->prm.x_w[k] / (double)nb;
+            for (int64_t i = 0; i < nb; ++i) {
+                const double c = p->prm.x_lo[k] + ((double)i + 0.5) * w;
+                for (int j = 0; j < q + 2; ++j) {
+                    double x = j < q ? c + w * p->z[j] : (j == q ? c : p->prm.x_lo[k] + ((double)i + p->prm.tgt_off) * w);
+                    tfeat(p->kind, s, k, x, &T[((((1LL << l) - 1) * (q + 2)) + i * (q + 2) + j) * 3]);
+                }
+            }
+            const int64_t ns = 1LL << (L - l);
+            const double ws = p->prm.y_w[k] * (double)(1LL << l) / (double)(1LL << L);
+            for (int64_t i = 0; i < ns; ++i) {
+                const double c = p->prm.y_lo[k] + ((double)i + 0.5) * ws;
+                for (int j = 0; j < q + 2; ++j) {
+                    double y = j < q ? c + ws * p->z[j] : (j == q ? c : p->prm.y_lo[k] + ((double)i + p->prm.src_off) * ws);
+                    const int64_t off = ((2LL << L) - (2LL << (L - l))) * (q + 2);
+                    sfeat(p->kind, s, k, y, &S[(off + i * (q + 2) + j) * 2]);
+                }
+            }
+        }
+        bf_status st;
+        if (p->prec == BF_PREC_FP64) {
+            std::vector<bfk::PF64::TE> te(nent);
+            std::vector<bfk::PF64::SE> se(nent);
+            for (int64_t e = 0; e < nent; ++e) {
+                te[e].a = make_double2(T[3 * e], T[3 * e + 1]);
+                te[e].b = make_double2(T[3 * e + 2], 0.0);
+                se[e].a = make_double2(S[2 * e], S[2 * e + 1]);
+            }
+            if ((st = upload(p, te, &p->tt[k])) != BF_OK) return st;
+            if ((st = upload(p, se, &p->st[k])) != BF_OK) return st;
+        } else {
+            std::vector<bfk::PMIX::TE> te(nent);
+            std::vector<bfk::PMIX::SE> se(nent);
+            for (int64_t e = 0; e < nent; ++e) {
+                float a[8] = {};
+                for (int f = 0; f < 3; ++f) split(T[3 * e + f], a[2 * f], a[2 * f + 1]);
+                te[e].a = make_float4(a[0], a[1], a[2], a[3]);
+                te[e].b = make_float4(a[4], a[5], 0.f, 0.f);
+                float b[4];
+                split(S[2 * e], b[0], b[1]);
+                split(S[2 * e + 1], b[2], b[3]);
+                se[e].a = make_float4(b[0], b[1], b[2], b[3]);
+            }
+            if ((st = upload(p, te, &p->tt[k])) != BF_OK) return st;
+            if ((st = upload(p, se, &p->st[k])) != BF_OK) return st;
+        }
+    }
+    return BF_OK;
+}
+
+// shared memory of a pass: T tiles of 2^{dk} pairs, plus twice that as stage scratch
+size_t pass_smem(const bf_plan_s *p, const Pass &ps)
+{
+    return (size_t)3 * (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (size_t)p->r * p->csize;
+}
+
+// A CTA owns np pairs (np = 2^{d kmax} of the instantiation, fewer for tiny problems):
+// T = np / 2^{dk} tiles of a k-level pass.
+Pass make_pass(const bf_plan_s *p, int row, int l0, int k, int flags)
+{
+    const int64_t np = p->npts < p->fns->np ? p->npts : p->fns->np;
+    Pass ps{row, l0, k, flags, (int)(np >> (p->d * k))};
+    if (ps.T < 1) ps.T = 1;
+    return ps;
+}
+
+void schedule(bf_plan p)
+{
+    p->passes.clear();
+    const int m = p->m, L = p->L;
+    if (m == 0) {
+        p->passes.push_back(make_pass(p, 0, 0, 0, bfk::F_INIT | bfk::F_SWITCH));
+    } else {
+        int l = 0;
+        while (l < m) {
+            const int k = (m - l) < p->kc ? (m - l) : p->kc;
+            int fl = 0;
+            if (l == 0) fl |= bfk::F_INIT;
+            if (l + k == m) fl |= bfk::F_SWITCH;
+            p->passes.push_back(make_pass(p, 0, l, k, fl));
+            l += k;
+        }
+    }
+    int l = m;
+    while (l < L) {
+        const int k = (L - l) < p->kr ? (L - l) : p->kr;
+        p->passes.push_back(make_pass(p, 1, l, k, (l + k == L) ? bfk::F_FINAL : 0));
+        l += k;
+    }
+}
+
+template <class P>
+void fill_args(const bf_plan_s *p, bfk::KArgs<P> &a)
+{
+    std::memset(&a, 0, sizeof(a));
+    for (int k = 0; k < p->d; ++k) {
+        a.tt[k] = static_cast<const typename P::TE *>(p->tt[k]);
+        a.st[k] = static_cast<const typename P::SE *>(p->st[k]);
+    }
+    for (int h = 0; h < 2; ++h)
+        for (int t = 0; t < p->q; ++t)
+            for (int u = 0; u < p->q; ++u) a.M[h][t][u] = (typename P::R)p->M[h][t][u];
+    for (int t = 0; t < p->q; ++t) {
+        a.lsrc[t] = (typename P::R)p->lsrc[t];
+        a.ltgt[t] = (typename P::R)p->ltgt[t];
+    }
+    const double s = p->prm.phase_scale;
+    const double sgn = s > 0 ? 1.0 : (s < 0 ? -1.0 : 0.0);
+    if constexpr (P::is_f64) {
+        a.sc.s3 = s / 3.0;
+        a.sc.sgn = sgn;
+    } else {
+        float hi, lo;
+        split(s / 3.0, hi, lo);
+        a.sc.s3hi = hi;
+        a.sc.s3lo = lo;
+        a.sc.sgn = (float)sgn;
+    }
+    a.L = p->L;
+    a.kind = p->kind;
+    a.npts = p->npts;
+    a.wstride = p->npts * p->r;
+}
+
+// Run passes [first, last) of the forward schedule.  Pass i reads workspace
+// buffer i % 2 (or g when it initialises) and writes buffer (i + 1) % 2 (or f
+// when it evaluates the targets).
+template <class P>
+bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last)
+{
+    bfk::KArgs<P> a;
+    fill_args<P>(p, a);
+    a.g = static_cast<const typename P::C *>(g);
+    a.f = static_cast<typename P::C *>(f);
+    void *buf[2] = {p->w0, p->w1};
+    for (int i = first; i < last; ++i) {
+        const Pass &ps = p->passes[i];
+        a.l0 = ps.l0;
+        a.k = ps.k;
+        a.flags = ps.flags;
+        a.T = ps.T;
+        a.win = static_cast<const typename P::C *>(buf[i & 1]);
+        a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
+        const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
+        const size_t smem = pass_smem(p, ps);
+        cudaError_t e = (ps.row ? p->fns->row : p->fns->col)(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
+        if (e != cudaSuccess) return cuda_fail(p, e);
+    }
+    return BF_OK;
+}
+
+bool supported_q(int d, int q) { return bfl::get_fns(d, q, 1) != nullptr && bfl::get_fns(d, q, 0) != nullptr; }
+
+}  // namespace
+
+extern "C" {
+
+const char *bf_status_string(bf_status s)
+{
+    switch (s) {
+    case BF_OK: return "BF_OK";
+    case BF_ERR_INVALID_ARG: return "BF_ERR_INVALID_ARG";
+    case BF_ERR_UNSUPPORTED: return "BF_ERR_UNSUPPORTED";
+    case BF_ERR_NOMEM: return "BF_ERR_NOMEM";
+    case BF_ERR_CUDA: return "BF_ERR_CUDA";
+    case BF_ERR_TIMEOUT: return "BF_ERR_TIMEOUT";
+    case BF_ERR_INTERNAL: return "BF_ERR_INTERNAL";
+    }
+    return "BF_ERR_UNKNOWN";
+}
+
+bf_status bf_params_default(int d, int64_t N, bf_params *out)
+{
+    if (!out || d < 1 || d > 3 || N < 1) return BF_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    for (int k = 0; k < 3; ++k) {
+        out->x_lo[k] = 0.0;
+        out->x_w[k] = 1.0;
+        out->y_lo[k] = -0.5 * (double)N;
+        out->y_w[k] = (double)N;
+    }
+    out->phase_scale = 1.0;
+    out->precision = BF_PREC_MIXED;
+    out->switch_level = -1;
+    out->max_nrhs = 1;
+    return BF_OK;
+}
+
+bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_params *prm, bf_plan *out)
+{
+    if (!out || !prm) return BF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (d < 2 || d > 3) return d == 1 ? BF_ERR_UNSUPPORTED : BF_ERR_INVALID_ARG;
+    if (N < 2 || (N & (N - 1))) return BF_ERR_INVALID_ARG;
+    int L = 0;
+    while ((1LL << L) < N) ++L;
+    if ((int64_t)L * d > 30) return BF_ERR_INVALID_ARG;
+    if (q < 2 || q > bfk::QMAX) return BF_ERR_INVALID_ARG;
+    if ((int)phase < 0 || (int)phase > 3) return BF_ERR_INVALID_ARG;
+    if (phase == BF_PHASE_HYPRADON && d != 2) return BF_ERR_INVALID_ARG;
+    if (prm->precision != BF_PREC_FP64 && prm->precision != BF_PREC_MIXED) return BF_ERR_INVALID_ARG;
+    if (!supported_q(d, q)) return BF_ERR_UNSUPPORTED;
+    for (int k = 0; k < d; ++k) {
+        if (!(prm->x_w[k] > 0.0) || !(prm->y_w[k] > 0.0)) return BF_ERR_INVALID_ARG;
+        if (!std::isfinite(prm->x_lo[k]) || !std::isfinite(prm->y_lo[k]) || !std::isfinite(prm->x_w[k]) ||
+            !std::isfinite(prm->y_w[k]))
+            return BF_ERR_INVALID_ARG;
+    }
+    if (!std::isfinite(prm->phase_scale)) return BF_ERR_INVALID_ARG;
+    if (!(prm->tgt_off >= 0.0 && prm->tgt_off < 1.0 && prm->src_off >= 0.0 && prm->src_off < 1.0))
+        return BF_ERR_INVALID_ARG;
+    if (prm->switch_level < -1 || prm->switch_level >= L) return BF_ERR_INVALID_ARG;
+    if (prm->node_kind != 0 && prm->node_kind != 1) return BF_ERR_INVALID_ARG;
+    if (prm->max_nrhs < 1 || prm->max_nrhs > 65535) return BF_ERR_INVALID_ARG;
+    if (prm->fuse_levels < 0 || prm->fuse_levels > 8) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < 7; ++i)
+        if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
+
+    bf_plan p = new (std::nothrow) bf_plan_s();
+    if (!p) return BF_ERR_NOMEM;
+    p->d = d;
+    p->L = L;
+    p->q = q;
+    p->r = bfk::ipow(q, d);
+    p->N = N;
+    p->npts = 1LL << (L * d);
+    p->m = prm->switch_level < 0 ? L / 2 : prm->switch_level;
+    p->kind = (int)phase;
+    p->prec = prm->precision;
+    p->node_kind = prm->node_kind;
+    p->max_nrhs = prm->max_nrhs;
+    p->prm = *prm;
+    p->csize = p->prec == BF_PREC_FP64 ? 16 : 8;
+    p->fns = bfl::get_fns(d, q, p->prec == BF_PREC_FP64 ? 0 : 1);
+
+    for (int j = 0; j < q; ++j)
+        p->z[j] = p->node_kind == 0 ? 0.5 * std::cos(j * kPi / (q - 1)) : 0.5 * std::cos((2 * j + 1) * kPi / (2.0 * q));
+    for (int h = 0; h < 2; ++h)
+        for (int t = 0; t < q; ++t)
+            for (int u = 0; u < q; ++u) p->M[h][t][u] = lagrange1(q, p->z, t, (p->z[u] + h - 0.5) / 2.0);
+    for (int t = 0; t < q; ++t) {
+        p->lsrc[t] = lagrange1(q, p->z, t, prm->src_off - 0.5);
+        p->ltgt[t] = lagrange1(q, p->z, t, prm->tgt_off - 0.5);
+    }
+
+    const int kfit = p->fns->kmax;
+    const int kreq = prm->fuse_levels > 0 ? prm->fuse_levels : kfit;
+    p->kc = p->kr = kreq < kfit ? kreq : kfit;
+    schedule(p);
+
+    bf_status st = build_tables(p);
+    if (st == BF_OK) {
+        const size_t wbytes = (size_t)p->max_nrhs * (size_t)p->npts * (size_t)p->r * p->csize;
+        cudaError_t e = cudaMalloc(&p->w0, wbytes);
+        if (e == cudaSuccess) e = cudaMalloc(&p->w1, wbytes);
+        if (e != cudaSuccess) st = cuda_fail(p, e);
+        p->ws_bytes = (int64_t)(2 * wbytes);
+    }
+    if (st != BF_OK) {
+        bf_destroy(p);
+        return st;
+    }
+    *out = p;
+    return BF_OK;
+}
+
+bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
+    if (nrhs == 0) return BF_OK;
+    if (!g || !f) return BF_ERR_INVALID_ARG;
+    if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int n = (int)p->passes.size();
+    if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n);
+    return run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
+}
+
+bf_status bf_apply_pass(bf_plan p, int i, const void *g, void *f, int nrhs, void *stream)
+{
+    if (!p || i < 0 || i >= (int)p->passes.size()) return BF_ERR_INVALID_ARG;
+    if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
+    if (nrhs == 0) return BF_OK;
+    if (!g || !f) return BF_ERR_INVALID_ARG;
+    if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, i, i + 1);
+    return run_forward<bfk::PMIX>(p, g, f, nrhs, s, i, i + 1);
+}
+
+bf_status bf_pass_info(bf_plan p, int i, int *kind, int *l0, int *k, int *flags)
+{
+    if (!p || i < 0 || i >= (int)p->passes.size()) return BF_ERR_INVALID_ARG;
+    const Pass &ps = p->passes[i];
+    if (kind) *kind = ps.row;
+    if (l0) *l0 = ps.l0;
+    if (k) *k = ps.k;
+    if (flags) *flags = ps.flags;
+    return BF_OK;
+}
+
+bf_status bf_apply_adjoint(bf_plan p, const void *f, void *g, int nrhs, void *stream)
+{
+    (void)f;
+    (void)g;
+    (void)stream;
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
+    return BF_ERR_UNSUPPORTED;
+}
+
+bf_status bf_apply_host(bf_plan p, const void *g_host, void *f_host, int nrhs, void *stream)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
+    if (nrhs == 0) return BF_OK;
+    if (!g_host || !f_host) return BF_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)p->max_nrhs * (size_t)p->npts * p->csize;
+    cudaError_t e;
+    if (!p->gstage) {
+        if ((e = cudaMalloc(&p->gstage, bytes)) != cudaSuccess) return cuda_fail(p, e);
+        if ((e = cudaMalloc(&p->fstage, bytes)) != cudaSuccess) return cuda_fail(p, e);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t n = (size_t)nrhs * (size_t)p->npts * p->csize;
+    if ((e = cudaMemcpyAsync(p->gstage, g_host, n, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(p, e);
+    bf_status st = bf_apply(p, p->gstage, p->fstage, nrhs, stream);
+    if (st != BF_OK) return st;
+    if ((e = cudaMemcpyAsync(f_host, p->fstage, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(p, e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(p, e);
+    return BF_OK;
+}
+
+bf_status bf_apply_batched(const bf_plan *plans, const void *const *g, void *const *f, const int *nrhs, int count,
+                           void *stream)
+{
+    if (count < 0) return BF_ERR_INVALID_ARG;
+    if (count == 0) return BF_OK;
+    if (!plans || !g || !f || !nrhs) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!plans[i] || nrhs[i] < 0 || nrhs[i] > plans[i]->max_nrhs) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i) {
+        bf_status st = bf_apply(plans[i], g[i], f[i], nrhs[i], stream);
+        if (st != BF_OK) return st;
+    }
+    return BF_OK;
+}
+
+bf_status bf_destroy(bf_plan p)
+{
+    if (!p) return BF_OK;
+    for (int k = 0; k < 3; ++k) {
+        if (p->tt[k]) cudaFree(p->tt[k]);
+        if (p->st[k]) cudaFree(p->st[k]);
+    }
+    if (p->w0) cudaFree(p->w0);
+    if (p->w1) cudaFree(p->w1);
+    if (p->gstage) cudaFree(p->gstage);
+    if (p->fstage) cudaFree(p->fstage);
+    delete p;
+    return BF_OK;
+}
+
+bf_status bf_last_cuda_error(bf_plan p, int *cuda_err)
+{
+    if (!p || !cuda_err) return BF_ERR_INVALID_ARG;
+    *cuda_err = p->last_cuda;
+    return BF_OK;
+}
+
+bf_status bf_plan_info(bf_plan p, int *d, int64_t *N, int *q, int *m, int *fuse_levels, int *launches,
+                       int64_t *ws_bytes)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (d) *d = p->d;
+    if (N) *N = p->N;
+    if (q) *q = p->q;
+    if (m) *m = p->m;
+    if (fuse_levels) *fuse_levels = p->kc;
+    if (launches) *launches = (int)p->passes.size();
+    if (ws_bytes) *ws_bytes = p->ws_bytes;
+    return BF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,879 @@
+// Device code of the sm_103a Chebyshev-interpolation butterfly.
+//
+// The operator and the butterfly (Algorithm 1, Section 1.4 of Poulson,
+// Demanet, Maxwell, Ying, "A Parallel Butterfly Algorithm"):
+//   init   delta_t^{XB} = e^{-2pi i Phi(x0(X), y_t^B)} L_t^B(y) e^{2pi i Phi(x0(X), y)} g(y)
+//   column w_{A_a,B'}(t) = e^{-2pi i Phi(x0(A_a), y_t^{B'})}
+//                          sum_c sum_t' L_t^{B'}(y_t'^{B_c}) e^{2pi i Phi(x0(A_a), y_t'^{B_c})} w_{A,B_c}(t')
+//   switch delta_s^{AB} = sum_t e^{2pi i Phi(x_s^A, y_t^B)} delta_t^{AB}               (level m)
+//   row    w_{A_a,B'}(s) = sum_c e^{2pi i Phi(x_s^{A_a}, y0(B_c))}
+//                          sum_t L_t^A(x_s^{A_a}) e^{-2pi i Phi(x_t^A, y0(B_c))} w_{A,B_c}(t)
+//   final  f(x) = e^{2pi i Phi(x, y0(Y))} sum_t L_t^A(x) e^{-2pi i Phi(x_t^A, y0(Y))} w_{A,Y}(t)
+//
+// Layout.  Level-l weights live in HBM as [rhs][pair][r] complex numbers with
+// pair index A * 2^{d(L-l)} + B (A, B Morton indices, dimension 0 in the lowest
+// bit), node index t = sum_k t_k q^k.  A kernel pass handles "tiles": the
+// 2^{dk} pairs (Ap, B) with Ap fixed at level l0 and B under one box B* at
+// level l0+k.  Their inputs are contiguous and k merge levels close over them,
+// so one CTA runs k levels in shared memory.  Inside the tile the update is
+// in place: the 2^d outputs of a merge block overwrite its 2^d input slots,
+// which leaves the tile in base-2^d digit-reversed order after k levels (the
+// bit-reversal view of Section 2.2).
+//
+// Phases.  Phi is evaluated from per-level, per-dimension feature tables
+// (coordinates, and sin/cos or squares of them, for box centres, Chebyshev
+// nodes and grid points), so every feature is a table read.  In the mixed
+// precision Phi is accumulated and reduced mod 1 in double-float arithmetic
+// (pairs of FP32 numbers: Dekker's product via FMA and Knuth's two-sum), then
+// the FP32 sincospif gives e^{2 pi i Phi}.  The FP64 variant uses doubles.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace bfk {
+
+constexpr int QMAX = 8;
+constexpr int DMAX = 3;
+
+enum { KIND_DOT = 0, KIND_GENRADON = 1, KIND_HYPRADON = 2, KIND_SEPARABLE = 3 };
+enum { F_INIT = 1, F_SWITCH = 2, F_FINAL = 4 };
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// ------------------------------------------------------------ double-float
+
+struct df {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ df fast_two_sum(float a, float b)
+{
+    float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ df df_mul(df x, df y)
+{
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ df df_add(df x, df y)
+{
+    df s = two_sum(x.hi, y.hi);
+    return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+
+// sqrt of a non-negative double-float, to about 2^-44 relative
+__device__ __forceinline__ df df_sqrt(df x)
+{
+    if (x.hi <= 0.0f) return {0.0f, 0.0f};
+    float r = rsqrtf(x.hi);
+    float s = __fmul_rn(x.hi, r);
+    float res = __fadd_rn(__fmaf_rn(-s, s, x.hi), x.lo);
+    return fast_two_sum(s, __fmul_rn(res, __fmul_rn(0.5f, r)));
+}
+
+// x - nearest integer, as one float in [-0.5, 0.5] (about 2^-24 absolute of the exact value)
+__device__ __forceinline__ float df_frac(df x)
+{
+    float n = rintf(x.hi);
+    float f = __fadd_rn(__fsub_rn(x.hi, n), x.lo);
+    return __fsub_rn(f, rintf(f));
+}
+
+// frac of a product x*y with both factors double-float (the product itself may be large)
+__device__ __forceinline__ float df_mul_frac(df x, df y)
+{
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    e = __fmaf_rn(x.hi, y.lo, e);
+    e = __fmaf_rn(x.lo, y.hi, e);
+    float n = rintf(p);
+    return __fadd_rn(__fsub_rn(p, n), e);
+}
+
+// ------------------------------------------------------- precision traits
+
+struct PF64 {
+    using R = double;
+    using C = double2;
+    struct TE { double2 a, b; };   // target feature table entry: f0, f1 | f2, pad
+    struct SE { double2 a; };      // source feature table entry: f0, f1
+    struct Sc { double s3, sgn; }; // s/3 and sign(s)
+    static constexpr bool is_f64 = true;
+};
+
+struct PMIX {
+    using R = float;
+    using C = float2;
+    struct TE { float4 a, b; };    // (f0.hi, f0.lo, f1.hi, f1.lo) | (f2.hi, f2.lo, -, -)
+    struct SE { float4 a; };       // (f0.hi, f0.lo, f1.hi, f1.lo)
+    struct Sc { float s3hi, s3lo, sgn, pad; };
+    static constexpr bool is_f64 = false;
+};
+
+__device__ __forceinline__ void sincos2pi(double fr, double &s, double &c) { sincospi(2.0 * fr, &s, &c); }
+__device__ __forceinline__ void sincos2pi(float fr, float &s, float &c) { sincospif(2.0f * fr, &s, &c); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// conj(a) * b
+__device__ __forceinline__ float2 cjmul(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+__device__ __forceinline__ double2 cjmul(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+__device__ __forceinline__ void cfma(float2 &acc, float m, float2 v) { acc.x = fmaf(m, v.x, acc.x); acc.y = fmaf(m, v.y, acc.y); }
+__device__ __forceinline__ void cfma(double2 &acc, double m, double2 v) { acc.x = fma(m, v.x, acc.x); acc.y = fma(m, v.y, acc.y); }
+template <class C> __device__ __forceinline__ C czero();
+template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
+template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
+
+// ------------------------------------------------------------ kernel args
+
+template <class P>
+struct KArgs {
+    using R = typename P::R;
+    using C = typename P::C;
+    const typename P::TE *tt[DMAX];   // target feature tables, one per dimension
+    const typename P::SE *st[DMAX];   // source feature tables
+    const C *win;                     // input weights  [rhs][pair][r] (unused with F_INIT)
+    C *wout;                          // output weights (unused with F_FINAL)
+    const C *g;                       // sources [rhs][N^d] (F_INIT)
+    C *f;                             // targets [rhs][N^d] (F_FINAL)
+    int64_t wstride;                  // per-rhs stride of weights, in complex numbers
+    int64_t npts;                     // N^d
+    R M[2][QMAX][QMAX];               // M[h][t][t'] = l_t((z_t' + h - 1/2)/2)
+    R lsrc[QMAX], ltgt[QMAX];         // l_t(off - 1/2): Lagrange values of the grid point in its leaf box
+    typename P::Sc sc;
+    int L, l0, k, flags, kind;
+    int T;                            // tiles per CTA (T * 2^{dk} pairs)
+};
+
+// --------------------------------------------------------- index helpers
+
+template <int D>
+__device__ __forceinline__ void morton_decode(uint32_t m, int bits, int *c)
+{
+#pragma unroll
+    for (int k = 0; k < D; ++k) c[k] = 0;
+    for (int j = 0; j < bits; ++j) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) c[k] |= ((m >> (j * D + k)) & 1u) << j;
+    }
+}
+
+// reverse the order of the first n base-2^D digits of x
+template <int D>
+__device__ __forceinline__ uint32_t digit_rev(uint32_t x, int n)
+{
+    uint32_t y = 0;
+    for (int j = 0; j < n; ++j) {
+        y = (y << D) | (x & ((1u << D) - 1));
+        x >>= D;
+    }
+    return y;
+}
+
+// target table: level l has 2^l boxes per dimension, (Q+2) slots each
+template <int Q> __device__ __forceinline__ int64_t toff(int l) { return ((1LL << l) - 1) * (Q + 2); }
+// source table: level l has 2^(L-l) boxes per dimension
+template <int Q> __device__ __forceinline__ int64_t soff(int L, int l) { return ((2LL << L) - (2LL << (L - l))) * (Q + 2); }
+
+// ------------------------------------------------------------------ phase
+//
+// Target features per dimension (built on the host, kind-specific):
+//   DOT        f0 = s x
+//   GENRADON   f0 = s x, f1 = sin 2pi x, f2 = cos 2pi x
+//   HYPRADON   f0 = s x, f1 = x^2
+//   SEPARABLE  f0 = s sin 2pi (x + (k+1)/7)
+// Source features per dimension:
+//   DOT y | GENRADON y, y^2 | HYPRADON -, y^2 | SEPARABLE s y^2/(k+2)
+
+template <class P, int D> struct Ph;
+
+template <int D>
+struct Ph<PMIX, D> {
+    struct T { df x[D]; df A[D]; };
+    struct S { df y[D]; df y2[D]; };
+
+    static __device__ __forceinline__ df hi(const float4 &v) { return {v.x, v.y}; }
+    static __device__ __forceinline__ df lo(const float4 &v) { return {v.z, v.w}; }
+
+    static __device__ __forceinline__ T tgt(const KArgs<PMIX> &a, const PMIX::TE *e)
+    {
+        T t;
+#pragma unroll
+        for (int k = 0; k < D; ++k) { t.x[k] = hi(e[k].a); t.A[k] = lo(e[k].a); }
+        if (a.kind == KIND_GENRADON) {
+            const df s3 = {a.sc.s3hi, a.sc.s3lo};
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                df u;
+                if (D == 2) u = (k == 0) ? df_mul(lo(e[0].a), lo(e[1].a)) : df_mul(hi(e[0].b), hi(e[1].b));
+                else u = df_mul(lo(e[k].a), hi(e[(k + 1) % D].b));
+                df two = two_sum(2.0f, u.hi);
+                u = fast_two_sum(two.hi, __fadd_rn(two.lo, u.lo));
+                u = df_mul(u, s3);
+                t.A[k] = df_mul(u, u);
+            }
+        }
+        return t;
+    }
+
+    static __device__ __forceinline__ void src1(S &s, int k, const PMIX::SE &e)
+    {
+        s.y[k] = hi(e.a);
+        s.y2[k] = lo(e.a);
+    }
+
+    // Phi(x, y) - nearest integer, in [-0.5, 0.5]
+    static __device__ __forceinline__ float frac(const KArgs<PMIX> &a, const T &t, const S &s)
+    {
+        switch (a.kind) {
+        case KIND_DOT: {
+            float f = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) f += df_mul_frac(t.x[k], s.y[k]);
+            return f - rintf(f);
+        }
+        case KIND_GENRADON: {
+            float f = 0.0f;
+#pragma unroll
+            for (int k = 0; k < D; ++k) f += df_mul_frac(t.x[k], s.y[k]);
+            df q = df_mul(t.A[0], s.y2[0]);
+#pragma unroll
+            for (int k = 1; k < D; ++k) q = df_add(q, df_mul(t.A[k], s.y2[k]));
+            df r = df_sqrt(q);
+            float fr = df_frac(r);
+            f += (a.sc.sgn < 0.0f) ? -fr : fr;
+            return f - rintf(f);
+        }
+        case KIND_HYPRADON: {
+            df q = df_add(s.y2[0], df_mul(t.A[1], s.y2[1]));
+            df r = df_sqrt(q);
+            float f = df_mul_frac(t.x[0], r);
+            return f - rintf(f);
+        }
+        default: { // SEPARABLE
+            df acc = {0.0f, 0.0f};
+#pragma unroll
+            for (int k = 0; k < D; ++k) acc = df_add(acc, df_add(t.x[k], s.y[k]));
+            return df_frac(acc);
+        }
+        }
+    }
+};
+
+template <int D>
+struct Ph<PF64, D> {
+    struct T { double x[D]; double A[D]; };
+    struct S { double y[D]; double y2[D]; };
+
+    static __device__ __forceinline__ T tgt(const KArgs<PF64> &a, const PF64::TE *e)
+    {
+        T t;
+#pragma unroll
+        for (int k = 0; k < D; ++k) { t.x[k] = e[k].a.x; t.A[k] = e[k].a.y; }
+        if (a.kind == KIND_GENRADON) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                double u;
+                if (D == 2) u = (k == 0) ? e[0].a.y * e[1].a.y : e[0].b.x * e[1].b.x;
+                else u = e[k].a.y * e[(k + 1) % D].b.x;
+                u = (2.0 + u) * a.sc.s3;
+                t.A[k] = u * u;
+            }
+        }
+        return t;
+    }
+
+    static __device__ __forceinline__ void src1(S &s, int k, const PF64::SE &e)
+    {
+        s.y[k] = e.a.x;
+        s.y2[k] = e.a.y;
+    }
+
+    static __device__ __forceinline__ double frac(const KArgs<PF64> &a, const T &t, const S &s)
+    {
+        double p = 0.0;
+        switch (a.kind) {
+        case KIND_DOT:
+#pragma unroll
+            for (int k = 0; k < D; ++k) p += t.x[k] * s.y[k];
+            break;
+        case KIND_GENRADON: {
+            double q = 0.0;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                p += t.x[k] * s.y[k];
+                q += t.A[k] * s.y2[k];
+            }
+            p += a.sc.sgn * sqrt(q);
+            break;
+        }
+        case KIND_HYPRADON:
+            p = t.x[0] * sqrt(s.y2[0] + t.A[1] * s.y2[1]);
+            break;
+        default:
+#pragma unroll
+            for (int k = 0; k < D; ++k) p += t.x[k] + s.y[k];
+        }
+        return p - rint(p);
+    }
+};
+
+// e^{2 pi i Phi} as a complex number of the working precision
+template <class P, int D>
+__device__ __forceinline__ typename P::C expphase(const KArgs<P> &a, const typename Ph<P, D>::T &t,
+                                                  const typename Ph<P, D>::S &s)
+{
+    typename P::R fr = Ph<P, D>::frac(a, t, s), sn, cs;
+    sincos2pi(fr, sn, cs);
+    typename P::C e;
+    e.x = cs;
+    e.y = sn;
+    return e;
+}
+
+// table reads
+template <class P, int Q>
+__device__ __forceinline__ typename P::TE tget(const KArgs<P> &a, int k, int l, int box, int slot)
+{
+    return a.tt[k][toff<Q>(l) + (int64_t)box * (Q + 2) + slot];
+}
+template <class P, int Q>
+__device__ __forceinline__ typename P::SE sget(const KArgs<P> &a, int k, int l, int box, int slot)
+{
+    return a.st[k][soff<Q>(a.L, l) + (int64_t)box * (Q + 2) + slot];
+}
+
+// features of the target point of box `coords` at level l, slot per dimension
+template <class P, int D, int Q>
+__device__ __forceinline__ typename Ph<P, D>::T tpoint(const KArgs<P> &a, int l, const int *coords, const int *slot)
+{
+    typename P::TE e[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) e[k] = tget<P, Q>(a, k, l, coords[k], slot[k]);
+    return Ph<P, D>::tgt(a, e);
+}
+
+template <class P, int D, int Q>
+__device__ __forceinline__ typename Ph<P, D>::S spoint(const KArgs<P> &a, int l, const int *coords, const int *slot)
+{
+    typename Ph<P, D>::S s;
+#pragma unroll
+    for (int k = 0; k < D; ++k) Ph<P, D>::src1(s, k, sget<P, Q>(a, k, l, coords[k], slot[k]));
+    return s;
+}
+
+// ------------------------------------------------------------ tile passes
+//
+// A CTA owns NP consecutive pairs of the pass's input level: T = NP / 2^{dk}
+// tiles of 2^{dk} pairs.  It runs NT = NP * q threads, and every stage below is
+// cut into a multiple of NT equal work items, so no thread idles at a barrier
+// while others finish a longer item.
+
+constexpr int kmax_for(int D, int RR, int CS, int Q)
+{
+    int k = 1;
+    while (k < (D == 2 ? 4 : 2) && 3 * (1 << (D * (k + 1))) * RR * CS <= 100 * 1024 && (1 << (D * (k + 1))) * Q <= 512) ++k;
+    return k;
+}
+
+template <int D, int Q, class P>
+struct Cfg {
+    static constexpr int RR = ipow(Q, D);
+    static constexpr int KMAX = kmax_for(D, RR, (int)sizeof(typename P::C), Q);
+    static constexpr int NP = 1 << (D * KMAX);    // pairs per CTA
+    static constexpr int NT = NP * Q;             // threads per CTA
+    static constexpr int MINB = (640 / NT) < 1 ? 1 : ((640 / NT) > 8 ? 8 : 640 / NT);
+};
+
+template <int D, int Q, class P>
+struct Tile {
+    using R = typename P::R;
+    using C = typename P::C;
+    using PH = Ph<P, D>;
+    static constexpr int NC = 1 << D;
+    static constexpr int RR = ipow(Q, D);
+    static constexpr int QD1 = ipow(Q, D - 1);
+
+    static __device__ __forceinline__ float2 cadd(float2 x, float2 y) { return make_float2(x.x + y.x, x.y + y.y); }
+    static __device__ __forceinline__ double2 cadd(double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); }
+
+    // (Ap, B*) of the CTA's tile tau: tile index = Ap * 2^{D(L-l0-k)} + B*
+    static __device__ __forceinline__ void tile_of(const KArgs<P> &a, int tau, uint32_t &Ap, uint32_t &Bstar)
+    {
+        const uint64_t tile = (uint64_t)blockIdx.x * a.T + tau;
+        const int sh = D * (a.L - a.l0 - a.k);
+        Ap = (uint32_t)(tile >> sh);
+        Bstar = (uint32_t)(tile & ((1ull << sh) - 1));
+    }
+
+    // ---- init: weights of the leaf pairs (X, B); items (tau, b, t)
+    static __device__ void init(const KArgs<P> &a, C *Wt, int rhs)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int L = a.L;
+        const int cX[DMAX] = {0, 0, 0};
+        const int ctr[DMAX] = {Q, Q, Q};
+        const typename PH::T tX = tpoint<P, D, Q>(a, 0, cX, ctr);   // centre of X
+        for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) {
+            const int t = it % RR, b = (it / RR) % n, tau = it / (RR * n);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            const uint32_t B = (Bstar << (D * k)) + b;
+            int cb[DMAX];
+            morton_decode<D>(B, L, cb);
+            R lag = R(1);
+            int tk[DMAX], tt = t;
+#pragma unroll
+            for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.lsrc[tk[j]]; }
+            C out = czero<C>();
+            if (lag != R(0)) {
+                int64_t flat = 0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) flat = (flat << L) + cb[j];
+                const C gv = a.g[(int64_t)rhs * a.npts + flat];
+                const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
+                const C e1 = expphase<P, D>(a, tX, spoint<P, D, Q>(a, 0, cb, pslot));
+                const C e0 = expphase<P, D>(a, tX, spoint<P, D, Q>(a, 0, cb, tk));
+                C v = cjmul(e0, cmul(e1, gv));
+                out.x = lag * v.x;
+                out.y = lag * v.y;
+            }
+            Wt[it] = out;
+        }
+    }
+
+    // block beta of tile level i: target box index at level l (for the row form, the parent)
+    // and source box index at level l+1; base slot of the block
+    static __device__ __forceinline__ void block_geo(uint32_t Ap, uint32_t Bstar, int beta, int i, int k,
+                                                     uint32_t &Apg, uint32_t &Bq, int &base)
+    {
+        const uint32_t ra = beta & ((1u << (D * i)) - 1);
+        const uint32_t bp = beta >> (D * i);
+        base = (bp << (D * (i + 1))) + ra;
+        Apg = (Ap << (D * i)) + digit_rev<D>(ra, i);
+        Bq = (Bstar << (D * (k - i - 1))) + bp;
+    }
+
+    // ---- one column-form merge level (l -> l+1) on all tiles of the CTA
+    static __device__ void col_level(const KArgs<P> &a, C *Wt, C *S, int l, int i)
+    {
+        const int k = a.k, n = 1 << (D * k), nblk = n >> D;
+        const int L = a.L;
+        // stage A: items (tau, block, alpha, c_{D-1}, t'_{D-1}): modulate and contract dims 0..D-2
+        for (int it = threadIdx.x; it < a.T * nblk * NC * 2 * Q; it += blockDim.x) {
+            const int tq = it % Q;
+            const int chi = (it / Q) & 1;
+            const int alpha = (it / (2 * Q)) % NC;
+            const int beta = (it / (2 * Q * NC)) % nblk;
+            const int tau = it / (2 * Q * NC * nblk);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            const uint32_t Aa = (Apg << D) + alpha;                          // level l+1
+            int ca[DMAX], cbq[DMAX];
+            morton_decode<D>(Aa, l + 1, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+            const int ctr[DMAX] = {Q, Q, Q};
+            const typename PH::T tA = tpoint<P, D, Q>(a, l + 1, ca, ctr);
+            const C *Wtau = Wt + tau * n * RR;
+            C acc[QD1];
+#pragma unroll
+            for (int j = 0; j < QD1; ++j) acc[j] = czero<C>();
+#pragma unroll
+            for (int cl = 0; cl < (NC >> 1); ++cl) {
+                const int c = cl | (chi << (D - 1));
+                const C *win = Wtau + (base + (c << (D * i))) * RR;
+                int cb[DMAX];
+#pragma unroll
+                for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+                typename PH::S sp;
+                PH::src1(sp, D - 1, sget<P, Q>(a, D - 1, l, cb[D - 1], tq));
+                if constexpr (D == 2) {
+                    const int c0 = c & 1;
+#pragma unroll
+                    for (int t0p = 0; t0p < Q; ++t0p) {
+                        PH::src1(sp, 0, sget<P, Q>(a, 0, l, cb[0], t0p));
+                        const C u = cmul(expphase<P, D>(a, tA, sp), win[t0p + Q * tq]);
+#pragma unroll
+                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[c0][t0][t0p], u);
+                    }
+                } else {
+                    const int c0 = c & 1, c1 = (c >> 1) & 1;
+#pragma unroll
+                    for (int t1p = 0; t1p < Q; ++t1p) {
+                        PH::src1(sp, 1, sget<P, Q>(a, 1, l, cb[1], t1p));
+                        C tmp[Q];
+#pragma unroll
+                        for (int t0 = 0; t0 < Q; ++t0) tmp[t0] = czero<C>();
+#pragma unroll
+                        for (int t0p = 0; t0p < Q; ++t0p) {
+                            PH::src1(sp, 0, sget<P, Q>(a, 0, l, cb[0], t0p));
+                            const C u = cmul(expphase<P, D>(a, tA, sp), win[t0p + Q * t1p + Q * Q * tq]);
+#pragma unroll
+                            for (int t0 = 0; t0 < Q; ++t0) cfma(tmp[t0], a.M[c0][t0][t0p], u);
+                        }
+#pragma unroll
+                        for (int t1 = 0; t1 < Q; ++t1)
+#pragma unroll
+                            for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0 + Q * t1], a.M[c1][t1][t1p], tmp[t0]);
+                    }
+                }
+            }
+            // scratch [tau][block][alpha][c_{D-1}][t'_{D-1}][t_{<D-1}]
+            C *so = S + ((((tau * nblk + beta) * NC + alpha) * 2 + chi) * Q + tq) * QD1;
+#pragma unroll
+            for (int j = 0; j < QD1; ++j) so[j] = acc[j];
+        }
+        __syncthreads();
+        // stage B: items (tau, block, alpha, t_{<D-1}): contract dim D-1 and c_{D-1}, demodulate
+        for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
+            const int tl = it % QD1;
+            const int alpha = (it / QD1) % NC;
+            const int beta = (it / (QD1 * NC)) % nblk;
+            const int tau = it / (QD1 * NC * nblk);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            const uint32_t Aa = (Apg << D) + alpha;
+            int ca[DMAX], cbq[DMAX];
+            morton_decode<D>(Aa, l + 1, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+            const int ctr[DMAX] = {Q, Q, Q};
+            const typename PH::T tA = tpoint<P, D, Q>(a, l + 1, ca, ctr);
+            C acc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
+#pragma unroll
+            for (int chi = 0; chi < 2; ++chi) {
+                const C *si = S + ((((tau * nblk + beta) * NC + alpha) * 2 + chi) * Q) * QD1 + tl;
+#pragma unroll
+                for (int tqp = 0; tqp < Q; ++tqp) {
+                    const C v = si[tqp * QD1];
+#pragma unroll
+                    for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], a.M[chi][tq][tqp], v);
+                }
+            }
+            typename PH::S sp;
+            int tk[DMAX];
+            {
+                int tt = tl;
+#pragma unroll
+                for (int j = 0; j < D - 1; ++j) { tk[j] = tt % Q; tt /= Q; }
+            }
+#pragma unroll
+            for (int j = 0; j < D - 1; ++j) PH::src1(sp, j, sget<P, Q>(a, j, l + 1, cbq[j], tk[j]));
+            C *wo = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR + tl;
+#pragma unroll
+            for (int tq = 0; tq < Q; ++tq) {
+                PH::src1(sp, D - 1, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq));
+                wo[tq * QD1] = cjmul(expphase<P, D>(a, tA, sp), acc[tq]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- switch at level l on every pair (slots in digit-reversed order); items (tau, slot, s_{>=1})
+    // accumulate over t for the q values of s_0.  Results go through S so no item reads a
+    // slot that another item has already rewritten.
+    static __device__ void switch_tiles(const KArgs<P> &a, C *Wt, C *S, int l)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int L = a.L;
+        for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
+            const int sh = it % QD1;
+            const int sl = (it / QD1) % n;
+            const int tau = it / (QD1 * n);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
+            int ca[DMAX], cb[DMAX];
+            morton_decode<D>(A, l, ca);
+            morton_decode<D>(Bstar, L - l, cb);
+            typename PH::T tS[Q];
+            C acc[Q];
+            int sk[DMAX];
+            {
+                int tt = sh;
+#pragma unroll
+                for (int j = 1; j < D; ++j) { sk[j] = tt % Q; tt /= Q; }
+            }
+#pragma unroll
+            for (int s0 = 0; s0 < Q; ++s0) {
+                sk[0] = s0;
+                tS[s0] = tpoint<P, D, Q>(a, l, ca, sk);
+                acc[s0] = czero<C>();
+            }
+            const C *u = Wt + (tau * n + sl) * RR;
+            for (int t = 0; t < RR; ++t) {
+                int tk[DMAX], tt = t;
+#pragma unroll
+                for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; }
+                const typename PH::S sp = spoint<P, D, Q>(a, l, cb, tk);
+                const C ut = u[t];
+#pragma unroll
+                for (int s0 = 0; s0 < Q; ++s0) acc[s0] = cadd(acc[s0], cmul(expphase<P, D>(a, tS[s0], sp), ut));
+            }
+            C *w = S + (tau * n + sl) * RR + sh * Q;
+#pragma unroll
+            for (int s0 = 0; s0 < Q; ++s0) w[s0] = acc[s0];
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) Wt[j] = S[j];
+        __syncthreads();
+    }
+
+    // ---- one row-form merge level (l -> l+1) on all tiles of the CTA
+    static __device__ void row_level(const KArgs<P> &a, C *Wt, C *S, int l, int i)
+    {
+        const int k = a.k, n = 1 << (D * k), nblk = n >> D;
+        const int L = a.L;
+        // stage A: items (tau, block, c, t_{>=1}): pre-modulate input c at the nodes of the
+        // parent target box and contract dim 0 for both children alpha_0
+        //   -> S[tau][block][c][t_{>=1}][alpha_0][s_0]
+        for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
+            const int th = it % QD1;
+            const int c = (it / QD1) % NC;
+            const int beta = (it / (QD1 * NC)) % nblk;
+            const int tau = it / (QD1 * NC * nblk);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            int ca[DMAX], cbq[DMAX], cb[DMAX];
+            morton_decode<D>(Apg, l, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+#pragma unroll
+            for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+            const int ctr[DMAX] = {Q, Q, Q};
+            const typename PH::S sc = spoint<P, D, Q>(a, l, cb, ctr);
+            int tk[DMAX];
+            {
+                int tt = th;
+#pragma unroll
+                for (int j = 1; j < D; ++j) { tk[j] = tt % Q; tt /= Q; }
+            }
+            const C *win = Wt + tau * n * RR + (base + (c << (D * i))) * RR + th * Q;
+            C z[2][Q];
+#pragma unroll
+            for (int s0 = 0; s0 < Q; ++s0) { z[0][s0] = czero<C>(); z[1][s0] = czero<C>(); }
+#pragma unroll
+            for (int t0 = 0; t0 < Q; ++t0) {
+                tk[0] = t0;
+                const C u = cjmul(expphase<P, D>(a, tpoint<P, D, Q>(a, l, ca, tk), sc), win[t0]);
+#pragma unroll
+                for (int s0 = 0; s0 < Q; ++s0) {
+                    cfma(z[0][s0], a.M[0][t0][s0], u);
+                    cfma(z[1][s0], a.M[1][t0][s0], u);
+                }
+            }
+            C *so = S + (((tau * nblk + beta) * NC + c) * QD1 + th) * 2 * Q;
+#pragma unroll
+            for (int s0 = 0; s0 < Q; ++s0) { so[s0] = z[0][s0]; so[Q + s0] = z[1][s0]; }
+        }
+        __syncthreads();
+        // stage B: items (tau, block, alpha, s_0): contract dims >= 1 per child c,
+        // post-modulate at the child's nodes, sum over c
+        for (int it = threadIdx.x; it < a.T * nblk * NC * Q; it += blockDim.x) {
+            const int s0 = it % Q;
+            const int alpha = (it / Q) % NC;
+            const int beta = (it / (Q * NC)) % nblk;
+            const int tau = it / (Q * NC * nblk);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            const uint32_t Aa = (Apg << D) + alpha;                      // level l+1
+            int ca[DMAX], cbq[DMAX];
+            morton_decode<D>(Aa, l + 1, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+            const int a0 = alpha & 1;
+            const C *Sblk = S + ((tau * nblk + beta) * NC) * QD1 * 2 * Q;
+            C acc[QD1];
+#pragma unroll
+            for (int j = 0; j < QD1; ++j) acc[j] = czero<C>();
+            if constexpr (D == 2) {
+                const int a1 = (alpha >> 1) & 1;
+                C v[NC][Q];
+                typename PH::S sc[NC];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    int cb[DMAX], ctr[DMAX] = {Q, Q, Q};
+#pragma unroll
+                    for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+                    sc[c] = spoint<P, D, Q>(a, l, cb, ctr);
+                    const C *si = Sblk + c * QD1 * 2 * Q + a0 * Q + s0;   // [t1] stride 2Q
+#pragma unroll
+                    for (int s1 = 0; s1 < Q; ++s1) v[c][s1] = czero<C>();
+#pragma unroll
+                    for (int t1 = 0; t1 < Q; ++t1) {
+                        const C zz = si[t1 * 2 * Q];
+#pragma unroll
+                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[c][s1], a.M[a1][t1][s1], zz);
+                    }
+                }
+#pragma unroll
+                for (int s1 = 0; s1 < Q; ++s1) {
+                    const int sk[DMAX] = {s0, s1, 0};
+                    const typename PH::T tS = tpoint<P, D, Q>(a, l + 1, ca, sk);
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc[s1] = cadd(acc[s1], cmul(expphase<P, D>(a, tS, sc[c]), v[c][s1]));
+                }
+            } else {
+                const int a1 = (alpha >> 1) & 1, a2 = (alpha >> 2) & 1;
+#pragma unroll 1
+                for (int c = 0; c < NC; ++c) {
+                    int cb[DMAX], ctr[DMAX] = {Q, Q, Q};
+#pragma unroll
+                    for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+                    const typename PH::S sc = spoint<P, D, Q>(a, l, cb, ctr);
+                    const C *si = Sblk + c * QD1 * 2 * Q + a0 * Q + s0;   // [t1 + Q t2] stride 2Q
+                    C w[Q * Q];   // [t1][s2]
+#pragma unroll
+                    for (int j = 0; j < Q * Q; ++j) w[j] = czero<C>();
+#pragma unroll
+                    for (int t2 = 0; t2 < Q; ++t2)
+#pragma unroll
+                        for (int t1 = 0; t1 < Q; ++t1) {
+                            const C zz = si[(t1 + Q * t2) * 2 * Q];
+#pragma unroll
+                            for (int s2 = 0; s2 < Q; ++s2) cfma(w[t1 * Q + s2], a.M[a2][t2][s2], zz);
+                        }
+#pragma unroll
+                    for (int s2 = 0; s2 < Q; ++s2)
+#pragma unroll
+                        for (int s1 = 0; s1 < Q; ++s1) {
+                            C v = czero<C>();
+#pragma unroll
+                            for (int t1 = 0; t1 < Q; ++t1) cfma(v, a.M[a1][t1][s1], w[t1 * Q + s2]);
+                            const int sk[DMAX] = {s0, s1, s2};
+                            const typename PH::T tS = tpoint<P, D, Q>(a, l + 1, ca, sk);
+                            acc[s1 + Q * s2] = cadd(acc[s1 + Q * s2], cmul(expphase<P, D>(a, tS, sc), v));
+                        }
+                }
+            }
+            C *wo = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
+#pragma unroll
+            for (int sh = 0; sh < QD1; ++sh) wo[sh * Q] = acc[sh];
+        }
+        __syncthreads();
+    }
+
+    // ---- final evaluation of the leaf targets (pairs (A, Y) at level L); items (tau, slot)
+    static __device__ void final_eval(const KArgs<P> &a, const C *Wt, int rhs)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int L = a.L;
+        const int cY[DMAX] = {0, 0, 0};
+        const int ctr[DMAX] = {Q, Q, Q};
+        const typename PH::S sY = spoint<P, D, Q>(a, L, cY, ctr);      // centre of Y
+        for (int it = threadIdx.x; it < a.T * n; it += blockDim.x) {
+            const int sl = it % n, tau = it / n;
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
+            int ca[DMAX];
+            morton_decode<D>(A, L, ca);
+            const C *w = Wt + it * RR;
+            C acc = czero<C>();
+            for (int t = 0; t < RR; ++t) {
+                R lag = R(1);
+                int tk[DMAX], tt = t;
+#pragma unroll
+                for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.ltgt[tk[j]]; }
+                if (lag == R(0)) continue;
+                const C e = expphase<P, D>(a, tpoint<P, D, Q>(a, L, ca, tk), sY);
+                cfma(acc, lag, cjmul(e, w[t]));
+            }
+            const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
+            const C e = expphase<P, D>(a, tpoint<P, D, Q>(a, L, ca, pslot), sY);
+            int64_t flat = 0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) flat = (flat << L) + ca[j];
+            a.f[(int64_t)rhs * a.npts + flat] = cmul(e, acc);
+        }
+    }
+
+    // ---- CTA input: T * 2^{dk} consecutive pairs (contiguous in HBM)
+    static __device__ __forceinline__ void load(const KArgs<P> &a, C *Wt, int rhs)
+    {
+        const int cnt = a.T * (1 << (D * a.k)) * RR;
+        const C *src = a.win + (int64_t)rhs * a.wstride + (int64_t)blockIdx.x * cnt;
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) Wt[j] = src[j];
+    }
+
+    // ---- CTA output: tile slots are in digit-reversed order after k merges
+    static __device__ __forceinline__ void store(const KArgs<P> &a, const C *Wt, int rhs)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int64_t Sstar = 1LL << (D * (a.L - a.l0 - k));
+        C *dst = a.wout + (int64_t)rhs * a.wstride;
+        for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) {
+            const int t = j % RR, sl = (j / RR) % n, tau = j / (RR * n);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            const int64_t pair = ((int64_t)(((int64_t)Ap << (D * k)) + digit_rev<D>(sl, k))) * Sstar + Bstar;
+            dst[pair * RR + t] = Wt[j];
+        }
+    }
+};
+
+// ------------------------------------------------------------------ kernels
+
+// init (l0 = 0) + k column merges + optional switch at level l0 + k
+template <int D, int Q, class P>
+__global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pass(const KArgs<P> a)
+{
+    using C = typename P::C;
+    using TL = Tile<D, Q, P>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *Wt = reinterpret_cast<C *>(smem_raw);
+    C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
+    const int rhs = blockIdx.y;
+    if (a.flags & F_INIT)
+        TL::init(a, Wt, rhs);
+    else
+        TL::load(a, Wt, rhs);
+    __syncthreads();
+    for (int i = 0; i < a.k; ++i) TL::col_level(a, Wt, S, a.l0 + i, i);
+    if (a.flags & F_SWITCH) TL::switch_tiles(a, Wt, S, a.l0 + a.k);
+    TL::store(a, Wt, rhs);
+}
+
+// k row merges + optional final evaluation (l0 + k = L)
+template <int D, int Q, class P>
+__global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pass(const KArgs<P> a)
+{
+    using C = typename P::C;
+    using TL = Tile<D, Q, P>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *Wt = reinterpret_cast<C *>(smem_raw);
+    C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
+    const int rhs = blockIdx.y;
+    TL::load(a, Wt, rhs);
+    __syncthreads();
+    for (int i = 0; i < a.k; ++i) TL::row_level(a, Wt, S, a.l0 + i, i);
+    if (a.flags & F_FINAL)
+        TL::final_eval(a, Wt, rhs);
+    else
+        TL::store(a, Wt, rhs);
+}
+
+}  // namespace bfk

@@ -1,0 +1,58 @@
+// Explicit instantiation helpers: one translation unit per (d, precision).
+#pragma once
+
+#include "bf_device.cuh"
+#include "bf_launch.h"
+
+namespace bfl {
+
+// Raise the kernel's dynamic shared-memory limit to what this launch needs,
+// checked against the device's opt-in maximum.  `granted` is owned by the one
+// kernel instantiation that calls this (per device).
+template <class K>
+inline cudaError_t prepare(K kern, size_t smem, size_t *granted)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (smem <= 48 * 1024 || smem <= granted[dev]) return cudaSuccess;
+    int optin = 0;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
+    if (smem > (size_t)optin) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    granted[dev] = smem;
+    return cudaSuccess;
+}
+
+template <int D, int Q, class P>
+cudaError_t launch_col(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_col_pass<D, Q, P>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_col_pass<D, Q, P><<<dim3(gx, gy), bfk::Cfg<D, Q, P>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    return cudaGetLastError();
+}
+
+template <int D, int Q, class P>
+cudaError_t launch_row(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_row_pass<D, Q, P>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_row_pass<D, Q, P><<<dim3(gx, gy), bfk::Cfg<D, Q, P>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    return cudaGetLastError();
+}
+
+template <int D, int Q, class P>
+const PassFns *fns_for()
+{
+    using CF = bfk::Cfg<D, Q, P>;
+    static const PassFns f = {launch_col<D, Q, P>, launch_row<D, Q, P>, nullptr, nullptr, CF::KMAX, CF::NP, CF::NT};
+    return &f;
+}
+
+}  // namespace bfl
