@@ -145,6 +145,34 @@ bf_status bf_plan_info(bf_plan plan, int *d, int64_t *N, int *q, int *m, int *fu
 bf_status bf_apply_pass(bf_plan plan, int i, const void *g_dev, void *f_dev, int nrhs, void *stream);
 bf_status bf_pass_info(bf_plan plan, int i, int *kind, int *l0, int *k, int *flags);
 
+/* Forward apply that allocates no device memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot call cudaMalloc themselves or
+ * let a library do it -- for example a host application that hands the GPU to
+ * a fixed memory pool and forbids allocations after start-up, or code running
+ * where an allocation could block or fail mid-stream.  Arguments are those of
+ * bf_plan_create followed by those of bf_apply; the result equals bf_apply's on
+ * a plan built with the same arguments, up to the last bits of the
+ * geometry tables (they are built on the device here).
+ *
+ * Scratch.  The geometry tables and the two weight buffers live in one static
+ * device array of BF_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the
+ * library holds until the process exits.  A problem needs
+ *     48 * d * (2^(L+1) - 1) * (q + 2)  +  2 * nrhs * N^d * q^d * c  bytes
+ * (c = 16 for BF_PREC_FP64, 8 otherwise; plus up to 256 bytes of alignment per
+ * table); larger problems return BF_ERR_INVALID_ARG before any work is queued.
+ * For d = 2, q = 5 and one right-hand side this admits N <= 128 in either
+ * precision; for d = 3, q = 4 it admits N <= 16.  Nothing is read from the array before this call has written
+ * it, so no clearing is needed, but every call uses the same array: calls that
+ * overlap on the GPU (different streams, or different host threads without
+ * ordering) race on it and must be serialised by the caller.
+ *
+ * Set-up.  The first call on each device (with that device current) looks up
+ * the array's device address with cudaGetSymbolAddress; make that first call
+ * before any stream capture begins.  Asynchronous on `stream` like bf_apply. */
+#define BF_NOALLOC_SCRATCH_BYTES (16u << 20)
+bf_status bf_apply_noalloc(int d, int64_t N, int q, bf_phase_kind phase, const bf_params *p,
+                           const void *g_dev, void *f_dev, int nrhs, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -235,3 +235,33 @@ def apply_batched(plans, gs, fs, nrhs, stream=None) -> None:
     F = (vp * n)(*[f.data_ptr() for f in fs])
     R = (ctypes.c_int * n)(*nrhs)
     _check(load().bf_apply_batched(P, G, F, R, n, _stream_ptr(stream)), "bf_apply_batched")
+
+
+def apply_noalloc(d: int, N: int, q: int, phase: str, g, f, precision: str = "mixed", scale: float = 1.0,
+                  x_lo=None, x_w=None, y_lo=None, y_w=None, tgt_off: float = 0.0, src_off: float = 0.0,
+                  switch_level: int = -1, node_kind: int = 0, fuse_levels: int = 0, stream=None) -> None:
+    """bf_apply_noalloc: forward apply whose tables and workspace live in the library's
+    static device array (no device allocation).  g, f: CUDA tensors of nrhs x N^d values."""
+    lib = load()
+    fn = lib.bf_apply_noalloc
+    fn.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(BfParams),
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p]
+    fn.restype = ctypes.c_int
+    p = BfParams()
+    _check(lib.bf_params_default(d, N, ctypes.byref(p)), "bf_params_default")
+    for name, val in (("x_lo", x_lo), ("x_w", x_w), ("y_lo", y_lo), ("y_w", y_w)):
+        if val is not None:
+            arr = getattr(p, name)
+            for k, v in enumerate(list(val)[:3]):
+                arr[k] = float(v)
+    p.phase_scale = scale
+    p.tgt_off, p.src_off = tgt_off, src_off
+    p.precision = PREC[precision]
+    p.switch_level = switch_level
+    p.node_kind = node_kind
+    p.fuse_levels = fuse_levels
+    npts = N ** d
+    if g.numel() % npts or g.numel() != f.numel():
+        raise ValueError("g and f must hold nrhs x N^d values each")
+    _check(fn(d, N, q, PHASE[phase], ctypes.byref(p), g.data_ptr(), f.data_ptr(), g.numel() // npts,
+              _stream_ptr(stream)), "bf_apply_noalloc")
