@@ -145,6 +145,17 @@ bf_status bf_plan_info(bf_plan plan, int *d, int64_t *N, int *q, int *m, int *fu
 bf_status bf_apply_pass(bf_plan plan, int i, const void *g_dev, void *f_dev, int nrhs, void *stream);
 bf_status bf_pass_info(bf_plan plan, int i, int *kind, int *l0, int *k, int *flags);
 
+/* Self-checks of the mixed-precision arithmetic on the current device (they
+ * allocate and free a few bytes of device memory and synchronise).
+ *   bf_selfcheck_sincos: largest |error| of the FP32 sin/cos of 2 pi f used by the
+ *     mixed path, against CUDA's FP64 sincospi, over n evenly spaced f in [-1, 1).
+ *   bf_selfcheck_phase: largest |error|, in cycles and modulo 1, of the mixed
+ *     path's double-float Phi against FP64 arithmetic on the same table features,
+ *     over n pseudo-random (target node, source node) pairs of a BF_PREC_MIXED plan
+ *     (BF_ERR_INVALID_ARG for an FP64 plan). */
+bf_status bf_selfcheck_sincos(int n, double *max_abs_err);
+bf_status bf_selfcheck_phase(bf_plan plan, int n, double *max_err_cycles);
+
 /* Forward apply that allocates no device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc themselves or
  * let a library do it -- for example a host application that hands the GPU to

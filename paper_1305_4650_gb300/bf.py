@@ -22,7 +22,7 @@ STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_E
 
 EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_apply_host",
            "bf_apply_batched", "bf_destroy", "bf_status_string", "bf_last_cuda_error", "bf_plan_info",
-           "bf_apply_pass", "bf_pass_info"]
+           "bf_apply_pass", "bf_pass_info", "bf_selfcheck_sincos", "bf_selfcheck_phase"]
 
 
 class BfError(RuntimeError):
@@ -68,6 +68,8 @@ def load():
         lib.bf_apply_pass.argtypes = [vp, i32, vp, vp, i32, vp]
         lib.bf_pass_info.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]
+        lib.bf_selfcheck_sincos.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+        lib.bf_selfcheck_phase.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         for name in EXPORTS:
             getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
         lib.bf_status_string.restype = ctypes.c_char_p
@@ -209,6 +211,12 @@ class Plan:
         return dict(d=d.value, N=N.value, q=q.value, m=m.value, fuse_levels=k.value, launches=nl.value,
                     workspace_bytes=ws.value)
 
+    def selfcheck_phase(self, n: int = 1 << 20) -> float:
+        """Largest error (cycles, mod 1) of the double-float phase against FP64 on the same features."""
+        e = ctypes.c_double()
+        _check(load().bf_selfcheck_phase(self._h, n, ctypes.byref(e)), "bf_selfcheck_phase", self._h)
+        return e.value
+
     def last_cuda_error(self) -> int:
         e = ctypes.c_int()
         _check(load().bf_last_cuda_error(self._h, ctypes.byref(e)), "bf_last_cuda_error")
@@ -224,6 +232,13 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def selfcheck_sincos(n: int = 1 << 22) -> float:
+    """Largest |error| of the mixed path's FP32 sin/cos of 2 pi f against FP64 sincospi."""
+    e = ctypes.c_double()
+    _check(load().bf_selfcheck_sincos(n, ctypes.byref(e)), "bf_selfcheck_sincos")
+    return e.value
 
 
 def apply_batched(plans, gs, fs, nrhs, stream=None) -> None:

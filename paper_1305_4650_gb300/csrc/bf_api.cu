@@ -42,10 +42,22 @@ struct bf_plan_s {
 };
 
 namespace bfl {
-const PassFns *get_fns(int d, int q, int prec)
+const PassFns *get_fns(int d, int q, int prec, int kind)
 {
-    if (d == 2) return prec == 0 ? fns_d2_f64(q) : fns_d2_mix(q);
-    if (d == 3) return prec == 0 ? fns_d3_f64(q) : fns_d3_mix(q);
+    if (d == 2) {
+        switch (kind) {
+        case BF_PHASE_DOT: return prec == 0 ? fns_d2_f64_dot(q) : fns_d2_mix_dot(q);
+        case BF_PHASE_GENRADON: return prec == 0 ? fns_d2_f64_genradon(q) : fns_d2_mix_genradon(q);
+        case BF_PHASE_HYPRADON: return prec == 0 ? fns_d2_f64_hypradon(q) : fns_d2_mix_hypradon(q);
+        case BF_PHASE_SEPARABLE: return prec == 0 ? fns_d2_f64_separable(q) : fns_d2_mix_separable(q);
+        }
+    } else if (d == 3) {
+        switch (kind) {
+        case BF_PHASE_DOT: return prec == 0 ? fns_d3_f64_dot(q) : fns_d3_mix_dot(q);
+        case BF_PHASE_GENRADON: return prec == 0 ? fns_d3_f64_genradon(q) : fns_d3_mix_genradon(q);
+        case BF_PHASE_SEPARABLE: return prec == 0 ? fns_d3_f64_separable(q) : fns_d3_mix_separable(q);
+        }
+    }
     return nullptr;
 }
 }  // namespace bfl
@@ -266,7 +278,7 @@ bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t 
     return BF_OK;
 }
 
-bool supported_q(int d, int q) { return bfl::get_fns(d, q, 1) != nullptr && bfl::get_fns(d, q, 0) != nullptr; }
+bool supported_q(int d, int q) { return bfl::get_fns(d, q, 1, 0) != nullptr && bfl::get_fns(d, q, 0, 0) != nullptr; }
 
 }  // namespace
 
@@ -348,7 +360,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     p->max_nrhs = prm->max_nrhs;
     p->prm = *prm;
     p->csize = p->prec == BF_PREC_FP64 ? 16 : 8;
-    p->fns = bfl::get_fns(d, q, p->prec == BF_PREC_FP64 ? 0 : 1);
+    p->fns = bfl::get_fns(d, q, p->prec == BF_PREC_FP64 ? 0 : 1, (int)phase);
 
     for (int j = 0; j < q; ++j)
         p->z[j] = p->node_kind == 0 ? 0.5 * std::cos(j * kPi / (q - 1)) : 0.5 * std::cos((2 * j + 1) * kPi / (2.0 * q));
@@ -476,6 +488,25 @@ bf_status bf_destroy(bf_plan p)
     if (p->gstage) cudaFree(p->gstage);
     if (p->fstage) cudaFree(p->fstage);
     delete p;
+    return BF_OK;
+}
+
+bf_status bf_selfcheck_sincos(int n, double *max_abs_err)
+{
+    if (n < 1 || !max_abs_err) return BF_ERR_INVALID_ARG;
+    cudaError_t e = bfl::selfcheck_sincos(n, max_abs_err);
+    return e == cudaSuccess ? BF_OK : BF_ERR_CUDA;
+}
+
+bf_status bf_selfcheck_phase(bf_plan p, int n, double *max_err_cycles)
+{
+    if (!p || n < 1 || !max_err_cycles || p->prec != BF_PREC_MIXED) return BF_ERR_INVALID_ARG;
+    bfk::KArgs<bfk::PMIX> am;
+    bfk::KArgs<bfk::PF64> ad;
+    fill_args<bfk::PMIX>(p, am);
+    fill_args<bfk::PF64>(p, ad);
+    cudaError_t e = bfl::selfcheck_phase(&am, &ad, p->d, p->L, p->q, p->kind, n, max_err_cycles);
+    if (e != cudaSuccess) return cuda_fail(p, e);
     return BF_OK;
 }
 

@@ -77,33 +77,42 @@ __device__ __forceinline__ df df_add(df x, df y)
     return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
 
-// sqrt of a non-negative double-float, to about 2^-44 relative
-__device__ __forceinline__ df df_sqrt(df x)
+// nearest integer of |x| < 2^22: adding 1.5 * 2^23 leaves an ulp of 1, so the
+// rounding of the addition is the round-to-nearest-even of x (two full-rate adds)
+__device__ __forceinline__ float fround(float x)
 {
-    if (x.hi <= 0.0f) return {0.0f, 0.0f};
-    float r = rsqrtf(x.hi);
-    float s = __fmul_rn(x.hi, r);
-    float res = __fadd_rn(__fmaf_rn(-s, s, x.hi), x.lo);
-    return fast_two_sum(s, __fmul_rn(res, __fmul_rn(0.5f, r)));
+    const float M = 12582912.0f;
+    return __fsub_rn(__fadd_rn(x, M), M);
 }
 
-// x - nearest integer, as one float in [-0.5, 0.5] (about 2^-24 absolute of the exact value)
-__device__ __forceinline__ float df_frac(df x)
-{
-    float n = rintf(x.hi);
-    float f = __fadd_rn(__fsub_rn(x.hi, n), x.lo);
-    return __fsub_rn(f, rintf(f));
-}
-
-// frac of a product x*y with both factors double-float (the product itself may be large)
-__device__ __forceinline__ float df_mul_frac(df x, df y)
+// unnormalised product hi + lo = x * y (all but the x.lo * y.lo term)
+__device__ __forceinline__ df df_mul_u(df x, df y)
 {
     float p = __fmul_rn(x.hi, y.hi);
     float e = __fmaf_rn(x.hi, y.hi, -p);
     e = __fmaf_rn(x.hi, y.lo, e);
     e = __fmaf_rn(x.lo, y.hi, e);
-    float n = rintf(p);
-    return __fadd_rn(__fsub_rn(p, n), e);
+    return {p, e};
+}
+
+// sqrt of a non-negative (possibly unnormalised) double-float, to about 2^-44
+// relative, returned unnormalised: one Newton step from the FP32 reciprocal root
+__device__ __forceinline__ df df_sqrt_u(df x)
+{
+    float r = rsqrtf(fmaxf(x.hi, 1e-30f));
+    float s = __fmul_rn(x.hi, r);
+    float res = __fadd_rn(__fmaf_rn(-s, s, x.hi), x.lo);
+    return {s, __fmul_rn(res, __fmul_rn(0.5f, r))};
+}
+
+// x - nearest integer (|x| < 2^22), one float in about [-0.5, 0.5]
+__device__ __forceinline__ float df_frac(df x) { return __fadd_rn(__fsub_rn(x.hi, fround(x.hi)), x.lo); }
+
+// frac of a product x*y with both factors double-float (the product itself may be large)
+__device__ __forceinline__ float df_mul_frac(df x, df y)
+{
+    df p = df_mul_u(x, y);
+    return __fadd_rn(__fsub_rn(p.hi, fround(p.hi)), p.lo);
 }
 
 // ------------------------------------------------------- precision traits
@@ -127,7 +136,33 @@ struct PMIX {
 };
 
 __device__ __forceinline__ void sincos2pi(double fr, double &s, double &c) { sincospi(2.0 * fr, &s, &c); }
-__device__ __forceinline__ void sincos2pi(float fr, float &s, float &c) { sincospif(2.0f * fr, &s, &c); }
+// sin and cos of 2 pi f for |f| < 2^20, written from the Taylor series: quadrant
+// reduction f = j/4 + r with |r| <= 1/8, then sin a (degree 9) and cos a (degree 10)
+// for a = 2 pi r, |a| <= pi/4 (truncation error < 3e-8); the quadrant j rotates
+// (cos, sin) by j * 90 degrees.  Max abs error ~1e-7 (checked against FP64 sincospi
+// by bf_selfcheck_sincos).
+__device__ __forceinline__ void sincos2pi(float f, float &s, float &c)
+{
+    const float M = 12582912.0f;
+    const float t = __fmaf_rn(4.0f, f, M);                 // j + 1.5 * 2^23
+    const int q = __float_as_int(t);                       // low two bits: j mod 4
+    const float r = __fmaf_rn(-0.25f, __fsub_rn(t, M), f);
+    const float a = __fmul_rn(r, 6.28318530717958647692f);
+    const float a2 = __fmul_rn(a, a);
+    float ps = __fmaf_rn(a2, 2.75573192e-06f, -1.98412698e-04f);
+    ps = __fmaf_rn(a2, ps, 8.33333333e-03f);
+    ps = __fmaf_rn(a2, ps, -1.66666667e-01f);
+    const float sn = __fmaf_rn(__fmul_rn(a, a2), ps, a);
+    float pc = __fmaf_rn(a2, -2.75573192e-07f, 2.48015873e-05f);
+    pc = __fmaf_rn(a2, pc, -1.38888889e-03f);
+    pc = __fmaf_rn(a2, pc, 4.16666667e-02f);
+    pc = __fmaf_rn(a2, pc, -0.5f);
+    const float cs = __fmaf_rn(a2, pc, 1.0f);
+    const float s1 = (q & 1) ? cs : sn;
+    const float c1 = (q & 1) ? sn : cs;
+    s = __int_as_float(__float_as_int(s1) ^ ((q & 2) << 30));
+    c = __int_as_float(__float_as_int(c1) ^ (((q + 1) & 2) << 30));
+}
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -201,31 +236,32 @@ template <int Q> __device__ __forceinline__ int64_t soff(int L, int l) { return 
 // Source features per dimension:
 //   DOT y | GENRADON y, y^2 | HYPRADON -, y^2 | SEPARABLE s y^2/(k+2)
 
-template <class P, int D> struct Ph;
+template <class P, int D, int K> struct Ph;
 
-template <int D>
-struct Ph<PMIX, D> {
+template <int D, int K>
+struct Ph<PMIX, D, K> {
     struct T { df x[D]; df A[D]; };
     struct S { df y[D]; df y2[D]; };
 
     static __device__ __forceinline__ df hi(const float4 &v) { return {v.x, v.y}; }
     static __device__ __forceinline__ df lo(const float4 &v) { return {v.z, v.w}; }
 
+    // target point from its per-dimension table entries; GENRADON forms A_k = (s a_k(x))^2
     static __device__ __forceinline__ T tgt(const KArgs<PMIX> &a, const PMIX::TE *e)
     {
         T t;
 #pragma unroll
         for (int k = 0; k < D; ++k) { t.x[k] = hi(e[k].a); t.A[k] = lo(e[k].a); }
-        if (a.kind == KIND_GENRADON) {
+        if constexpr (K == KIND_GENRADON) {
             const df s3 = {a.sc.s3hi, a.sc.s3lo};
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 df u;
-                if (D == 2) u = (k == 0) ? df_mul(lo(e[0].a), lo(e[1].a)) : df_mul(hi(e[0].b), hi(e[1].b));
-                else u = df_mul(lo(e[k].a), hi(e[(k + 1) % D].b));
+                if constexpr (D == 2) u = (k == 0) ? df_mul_u(lo(e[0].a), lo(e[1].a)) : df_mul_u(hi(e[0].b), hi(e[1].b));
+                else u = df_mul_u(lo(e[k].a), hi(e[(k + 1) % D].b));
                 df two = two_sum(2.0f, u.hi);
-                u = fast_two_sum(two.hi, __fadd_rn(two.lo, u.lo));
-                u = df_mul(u, s3);
+                u = {two.hi, __fadd_rn(two.lo, u.lo)};
+                u = df_mul_u(u, s3);
                 t.A[k] = df_mul(u, u);
             }
         }
@@ -238,46 +274,82 @@ struct Ph<PMIX, D> {
         s.y2[k] = lo(e.a);
     }
 
-    // Phi(x, y) - nearest integer, in [-0.5, 0.5]
+    // Per-dimension split of Phi: part(t, y_k entry, k) is the contribution of source
+    // coordinate k; parts add (add), and fin() turns their sum into Phi minus an integer.
+    // Loops hoist the parts of the source coordinates that do not change.
+    struct Part { float f; df q; };
+    static __device__ __forceinline__ Part part(const T &t, const PMIX::SE &e, int k)
+    {
+        Part p{0.0f, {0.0f, 0.0f}};
+        const df y = hi(e.a), y2 = lo(e.a);
+        if constexpr (K == KIND_DOT) {
+            p.f = df_mul_frac(t.x[k], y);
+        } else if constexpr (K == KIND_GENRADON) {
+            p.f = df_mul_frac(t.x[k], y);
+            p.q = df_mul_u(t.A[k], y2);
+        } else if constexpr (K == KIND_HYPRADON) {
+            p.q = (k == 0) ? y2 : df_mul_u(t.A[1], y2);
+        } else {
+            p.q = df_add(t.x[k], y);
+        }
+        return p;
+    }
+    static __device__ __forceinline__ Part add(const Part &u, const Part &v)
+    {
+        const df s = two_sum(u.q.hi, v.q.hi);
+        return Part{u.f + v.f, {s.hi, __fadd_rn(__fadd_rn(u.q.lo, v.q.lo), s.lo)}};
+    }
+    static __device__ __forceinline__ float fin(const KArgs<PMIX> &a, const T &t, const Part &p)
+    {
+        if constexpr (K == KIND_DOT) {
+            return p.f;
+        } else if constexpr (K == KIND_GENRADON) {
+            return __fmaf_rn(a.sc.sgn, df_frac(df_sqrt_u(p.q)), p.f);
+        } else if constexpr (K == KIND_HYPRADON) {
+            return df_mul_frac(t.x[0], df_sqrt_u(p.q));
+        } else {
+            return df_frac(p.q);
+        }
+    }
+
+    // Phi(x, y) minus an integer, |result| < 2 (the sincos reduces it further)
     static __device__ __forceinline__ float frac(const KArgs<PMIX> &a, const T &t, const S &s)
     {
-        switch (a.kind) {
-        case KIND_DOT: {
+        if constexpr (K == KIND_DOT) {
             float f = 0.0f;
 #pragma unroll
             for (int k = 0; k < D; ++k) f += df_mul_frac(t.x[k], s.y[k]);
-            return f - rintf(f);
-        }
-        case KIND_GENRADON: {
+            return f;
+        } else if constexpr (K == KIND_GENRADON) {
             float f = 0.0f;
 #pragma unroll
             for (int k = 0; k < D; ++k) f += df_mul_frac(t.x[k], s.y[k]);
-            df q = df_mul(t.A[0], s.y2[0]);
+            // sum_k A_k y_k^2 from unnormalised products and one two-sum of the leading parts
+            df p0 = df_mul_u(t.A[0], s.y2[0]);
+            float lo = p0.lo, hi = p0.hi;
 #pragma unroll
-            for (int k = 1; k < D; ++k) q = df_add(q, df_mul(t.A[k], s.y2[k]));
-            df r = df_sqrt(q);
-            float fr = df_frac(r);
-            f += (a.sc.sgn < 0.0f) ? -fr : fr;
-            return f - rintf(f);
-        }
-        case KIND_HYPRADON: {
+            for (int k = 1; k < D; ++k) {
+                df pk = df_mul_u(t.A[k], s.y2[k]);
+                df sk = two_sum(hi, pk.hi);
+                hi = sk.hi;
+                lo = __fadd_rn(lo, __fadd_rn(pk.lo, sk.lo));
+            }
+            const float fr = df_frac(df_sqrt_u({hi, lo}));
+            return __fmaf_rn(a.sc.sgn, fr, f);
+        } else if constexpr (K == KIND_HYPRADON) {
             df q = df_add(s.y2[0], df_mul(t.A[1], s.y2[1]));
-            df r = df_sqrt(q);
-            float f = df_mul_frac(t.x[0], r);
-            return f - rintf(f);
-        }
-        default: { // SEPARABLE
+            return df_mul_frac(t.x[0], df_sqrt_u(q));
+        } else {
             df acc = {0.0f, 0.0f};
 #pragma unroll
             for (int k = 0; k < D; ++k) acc = df_add(acc, df_add(t.x[k], s.y[k]));
             return df_frac(acc);
         }
-        }
     }
 };
 
-template <int D>
-struct Ph<PF64, D> {
+template <int D, int K>
+struct Ph<PF64, D, K> {
     struct T { double x[D]; double A[D]; };
     struct S { double y[D]; double y2[D]; };
 
@@ -286,11 +358,11 @@ struct Ph<PF64, D> {
         T t;
 #pragma unroll
         for (int k = 0; k < D; ++k) { t.x[k] = e[k].a.x; t.A[k] = e[k].a.y; }
-        if (a.kind == KIND_GENRADON) {
+        if constexpr (K == KIND_GENRADON) {
 #pragma unroll
             for (int k = 0; k < D; ++k) {
                 double u;
-                if (D == 2) u = (k == 0) ? e[0].a.y * e[1].a.y : e[0].b.x * e[1].b.x;
+                if constexpr (D == 2) u = (k == 0) ? e[0].a.y * e[1].a.y : e[0].b.x * e[1].b.x;
                 else u = e[k].a.y * e[(k + 1) % D].b.x;
                 u = (2.0 + u) * a.sc.s3;
                 t.A[k] = u * u;
@@ -305,15 +377,32 @@ struct Ph<PF64, D> {
         s.y2[k] = e.a.y;
     }
 
+    struct Part { double f, q; };
+    static __device__ __forceinline__ Part part(const T &t, const PF64::SE &e, int k)
+    {
+        const double y = e.a.x, y2 = e.a.y;
+        if constexpr (K == KIND_DOT) return Part{t.x[k] * y, 0.0};
+        else if constexpr (K == KIND_GENRADON) return Part{t.x[k] * y, t.A[k] * y2};
+        else if constexpr (K == KIND_HYPRADON) return Part{0.0, k == 0 ? y2 : t.A[1] * y2};
+        else return Part{t.x[k] + y, 0.0};
+    }
+    static __device__ __forceinline__ Part add(const Part &u, const Part &v) { return Part{u.f + v.f, u.q + v.q}; }
+    static __device__ __forceinline__ double fin(const KArgs<PF64> &a, const T &t, const Part &p)
+    {
+        double v;
+        if constexpr (K == KIND_DOT || K == KIND_SEPARABLE) v = p.f;
+        else if constexpr (K == KIND_GENRADON) v = p.f + a.sc.sgn * sqrt(p.q);
+        else v = t.x[0] * sqrt(p.q);
+        return v - rint(v);
+    }
+
     static __device__ __forceinline__ double frac(const KArgs<PF64> &a, const T &t, const S &s)
     {
         double p = 0.0;
-        switch (a.kind) {
-        case KIND_DOT:
+        if constexpr (K == KIND_DOT) {
 #pragma unroll
             for (int k = 0; k < D; ++k) p += t.x[k] * s.y[k];
-            break;
-        case KIND_GENRADON: {
+        } else if constexpr (K == KIND_GENRADON) {
             double q = 0.0;
 #pragma unroll
             for (int k = 0; k < D; ++k) {
@@ -321,12 +410,9 @@ struct Ph<PF64, D> {
                 q += t.A[k] * s.y2[k];
             }
             p += a.sc.sgn * sqrt(q);
-            break;
-        }
-        case KIND_HYPRADON:
+        } else if constexpr (K == KIND_HYPRADON) {
             p = t.x[0] * sqrt(s.y2[0] + t.A[1] * s.y2[1]);
-            break;
-        default:
+        } else {
 #pragma unroll
             for (int k = 0; k < D; ++k) p += t.x[k] + s.y[k];
         }
@@ -335,16 +421,44 @@ struct Ph<PF64, D> {
 };
 
 // e^{2 pi i Phi} as a complex number of the working precision
-template <class P, int D>
-__device__ __forceinline__ typename P::C expphase(const KArgs<P> &a, const typename Ph<P, D>::T &t,
-                                                  const typename Ph<P, D>::S &s)
+template <class P, int D, int K>
+__device__ __forceinline__ typename P::C expphase(const KArgs<P> &a, const typename Ph<P, D, K>::T &t,
+                                                  const typename Ph<P, D, K>::S &s)
 {
-    typename P::R fr = Ph<P, D>::frac(a, t, s), sn, cs;
+    typename P::R fr = Ph<P, D, K>::frac(a, t, s), sn, cs;
     sincos2pi(fr, sn, cs);
     typename P::C e;
     e.x = cs;
     e.y = sn;
     return e;
+}
+
+template <class P, int D, int K>
+__device__ __forceinline__ typename P::C expphase_part(const KArgs<P> &a, const typename Ph<P, D, K>::T &t,
+                                                       const typename Ph<P, D, K>::Part &pt)
+{
+    typename P::R fr = Ph<P, D, K>::fin(a, t, pt), sn, cs;
+    sincos2pi(fr, sn, cs);
+    typename P::C e;
+    e.x = cs;
+    e.y = sn;
+    return e;
+}
+
+// complex multiply-accumulate acc += e * u as four FMAs
+__device__ __forceinline__ void cmac(float2 &acc, float2 e, float2 u)
+{
+    acc.x = __fmaf_rn(e.x, u.x, acc.x);
+    acc.x = __fmaf_rn(-e.y, u.y, acc.x);
+    acc.y = __fmaf_rn(e.x, u.y, acc.y);
+    acc.y = __fmaf_rn(e.y, u.x, acc.y);
+}
+__device__ __forceinline__ void cmac(double2 &acc, double2 e, double2 u)
+{
+    acc.x = fma(e.x, u.x, acc.x);
+    acc.x = fma(-e.y, u.y, acc.x);
+    acc.y = fma(e.x, u.y, acc.y);
+    acc.y = fma(e.y, u.x, acc.y);
 }
 
 // table reads
@@ -360,21 +474,21 @@ __device__ __forceinline__ typename P::SE sget(const KArgs<P> &a, int k, int l, 
 }
 
 // features of the target point of box `coords` at level l, slot per dimension
-template <class P, int D, int Q>
-__device__ __forceinline__ typename Ph<P, D>::T tpoint(const KArgs<P> &a, int l, const int *coords, const int *slot)
+template <class P, int D, int Q, int K>
+__device__ __forceinline__ typename Ph<P, D, K>::T tpoint(const KArgs<P> &a, int l, const int *coords, const int *slot)
 {
     typename P::TE e[D];
 #pragma unroll
     for (int k = 0; k < D; ++k) e[k] = tget<P, Q>(a, k, l, coords[k], slot[k]);
-    return Ph<P, D>::tgt(a, e);
+    return Ph<P, D, K>::tgt(a, e);
 }
 
-template <class P, int D, int Q>
-__device__ __forceinline__ typename Ph<P, D>::S spoint(const KArgs<P> &a, int l, const int *coords, const int *slot)
+template <class P, int D, int Q, int K>
+__device__ __forceinline__ typename Ph<P, D, K>::S spoint(const KArgs<P> &a, int l, const int *coords, const int *slot)
 {
-    typename Ph<P, D>::S s;
+    typename Ph<P, D, K>::S s;
 #pragma unroll
-    for (int k = 0; k < D; ++k) Ph<P, D>::src1(s, k, sget<P, Q>(a, k, l, coords[k], slot[k]));
+    for (int k = 0; k < D; ++k) Ph<P, D, K>::src1(s, k, sget<P, Q>(a, k, l, coords[k], slot[k]));
     return s;
 }
 
@@ -401,11 +515,11 @@ struct Cfg {
     static constexpr int MINB = (640 / NT) < 1 ? 1 : ((640 / NT) > 8 ? 8 : 640 / NT);
 };
 
-template <int D, int Q, class P>
+template <int D, int Q, class P, int K>
 struct Tile {
     using R = typename P::R;
     using C = typename P::C;
-    using PH = Ph<P, D>;
+    using PH = Ph<P, D, K>;
     static constexpr int NC = 1 << D;
     static constexpr int RR = ipow(Q, D);
     static constexpr int QD1 = ipow(Q, D - 1);
@@ -429,7 +543,7 @@ struct Tile {
         const int L = a.L;
         const int cX[DMAX] = {0, 0, 0};
         const int ctr[DMAX] = {Q, Q, Q};
-        const typename PH::T tX = tpoint<P, D, Q>(a, 0, cX, ctr);   // centre of X
+        const typename PH::T tX = tpoint<P, D, Q, K>(a, 0, cX, ctr);   // centre of X
         for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) {
             const int t = it % RR, b = (it / RR) % n, tau = it / (RR * n);
             uint32_t Ap, Bstar;
@@ -448,8 +562,8 @@ struct Tile {
                 for (int j = 0; j < D; ++j) flat = (flat << L) + cb[j];
                 const C gv = a.g[(int64_t)rhs * a.npts + flat];
                 const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
-                const C e1 = expphase<P, D>(a, tX, spoint<P, D, Q>(a, 0, cb, pslot));
-                const C e0 = expphase<P, D>(a, tX, spoint<P, D, Q>(a, 0, cb, tk));
+                const C e1 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, pslot));
+                const C e0 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, tk));
                 C v = cjmul(e0, cmul(e1, gv));
                 out.x = lag * v.x;
                 out.y = lag * v.y;
@@ -491,7 +605,7 @@ struct Tile {
             morton_decode<D>(Aa, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
             const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tpoint<P, D, Q>(a, l + 1, ca, ctr);
+            const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
             const C *Wtau = Wt + tau * n * RR;
             C acc[QD1];
 #pragma unroll
@@ -510,7 +624,7 @@ struct Tile {
 #pragma unroll
                     for (int t0p = 0; t0p < Q; ++t0p) {
                         PH::src1(sp, 0, sget<P, Q>(a, 0, l, cb[0], t0p));
-                        const C u = cmul(expphase<P, D>(a, tA, sp), win[t0p + Q * tq]);
+                        const C u = cmul(expphase<P, D, K>(a, tA, sp), win[t0p + Q * tq]);
 #pragma unroll
                         for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[c0][t0][t0p], u);
                     }
@@ -525,7 +639,7 @@ struct Tile {
 #pragma unroll
                         for (int t0p = 0; t0p < Q; ++t0p) {
                             PH::src1(sp, 0, sget<P, Q>(a, 0, l, cb[0], t0p));
-                            const C u = cmul(expphase<P, D>(a, tA, sp), win[t0p + Q * t1p + Q * Q * tq]);
+                            const C u = cmul(expphase<P, D, K>(a, tA, sp), win[t0p + Q * t1p + Q * Q * tq]);
 #pragma unroll
                             for (int t0 = 0; t0 < Q; ++t0) cfma(tmp[t0], a.M[c0][t0][t0p], u);
                         }
@@ -557,7 +671,7 @@ struct Tile {
             morton_decode<D>(Aa, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
             const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tpoint<P, D, Q>(a, l + 1, ca, ctr);
+            const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
             C acc[Q];
 #pragma unroll
             for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
@@ -584,7 +698,7 @@ struct Tile {
 #pragma unroll
             for (int tq = 0; tq < Q; ++tq) {
                 PH::src1(sp, D - 1, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq));
-                wo[tq * QD1] = cjmul(expphase<P, D>(a, tA, sp), acc[tq]);
+                wo[tq * QD1] = cjmul(expphase<P, D, K>(a, tA, sp), acc[tq]);
             }
         }
         __syncthreads();
@@ -618,18 +732,30 @@ struct Tile {
 #pragma unroll
             for (int s0 = 0; s0 < Q; ++s0) {
                 sk[0] = s0;
-                tS[s0] = tpoint<P, D, Q>(a, l, ca, sk);
+                tS[s0] = tpoint<P, D, Q, K>(a, l, ca, sk);
                 acc[s0] = czero<C>();
             }
             const C *u = Wt + (tau * n + sl) * RR;
-            for (int t = 0; t < RR; ++t) {
-                int tk[DMAX], tt = t;
+            // t = t_0 + q t_{>=1}: the parts of coordinates >= 1 are fixed over the t_0 loop
+#pragma unroll 1
+            for (int th = 0; th < QD1; ++th) {
+                int tk[DMAX], tt = th;
 #pragma unroll
-                for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; }
-                const typename PH::S sp = spoint<P, D, Q>(a, l, cb, tk);
-                const C ut = u[t];
+                for (int j = 1; j < D; ++j) { tk[j] = tt % Q; tt /= Q; }
+                typename PH::Part hp[Q];
 #pragma unroll
-                for (int s0 = 0; s0 < Q; ++s0) acc[s0] = cadd(acc[s0], cmul(expphase<P, D>(a, tS[s0], sp), ut));
+                for (int s0 = 0; s0 < Q; ++s0) {
+                    hp[s0] = PH::part(tS[s0], sget<P, Q>(a, 1, l, cb[1], tk[1]), 1);
+                    if constexpr (D == 3) hp[s0] = PH::add(hp[s0], PH::part(tS[s0], sget<P, Q>(a, 2, l, cb[2], tk[2]), 2));
+                }
+#pragma unroll
+                for (int t0 = 0; t0 < Q; ++t0) {
+                    const typename P::SE e0 = sget<P, Q>(a, 0, l, cb[0], t0);
+                    const C ut = u[t0 + Q * th];
+#pragma unroll
+                    for (int s0 = 0; s0 < Q; ++s0)
+                        cmac(acc[s0], expphase_part<P, D, K>(a, tS[s0], PH::add(PH::part(tS[s0], e0, 0), hp[s0])), ut);
+                }
             }
             C *w = S + (tau * n + sl) * RR + sh * Q;
 #pragma unroll
@@ -663,7 +789,7 @@ struct Tile {
 #pragma unroll
             for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
             const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::S sc = spoint<P, D, Q>(a, l, cb, ctr);
+            const typename PH::S sc = spoint<P, D, Q, K>(a, l, cb, ctr);
             int tk[DMAX];
             {
                 int tt = th;
@@ -677,7 +803,7 @@ struct Tile {
 #pragma unroll
             for (int t0 = 0; t0 < Q; ++t0) {
                 tk[0] = t0;
-                const C u = cjmul(expphase<P, D>(a, tpoint<P, D, Q>(a, l, ca, tk), sc), win[t0]);
+                const C u = cjmul(expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l, ca, tk), sc), win[t0]);
 #pragma unroll
                 for (int s0 = 0; s0 < Q; ++s0) {
                     cfma(z[0][s0], a.M[0][t0][s0], u);
@@ -718,7 +844,7 @@ struct Tile {
                     int cb[DMAX], ctr[DMAX] = {Q, Q, Q};
 #pragma unroll
                     for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
-                    sc[c] = spoint<P, D, Q>(a, l, cb, ctr);
+                    sc[c] = spoint<P, D, Q, K>(a, l, cb, ctr);
                     const C *si = Sblk + c * QD1 * 2 * Q + a0 * Q + s0;   // [t1] stride 2Q
 #pragma unroll
                     for (int s1 = 0; s1 < Q; ++s1) v[c][s1] = czero<C>();
@@ -732,9 +858,9 @@ struct Tile {
 #pragma unroll
                 for (int s1 = 0; s1 < Q; ++s1) {
                     const int sk[DMAX] = {s0, s1, 0};
-                    const typename PH::T tS = tpoint<P, D, Q>(a, l + 1, ca, sk);
+                    const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) acc[s1] = cadd(acc[s1], cmul(expphase<P, D>(a, tS, sc[c]), v[c][s1]));
+                    for (int c = 0; c < NC; ++c) acc[s1] = cadd(acc[s1], cmul(expphase<P, D, K>(a, tS, sc[c]), v[c][s1]));
                 }
             } else {
                 const int a1 = (alpha >> 1) & 1, a2 = (alpha >> 2) & 1;
@@ -743,7 +869,7 @@ struct Tile {
                     int cb[DMAX], ctr[DMAX] = {Q, Q, Q};
 #pragma unroll
                     for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
-                    const typename PH::S sc = spoint<P, D, Q>(a, l, cb, ctr);
+                    const typename PH::S sc = spoint<P, D, Q, K>(a, l, cb, ctr);
                     const C *si = Sblk + c * QD1 * 2 * Q + a0 * Q + s0;   // [t1 + Q t2] stride 2Q
                     C w[Q * Q];   // [t1][s2]
 #pragma unroll
@@ -764,8 +890,8 @@ struct Tile {
 #pragma unroll
                             for (int t1 = 0; t1 < Q; ++t1) cfma(v, a.M[a1][t1][s1], w[t1 * Q + s2]);
                             const int sk[DMAX] = {s0, s1, s2};
-                            const typename PH::T tS = tpoint<P, D, Q>(a, l + 1, ca, sk);
-                            acc[s1 + Q * s2] = cadd(acc[s1 + Q * s2], cmul(expphase<P, D>(a, tS, sc), v));
+                            const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
+                            acc[s1 + Q * s2] = cadd(acc[s1 + Q * s2], cmul(expphase<P, D, K>(a, tS, sc), v));
                         }
                 }
             }
@@ -783,7 +909,7 @@ struct Tile {
         const int L = a.L;
         const int cY[DMAX] = {0, 0, 0};
         const int ctr[DMAX] = {Q, Q, Q};
-        const typename PH::S sY = spoint<P, D, Q>(a, L, cY, ctr);      // centre of Y
+        const typename PH::S sY = spoint<P, D, Q, K>(a, L, cY, ctr);      // centre of Y
         for (int it = threadIdx.x; it < a.T * n; it += blockDim.x) {
             const int sl = it % n, tau = it / n;
             uint32_t Ap, Bstar;
@@ -799,11 +925,11 @@ struct Tile {
 #pragma unroll
                 for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.ltgt[tk[j]]; }
                 if (lag == R(0)) continue;
-                const C e = expphase<P, D>(a, tpoint<P, D, Q>(a, L, ca, tk), sY);
+                const C e = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, tk), sY);
                 cfma(acc, lag, cjmul(e, w[t]));
             }
             const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
-            const C e = expphase<P, D>(a, tpoint<P, D, Q>(a, L, ca, pslot), sY);
+            const C e = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, pslot), sY);
             int64_t flat = 0;
 #pragma unroll
             for (int j = 0; j < D; ++j) flat = (flat << L) + ca[j];
@@ -838,11 +964,11 @@ struct Tile {
 // ------------------------------------------------------------------ kernels
 
 // init (l0 = 0) + k column merges + optional switch at level l0 + k
-template <int D, int Q, class P>
+template <int D, int Q, class P, int K>
 __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pass(const KArgs<P> a)
 {
     using C = typename P::C;
-    using TL = Tile<D, Q, P>;
+    using TL = Tile<D, Q, P, K>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *Wt = reinterpret_cast<C *>(smem_raw);
     C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
@@ -858,11 +984,11 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pa
 }
 
 // k row merges + optional final evaluation (l0 + k = L)
-template <int D, int Q, class P>
+template <int D, int Q, class P, int K>
 __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pass(const KArgs<P> a)
 {
     using C = typename P::C;
-    using TL = Tile<D, Q, P>;
+    using TL = Tile<D, Q, P, K>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *Wt = reinterpret_cast<C *>(smem_raw);
     C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;

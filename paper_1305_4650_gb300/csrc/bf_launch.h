@@ -17,14 +17,22 @@ struct PassFns {
     int nthreads;                // threads per CTA
 };
 
-// (d, q, precision) -> kernels, or null if that combination is not compiled.
-// precision: 0 FP64, 1 mixed
-const PassFns *get_fns(int d, int q, int prec);
+// (d, q, precision, phase kind) -> kernels, or null if that combination is not compiled.
+// precision: 0 FP64, 1 mixed; kind: bf_phase_kind
+const PassFns *get_fns(int d, int q, int prec, int kind);
 
-const PassFns *fns_d2_f64(int q);
-const PassFns *fns_d2_mix(int q);
-const PassFns *fns_d3_f64(int q);
-const PassFns *fns_d3_mix(int q);
+// one function per instantiation unit: bf_inst_d{d}_{f64|mix}_{kind}.cu
+#define BFL_DECLARE(d, pr, kn) const PassFns *fns_d##d##_##pr##_##kn(int q);
+BFL_DECLARE(2, f64, dot) BFL_DECLARE(2, f64, genradon) BFL_DECLARE(2, f64, hypradon) BFL_DECLARE(2, f64, separable)
+BFL_DECLARE(2, mix, dot) BFL_DECLARE(2, mix, genradon) BFL_DECLARE(2, mix, hypradon) BFL_DECLARE(2, mix, separable)
+BFL_DECLARE(3, f64, dot) BFL_DECLARE(3, f64, genradon) BFL_DECLARE(3, f64, separable)
+BFL_DECLARE(3, mix, dot) BFL_DECLARE(3, mix, genradon) BFL_DECLARE(3, mix, separable)
+#undef BFL_DECLARE
 
+
+// device self-checks (bf_selfcheck.cu)
+cudaError_t selfcheck_sincos(int n, double *max_err);
+cudaError_t selfcheck_phase(const void *kargs_mix, const void *kargs_f64, int d, int L, int q, int kind, int n,
+                            double *max_err);
 
 }  // namespace bfl

@@ -250,7 +250,7 @@ extern "C" bf_status bf_apply_noalloc(int d, int64_t N, int q, bf_phase_kind pha
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
     if (nrhs < 0 || nrhs > 65535) return BF_ERR_INVALID_ARG;
     const int prec = prm->precision == BF_PREC_FP64 ? 0 : 1;
-    const bfl::PassFns *fns = bfl::get_fns(d, q, prec);
+    const bfl::PassFns *fns = bfl::get_fns(d, q, prec, (int)phase);
     if (!fns) return BF_ERR_UNSUPPORTED;
 
     // scratch needed: 2d tables of nent entries (32 B target, 16 B source) + 2 weight buffers
