@@ -198,14 +198,35 @@ struct KArgs {
 
 // --------------------------------------------------------- index helpers
 
-template <int D>
-__device__ __forceinline__ void morton_decode(uint32_t m, int bits, int *c)
+// Morton decode by bit compaction: every D-th bit of m, starting at bit k, gathered
+// into c[k] (mask-and-shift steps, no loop; valid for up to 32/D bits per dimension)
+__device__ __forceinline__ uint32_t compact_by2(uint32_t x)
 {
-#pragma unroll
-    for (int k = 0; k < D; ++k) c[k] = 0;
-    for (int j = 0; j < bits; ++j) {
-#pragma unroll
-        for (int k = 0; k < D; ++k) c[k] |= ((m >> (j * D + k)) & 1u) << j;
+    x &= 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0f0f0f0fu;
+    x = (x | (x >> 4)) & 0x00ff00ffu;
+    return (x | (x >> 8)) & 0x0000ffffu;
+}
+__device__ __forceinline__ uint32_t compact_by3(uint32_t x)
+{
+    x &= 0x09249249u;
+    x = (x | (x >> 2)) & 0x030c30c3u;
+    x = (x | (x >> 4)) & 0x0300f00fu;
+    x = (x | (x >> 8)) & 0x030000ffu;
+    return (x | (x >> 16)) & 0x000003ffu;
+}
+
+template <int D>
+__device__ __forceinline__ void morton_decode(uint32_t m, int /*bits*/, int *c)
+{
+    if constexpr (D == 2) {
+        c[0] = (int)compact_by2(m);
+        c[1] = (int)compact_by2(m >> 1);
+    } else {
+        c[0] = (int)compact_by3(m);
+        c[1] = (int)compact_by3(m >> 1);
+        c[2] = (int)compact_by3(m >> 2);
     }
 }
 
@@ -221,10 +242,10 @@ __device__ __forceinline__ uint32_t digit_rev(uint32_t x, int n)
     return y;
 }
 
-// target table: level l has 2^l boxes per dimension, (Q+2) slots each
-template <int Q> __device__ __forceinline__ int64_t toff(int l) { return ((1LL << l) - 1) * (Q + 2); }
+// target table: level l has 2^l boxes per dimension, (Q+2) slots each (< 2^31 entries)
+template <int Q> __device__ __forceinline__ int toff(int l) { return ((1 << l) - 1) * (Q + 2); }
 // source table: level l has 2^(L-l) boxes per dimension
-template <int Q> __device__ __forceinline__ int64_t soff(int L, int l) { return ((2LL << L) - (2LL << (L - l))) * (Q + 2); }
+template <int Q> __device__ __forceinline__ int soff(int L, int l) { return ((2 << L) - (2 << (L - l))) * (Q + 2); }
 
 // ------------------------------------------------------------------ phase
 //
@@ -465,12 +486,12 @@ __device__ __forceinline__ void cmac(double2 &acc, double2 e, double2 u)
 template <class P, int Q>
 __device__ __forceinline__ typename P::TE tget(const KArgs<P> &a, int k, int l, int box, int slot)
 {
-    return a.tt[k][toff<Q>(l) + (int64_t)box * (Q + 2) + slot];
+    return a.tt[k][toff<Q>(l) + box * (Q + 2) + slot];
 }
 template <class P, int Q>
 __device__ __forceinline__ typename P::SE sget(const KArgs<P> &a, int k, int l, int box, int slot)
 {
-    return a.st[k][soff<Q>(a.L, l) + (int64_t)box * (Q + 2) + slot];
+    return a.st[k][soff<Q>(a.L, l) + box * (Q + 2) + slot];
 }
 
 // features of the target point of box `coords` at level l, slot per dimension
@@ -530,10 +551,10 @@ struct Tile {
     // (Ap, B*) of the CTA's tile tau: tile index = Ap * 2^{D(L-l0-k)} + B*
     static __device__ __forceinline__ void tile_of(const KArgs<P> &a, int tau, uint32_t &Ap, uint32_t &Bstar)
     {
-        const uint64_t tile = (uint64_t)blockIdx.x * a.T + tau;
+        const uint32_t tile = blockIdx.x * (uint32_t)a.T + (uint32_t)tau;   // < 2^30
         const int sh = D * (a.L - a.l0 - a.k);
-        Ap = (uint32_t)(tile >> sh);
-        Bstar = (uint32_t)(tile & ((1ull << sh) - 1));
+        Ap = tile >> sh;
+        Bstar = tile & ((1u << sh) - 1u);
     }
 
     // ---- init: weights of the leaf pairs (X, B); items (tau, b, t)
