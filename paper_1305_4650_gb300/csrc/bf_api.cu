@@ -278,6 +278,33 @@ bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t 
     return BF_OK;
 }
 
+// Adjoint: the forward schedule reversed.  The adjoint of forward pass i reads
+// buffer (i + 1) % 2 (or f when it starts with final^H) and writes buffer i % 2
+// (or g when it ends with init^H).
+template <class P>
+bf_status run_adjoint(bf_plan p, const void *f, void *g, int nrhs, cudaStream_t s)
+{
+    bfk::KArgs<P> a;
+    fill_args<P>(p, a);
+    a.fadj = static_cast<const typename P::C *>(f);
+    a.gadj = static_cast<typename P::C *>(g);
+    void *buf[2] = {p->w0, p->w1};
+    for (int i = (int)p->passes.size() - 1; i >= 0; --i) {
+        const Pass &ps = p->passes[i];
+        a.l0 = ps.l0;
+        a.k = ps.k;
+        a.flags = ps.flags;
+        a.T = ps.T;
+        a.win = static_cast<const typename P::C *>(buf[(i + 1) & 1]);
+        a.wout = static_cast<typename P::C *>(buf[i & 1]);
+        const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
+        const size_t smem = pass_smem(p, ps);
+        cudaError_t e = (ps.row ? p->fns->row_adj : p->fns->col_adj)(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
+        if (e != cudaSuccess) return cuda_fail(p, e);
+    }
+    return BF_OK;
+}
+
 bool supported_q(int d, int q) { return bfl::get_fns(d, q, 1, 0) != nullptr && bfl::get_fns(d, q, 0, 0) != nullptr; }
 
 }  // namespace
@@ -431,12 +458,14 @@ bf_status bf_pass_info(bf_plan p, int i, int *kind, int *l0, int *k, int *flags)
 
 bf_status bf_apply_adjoint(bf_plan p, const void *f, void *g, int nrhs, void *stream)
 {
-    (void)f;
-    (void)g;
-    (void)stream;
     if (!p) return BF_ERR_INVALID_ARG;
     if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
-    return BF_ERR_UNSUPPORTED;
+    if (nrhs == 0) return BF_OK;
+    if (!g || !f) return BF_ERR_INVALID_ARG;
+    if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->prec == BF_PREC_FP64) return run_adjoint<bfk::PF64>(p, f, g, nrhs, s);
+    return run_adjoint<bfk::PMIX>(p, f, g, nrhs, s);
 }
 
 bf_status bf_apply_host(bf_plan p, const void *g_host, void *f_host, int nrhs, void *stream)

@@ -187,6 +187,8 @@ struct KArgs {
     C *wout;                          // output weights (unused with F_FINAL)
     const C *g;                       // sources [rhs][N^d] (F_INIT)
     C *f;                             // targets [rhs][N^d] (F_FINAL)
+    const C *fadj;                    // adjoint input: target values [rhs][N^d] (final^H)
+    C *gadj;                          // adjoint output: source values [rhs][N^d] (init^H)
     int64_t wstride;                  // per-rhs stride of weights, in complex numbers
     int64_t npts;                     // N^d
     R M[2][QMAX][QMAX];               // M[h][t][t'] = l_t((z_t' + h - 1/2)/2)
@@ -958,6 +960,402 @@ struct Tile {
         }
     }
 
+    // =====================================================================
+    // Adjoint passes: every step conjugate-transposed, levels in reverse.
+    // On entry to a level the slot of output alpha of a merge block holds the
+    // level-(l+1) weights; on exit the slot of input c holds the level-l weights.
+
+    // ---- adjoint of one column merge (level l+1 -> l):
+    // in_c(t') = sum_alpha e^{-2pi i Phi(x0(A_alpha), y_t'^{B_c})} sum_t M_c[t][t'] e^{2pi i Phi(x0(A_alpha), y_t^{B'})} out_alpha(t)
+    static __device__ void col_level_adj(const KArgs<P> &a, C *Wt, C *S, int l, int i)
+    {
+        const int k = a.k, n = 1 << (D * k), nblk = n >> D;
+        const int L = a.L;
+        // stage A: items (tau, block, alpha, t_{>=1}): re-modulate out_alpha at the nodes of B',
+        // contract dim 0 into both children c_0 -> S[tau][block][alpha][t_{>=1}][c_0][t'_0]
+        for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
+            const int th = it % QD1;
+            const int alpha = (it / QD1) % NC;
+            const int beta = (it / (QD1 * NC)) % nblk;
+            const int tau = it / (QD1 * NC * nblk);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            int ca[DMAX], cbq[DMAX];
+            morton_decode<D>((Apg << D) + alpha, l + 1, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+            const int ctr[DMAX] = {Q, Q, Q};
+            const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
+            int tk[DMAX];
+            {
+                int tt = th;
+#pragma unroll
+                for (int j = 1; j < D; ++j) { tk[j] = tt % Q; tt /= Q; }
+            }
+            typename PH::Part hp = PH::part(tA, sget<P, Q>(a, 1, l + 1, cbq[1], tk[1]), 1);
+            if constexpr (D == 3) hp = PH::add(hp, PH::part(tA, sget<P, Q>(a, 2, l + 1, cbq[2], tk[2]), 2));
+            const C *wi = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR + th * Q;
+            C z[2][Q];
+#pragma unroll
+            for (int s0 = 0; s0 < Q; ++s0) { z[0][s0] = czero<C>(); z[1][s0] = czero<C>(); }
+#pragma unroll
+            for (int t0 = 0; t0 < Q; ++t0) {
+                const C e = expphase_part<P, D, K>(a, tA, PH::add(PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], t0), 0), hp));
+                const C u = cmul(e, wi[t0]);
+#pragma unroll
+                for (int s0 = 0; s0 < Q; ++s0) {
+                    cfma(z[0][s0], a.M[0][t0][s0], u);
+                    cfma(z[1][s0], a.M[1][t0][s0], u);
+                }
+            }
+            C *so = S + (((tau * nblk + beta) * NC + alpha) * QD1 + th) * 2 * Q;
+#pragma unroll
+            for (int s0 = 0; s0 < Q; ++s0) { so[s0] = z[0][s0]; so[Q + s0] = z[1][s0]; }
+        }
+        __syncthreads();
+        // stage B: items (tau, block, c, t'_0): contract dims >= 1 with M_{c_{>=1}} per alpha,
+        // conjugate modulation at the nodes of B_c, sum over alpha
+        for (int it = threadIdx.x; it < a.T * nblk * NC * Q; it += blockDim.x) {
+            const int s0 = it % Q;
+            const int c = (it / Q) % NC;
+            const int beta = (it / (Q * NC)) % nblk;
+            const int tau = it / (Q * NC * nblk);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            int cbq[DMAX], cb[DMAX];
+            morton_decode<D>(Bq, L - l - 1, cbq);
+#pragma unroll
+            for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+            const int c0 = c & 1;
+            const typename P::SE e0 = sget<P, Q>(a, 0, l, cb[0], s0);
+            C acc[QD1];
+#pragma unroll
+            for (int j = 0; j < QD1; ++j) acc[j] = czero<C>();
+#pragma unroll 1
+            for (int alpha = 0; alpha < NC; ++alpha) {
+                int ca[DMAX];
+                morton_decode<D>((Apg << D) + alpha, l + 1, ca);
+                const int ctr[DMAX] = {Q, Q, Q};
+                const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
+                const typename PH::Part p0 = PH::part(tA, e0, 0);
+                const C *si = S + ((tau * nblk + beta) * NC + alpha) * QD1 * 2 * Q + c0 * Q + s0;   // [t_{>=1}] stride 2Q
+                if constexpr (D == 2) {
+                    const int c1 = (c >> 1) & 1;
+                    C v[Q];
+#pragma unroll
+                    for (int s1 = 0; s1 < Q; ++s1) v[s1] = czero<C>();
+#pragma unroll
+                    for (int t1 = 0; t1 < Q; ++t1) {
+                        const C zz = si[t1 * 2 * Q];
+#pragma unroll
+                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[s1], a.M[c1][t1][s1], zz);
+                    }
+#pragma unroll
+                    for (int s1 = 0; s1 < Q; ++s1) {
+                        const C e = expphase_part<P, D, K>(a, tA, PH::add(p0, PH::part(tA, sget<P, Q>(a, 1, l, cb[1], s1), 1)));
+                        acc[s1] = cadd(acc[s1], cjmul(e, v[s1]));
+                    }
+                } else {
+                    const int c1 = (c >> 1) & 1, c2 = (c >> 2) & 1;
+                    C w[Q * Q];   // [t1][s2]
+#pragma unroll
+                    for (int j = 0; j < Q * Q; ++j) w[j] = czero<C>();
+#pragma unroll
+                    for (int t2 = 0; t2 < Q; ++t2)
+#pragma unroll
+                        for (int t1 = 0; t1 < Q; ++t1) {
+                            const C zz = si[(t1 + Q * t2) * 2 * Q];
+#pragma unroll
+                            for (int s2 = 0; s2 < Q; ++s2) cfma(w[t1 * Q + s2], a.M[c2][t2][s2], zz);
+                        }
+#pragma unroll
+                    for (int s2 = 0; s2 < Q; ++s2) {
+                        const typename PH::Part p2 = PH::add(p0, PH::part(tA, sget<P, Q>(a, 2, l, cb[2], s2), 2));
+#pragma unroll
+                        for (int s1 = 0; s1 < Q; ++s1) {
+                            C v = czero<C>();
+#pragma unroll
+                            for (int t1 = 0; t1 < Q; ++t1) cfma(v, a.M[c1][t1][s1], w[t1 * Q + s2]);
+                            const C e = expphase_part<P, D, K>(a, tA, PH::add(p2, PH::part(tA, sget<P, Q>(a, 1, l, cb[1], s1), 1)));
+                            acc[s1 + Q * s2] = cadd(acc[s1 + Q * s2], cjmul(e, v));
+                        }
+                    }
+                }
+            }
+            C *wo = Wt + tau * n * RR + (base + (c << (D * i))) * RR + s0;
+#pragma unroll
+            for (int sh = 0; sh < QD1; ++sh) wo[sh * Q] = acc[sh];
+        }
+        __syncthreads();
+    }
+
+    // ---- adjoint of one row merge (level l+1 -> l):
+    // in_c(t) = e^{2pi i Phi(x_t^{Ap}, y0(B_c))} sum_alpha sum_s M_alpha[t][s] e^{-2pi i Phi(x_s^{A_alpha}, y0(B_c))} out_alpha(s)
+    static __device__ void row_level_adj(const KArgs<P> &a, C *Wt, C *S, int l, int i)
+    {
+        const int k = a.k, n = 1 << (D * k), nblk = n >> D;
+        const int L = a.L;
+        // stage A: items (tau, block, c, alpha_{D-1}, s_{D-1}): conjugate post-modulation of every
+        // out_alpha at the child's nodes, contraction over dims 0..D-2 and alpha_{<D-1}
+        //   -> S[tau][block][c][alpha_{D-1}][s_{D-1}][t_{<D-1}]
+        for (int it = threadIdx.x; it < a.T * nblk * NC * 2 * Q; it += blockDim.x) {
+            const int sq = it % Q;
+            const int ahi = (it / Q) & 1;
+            const int c = (it / (2 * Q)) % NC;
+            const int beta = (it / (2 * Q * NC)) % nblk;
+            const int tau = it / (2 * Q * NC * nblk);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            int cbq[DMAX], cb[DMAX];
+            morton_decode<D>(Bq, L - l - 1, cbq);
+#pragma unroll
+            for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+            const int ctr[DMAX] = {Q, Q, Q};
+            const typename PH::S sc = spoint<P, D, Q, K>(a, l, cb, ctr);
+            C acc[QD1];
+#pragma unroll
+            for (int j = 0; j < QD1; ++j) acc[j] = czero<C>();
+#pragma unroll
+            for (int al = 0; al < (NC >> 1); ++al) {
+                const int alpha = al | (ahi << (D - 1));
+                int ca[DMAX];
+                morton_decode<D>((Apg << D) + alpha, l + 1, ca);
+                const C *wi = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR;
+                if constexpr (D == 2) {
+                    const int a0 = alpha & 1;
+#pragma unroll
+                    for (int s0 = 0; s0 < Q; ++s0) {
+                        const int sk[DMAX] = {s0, sq, 0};
+                        const C e = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l + 1, ca, sk), sc);
+                        const C u = cjmul(e, wi[s0 + Q * sq]);
+#pragma unroll
+                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[a0][t0][s0], u);
+                    }
+                } else {
+                    const int a0 = alpha & 1, a1 = (alpha >> 1) & 1;
+#pragma unroll 1
+                    for (int s1 = 0; s1 < Q; ++s1) {
+                        C tmp[Q];
+#pragma unroll
+                        for (int t0 = 0; t0 < Q; ++t0) tmp[t0] = czero<C>();
+#pragma unroll
+                        for (int s0 = 0; s0 < Q; ++s0) {
+                            const int sk[DMAX] = {s0, s1, sq};
+                            const C e = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l + 1, ca, sk), sc);
+                            const C u = cjmul(e, wi[s0 + Q * s1 + Q * Q * sq]);
+#pragma unroll
+                            for (int t0 = 0; t0 < Q; ++t0) cfma(tmp[t0], a.M[a0][t0][s0], u);
+                        }
+#pragma unroll
+                        for (int t1 = 0; t1 < Q; ++t1)
+#pragma unroll
+                            for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0 + Q * t1], a.M[a1][t1][s1], tmp[t0]);
+                    }
+                }
+            }
+            C *so = S + ((((tau * nblk + beta) * NC + c) * 2 + ahi) * Q + sq) * QD1;
+#pragma unroll
+            for (int j = 0; j < QD1; ++j) so[j] = acc[j];
+        }
+        __syncthreads();
+        // stage B: items (tau, block, c, t_{<D-1}): contract dim D-1 and alpha_{D-1},
+        // re-modulate at the nodes of the parent target box
+        for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
+            const int tl = it % QD1;
+            const int c = (it / QD1) % NC;
+            const int beta = (it / (QD1 * NC)) % nblk;
+            const int tau = it / (QD1 * NC * nblk);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            int ca[DMAX], cbq[DMAX], cb[DMAX];
+            morton_decode<D>(Apg, l, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+#pragma unroll
+            for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+            const int ctr[DMAX] = {Q, Q, Q};
+            const typename PH::S sc = spoint<P, D, Q, K>(a, l, cb, ctr);
+            C acc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
+#pragma unroll
+            for (int ahi = 0; ahi < 2; ++ahi) {
+                const C *si = S + ((((tau * nblk + beta) * NC + c) * 2 + ahi) * Q) * QD1 + tl;
+#pragma unroll
+                for (int sq = 0; sq < Q; ++sq) {
+                    const C v = si[sq * QD1];
+#pragma unroll
+                    for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], a.M[ahi][tq][sq], v);
+                }
+            }
+            int tk[DMAX];
+            {
+                int tt = tl;
+#pragma unroll
+                for (int j = 0; j < D - 1; ++j) { tk[j] = tt % Q; tt /= Q; }
+            }
+            C *wo = Wt + tau * n * RR + (base + (c << (D * i))) * RR + tl;
+#pragma unroll
+            for (int tq = 0; tq < Q; ++tq) {
+                tk[D - 1] = tq;
+                wo[tq * QD1] = cmul(expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l, ca, tk), sc), acc[tq]);
+            }
+        }
+        __syncthreads();
+    }
+
+    // ---- adjoint of the switch at level l: u(t) = sum_s e^{-2pi i Phi(x_s^A, y_t^B)} v(s);
+    // items (tau, slot, t_{>=1}), the q values of t_0 accumulated together
+    static __device__ void switch_adj(const KArgs<P> &a, C *Wt, C *S, int l)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int L = a.L;
+        for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
+            const int th = it % QD1;
+            const int sl = (it / QD1) % n;
+            const int tau = it / (QD1 * n);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
+            int ca[DMAX], cb[DMAX], tk[DMAX];
+            morton_decode<D>(A, l, ca);
+            morton_decode<D>(Bstar, L - l, cb);
+            {
+                int tt = th;
+#pragma unroll
+                for (int j = 1; j < D; ++j) { tk[j] = tt % Q; tt /= Q; }
+            }
+            typename P::SE eh[DMAX], e0[Q];
+#pragma unroll
+            for (int j = 1; j < D; ++j) eh[j] = sget<P, Q>(a, j, l, cb[j], tk[j]);
+#pragma unroll
+            for (int t0 = 0; t0 < Q; ++t0) e0[t0] = sget<P, Q>(a, 0, l, cb[0], t0);
+            C acc[Q];
+#pragma unroll
+            for (int t0 = 0; t0 < Q; ++t0) acc[t0] = czero<C>();
+            const C *v = Wt + (tau * n + sl) * RR;
+#pragma unroll 1
+            for (int s = 0; s < RR; ++s) {
+                int sk[DMAX], ss = s;
+#pragma unroll
+                for (int j = 0; j < D; ++j) { sk[j] = ss % Q; ss /= Q; }
+                const typename PH::T tS = tpoint<P, D, Q, K>(a, l, ca, sk);
+                typename PH::Part hp = PH::part(tS, eh[1], 1);
+                if constexpr (D == 3) hp = PH::add(hp, PH::part(tS, eh[2], 2));
+                const C vs = v[s];
+#pragma unroll
+                for (int t0 = 0; t0 < Q; ++t0)
+                    acc[t0] = cadd(acc[t0], cjmul(expphase_part<P, D, K>(a, tS, PH::add(PH::part(tS, e0[t0], 0), hp)), vs));
+            }
+            C *w = S + (tau * n + sl) * RR + th * Q;
+#pragma unroll
+            for (int t0 = 0; t0 < Q; ++t0) w[t0] = acc[t0];
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) Wt[j] = S[j];
+        __syncthreads();
+    }
+
+    // ---- adjoint of init: g(y) = e^{-2pi i Phi(x0(X), y)} sum_t L_t^B(y) e^{2pi i Phi(x0(X), y_t^B)} w_{XB}(t);
+    // slots in natural order (slot = b) at level 0; items (tau, b)
+    static __device__ void init_adj(const KArgs<P> &a, const C *Wt, int rhs)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int L = a.L;
+        const int cX[DMAX] = {0, 0, 0};
+        const int ctr[DMAX] = {Q, Q, Q};
+        const typename PH::T tX = tpoint<P, D, Q, K>(a, 0, cX, ctr);
+        for (int it = threadIdx.x; it < a.T * n; it += blockDim.x) {
+            const int b = it % n, tau = it / n;
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            int cb[DMAX];
+            morton_decode<D>((Bstar << (D * k)) + b, L, cb);
+            const C *w = Wt + it * RR;
+            C acc = czero<C>();
+            for (int t = 0; t < RR; ++t) {
+                R lag = R(1);
+                int tk[DMAX], tt = t;
+#pragma unroll
+                for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.lsrc[tk[j]]; }
+                if (lag == R(0)) continue;
+                cfma(acc, lag, cmul(expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, tk)), w[t]));
+            }
+            const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
+            const C e = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, pslot));
+            int64_t flat = 0;
+#pragma unroll
+            for (int j = 0; j < D; ++j) flat = (flat << L) + cb[j];
+            a.gadj[(int64_t)rhs * a.npts + flat] = cjmul(e, acc);
+        }
+    }
+
+    // ---- adjoint of final: w_{AY}(t) = e^{2pi i Phi(x_t^A, y0(Y))} L_t^A(x) e^{-2pi i Phi(x, y0(Y))} f(x);
+    // slots in digit-reversed order at level L; items (tau, slot, t)
+    static __device__ void final_adj(const KArgs<P> &a, C *Wt, int rhs)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int L = a.L;
+        const int cY[DMAX] = {0, 0, 0};
+        const int ctr[DMAX] = {Q, Q, Q};
+        const typename PH::S sY = spoint<P, D, Q, K>(a, L, cY, ctr);
+        for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) {
+            const int t = it % RR, sl = (it / RR) % n, tau = it / (RR * n);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
+            int ca[DMAX];
+            morton_decode<D>(A, L, ca);
+            R lag = R(1);
+            int tk[DMAX], tt = t;
+#pragma unroll
+            for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.ltgt[tk[j]]; }
+            C out = czero<C>();
+            if (lag != R(0)) {
+                int64_t flat = 0;
+#pragma unroll
+                for (int j = 0; j < D; ++j) flat = (flat << L) + ca[j];
+                const C fv = a.fadj[(int64_t)rhs * a.npts + flat];
+                const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
+                const C ex = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, pslot), sY);
+                const C et = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, tk), sY);
+                const C v = cmul(et, cjmul(ex, fv));
+                out.x = lag * v.x;
+                out.y = lag * v.y;
+            }
+            Wt[it] = out;
+        }
+    }
+
+    // ---- adjoint pass input: the forward pass's outputs (strided pairs) into digit-reversed slots
+    static __device__ __forceinline__ void load_strided(const KArgs<P> &a, C *Wt, int rhs)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int64_t Sstar = 1LL << (D * (a.L - a.l0 - k));
+        const C *src = a.win + (int64_t)rhs * a.wstride;
+        for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) {
+            const int t = j % RR, sl = (j / RR) % n, tau = j / (RR * n);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            const int64_t pair = ((int64_t)(((int64_t)Ap << (D * k)) + digit_rev<D>(sl, k))) * Sstar + Bstar;
+            Wt[j] = src[pair * RR + t];
+        }
+    }
+
+    // ---- adjoint pass output: natural order, contiguous
+    static __device__ __forceinline__ void store_contig(const KArgs<P> &a, const C *Wt, int rhs)
+    {
+        const int cnt = a.T * (1 << (D * a.k)) * RR;
+        C *dst = a.wout + (int64_t)rhs * a.wstride + (int64_t)blockIdx.x * cnt;
+        for (int j = threadIdx.x; j < cnt; j += blockDim.x) dst[j] = Wt[j];
+    }
+
     // ---- CTA input: T * 2^{dk} consecutive pairs (contiguous in HBM)
     static __device__ __forceinline__ void load(const KArgs<P> &a, C *Wt, int rhs)
     {
@@ -1021,6 +1419,46 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pa
         TL::final_eval(a, Wt, rhs);
     else
         TL::store(a, Wt, rhs);
+}
+
+// adjoint of a column pass: optional switch^H at level l0 + k, k column levels in
+// reverse, optional init^H (writes the source values)
+template <int D, int Q, class P, int K>
+__global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pass_adj(const KArgs<P> a)
+{
+    using C = typename P::C;
+    using TL = Tile<D, Q, P, K>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *Wt = reinterpret_cast<C *>(smem_raw);
+    C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
+    const int rhs = blockIdx.y;
+    TL::load_strided(a, Wt, rhs);
+    __syncthreads();
+    if (a.flags & F_SWITCH) TL::switch_adj(a, Wt, S, a.l0 + a.k);
+    for (int i = a.k - 1; i >= 0; --i) TL::col_level_adj(a, Wt, S, a.l0 + i, i);
+    if (a.flags & F_INIT)
+        TL::init_adj(a, Wt, rhs);
+    else
+        TL::store_contig(a, Wt, rhs);
+}
+
+// adjoint of a row pass: optional final^H (reads the target values), k row levels in reverse
+template <int D, int Q, class P, int K>
+__global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pass_adj(const KArgs<P> a)
+{
+    using C = typename P::C;
+    using TL = Tile<D, Q, P, K>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *Wt = reinterpret_cast<C *>(smem_raw);
+    C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
+    const int rhs = blockIdx.y;
+    if (a.flags & F_FINAL)
+        TL::final_adj(a, Wt, rhs);
+    else
+        TL::load_strided(a, Wt, rhs);
+    __syncthreads();
+    for (int i = a.k - 1; i >= 0; --i) TL::row_level_adj(a, Wt, S, a.l0 + i, i);
+    TL::store_contig(a, Wt, rhs);
 }
 
 }  // namespace bfk

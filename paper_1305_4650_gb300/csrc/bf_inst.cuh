@@ -48,10 +48,31 @@ cudaError_t launch_row(const void *kargs, unsigned gx, unsigned gy, size_t smem,
 }
 
 template <int D, int Q, class P, int K>
+cudaError_t launch_col_adj(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_col_pass_adj<D, Q, P, K>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_col_pass_adj<D, Q, P, K><<<dim3(gx, gy), bfk::Cfg<D, Q, P>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    return cudaGetLastError();
+}
+
+template <int D, int Q, class P, int K>
+cudaError_t launch_row_adj(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_row_pass_adj<D, Q, P, K>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_row_pass_adj<D, Q, P, K><<<dim3(gx, gy), bfk::Cfg<D, Q, P>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    return cudaGetLastError();
+}
+
+template <int D, int Q, class P, int K>
 const PassFns *fns_for()
 {
     using CF = bfk::Cfg<D, Q, P>;
-    static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, nullptr, nullptr, CF::KMAX, CF::NP, CF::NT};
+    static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
+                              launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT};
     return &f;
 }
 

@@ -11,7 +11,7 @@ typedef cudaError_t (*pass_fn)(const void *kargs, unsigned grid_x, unsigned grid
 
 struct PassFns {
     pass_fn col, row;            // forward: init/column/switch pass, row/final pass
-    pass_fn col_adj, row_adj;    // adjoint passes (null until compiled)
+    pass_fn col_adj, row_adj;    // adjoint passes: transposes of col and row, levels reversed
     int kmax;                    // most levels one pass fuses
     int np;                      // pairs per CTA (2^{d kmax})
     int nthreads;                // threads per CTA
