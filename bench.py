@@ -112,20 +112,22 @@ class Clocks:
 
 # ------------------------------------------------------- algorithmic work
 
-def phase_ops(phase: str, d: int, precision: str) -> int:
-    """FP32-pipe operations of one e^{2 pi i Phi} in the mixed path: the double-float
-    evaluation and mod-1 reduction of Phi (operation count of the formula) plus 20 for
-    the FP32 sincos of the reduced argument (range reduction and two short polynomials)."""
-    df_mul_frac, df_mul, df_add, df_sqrt, df_frac = 7, 7, 11, 10, 5
+def phase_ops(phase: str, d: int, q: int) -> float:
+    """FP32-pipe operations of one e^{2 pi i Phi} in the mixed path, counted from the
+    double-float formulas with the per-dimension split of Phi: the part of source
+    coordinate 0 (evaluated per phase), the parts of coordinates >= 1 (shared by the q
+    phases of a node row), the two-sum that adds parts, the final sqrt / mod-1 step,
+    and 22 for the quadrant-reduced sincos (setup 5, sin 5, cos 5, quadrant 7)."""
+    sincos, add = 22, 9
     if phase == "dot":
-        core = d * df_mul_frac + d + 2
+        part, fin = 8, 0
     elif phase == "genradon":
-        core = d * df_mul_frac + d * df_mul + (d - 1) * df_add + df_sqrt + df_frac + 4
+        part, fin = 12, 12
     elif phase == "hypradon":
-        core = df_mul + df_add + df_sqrt + df_mul_frac + 2
+        part, fin = 4, 15
     else:
-        core = 2 * d * df_add + df_frac
-    return core + 20
+        part, fin = 11, 4
+    return part + (d - 1) * part / q + add + fin + sincos
 
 
 def pass_work(spec, ps, nrhs=1):
@@ -156,7 +158,7 @@ def pass_work(spec, ps, nrhs=1):
 
 
 def work_ops(spec, w):
-    return w["phases"] * phase_ops(spec.phase, spec.d, spec.precision) + 2 * w["macs"] + 4 * w["cmuls"] + 4 * w["cmacs"]
+    return w["phases"] * phase_ops(spec.phase, spec.d, spec.q) + 2 * w["macs"] + 4 * w["cmuls"] + 4 * w["cmacs"]
 
 
 # ---------------------------------------------------------------- our arm
