@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="genradon2d", choices=["genradon2d", "genradon3d", "dft64"])
+    ap.add_argument("--workload", default="genradon2d", choices=["genradon2d", "genradon3d", "dft64", "hypradon48"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -239,6 +239,8 @@ def run_ours(args, rank, world, local_rank):
                 "pass_ms": [round(t, 4) for t in tpass]}
     all_ops = sum(work_ops(spec, pass_work(spec, p, nrhs)) for p in passes)
     roofline["apply_frac"] = round(all_ops / (ms * 1e-3) / 1e12 / peak, 4)
+    roofline["measured_fma_tflops"] = {"fp32": round(bf.measure_fma_rate(False), 1),
+                                       "fp64": round(bf.measure_fma_rate(True), 3)}
 
     # ---- FP64 GPU butterfly on the same problem (the baseline of the speedup)
     fp64 = None
@@ -323,6 +325,86 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+def run_batched(args, rank, world, local_rank):
+    """48 hyperbolic Radon problems (16 each of N = 128, 256, 512; 1..16 RHS each, drawn from the
+    seed) applied by one bf_apply_batched call, captured once in a CUDA graph and replayed.
+    Under torchrun the problems are dealt round-robin to the ranks (independent problems,
+    no exchange); value = all ranks' points*RHS / max time."""
+    import numpy as np
+    import torch
+    from paper_1305_4650_gb300 import bf, workloads as wl
+    if world > 1:
+        import torch.distributed as dist
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    probs, rng = wl.hypradon_batch()
+    mine = [(i, s, k) for i, (s, k) in enumerate(probs) if i % world == rank]
+    plans, gs, fs, nr = [], [], [], []
+    for i, spec, k in mine:
+        p = bf.Plan.from_spec(spec, max_nrhs=k, precision="mixed")
+        g = torch.from_numpy(wl.source_values(spec, k, np.complex64, seed=spec.seed + i)).to(dev)
+        plans.append(p)
+        gs.append(g)
+        fs.append(torch.empty_like(g))
+        nr.append(k)
+    pts_rhs_local = sum(s.npts * k for _, s, k in mine)
+    pts_rhs = sum(s.npts * k for s, k in probs)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(2):                               # kernel attributes set before capture
+            bf.apply_batched(plans, gs, fs, nr, stream=side)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bf.apply_batched(plans, gs, fs, nr)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    launches = sum(p.info()["launches"] for p in plans)
+    acc = None
+    if rank == 0 and not args.no_accuracy:
+        # problem 0 (N = 128) against the oracle butterfly, all outputs, every RHS
+        import oracle
+        i0, s0, k0 = mine[0]
+        P = oracle.Problem(**s0.oracle_kwargs())
+        ref = oracle.butterfly(P, gs[0].cpu().numpy().astype(np.complex128))
+        out = fs[0].cpu().numpy()
+        acc = {"rel_l2_vs_oracle_butterfly": float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
+               "sample": f"problem {i0} (N={s0.N}, {k0} RHS), all outputs"}
+    for p in plans:
+        p.close()
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": pts_rhs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "hypradon48_q5", "problems": len(probs), "N": [128, 256, 512],
+                       "nrhs_total": int(sum(nr)) if world == 1 else None, "points_rhs": pts_rhs,
+                       "points_rhs_rank0": pts_rhs_local, "precision": "mixed", "graph": "one CUDA graph per step",
+                       "parallelism": f"problems round-robin over {world} rank(s)"},
+            "accuracy": acc, "gpu_launches": args.steps * launches, "clocks": clk.summary()}
+
+
 def plan_fuse(passes):
     return max(p["k"] for p in passes)
 
@@ -388,7 +470,7 @@ def main():
             import torch.distributed as dist
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl")
-        line = run_ours(args, rank, world, local_rank)
+        line = (run_batched if args.workload == "hypradon48" else run_ours)(args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

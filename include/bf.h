@@ -154,6 +154,10 @@ bf_status bf_pass_info(bf_plan plan, int i, int *kind, int *l0, int *k, int *fla
  *     over n pseudo-random (target node, source node) pairs of a BF_PREC_MIXED plan
  *     (BF_ERR_INVALID_ARG for an FP64 plan). */
 bf_status bf_selfcheck_sincos(int n, double *max_abs_err);
+/* Measured FMA rate of the current device in TFLOP/s (an FMA counts 2): fp64 = 0 for
+ * FP32, 1 for FP64.  Independent dependent-FMA chains on every SM, timed with events;
+ * the context for the FP32-issue roofline and for evaluating phases in double-float. */
+bf_status bf_measure_fma_rate(int fp64, double *tflops);
 bf_status bf_selfcheck_phase(bf_plan plan, int n, double *max_err_cycles);
 
 /* Forward apply that allocates no device memory.  The paper has no counterpart:

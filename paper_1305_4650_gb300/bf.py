@@ -22,7 +22,7 @@ STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_E
 
 EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_apply_host",
            "bf_apply_batched", "bf_destroy", "bf_status_string", "bf_last_cuda_error", "bf_plan_info",
-           "bf_apply_pass", "bf_pass_info", "bf_selfcheck_sincos", "bf_selfcheck_phase"]
+           "bf_apply_pass", "bf_pass_info", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate"]
 
 
 class BfError(RuntimeError):
@@ -70,6 +70,7 @@ def load():
                                      ctypes.POINTER(i32)]
         lib.bf_selfcheck_sincos.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_selfcheck_phase.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+        lib.bf_measure_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         for name in EXPORTS:
             getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
         lib.bf_status_string.restype = ctypes.c_char_p
@@ -238,6 +239,13 @@ def selfcheck_sincos(n: int = 1 << 22) -> float:
     """Largest |error| of the mixed path's FP32 sin/cos of 2 pi f against FP64 sincospi."""
     e = ctypes.c_double()
     _check(load().bf_selfcheck_sincos(n, ctypes.byref(e)), "bf_selfcheck_sincos")
+    return e.value
+
+
+def measure_fma_rate(fp64: bool = False) -> float:
+    """Measured FP32 (or FP64) FMA rate of the current device, TFLOP/s."""
+    e = ctypes.c_double()
+    _check(load().bf_measure_fma_rate(1 if fp64 else 0, ctypes.byref(e)), "bf_measure_fma_rate")
     return e.value
 
 

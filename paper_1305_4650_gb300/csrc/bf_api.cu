@@ -527,6 +527,12 @@ bf_status bf_selfcheck_sincos(int n, double *max_abs_err)
     return e == cudaSuccess ? BF_OK : BF_ERR_CUDA;
 }
 
+bf_status bf_measure_fma_rate(int fp64, double *tflops)
+{
+    if (!tflops || (fp64 != 0 && fp64 != 1)) return BF_ERR_INVALID_ARG;
+    return bfl::measure_fma(fp64, tflops) == cudaSuccess ? BF_OK : BF_ERR_CUDA;
+}
+
 bf_status bf_selfcheck_phase(bf_plan p, int n, double *max_err_cycles)
 {
     if (!p || n < 1 || !max_err_cycles || p->prec != BF_PREC_MIXED) return BF_ERR_INVALID_ARG;

@@ -30,7 +30,8 @@ BFL_DECLARE(3, mix, dot) BFL_DECLARE(3, mix, genradon) BFL_DECLARE(3, mix, separ
 #undef BFL_DECLARE
 
 
-// device self-checks (bf_selfcheck.cu)
+// device self-checks and the FMA rate probe (bf_selfcheck.cu)
+cudaError_t measure_fma(int fp64, double *tflops);
 cudaError_t selfcheck_sincos(int n, double *max_err);
 cudaError_t selfcheck_phase(const void *kargs_mix, const void *kargs_f64, int d, int L, int q, int kind, int n,
                             double *max_err);

@@ -72,9 +72,68 @@ __global__ void k_check_phase(bfk::KArgs<bfk::PMIX> am, bfk::KArgs<bfk::PF64> ad
     }
 }
 
+// dependent FMA chains, 8 (FP32) or 4 (FP64) independent per thread
+__global__ void k_fma32(int iters, float *out)
+{
+    float a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3, a4 = a0 + 4, a5 = a0 + 5, a6 = a0 + 6, a7 = a0 + 7;
+    const float b = 0.999f, c = 0.001f;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            a0 = fmaf(a0, b, c); a1 = fmaf(a1, b, c); a2 = fmaf(a2, b, c); a3 = fmaf(a3, b, c);
+            a4 = fmaf(a4, b, c); a5 = fmaf(a5, b, c); a6 = fmaf(a6, b, c); a7 = fmaf(a7, b, c);
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+}
+
+__global__ void k_fma64(int iters, double *out)
+{
+    double a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
+    const double b = 0.999, c = 0.001;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) { a0 = fma(a0, b, c); a1 = fma(a1, b, c); a2 = fma(a2, b, c); a3 = fma(a3, b, c); }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3;
+}
+
 }  // namespace
 
 namespace bfl {
+
+cudaError_t measure_fma(int fp64, double *tflops)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 32, threads = 256;
+    void *out = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * 8);
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int iters = fp64 ? 100 : 2000;
+    for (int rep = 0; rep < 2; ++rep) {
+        if (rep == 1) cudaEventRecord(e0);
+        if (fp64)
+            k_fma64<<<blocks, threads>>>(rep ? iters : 2, static_cast<double *>(out));
+        else
+            k_fma32<<<blocks, threads>>>(rep ? iters : 10, static_cast<float *>(out));
+    }
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double flops = 2.0 * blocks * threads * (double)iters * 16 * (fp64 ? 4 : 8);
+    *tflops = flops / (ms * 1e-3) / 1e12;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
 
 cudaError_t selfcheck_sincos(int n, double *max_err)
 {

@@ -1,0 +1,70 @@
+"""Many independent problems of uneven size in one call (bf_apply_batched), also
+captured in a CUDA graph; every result equals the single-problem apply and the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_4650_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_4650_gb300 import build, bf as bfmod
+    build.build()
+    return bfmod
+
+
+def _problems():
+    # uneven N and RHS counts, as in the 48-problem hyperbolic Radon batch but small
+    out = []
+    for i, (L, k) in enumerate([(5, 3), (6, 1), (4, 7), (7, 2), (5, 16), (6, 5)]):
+        out.append((wl.hypradon(L), k, 500 + i))
+    return out
+
+
+def test_batched_equals_single_and_oracle(bf):
+    import torch
+    probs = _problems()
+    plans = [bf.Plan.from_spec(s, max_nrhs=k, precision="mixed") for s, k, _ in probs]
+    gs = [torch.from_numpy(wl.source_values(s, k, np.complex64, seed=sd)).cuda() for s, k, sd in probs]
+    fs = [torch.empty_like(g) for g in gs]
+    bf.apply_batched(plans, gs, fs, [k for _, k, _ in probs])
+    torch.cuda.synchronize()
+    for (s, k, _), p, g, f in zip(probs, plans, gs, fs):
+        single = p.apply(g)
+        torch.cuda.synchronize()
+        assert torch.equal(single, f)
+        ref = oracle.butterfly(oracle.Problem(**s.oracle_kwargs()), g.cpu().numpy().astype(np.complex128))
+        out = f.cpu().numpy()
+        assert np.linalg.norm(out - ref) <= 1e-5 * np.linalg.norm(ref)
+    for p in plans:
+        p.close()
+
+
+def test_batched_in_a_cuda_graph(bf):
+    import torch
+    probs = _problems()
+    plans = [bf.Plan.from_spec(s, max_nrhs=k, precision="mixed") for s, k, _ in probs]
+    gs = [torch.from_numpy(wl.source_values(s, k, np.complex64, seed=sd)).cuda() for s, k, sd in probs]
+    fs = [torch.empty_like(g) for g in gs]
+    nr = [k for _, k, _ in probs]
+    bf.apply_batched(plans, gs, fs, nr)                 # first call outside the capture
+    torch.cuda.synchronize()
+    ref = [f.clone() for f in fs]
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        bf.apply_batched(plans, gs, fs, nr)
+    for f in fs:
+        f.zero_()
+    graph.replay()
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(fs, ref):
+        assert torch.equal(a, b)
+    for p in plans:
+        p.close()
