@@ -37,6 +37,7 @@ struct bf_plan_s {
     size_t csize = 8;          // bytes per complex number
     int64_t ws_bytes = 0;
     std::vector<Pass> passes;
+    std::vector<Pass> passes_rb;   // schedule of the multi-RHS kernels (empty if not compiled)
     const bfl::PassFns *fns = nullptr;
     int last_cuda = 0;
 };
@@ -183,39 +184,39 @@ size_t pass_smem(const bf_plan_s *p, const Pass &ps)
     return (size_t)3 * (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (size_t)p->r * p->csize;
 }
 
-// A CTA owns np pairs (np = 2^{d kmax} of the instantiation, fewer for tiny problems):
+// A CTA owns np pairs (2^{d kmax} of the instantiation, fewer for tiny problems):
 // T = np / 2^{dk} tiles of a k-level pass.
-Pass make_pass(const bf_plan_s *p, int row, int l0, int k, int flags)
+Pass make_pass(const bf_plan_s *p, int64_t np_cta, int row, int l0, int k, int flags)
 {
-    const int64_t np = p->npts < p->fns->np ? p->npts : p->fns->np;
+    const int64_t np = p->npts < np_cta ? p->npts : np_cta;
     Pass ps{row, l0, k, flags, (int)(np >> (p->d * k))};
     if (ps.T < 1) ps.T = 1;
     return ps;
 }
 
-void schedule(bf_plan p)
+// column passes of <= kmax levels (init first, switch last), then row passes (final last)
+std::vector<Pass> schedule(const bf_plan_s *p, int kmax, int64_t np_cta)
 {
-    p->passes.clear();
+    std::vector<Pass> out;
     const int m = p->m, L = p->L;
     if (m == 0) {
-        p->passes.push_back(make_pass(p, 0, 0, 0, bfk::F_INIT | bfk::F_SWITCH));
+        out.push_back(make_pass(p, np_cta, 0, 0, 0, bfk::F_INIT | bfk::F_SWITCH));
     } else {
-        int l = 0;
-        while (l < m) {
-            const int k = (m - l) < p->kc ? (m - l) : p->kc;
+        for (int l = 0; l < m;) {
+            const int k = (m - l) < kmax ? (m - l) : kmax;
             int fl = 0;
             if (l == 0) fl |= bfk::F_INIT;
             if (l + k == m) fl |= bfk::F_SWITCH;
-            p->passes.push_back(make_pass(p, 0, l, k, fl));
+            out.push_back(make_pass(p, np_cta, 0, l, k, fl));
             l += k;
         }
     }
-    int l = m;
-    while (l < L) {
-        const int k = (L - l) < p->kr ? (L - l) : p->kr;
-        p->passes.push_back(make_pass(p, 1, l, k, (l + k == L) ? bfk::F_FINAL : 0));
+    for (int l = m; l < L;) {
+        const int k = (L - l) < kmax ? (L - l) : kmax;
+        out.push_back(make_pass(p, np_cta, 1, l, k, (l + k == L) ? bfk::F_FINAL : 0));
         l += k;
     }
+    return out;
 }
 
 template <class P>
@@ -254,6 +255,35 @@ void fill_args(const bf_plan_s *p, bfk::KArgs<P> &a)
 // Run passes [first, last) of the forward schedule.  Pass i reads workspace
 // buffer i % 2 (or g when it initialises) and writes buffer (i + 1) % 2 (or f
 // when it evaluates the targets).
+// Multi-RHS forward: every CTA keeps rb_count right-hand sides of its tiles and
+// evaluates each phase once for all of them.
+template <class P>
+bf_status run_forward_rb(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s)
+{
+    bfk::KArgs<P> a;
+    fill_args<P>(p, a);
+    a.g = static_cast<const typename P::C *>(g);
+    a.f = static_cast<typename P::C *>(f);
+    a.nrhs = nrhs;
+    const int rb = p->fns->rb_count;
+    void *buf[2] = {p->w0, p->w1};
+    for (size_t i = 0; i < p->passes_rb.size(); ++i) {
+        const Pass &ps = p->passes_rb[i];
+        a.l0 = ps.l0;
+        a.k = ps.k;
+        a.flags = ps.flags;
+        a.T = ps.T;
+        a.win = static_cast<const typename P::C *>(buf[i & 1]);
+        a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
+        const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
+        const size_t smem = (size_t)rb * pass_smem(p, ps);
+        cudaError_t e = (ps.row ? p->fns->row_rb : p->fns->col_rb)(&a, (unsigned)ctas, (unsigned)((nrhs + rb - 1) / rb),
+                                                                   smem, s);
+        if (e != cudaSuccess) return cuda_fail(p, e);
+    }
+    return BF_OK;
+}
+
 template <class P>
 bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last)
 {
@@ -402,7 +432,11 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     const int kfit = p->fns->kmax;
     const int kreq = prm->fuse_levels > 0 ? prm->fuse_levels : kfit;
     p->kc = p->kr = kreq < kfit ? kreq : kfit;
-    schedule(p);
+    p->passes = schedule(p, p->kc, p->fns->np);
+    if (p->fns->col_rb) {
+        const int krb = kreq < p->fns->kmax_rb ? kreq : p->fns->kmax_rb;
+        p->passes_rb = schedule(p, krb, p->fns->np_rb);
+    }
 
     bf_status st = build_tables(p);
     if (st == BF_OK) {
@@ -430,6 +464,7 @@ bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int n = (int)p->passes.size();
     if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n);
+    if (nrhs >= 2 && !p->passes_rb.empty()) return run_forward_rb<bfk::PMIX>(p, g, f, nrhs, s);
     return run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
 }
 

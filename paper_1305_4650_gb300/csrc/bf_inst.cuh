@@ -67,13 +67,43 @@ cudaError_t launch_row_adj(const void *kargs, unsigned gx, unsigned gy, size_t s
     return cudaGetLastError();
 }
 
+template <int Q, class P, int K, int RB>
+cudaError_t launch_col_rb(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_col_pass_rb<Q, P, K, RB>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_col_pass_rb<Q, P, K, RB><<<dim3(gx, gy), bfk::CfgRB<Q, P, RB>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    return cudaGetLastError();
+}
+
+template <int Q, class P, int K, int RB>
+cudaError_t launch_row_rb(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_row_pass_rb<Q, P, K, RB>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_row_pass_rb<Q, P, K, RB><<<dim3(gx, gy), bfk::CfgRB<Q, P, RB>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    return cudaGetLastError();
+}
+
+constexpr int kRB = 4;   // right-hand sides per CTA in the multi-RHS kernels
+
 template <int D, int Q, class P, int K>
 const PassFns *fns_for()
 {
     using CF = bfk::Cfg<D, Q, P>;
-    static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
-                              launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT};
-    return &f;
+    if constexpr (D == 2 && !P::is_f64) {
+        using CR = bfk::CfgRB<Q, P, kRB>;
+        static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
+                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT,
+                                  launch_col_rb<Q, P, K, kRB>, launch_row_rb<Q, P, K, kRB>, CR::KMAX, CR::NP, kRB};
+        return &f;
+    } else {
+        static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
+                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, nullptr, nullptr, 0, 0, 1};
+        return &f;
+    }
 }
 
 }  // namespace bfl

@@ -15,6 +15,8 @@ struct PassFns {
     int kmax;                    // most levels one pass fuses
     int np;                      // pairs per CTA (2^{d kmax})
     int nthreads;                // threads per CTA
+    pass_fn col_rb, row_rb;      // forward passes sharing phases over rb_count RHS (null if absent)
+    int kmax_rb, np_rb, rb_count;
 };
 
 // (d, q, precision, phase kind) -> kernels, or null if that combination is not compiled.
