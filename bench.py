@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="genradon2d", choices=["genradon2d", "genradon3d", "dft64", "hypradon48"])
+    ap.add_argument("--workload", default="genradon2d", choices=["genradon2d", "genradon3d", "dft64", "hypradon48", "cg1024"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -405,6 +405,47 @@ def run_batched(args, rank, world, local_rank):
             "accuracy": acc, "gpu_launches": args.steps * launches, "clocks": clk.summary()}
 
 
+def run_cg(args, rank, world, local_rank):
+    """20 CGLS iterations on B^H B m = B^H d, d = B m_true (1% spikes), generalized Radon
+    N = 1024, q = 5, mixed: each iteration is one forward and one adjoint apply plus vector
+    updates.  value = applies * N^d / time; the residual history is reported."""
+    import numpy as np
+    import torch
+    from paper_1305_4650_gb300 import bf, workloads as wl
+    from paper_1305_4650_gb300.autograd import cgls
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    spec = wl.genradon2d()
+    plan = bf.Plan.from_spec(spec, precision="mixed")
+    mt = torch.from_numpy(wl.sparse_spikes(spec, 0.01)).to(dev)
+    d = plan.apply(mt)
+    iters = 20
+    for _ in range(max(1, args.warmup // 3)):
+        cgls(plan, d, 2)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        m, hist = cgls(plan, d, iters)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    applies = 2 * iters + 1
+    plan.close()
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": applies * spec.npts * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+            "steps": 1, "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": "cg20_genradon2d_N1024_q5", "iterations": iters, "applies": applies,
+                       "m_true": "1% spikes, N(0,1) amplitudes", "precision": "mixed"},
+            "residual_history": [round(h / hist[0], 6) for h in hist],
+            "gpu_launches": applies * len(bf.Plan.from_spec(spec, precision="mixed").passes()),
+            "clocks": clk.summary()}
+
+
 def plan_fuse(passes):
     return max(p["k"] for p in passes)
 
@@ -470,7 +511,8 @@ def main():
             import torch.distributed as dist
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl")
-        line = (run_batched if args.workload == "hypradon48" else run_ours)(args, rank, world, local_rank)
+        runner = {"hypradon48": run_batched, "cg1024": run_cg}.get(args.workload, run_ours)
+        line = runner(args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()
