@@ -33,6 +33,8 @@ struct bf_plan_s {
     double lsrc[bfk::QMAX] = {}, ltgt[bfk::QMAX] = {};
     void *tt[3] = {}, *st[3] = {};
     void *w0 = nullptr, *w1 = nullptr;
+    void *ctab = nullptr;      // target features at box centres, levels 0..ctab_levels
+    int ctab_levels = -1;
     void *gstage = nullptr, *fstage = nullptr;
     size_t csize = 8;          // bytes per complex number
     int64_t ws_bytes = 0;
@@ -184,6 +186,13 @@ size_t pass_smem(const bf_plan_s *p, const Pass &ps)
     return (size_t)3 * (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (size_t)p->r * p->csize;
 }
 
+// plus, for a row pass, the cache of the parents' node features (T 2^{d(k-1)} boxes x r nodes)
+size_t row_cache_smem(const bf_plan_s *p, const Pass &ps)
+{
+    if (!ps.row || ps.k < 1) return 0;
+    return (size_t)ps.T * ((size_t)1 << (p->d * (ps.k - 1))) * (size_t)p->r * (size_t)p->fns->tsize;
+}
+
 // A CTA owns np pairs (2^{d kmax} of the instantiation, fewer for tiny problems):
 // T = np / 2^{dk} tiles of a k-level pass.
 Pass make_pass(const bf_plan_s *p, int64_t np_cta, int row, int l0, int k, int flags)
@@ -246,6 +255,8 @@ void fill_args(const bf_plan_s *p, bfk::KArgs<P> &a)
         a.sc.s3lo = lo;
         a.sc.sgn = (float)sgn;
     }
+    a.ctab = p->ctab;
+    a.ctab_levels = p->ctab_levels;
     a.L = p->L;
     a.kind = p->kind;
     a.npts = p->npts;
@@ -301,7 +312,7 @@ bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t 
         a.win = static_cast<const typename P::C *>(buf[i & 1]);
         a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
         const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
-        const size_t smem = pass_smem(p, ps);
+        const size_t smem = pass_smem(p, ps) + row_cache_smem(p, ps);
         cudaError_t e = (ps.row ? p->fns->row : p->fns->col)(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
         if (e != cudaSuccess) return cuda_fail(p, e);
     }
@@ -440,6 +451,29 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
 
     bf_status st = build_tables(p);
     if (st == BF_OK) {
+        // target features at box centres for the column levels (<= 2^18 records)
+        int lv = p->m;
+        while (lv > 0 && (((1LL << (d * (lv + 1))) - 1) / ((1LL << d) - 1)) > (1LL << 18)) --lv;
+        const size_t bytes = (size_t)((((1LL << (d * (lv + 1))) - 1) / ((1LL << d) - 1))) * p->fns->tsize;
+        cudaError_t e = cudaMalloc(&p->ctab, bytes);
+        if (e == cudaSuccess) {
+            if (p->prec == BF_PREC_FP64) {
+                bfk::KArgs<bfk::PF64> a;
+                fill_args<bfk::PF64>(p, a);
+                e = p->fns->center_table(&a, p->ctab, lv);
+            } else {
+                bfk::KArgs<bfk::PMIX> a;
+                fill_args<bfk::PMIX>(p, a);
+                e = p->fns->center_table(&a, p->ctab, lv);
+            }
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        }
+        if (e != cudaSuccess)
+            st = cuda_fail(p, e);
+        else
+            p->ctab_levels = lv;
+    }
+    if (st == BF_OK) {
         const size_t wbytes = (size_t)p->max_nrhs * (size_t)p->npts * (size_t)p->r * p->csize;
         cudaError_t e = cudaMalloc(&p->w0, wbytes);
         if (e == cudaSuccess) e = cudaMalloc(&p->w1, wbytes);
@@ -549,6 +583,7 @@ bf_status bf_destroy(bf_plan p)
     }
     if (p->w0) cudaFree(p->w0);
     if (p->w1) cudaFree(p->w1);
+    if (p->ctab) cudaFree(p->ctab);
     if (p->gstage) cudaFree(p->gstage);
     if (p->fstage) cudaFree(p->fstage);
     delete p;

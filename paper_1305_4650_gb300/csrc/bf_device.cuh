@@ -197,6 +197,8 @@ struct KArgs {
     int L, l0, k, flags, kind;
     int T;                            // tiles per CTA (T * 2^{dk} pairs)
     int nrhs;                         // right-hand sides of the launch (multi-RHS kernels)
+    const void *ctab;                 // target features at box centres, levels 0..ctab_levels (or null)
+    int ctab_levels;
 };
 
 // --------------------------------------------------------- index helpers
@@ -516,6 +518,36 @@ __device__ __forceinline__ typename Ph<P, D, K>::S spoint(const KArgs<P> &a, int
     return s;
 }
 
+// Target features at the centre of box A (Morton) at level l: from the plan's centre
+// table when it covers the level (filled by k_center_table with this same code), else
+// built from the per-dimension tables.
+template <class P, int D, int Q, int K>
+__device__ __forceinline__ typename Ph<P, D, K>::T tcenter(const KArgs<P> &a, int l, uint32_t A, const int *ca)
+{
+    using T = typename Ph<P, D, K>::T;
+    if (l <= a.ctab_levels) {
+        const int off = (int)((((uint32_t)1 << (D * l)) - 1u) / ((1u << D) - 1u));
+        return static_cast<const T *>(a.ctab)[off + A];
+    }
+    const int ctr[DMAX] = {Q, Q, Q};
+    return tpoint<P, D, Q, K>(a, l, ca, ctr);
+}
+
+template <class P, int D, int Q, int K>
+__global__ void k_center_table(const KArgs<P> a, typename Ph<P, D, K>::T *out, int levels)
+{
+    const int total = (int)((((uint32_t)1 << (D * (levels + 1))) - 1u) / ((1u << D) - 1u));
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+        int l = 0;
+        while ((int)((((uint32_t)1 << (D * (l + 1))) - 1u) / ((1u << D) - 1u)) <= e) ++l;
+        const uint32_t A = (uint32_t)(e - (int)((((uint32_t)1 << (D * l)) - 1u) / ((1u << D) - 1u)));
+        int ca[DMAX];
+        morton_decode<D>(A, l, ca);
+        const int ctr[DMAX] = {Q, Q, Q};
+        out[e] = tpoint<P, D, Q, K>(a, l, ca, ctr);
+    }
+}
+
 // ------------------------------------------------------------ tile passes
 //
 // A CTA owns NP consecutive pairs of the pass's input level: T = NP / 2^{dk}
@@ -629,7 +661,7 @@ struct Tile {
             morton_decode<D>(Aa, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
             const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
+            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
             const C *Wtau = Wt + tau * n * RR;
             C acc[QD1];
 #pragma unroll
@@ -645,10 +677,11 @@ struct Tile {
                 PH::src1(sp, D - 1, sget<P, Q>(a, D - 1, l, cb[D - 1], tq));
                 if constexpr (D == 2) {
                     const int c0 = c & 1;
+                    const typename PH::Part p1 = PH::part(tA, sget<P, Q>(a, 1, l, cb[1], tq), 1);
 #pragma unroll
                     for (int t0p = 0; t0p < Q; ++t0p) {
-                        PH::src1(sp, 0, sget<P, Q>(a, 0, l, cb[0], t0p));
-                        const C u = cmul(expphase<P, D, K>(a, tA, sp), win[t0p + Q * tq]);
+                        const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], t0p), 0), p1);
+                        const C u = cmul(expphase_part<P, D, K>(a, tA, pt), win[t0p + Q * tq]);
 #pragma unroll
                         for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[c0][t0][t0p], u);
                     }
@@ -695,7 +728,7 @@ struct Tile {
             morton_decode<D>(Aa, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
             const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
+            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
             C acc[Q];
 #pragma unroll
             for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
@@ -709,20 +742,19 @@ struct Tile {
                     for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], a.M[chi][tq][tqp], v);
                 }
             }
-            typename PH::S sp;
             int tk[DMAX];
             {
                 int tt = tl;
 #pragma unroll
                 for (int j = 0; j < D - 1; ++j) { tk[j] = tt % Q; tt /= Q; }
             }
-#pragma unroll
-            for (int j = 0; j < D - 1; ++j) PH::src1(sp, j, sget<P, Q>(a, j, l + 1, cbq[j], tk[j]));
+            typename PH::Part pl = PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], tk[0]), 0);
+            if constexpr (D == 3) pl = PH::add(pl, PH::part(tA, sget<P, Q>(a, 1, l + 1, cbq[1], tk[1]), 1));
             C *wo = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR + tl;
 #pragma unroll
             for (int tq = 0; tq < Q; ++tq) {
-                PH::src1(sp, D - 1, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq));
-                wo[tq * QD1] = cjmul(expphase<P, D, K>(a, tA, sp), acc[tq]);
+                const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq), D - 1), pl);
+                wo[tq * QD1] = cjmul(expphase_part<P, D, K>(a, tA, pt), acc[tq]);
             }
         }
         __syncthreads();
@@ -790,11 +822,24 @@ struct Tile {
         __syncthreads();
     }
 
-    // ---- one row-form merge level (l -> l+1) on all tiles of the CTA
-    static __device__ void row_level(const KArgs<P> &a, C *Wt, C *S, int l, int i)
+    // ---- one row-form merge level (l -> l+1) on all tiles of the CTA.  TC caches the
+    // target features of the parents' nodes (T * 2^{Di} boxes x q^d nodes) for stage A.
+    static __device__ void row_level(const KArgs<P> &a, C *Wt, C *S, typename PH::T *TC, int l, int i)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D;
         const int L = a.L;
+        const int nbox = 1 << (D * i);
+        for (int j = threadIdx.x; j < a.T * nbox * RR; j += blockDim.x) {
+            const int t = j % RR, aloc = (j / RR) % nbox, tau = j / (RR * nbox);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            int ca[DMAX], tk[DMAX], tt = t;
+            morton_decode<D>((Ap << (D * i)) + aloc, l, ca);
+#pragma unroll
+            for (int jj = 0; jj < D; ++jj) { tk[jj] = tt % Q; tt /= Q; }
+            TC[j] = tpoint<P, D, Q, K>(a, l, ca, tk);
+        }
+        __syncthreads();
         // stage A: items (tau, block, c, t_{>=1}): pre-modulate input c at the nodes of the
         // parent target box and contract dim 0 for both children alpha_0
         //   -> S[tau][block][c][t_{>=1}][alpha_0][s_0]
@@ -807,27 +852,20 @@ struct Tile {
             int base;
             tile_of(a, tau, Ap, Bstar);
             block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            int ca[DMAX], cbq[DMAX], cb[DMAX];
-            morton_decode<D>(Apg, l, ca);
+            int cbq[DMAX], cb[DMAX];
             morton_decode<D>(Bq, L - l - 1, cbq);
 #pragma unroll
             for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
             const int ctr[DMAX] = {Q, Q, Q};
             const typename PH::S sc = spoint<P, D, Q, K>(a, l, cb, ctr);
-            int tk[DMAX];
-            {
-                int tt = th;
-#pragma unroll
-                for (int j = 1; j < D; ++j) { tk[j] = tt % Q; tt /= Q; }
-            }
+            const typename PH::T *tn = TC + (tau * nbox + (int)digit_rev<D>(beta & (nbox - 1), i)) * RR + th * Q;
             const C *win = Wt + tau * n * RR + (base + (c << (D * i))) * RR + th * Q;
             C z[2][Q];
 #pragma unroll
             for (int s0 = 0; s0 < Q; ++s0) { z[0][s0] = czero<C>(); z[1][s0] = czero<C>(); }
 #pragma unroll
             for (int t0 = 0; t0 < Q; ++t0) {
-                tk[0] = t0;
-                const C u = cjmul(expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l, ca, tk), sc), win[t0]);
+                const C u = cjmul(expphase<P, D, K>(a, tn[t0], sc), win[t0]);
 #pragma unroll
                 for (int s0 = 0; s0 < Q; ++s0) {
                     cfma(z[0][s0], a.M[0][t0][s0], u);
@@ -862,13 +900,14 @@ struct Tile {
             if constexpr (D == 2) {
                 const int a1 = (alpha >> 1) & 1;
                 C v[NC][Q];
-                typename PH::S sc[NC];
+                typename P::SE sc0[2], sc1[2];        // children's centres per dimension
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    sc0[h] = sget<P, Q>(a, 0, l, 2 * cbq[0] + h, Q);
+                    sc1[h] = sget<P, Q>(a, 1, l, 2 * cbq[1] + h, Q);
+                }
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    int cb[DMAX], ctr[DMAX] = {Q, Q, Q};
-#pragma unroll
-                    for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
-                    sc[c] = spoint<P, D, Q, K>(a, l, cb, ctr);
                     const C *si = Sblk + c * QD1 * 2 * Q + a0 * Q + s0;   // [t1] stride 2Q
 #pragma unroll
                     for (int s1 = 0; s1 < Q; ++s1) v[c][s1] = czero<C>();
@@ -883,8 +922,11 @@ struct Tile {
                 for (int s1 = 0; s1 < Q; ++s1) {
                     const int sk[DMAX] = {s0, s1, 0};
                     const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
+                    const typename PH::Part q0[2] = {PH::part(tS, sc0[0], 0), PH::part(tS, sc0[1], 0)};
+                    const typename PH::Part q1[2] = {PH::part(tS, sc1[0], 1), PH::part(tS, sc1[1], 1)};
 #pragma unroll
-                    for (int c = 0; c < NC; ++c) acc[s1] = cadd(acc[s1], cmul(expphase<P, D, K>(a, tS, sc[c]), v[c][s1]));
+                    for (int c = 0; c < NC; ++c)
+                        acc[s1] = cadd(acc[s1], cmul(expphase_part<P, D, K>(a, tS, PH::add(q0[c & 1], q1[c >> 1])), v[c][s1]));
                 }
             } else {
                 const int a1 = (alpha >> 1) & 1, a2 = (alpha >> 2) & 1;
@@ -987,7 +1029,7 @@ struct Tile {
             morton_decode<D>((Apg << D) + alpha, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
             const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
+            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, (Apg << D) + alpha, ca);
             int tk[DMAX];
             {
                 int tt = th;
@@ -1040,7 +1082,7 @@ struct Tile {
                 int ca[DMAX];
                 morton_decode<D>((Apg << D) + alpha, l + 1, ca);
                 const int ctr[DMAX] = {Q, Q, Q};
-                const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
+                const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, (Apg << D) + alpha, ca);
                 const typename PH::Part p0 = PH::part(tA, e0, 0);
                 const C *si = S + ((tau * nblk + beta) * NC + alpha) * QD1 * 2 * Q + c0 * Q + s0;   // [t_{>=1}] stride 2Q
                 if constexpr (D == 2) {
@@ -1413,9 +1455,10 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pa
     C *Wt = reinterpret_cast<C *>(smem_raw);
     C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
     const int rhs = blockIdx.y;
+    typename TL::PH::T *TC = reinterpret_cast<typename TL::PH::T *>(S + 2 * a.T * (1 << (D * a.k)) * TL::RR);
     TL::load(a, Wt, rhs);
     __syncthreads();
-    for (int i = 0; i < a.k; ++i) TL::row_level(a, Wt, S, a.l0 + i, i);
+    for (int i = 0; i < a.k; ++i) TL::row_level(a, Wt, S, TC, a.l0 + i, i);
     if (a.flags & F_FINAL)
         TL::final_eval(a, Wt, rhs);
     else
@@ -1552,7 +1595,7 @@ struct TileRB {
             morton_decode<D>((Apg << D) + alpha, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
             const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
+            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, (Apg << D) + alpha, ca);
             C ph[2][Q];
 #pragma unroll
             for (int cl = 0; cl < 2; ++cl) {
@@ -1601,7 +1644,7 @@ struct TileRB {
             morton_decode<D>((Apg << D) + alpha, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
             const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tpoint<P, D, Q, K>(a, l + 1, ca, ctr);
+            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, (Apg << D) + alpha, ca);
             C ph[Q];
             {
                 typename PH::S sp;

@@ -90,6 +90,16 @@ cudaError_t launch_row_rb(const void *kargs, unsigned gx, unsigned gy, size_t sm
 constexpr int kRB = 4;   // right-hand sides per CTA in the multi-RHS kernels
 
 template <int D, int Q, class P, int K>
+cudaError_t launch_ctab(const void *kargs, void *out, int levels)
+{
+    const int total = (int)((((uint32_t)1 << (D * (levels + 1))) - 1u) / ((1u << D) - 1u));
+    const int blocks = (total + 255) / 256;
+    bfk::k_center_table<P, D, Q, K><<<blocks < 4096 ? blocks : 4096, 256>>>(
+        *static_cast<const bfk::KArgs<P> *>(kargs), static_cast<typename bfk::Ph<P, D, K>::T *>(out), levels);
+    return cudaGetLastError();
+}
+
+template <int D, int Q, class P, int K>
 const PassFns *fns_for()
 {
     using CF = bfk::Cfg<D, Q, P>;
@@ -97,11 +107,13 @@ const PassFns *fns_for()
         using CR = bfk::CfgRB<Q, P, kRB>;
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT,
-                                  launch_col_rb<Q, P, K, kRB>, launch_row_rb<Q, P, K, kRB>, CR::KMAX, CR::NP, kRB};
+                                  launch_col_rb<Q, P, K, kRB>, launch_row_rb<Q, P, K, kRB>, CR::KMAX, CR::NP, kRB,
+                                  launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
         return &f;
     } else {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
-                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, nullptr, nullptr, 0, 0, 1};
+                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, nullptr, nullptr, 0, 0, 1,
+                                  launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
         return &f;
     }
 }

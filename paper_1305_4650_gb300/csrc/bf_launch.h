@@ -17,6 +17,8 @@ struct PassFns {
     int nthreads;                // threads per CTA
     pass_fn col_rb, row_rb;      // forward passes sharing phases over rb_count RHS (null if absent)
     int kmax_rb, np_rb, rb_count;
+    cudaError_t (*center_table)(const void *kargs, void *out, int levels);   // target features at box centres
+    int tsize;                   // bytes of one target-feature record
 };
 
 // (d, q, precision, phase kind) -> kernels, or null if that combination is not compiled.

@@ -171,6 +171,8 @@ bf_status run(int d, int L, int q, int kind, const bf_params *prm, const void *g
         a.sc.s3lo = (float)(sc / 3.0 - (double)a.sc.s3hi);
         a.sc.sgn = (float)sgn;
     }
+    a.ctab = nullptr;
+    a.ctab_levels = -1;
     a.L = L;
     a.kind = kind;
     a.npts = npts;
@@ -212,7 +214,9 @@ bf_status run(int d, int L, int q, int kind, const bf_params *prm, const void *g
         a.win = static_cast<const typename P::C *>(buf[i & 1]);
         a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
         const int64_t ctas = (npts >> (d * ps[i].k)) / ps[i].T;
-        const size_t smem = (size_t)3 * ps[i].T * ((size_t)1 << (d * ps[i].k)) * r * sizeof(typename P::C);
+        size_t smem = (size_t)3 * ps[i].T * ((size_t)1 << (d * ps[i].k)) * r * sizeof(typename P::C);
+        if (ps[i].row && ps[i].k >= 1)   // cache of the parents' node features in the row kernels
+            smem += (size_t)ps[i].T * ((size_t)1 << (d * (ps[i].k - 1))) * r * (size_t)fns->tsize;
         cudaError_t e = (ps[i].row ? fns->row : fns->col)(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
         if (e != cudaSuccess) return BF_ERR_CUDA;
     }
