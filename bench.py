@@ -262,6 +262,26 @@ def run_ours(args, rank, world, local_rank):
         out64 = f64.cpu().numpy()
         p64.close()
 
+    # ---- the same apply with the special-function-unit sincos (BF_PREC_MIXED_SFU)
+    sfu = None
+    if prec == "mixed":
+        psf = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="mixed_sfu")
+        fsf = torch.empty_like(g)
+        for _ in range(args.warmup):
+            psf.apply(g, fsf)
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(args.steps):
+            psf.apply(g, fsf)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        ms_sfu = max_over_ranks(b0.elapsed_time(b1) / args.steps)
+        sfu = {"value": spec.npts * nrhs * world / (ms_sfu * 1e-3), "ms_per_step": round(ms_sfu, 4),
+               "precision": "mixed_sfu (complex64, double-float phase, SFU sin/cos)"}
+        out_sfu = fsf.cpu().numpy()
+        psf.close()
+
     # ---- end to end through the C ABI with host buffers (H2D + apply + D2H per step)
     gh = torch.from_numpy(g_np).pin_memory()
     fh = torch.empty_like(gh).pin_memory()
@@ -301,6 +321,9 @@ def run_ours(args, rank, world, local_rank):
         if fp64 is not None:
             fp64["rel_l2_vs_oracle_butterfly"] = rel(out64[0][tg], ref)
             fp64["rel_l2_vs_direct_sum"] = rel(out64[0][samp], direct)
+        if sfu is not None:
+            sfu["rel_l2_vs_oracle_butterfly"] = rel(out_sfu[0][tg], ref)
+            sfu["rel_l2_vs_direct_sum"] = rel(out_sfu[0][samp], direct)
 
     # ---- CPU oracle baseline (rank 0 at N = 1): restricted butterfly on one level-1 target box,
     # which does 1/2^d of the apply's work and yields 1/2^d of the outputs
@@ -320,7 +343,7 @@ def run_ours(args, rank, world, local_rank):
                        "passes": len(passes), "fuse_levels": plan_fuse(passes),
                        "l2": "no flush: each step streams ~1.7 GB of weights through the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "fp64_gpu": fp64, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "fp64_gpu": fp64, "sfu_sincos": sfu, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * len(passes), "clocks": clocks}
     return line
 

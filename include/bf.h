@@ -67,11 +67,14 @@ typedef enum {
 } bf_phase_kind;
 
 /* Arithmetic of an apply.
- *   BF_PREC_FP64   complex128 weights, FP64 interpolation, FP64 phase, FP64 sincos.
- *   BF_PREC_MIXED  complex64 weights, FP32 interpolation and sincos; Phi is evaluated
- *                  and reduced mod 1 in double-float (pairs of FP32 numbers, >= 44
- *                  significant bits) before the FP32 sincos. */
-typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1 } bf_precision;
+ *   BF_PREC_FP64       complex128 weights, FP64 interpolation, FP64 phase, FP64 sincos.
+ *   BF_PREC_MIXED      complex64 weights, FP32 interpolation and sincos; Phi is evaluated
+ *                      and reduced mod 1 in double-float (pairs of FP32 numbers, >= 44
+ *                      significant bits) before an FP32 polynomial sincos (error ~1e-7).
+ *   BF_PREC_MIXED_SFU  as BF_PREC_MIXED but the sin/cos of the reduced phase come from the
+ *                      special-function unit (error ~3.4e-7): faster, a few times the
+ *                      FP32 weight rounding at the output. */
+typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1, BF_PREC_MIXED_SFU = 2 } bf_precision;
 
 typedef struct {
     double x_lo[3], x_w[3];   /* target domain: prod_k [x_lo[k], x_lo[k] + x_w[k]), x_w > 0  */

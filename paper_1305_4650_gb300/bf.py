@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbf_gb300.so")
 
 PHASE = {"dot": 0, "genradon": 1, "hypradon": 2, "separable": 3}
-PREC = {"fp64": 0, "mixed": 1}
+PREC = {"fp64": 0, "mixed": 1, "mixed_sfu": 2}
 STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_ERR_NOMEM",
           4: "BF_ERR_CUDA", 5: "BF_ERR_TIMEOUT", 6: "BF_ERR_INTERNAL"}
 

@@ -47,20 +47,22 @@ struct bf_plan_s {
 namespace bfl {
 const PassFns *get_fns(int d, int q, int prec, int kind)
 {
+#define BFL_PICK(dd, kn) (prec == 0 ? fns_d##dd##_f64_##kn(q) : prec == 1 ? fns_d##dd##_mix_##kn(q) : fns_d##dd##_sfu_##kn(q))
     if (d == 2) {
         switch (kind) {
-        case BF_PHASE_DOT: return prec == 0 ? fns_d2_f64_dot(q) : fns_d2_mix_dot(q);
-        case BF_PHASE_GENRADON: return prec == 0 ? fns_d2_f64_genradon(q) : fns_d2_mix_genradon(q);
-        case BF_PHASE_HYPRADON: return prec == 0 ? fns_d2_f64_hypradon(q) : fns_d2_mix_hypradon(q);
-        case BF_PHASE_SEPARABLE: return prec == 0 ? fns_d2_f64_separable(q) : fns_d2_mix_separable(q);
+        case BF_PHASE_DOT: return BFL_PICK(2, dot);
+        case BF_PHASE_GENRADON: return BFL_PICK(2, genradon);
+        case BF_PHASE_HYPRADON: return BFL_PICK(2, hypradon);
+        case BF_PHASE_SEPARABLE: return BFL_PICK(2, separable);
         }
     } else if (d == 3) {
         switch (kind) {
-        case BF_PHASE_DOT: return prec == 0 ? fns_d3_f64_dot(q) : fns_d3_mix_dot(q);
-        case BF_PHASE_GENRADON: return prec == 0 ? fns_d3_f64_genradon(q) : fns_d3_mix_genradon(q);
-        case BF_PHASE_SEPARABLE: return prec == 0 ? fns_d3_f64_separable(q) : fns_d3_mix_separable(q);
+        case BF_PHASE_DOT: return BFL_PICK(3, dot);
+        case BF_PHASE_GENRADON: return BFL_PICK(3, genradon);
+        case BF_PHASE_SEPARABLE: return BFL_PICK(3, separable);
         }
     }
+#undef BFL_PICK
     return nullptr;
 }
 }  // namespace bfl
@@ -395,7 +397,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     if (q < 2 || q > bfk::QMAX) return BF_ERR_INVALID_ARG;
     if ((int)phase < 0 || (int)phase > 3) return BF_ERR_INVALID_ARG;
     if (phase == BF_PHASE_HYPRADON && d != 2) return BF_ERR_INVALID_ARG;
-    if (prm->precision != BF_PREC_FP64 && prm->precision != BF_PREC_MIXED) return BF_ERR_INVALID_ARG;
+    if (prm->precision < BF_PREC_FP64 || prm->precision > BF_PREC_MIXED_SFU) return BF_ERR_INVALID_ARG;
     if (!supported_q(d, q)) return BF_ERR_UNSUPPORTED;
     for (int k = 0; k < d; ++k) {
         if (!(prm->x_w[k] > 0.0) || !(prm->y_w[k] > 0.0)) return BF_ERR_INVALID_ARG;
@@ -428,7 +430,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     p->max_nrhs = prm->max_nrhs;
     p->prm = *prm;
     p->csize = p->prec == BF_PREC_FP64 ? 16 : 8;
-    p->fns = bfl::get_fns(d, q, p->prec == BF_PREC_FP64 ? 0 : 1, (int)phase);
+    p->fns = bfl::get_fns(d, q, (int)p->prec, (int)phase);
 
     for (int j = 0; j < q; ++j)
         p->z[j] = p->node_kind == 0 ? 0.5 * std::cos(j * kPi / (q - 1)) : 0.5 * std::cos((2 * j + 1) * kPi / (2.0 * q));
@@ -498,6 +500,10 @@ bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int n = (int)p->passes.size();
     if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n);
+    if (p->prec == BF_PREC_MIXED_SFU) {
+        if (nrhs >= 2 && !p->passes_rb.empty()) return run_forward_rb<bfk::PMIXF>(p, g, f, nrhs, s);
+        return run_forward<bfk::PMIXF>(p, g, f, nrhs, s, 0, n);
+    }
     if (nrhs >= 2 && !p->passes_rb.empty()) return run_forward_rb<bfk::PMIX>(p, g, f, nrhs, s);
     return run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
 }
@@ -511,6 +517,7 @@ bf_status bf_apply_pass(bf_plan p, int i, const void *g, void *f, int nrhs, void
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, i, i + 1);
+    if (p->prec == BF_PREC_MIXED_SFU) return run_forward<bfk::PMIXF>(p, g, f, nrhs, s, i, i + 1);
     return run_forward<bfk::PMIX>(p, g, f, nrhs, s, i, i + 1);
 }
 
@@ -534,6 +541,7 @@ bf_status bf_apply_adjoint(bf_plan p, const void *f, void *g, int nrhs, void *st
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->prec == BF_PREC_FP64) return run_adjoint<bfk::PF64>(p, f, g, nrhs, s);
+    if (p->prec == BF_PREC_MIXED_SFU) return run_adjoint<bfk::PMIXF>(p, f, g, nrhs, s);
     return run_adjoint<bfk::PMIX>(p, f, g, nrhs, s);
 }
 
@@ -605,7 +613,7 @@ bf_status bf_measure_fma_rate(int fp64, double *tflops)
 
 bf_status bf_selfcheck_phase(bf_plan p, int n, double *max_err_cycles)
 {
-    if (!p || n < 1 || !max_err_cycles || p->prec != BF_PREC_MIXED) return BF_ERR_INVALID_ARG;
+    if (!p || n < 1 || !max_err_cycles || p->prec == BF_PREC_FP64) return BF_ERR_INVALID_ARG;
     bfk::KArgs<bfk::PMIX> am;
     bfk::KArgs<bfk::PF64> ad;
     fill_args<bfk::PMIX>(p, am);

@@ -124,16 +124,27 @@ struct PF64 {
     struct SE { double2 a; };      // source feature table entry: f0, f1
     struct Sc { double s3, sgn; }; // s/3 and sign(s)
     static constexpr bool is_f64 = true;
+    static constexpr bool sfu = false;
 };
 
-struct PMIX {
+struct MixTE { float4 a, b; };  // (f0.hi, f0.lo, f1.hi, f1.lo) | (f2.hi, f2.lo, -, -)
+struct MixSE { float4 a; };     // (f0.hi, f0.lo, f1.hi, f1.lo)
+struct MixSc { float s3hi, s3lo, sgn, pad; };
+
+// complex64 weights, double-float phase; SFU = true takes sin/cos of the reduced phase
+// from the special-function unit (__sincosf) instead of the polynomial below
+template <bool SFU>
+struct PMIXT {
     using R = float;
     using C = float2;
-    struct TE { float4 a, b; };    // (f0.hi, f0.lo, f1.hi, f1.lo) | (f2.hi, f2.lo, -, -)
-    struct SE { float4 a; };       // (f0.hi, f0.lo, f1.hi, f1.lo)
-    struct Sc { float s3hi, s3lo, sgn, pad; };
+    using TE = MixTE;
+    using SE = MixSE;
+    using Sc = MixSc;
     static constexpr bool is_f64 = false;
+    static constexpr bool sfu = SFU;
 };
+using PMIX = PMIXT<false>;
+using PMIXF = PMIXT<true>;
 
 __device__ __forceinline__ void sincos2pi(double fr, double &s, double &c) { sincospi(2.0 * fr, &s, &c); }
 // sin and cos of 2 pi f for |f| < 2^20, written from the Taylor series: quadrant
@@ -162,6 +173,14 @@ __device__ __forceinline__ void sincos2pi(float f, float &s, float &c)
     const float c1 = (q & 1) ? sn : cs;
     s = __int_as_float(__float_as_int(s1) ^ ((q & 2) << 30));
     c = __int_as_float(__float_as_int(c1) ^ (((q + 1) & 2) << 30));
+}
+
+// sin and cos of 2 pi f from the special-function unit after reduction to |f| <= 1/2
+// (CUDA documents 2^-21.41 absolute error for |x| <= pi)
+__device__ __forceinline__ void sincos2pi_sfu(float f, float &s, float &c)
+{
+    const float r = __fsub_rn(f, fround(f));
+    __sincosf(__fmul_rn(r, 6.28318530717958647692f), &s, &c);
 }
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
@@ -264,8 +283,8 @@ template <int Q> __device__ __forceinline__ int soff(int L, int l) { return ((2 
 
 template <class P, int D, int K> struct Ph;
 
-template <int D, int K>
-struct Ph<PMIX, D, K> {
+template <bool F, int D, int K>
+struct Ph<PMIXT<F>, D, K> {
     struct T { df x[D]; df A[D]; };
     struct S { df y[D]; df y2[D]; };
 
@@ -273,7 +292,7 @@ struct Ph<PMIX, D, K> {
     static __device__ __forceinline__ df lo(const float4 &v) { return {v.z, v.w}; }
 
     // target point from its per-dimension table entries; GENRADON forms A_k = (s a_k(x))^2
-    static __device__ __forceinline__ T tgt(const KArgs<PMIX> &a, const PMIX::TE *e)
+    static __device__ __forceinline__ T tgt(const KArgs<PMIXT<F>> &a, const MixTE *e)
     {
         T t;
 #pragma unroll
@@ -294,7 +313,7 @@ struct Ph<PMIX, D, K> {
         return t;
     }
 
-    static __device__ __forceinline__ void src1(S &s, int k, const PMIX::SE &e)
+    static __device__ __forceinline__ void src1(S &s, int k, const MixSE &e)
     {
         s.y[k] = hi(e.a);
         s.y2[k] = lo(e.a);
@@ -304,7 +323,7 @@ struct Ph<PMIX, D, K> {
     // coordinate k; parts add (add), and fin() turns their sum into Phi minus an integer.
     // Loops hoist the parts of the source coordinates that do not change.
     struct Part { float f; df q; };
-    static __device__ __forceinline__ Part part(const T &t, const PMIX::SE &e, int k)
+    static __device__ __forceinline__ Part part(const T &t, const MixSE &e, int k)
     {
         Part p{0.0f, {0.0f, 0.0f}};
         const df y = hi(e.a), y2 = lo(e.a);
@@ -325,7 +344,7 @@ struct Ph<PMIX, D, K> {
         const df s = two_sum(u.q.hi, v.q.hi);
         return Part{u.f + v.f, {s.hi, __fadd_rn(__fadd_rn(u.q.lo, v.q.lo), s.lo)}};
     }
-    static __device__ __forceinline__ float fin(const KArgs<PMIX> &a, const T &t, const Part &p)
+    static __device__ __forceinline__ float fin(const KArgs<PMIXT<F>> &a, const T &t, const Part &p)
     {
         if constexpr (K == KIND_DOT) {
             return p.f;
@@ -339,7 +358,7 @@ struct Ph<PMIX, D, K> {
     }
 
     // Phi(x, y) minus an integer, |result| < 2 (the sincos reduces it further)
-    static __device__ __forceinline__ float frac(const KArgs<PMIX> &a, const T &t, const S &s)
+    static __device__ __forceinline__ float frac(const KArgs<PMIXT<F>> &a, const T &t, const S &s)
     {
         if constexpr (K == KIND_DOT) {
             float f = 0.0f;
@@ -452,7 +471,10 @@ __device__ __forceinline__ typename P::C expphase(const KArgs<P> &a, const typen
                                                   const typename Ph<P, D, K>::S &s)
 {
     typename P::R fr = Ph<P, D, K>::frac(a, t, s), sn, cs;
-    sincos2pi(fr, sn, cs);
+    if constexpr (P::sfu)
+        sincos2pi_sfu(fr, sn, cs);
+    else
+        sincos2pi(fr, sn, cs);
     typename P::C e;
     e.x = cs;
     e.y = sn;
@@ -464,7 +486,10 @@ __device__ __forceinline__ typename P::C expphase_part(const KArgs<P> &a, const 
                                                        const typename Ph<P, D, K>::Part &pt)
 {
     typename P::R fr = Ph<P, D, K>::fin(a, t, pt), sn, cs;
-    sincos2pi(fr, sn, cs);
+    if constexpr (P::sfu)
+        sincos2pi_sfu(fr, sn, cs);
+    else
+        sincos2pi(fr, sn, cs);
     typename P::C e;
     e.x = cs;
     e.y = sn;

@@ -22,7 +22,7 @@ struct PassFns {
 };
 
 // (d, q, precision, phase kind) -> kernels, or null if that combination is not compiled.
-// precision: 0 FP64, 1 mixed; kind: bf_phase_kind
+// precision: 0 FP64, 1 mixed, 2 mixed with SFU sincos; kind: bf_phase_kind
 const PassFns *get_fns(int d, int q, int prec, int kind);
 
 // one function per instantiation unit: bf_inst_d{d}_{f64|mix}_{kind}.cu
@@ -31,6 +31,8 @@ BFL_DECLARE(2, f64, dot) BFL_DECLARE(2, f64, genradon) BFL_DECLARE(2, f64, hypra
 BFL_DECLARE(2, mix, dot) BFL_DECLARE(2, mix, genradon) BFL_DECLARE(2, mix, hypradon) BFL_DECLARE(2, mix, separable)
 BFL_DECLARE(3, f64, dot) BFL_DECLARE(3, f64, genradon) BFL_DECLARE(3, f64, separable)
 BFL_DECLARE(3, mix, dot) BFL_DECLARE(3, mix, genradon) BFL_DECLARE(3, mix, separable)
+BFL_DECLARE(2, sfu, dot) BFL_DECLARE(2, sfu, genradon) BFL_DECLARE(2, sfu, hypradon) BFL_DECLARE(2, sfu, separable)
+BFL_DECLARE(3, sfu, dot) BFL_DECLARE(3, sfu, genradon) BFL_DECLARE(3, sfu, separable)
 #undef BFL_DECLARE
 
 

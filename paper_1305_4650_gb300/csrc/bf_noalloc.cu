@@ -237,7 +237,7 @@ extern "C" bf_status bf_apply_noalloc(int d, int64_t N, int q, bf_phase_kind pha
     if (q < 2 || q > bfk::QMAX) return BF_ERR_INVALID_ARG;
     if ((int)phase < 0 || (int)phase > 3) return BF_ERR_INVALID_ARG;
     if (phase == BF_PHASE_HYPRADON && d != 2) return BF_ERR_INVALID_ARG;
-    if (prm->precision != BF_PREC_FP64 && prm->precision != BF_PREC_MIXED) return BF_ERR_INVALID_ARG;
+    if (prm->precision < BF_PREC_FP64 || prm->precision > BF_PREC_MIXED_SFU) return BF_ERR_INVALID_ARG;
     for (int k = 0; k < d; ++k) {
         if (!(prm->x_w[k] > 0.0) || !(prm->y_w[k] > 0.0)) return BF_ERR_INVALID_ARG;
         if (!std::isfinite(prm->x_lo[k]) || !std::isfinite(prm->y_lo[k]) || !std::isfinite(prm->x_w[k]) ||
@@ -253,7 +253,7 @@ extern "C" bf_status bf_apply_noalloc(int d, int64_t N, int q, bf_phase_kind pha
     for (int i = 0; i < 7; ++i)
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
     if (nrhs < 0 || nrhs > 65535) return BF_ERR_INVALID_ARG;
-    const int prec = prm->precision == BF_PREC_FP64 ? 0 : 1;
+    const int prec = prm->precision;
     const bfl::PassFns *fns = bfl::get_fns(d, q, prec, (int)phase);
     if (!fns) return BF_ERR_UNSUPPORTED;
 
@@ -272,5 +272,6 @@ extern "C" bf_status bf_apply_noalloc(int d, int64_t N, int q, bf_phase_kind pha
     if (st != BF_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (prec == 0) return run<bfk::PF64>(d, L, q, (int)phase, prm, g, f, nrhs, s, base, fns);
+    if (prec == 2) return run<bfk::PMIXF>(d, L, q, (int)phase, prm, g, f, nrhs, s, base, fns);
     return run<bfk::PMIX>(d, L, q, (int)phase, prm, g, f, nrhs, s, base, fns);
 }

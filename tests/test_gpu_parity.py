@@ -17,7 +17,8 @@ from paper_1305_4650_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-TOL = {("fp64", 2): 1e-11, ("fp64", 3): 1e-11, ("mixed", 2): 1e-5, ("mixed", 3): 1e-4}
+TOL = {("fp64", 2): 1e-11, ("fp64", 3): 1e-11, ("mixed", 2): 1e-5, ("mixed", 3): 1e-4,
+       ("mixed_sfu", 2): 1e-5, ("mixed_sfu", 3): 1e-4}
 
 
 @pytest.fixture(scope="module")
@@ -72,13 +73,14 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "mixed_sfu"])
 @pytest.mark.parametrize("case", CASES, ids=[f"d{c[0]}L{c[1]}q{c[2]}{c[3]}" for c in CASES])
 def test_parity_small(bf, case, precision):
     d, L, q, phase, kw = case
     spec = spec_of(d, L, q, phase, **kw)
     dt = np.complex128 if precision == "fp64" else np.complex64
     g = wl.source_values(spec, 2, dt, seed=11 + L)
+    assert precision in ("fp64", "mixed", "mixed_sfu")
     ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.astype(np.complex128))
     out = run_gpu(bf, spec, g, precision)
     assert rel(out, ref) <= TOL[(precision, d)], rel(out, ref)
@@ -151,6 +153,16 @@ def _sampled_parity(bfmod, spec, precision, box, tol):
 def test_parity_genradon2d_full_size_mixed(bf):
     spec = wl.genradon2d()                                   # d=2, N=1024, q=5
     _sampled_parity(bf, spec, "mixed", box=(1 << (2 * spec.switch_level)) // 3, tol=TOL[("mixed", 2)])
+
+
+def test_parity_genradon2d_full_size_mixed_sfu(bf):
+    spec = wl.genradon2d()
+    _sampled_parity(bf, spec, "mixed_sfu", box=(1 << (2 * spec.switch_level)) // 3, tol=TOL[("mixed_sfu", 2)])
+
+
+def test_parity_genradon3d_full_size_mixed_sfu(bf):
+    spec = wl.genradon3d()
+    _sampled_parity(bf, spec, "mixed_sfu", box=300, tol=TOL[("mixed_sfu", 3)])
 
 
 def test_parity_genradon2d_full_size_fp64(bf):
