@@ -473,6 +473,18 @@ def plan_fuse(passes):
     return max(p["k"] for p in passes)
 
 
+def restricted_work_fraction(d: int, L: int, level: int) -> float:
+    """Share of the apply's translations done by the oracle restricted to one target box at
+    `level`: stage l touches the pairs whose target box lies on the box's path, and of their
+    2^d children only those on the path (exactly 1/2^(d level) when level <= 1)."""
+    tot = 0.0
+    for l in range(L):
+        act_pairs = 2.0 ** (-d * min(l, level))             # active target boxes at level l
+        act_child = 2.0 ** (-d) if l < level else 1.0        # active children of each
+        tot += act_pairs * act_child
+    return tot / L
+
+
 def cpu_sample(spec, g0, level=1):
     import numpy as np
     import oracle
@@ -482,10 +494,12 @@ def cpu_sample(spec, g0, level=1):
     t0 = time.perf_counter()
     oracle.butterfly(P, np.asarray(g0, np.complex128), restrict=(level, box))
     dt = time.perf_counter() - t0
+    frac = restricted_work_fraction(spec.d, spec.L, level)
     return {"value": n_out / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
             "seconds": round(dt, 2),
             "sample": f"FP64 oracle butterfly restricted to target box {box} at level {level}: "
-                      f"{n_out} of {spec.npts} outputs, 1/{2 ** (spec.d * level)} of the apply's translations"}
+                      f"{n_out} of {spec.npts} outputs, {frac:.4f} of the apply's translations "
+                      f"(value = outputs / time)"}
 
 
 # ---------------------------------------------------------- reference arm
@@ -498,7 +512,7 @@ def run_reference(args, rank, world):
     from paper_1305_4650_gb300 import workloads as wl
     spec = workload(args.workload)
     g0 = wl.source_values(spec, 1, np.complex64)[0]
-    level = 2 if spec.d == 2 else 1
+    level = 1
     for _ in range(args.warmup):
         cpu_sample(spec, g0, level)
     vals, secs = [], []
