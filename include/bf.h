@@ -97,7 +97,9 @@ bf_status bf_params_default(int d, int64_t N, bf_params *out);
 /* Build a plan for d in {2,3} (d = 1 is not compiled), N = 2^L with 1 <= L and
  * N^d <= 2^30, q nodes per dimension (q in {2,3,4,5,6,8} for d = 2, q in {2,3,4}
  * for d = 3; other q return BF_ERR_UNSUPPORTED),
- * phase kind `phase` (HYPRADON needs d = 2).  Allocates device workspace of
+ * phase kind `phase` (HYPRADON needs d = 2).  The mixed precisions need |Phi| < 2^21
+ * cycles over X x Y (bounded from the domain and the phase formula; BF_ERR_UNSUPPORTED
+ * otherwise, use BF_PREC_FP64).  Allocates device workspace of
  * 2 * max_nrhs * N^d * q^d complex numbers plus small geometry tables on the
  * current CUDA device.  On success *out owns that memory until bf_destroy. */
 bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_params *p,

@@ -40,6 +40,7 @@ struct bf_plan_s {
     int64_t ws_bytes = 0;
     std::vector<Pass> passes;
     std::vector<Pass> passes_rb;   // schedule of the multi-RHS kernels (empty if not compiled)
+    std::vector<Pass> passes_adj;  // schedule whose reverse is the adjoint (fits the row caches)
     const bfl::PassFns *fns = nullptr;
     int last_cuda = 0;
 };
@@ -195,6 +196,14 @@ size_t row_cache_smem(const bf_plan_s *p, const Pass &ps)
     return (size_t)ps.T * ((size_t)1 << (p->d * (ps.k - 1))) * (size_t)p->r * (size_t)p->fns->tsize;
 }
 
+// the adjoint row pass caches children's and parents' node features (T (2^{dk} + 2^{d(k-1)}) boxes x r)
+size_t row_adj_cache_smem(const bf_plan_s *p, const Pass &ps)
+{
+    if (!ps.row || ps.k < 1) return 0;
+    return (size_t)ps.T * (((size_t)1 << (p->d * ps.k)) + ((size_t)1 << (p->d * (ps.k - 1)))) * (size_t)p->r *
+           (size_t)p->fns->tsize;
+}
+
 // A CTA owns np pairs (2^{d kmax} of the instantiation, fewer for tiny problems):
 // T = np / 2^{dk} tiles of a k-level pass.
 Pass make_pass(const bf_plan_s *p, int64_t np_cta, int row, int l0, int k, int flags)
@@ -332,8 +341,8 @@ bf_status run_adjoint(bf_plan p, const void *f, void *g, int nrhs, cudaStream_t 
     a.fadj = static_cast<const typename P::C *>(f);
     a.gadj = static_cast<typename P::C *>(g);
     void *buf[2] = {p->w0, p->w1};
-    for (int i = (int)p->passes.size() - 1; i >= 0; --i) {
-        const Pass &ps = p->passes[i];
+    for (int i = (int)p->passes_adj.size() - 1; i >= 0; --i) {
+        const Pass &ps = p->passes_adj[i];
         a.l0 = ps.l0;
         a.k = ps.k;
         a.flags = ps.flags;
@@ -341,11 +350,43 @@ bf_status run_adjoint(bf_plan p, const void *f, void *g, int nrhs, cudaStream_t 
         a.win = static_cast<const typename P::C *>(buf[(i + 1) & 1]);
         a.wout = static_cast<typename P::C *>(buf[i & 1]);
         const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
-        const size_t smem = pass_smem(p, ps);
+        const size_t smem = pass_smem(p, ps) + row_adj_cache_smem(p, ps);
         cudaError_t e = (ps.row ? p->fns->row_adj : p->fns->col_adj)(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
         if (e != cudaSuccess) return cuda_fail(p, e);
     }
     return BF_OK;
+}
+
+// Upper bound of |Phi| over X x Y.  The mixed path rounds to integers by adding
+// 1.5 * 2^23, which is exact only below 2^22 cycles (kept under 2^21 here).
+double phase_bound(int d, int kind, const bf_params *p)
+{
+    double mx[3], my[3];
+    for (int k = 0; k < d; ++k) {
+        mx[k] = std::fmax(std::fabs(p->x_lo[k]), std::fabs(p->x_lo[k] + p->x_w[k]));
+        my[k] = std::fmax(std::fabs(p->y_lo[k]), std::fabs(p->y_lo[k] + p->y_w[k]));
+    }
+    double b = 0.0;
+    switch (kind) {
+    case BF_PHASE_DOT:
+        for (int k = 0; k < d; ++k) b += mx[k] * my[k];
+        break;
+    case BF_PHASE_GENRADON: {
+        double q2 = 0.0;
+        for (int k = 0; k < d; ++k) {
+            b += mx[k] * my[k];
+            q2 += my[k] * my[k];                      // a_k(x) <= 1
+        }
+        b += std::sqrt(q2);
+        break;
+    }
+    case BF_PHASE_HYPRADON:
+        b = mx[0] * std::sqrt(my[0] * my[0] + my[1] * my[1] * mx[1] * mx[1]);
+        break;
+    default:
+        for (int k = 0; k < d; ++k) b += 1.0 + my[k] * my[k] / (k + 2.0);
+    }
+    return std::fabs(p->phase_scale) * b;
 }
 
 bool supported_q(int d, int q) { return bfl::get_fns(d, q, 1, 0) != nullptr && bfl::get_fns(d, q, 0, 0) != nullptr; }
@@ -399,6 +440,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     if (phase == BF_PHASE_HYPRADON && d != 2) return BF_ERR_INVALID_ARG;
     if (prm->precision < BF_PREC_FP64 || prm->precision > BF_PREC_MIXED_SFU) return BF_ERR_INVALID_ARG;
     if (!supported_q(d, q)) return BF_ERR_UNSUPPORTED;
+    if (prm->precision != BF_PREC_FP64 && phase_bound(d, (int)phase, prm) >= 2097152.0) return BF_ERR_UNSUPPORTED;
     for (int k = 0; k < d; ++k) {
         if (!(prm->x_w[k] > 0.0) || !(prm->y_w[k] > 0.0)) return BF_ERR_INVALID_ARG;
         if (!std::isfinite(prm->x_lo[k]) || !std::isfinite(prm->y_lo[k]) || !std::isfinite(prm->x_w[k]) ||
@@ -449,6 +491,19 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     if (p->fns->col_rb) {
         const int krb = kreq < p->fns->kmax_rb ? kreq : p->fns->kmax_rb;
         p->passes_rb = schedule(p, krb, p->fns->np_rb);
+    }
+    // the adjoint's row passes also hold target-feature caches: fuse fewer levels, then put
+    // fewer tiles in a CTA, until every pass fits the shared memory of one CTA
+    {
+        bool fits = false;
+        for (int ka = p->kc; ka >= 1 && !fits; --ka) {
+            for (int64_t np = p->fns->np; np >= (1LL << (d * ka)) && !fits; np >>= d) {
+                p->passes_adj = schedule(p, ka, np);
+                fits = true;
+                for (const Pass &ps : p->passes_adj)
+                    if (pass_smem(p, ps) + row_adj_cache_smem(p, ps) > 227 * 1024) fits = false;
+            }
+        }
     }
 
     bf_status st = build_tables(p);

@@ -1162,10 +1162,29 @@ struct Tile {
 
     // ---- adjoint of one row merge (level l+1 -> l):
     // in_c(t) = e^{2pi i Phi(x_t^{Ap}, y0(B_c))} sum_alpha sum_s M_alpha[t][s] e^{-2pi i Phi(x_s^{A_alpha}, y0(B_c))} out_alpha(s)
-    static __device__ void row_level_adj(const KArgs<P> &a, C *Wt, C *S, int l, int i)
+    static __device__ void row_level_adj(const KArgs<P> &a, C *Wt, C *S, typename PH::T *TC, int l, int i)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D;
         const int L = a.L;
+        // target features of the children's nodes (level l+1; T 2^{D(i+1)} boxes x q^d) and,
+        // after them, of the parents' nodes (level l; T 2^{Di} boxes x q^d)
+        const int nb1 = 1 << (D * (i + 1)), nb0 = 1 << (D * i);
+        typename PH::T *TP = TC + a.T * nb1 * RR;
+        for (int j = threadIdx.x; j < a.T * (nb1 + nb0) * RR; j += blockDim.x) {
+            const bool child = j < a.T * nb1 * RR;
+            const int jj = child ? j : j - a.T * nb1 * RR;
+            const int nb = child ? nb1 : nb0;
+            const int t = jj % RR, aloc = (jj / RR) % nb, tau = jj / (RR * nb);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            int ca[DMAX], tk[DMAX], tt = t;
+            const int lv = child ? l + 1 : l;
+            morton_decode<D>((Ap << (D * (child ? i + 1 : i))) + aloc, lv, ca);
+#pragma unroll
+            for (int q = 0; q < D; ++q) { tk[q] = tt % Q; tt /= Q; }
+            TC[j] = tpoint<P, D, Q, K>(a, lv, ca, tk);
+        }
+        __syncthreads();
         // stage A: items (tau, block, c, alpha_{D-1}, s_{D-1}): conjugate post-modulation of every
         // out_alpha at the child's nodes, contraction over dims 0..D-2 and alpha_{<D-1}
         //   -> S[tau][block][c][alpha_{D-1}][s_{D-1}][t_{<D-1}]
@@ -1191,15 +1210,13 @@ struct Tile {
 #pragma unroll
             for (int al = 0; al < (NC >> 1); ++al) {
                 const int alpha = al | (ahi << (D - 1));
-                int ca[DMAX];
-                morton_decode<D>((Apg << D) + alpha, l + 1, ca);
+                const typename PH::T *tn = TC + (tau * nb1 + (int)((digit_rev<D>(beta & (nb0 - 1), i) << D) + alpha)) * RR;
                 const C *wi = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR;
                 if constexpr (D == 2) {
                     const int a0 = alpha & 1;
 #pragma unroll
                     for (int s0 = 0; s0 < Q; ++s0) {
-                        const int sk[DMAX] = {s0, sq, 0};
-                        const C e = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l + 1, ca, sk), sc);
+                        const C e = expphase<P, D, K>(a, tn[s0 + Q * sq], sc);
                         const C u = cjmul(e, wi[s0 + Q * sq]);
 #pragma unroll
                         for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[a0][t0][s0], u);
@@ -1213,8 +1230,7 @@ struct Tile {
                         for (int t0 = 0; t0 < Q; ++t0) tmp[t0] = czero<C>();
 #pragma unroll
                         for (int s0 = 0; s0 < Q; ++s0) {
-                            const int sk[DMAX] = {s0, s1, sq};
-                            const C e = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l + 1, ca, sk), sc);
+                            const C e = expphase<P, D, K>(a, tn[s0 + Q * s1 + Q * Q * sq], sc);
                             const C u = cjmul(e, wi[s0 + Q * s1 + Q * Q * sq]);
 #pragma unroll
                             for (int t0 = 0; t0 < Q; ++t0) cfma(tmp[t0], a.M[a0][t0][s0], u);
@@ -1269,11 +1285,9 @@ struct Tile {
                 for (int j = 0; j < D - 1; ++j) { tk[j] = tt % Q; tt /= Q; }
             }
             C *wo = Wt + tau * n * RR + (base + (c << (D * i))) * RR + tl;
+            const typename PH::T *tp = TP + (tau * nb0 + (int)digit_rev<D>(beta & (nb0 - 1), i)) * RR + tl;
 #pragma unroll
-            for (int tq = 0; tq < Q; ++tq) {
-                tk[D - 1] = tq;
-                wo[tq * QD1] = cmul(expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l, ca, tk), sc), acc[tq]);
-            }
+            for (int tq = 0; tq < Q; ++tq) wo[tq * QD1] = cmul(expphase<P, D, K>(a, tp[tq * QD1], sc), acc[tq]);
         }
         __syncthreads();
     }
@@ -1521,12 +1535,13 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pa
     C *Wt = reinterpret_cast<C *>(smem_raw);
     C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
     const int rhs = blockIdx.y;
+    typename TL::PH::T *TC = reinterpret_cast<typename TL::PH::T *>(S + 2 * a.T * (1 << (D * a.k)) * TL::RR);
     if (a.flags & F_FINAL)
         TL::final_adj(a, Wt, rhs);
     else
         TL::load_strided(a, Wt, rhs);
     __syncthreads();
-    for (int i = a.k - 1; i >= 0; --i) TL::row_level_adj(a, Wt, S, a.l0 + i, i);
+    for (int i = a.k - 1; i >= 0; --i) TL::row_level_adj(a, Wt, S, TC, a.l0 + i, i);
     TL::store_contig(a, Wt, rhs);
 }
 

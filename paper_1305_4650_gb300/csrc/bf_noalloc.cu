@@ -254,6 +254,23 @@ extern "C" bf_status bf_apply_noalloc(int d, int64_t N, int q, bf_phase_kind pha
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
     if (nrhs < 0 || nrhs > 65535) return BF_ERR_INVALID_ARG;
     const int prec = prm->precision;
+    if (prec != BF_PREC_FP64) {   // |Phi| < 2^21 cycles for the mixed path's integer rounding
+        double b = 0.0, mx[3], my[3];
+        for (int k = 0; k < d; ++k) {
+            mx[k] = std::fmax(std::fabs(prm->x_lo[k]), std::fabs(prm->x_lo[k] + prm->x_w[k]));
+            my[k] = std::fmax(std::fabs(prm->y_lo[k]), std::fabs(prm->y_lo[k] + prm->y_w[k]));
+        }
+        if (phase == BF_PHASE_DOT || phase == BF_PHASE_GENRADON) {
+            double q2 = 0.0;
+            for (int k = 0; k < d; ++k) { b += mx[k] * my[k]; q2 += my[k] * my[k]; }
+            if (phase == BF_PHASE_GENRADON) b += std::sqrt(q2);
+        } else if (phase == BF_PHASE_HYPRADON) {
+            b = mx[0] * std::sqrt(my[0] * my[0] + my[1] * my[1] * mx[1] * mx[1]);
+        } else {
+            for (int k = 0; k < d; ++k) b += 1.0 + my[k] * my[k] / (k + 2.0);
+        }
+        if (std::fabs(prm->phase_scale) * b >= 2097152.0) return BF_ERR_UNSUPPORTED;
+    }
     const bfl::PassFns *fns = bfl::get_fns(d, q, prec, (int)phase);
     if (!fns) return BF_ERR_UNSUPPORTED;
 

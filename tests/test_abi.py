@@ -76,6 +76,10 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     lib.bf_params_default(2, 64, ctypes.byref(q))
     q.reserved[3] = 1
     assert create(2, 64, 5, 1, q) == 1
+    # the mixed path needs |Phi| < 2^21 cycles: the separable test phase reaches y^2/2 = 8.4e6 at N = 4096
+    q = BfParams()
+    lib.bf_params_default(2, 4096, ctypes.byref(q))
+    assert create(2, 4096, 3, 3, q) == 2
     assert h.value is None
     assert lib.bf_destroy(None) == 0
     assert lib.bf_apply(None, None, None, 1, None) == 1
