@@ -67,7 +67,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="genradon2d", choices=["genradon2d", "genradon3d", "dft64", "hypradon48", "cg1024"])
+    ap.add_argument("--workload", default="genradon2d",
+                    choices=["genradon2d", "genradon3d", "dft64", "hypradon512", "hypradon48", "cg1024"])
+    ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per apply (single-problem workloads)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -76,7 +78,8 @@ def parse():
 
 def workload(name):
     from paper_1305_4650_gb300 import workloads as wl
-    return {"genradon2d": wl.genradon2d, "genradon3d": wl.genradon3d, "dft64": wl.dft64}[name]()
+    return {"genradon2d": wl.genradon2d, "genradon3d": wl.genradon3d, "dft64": wl.dft64,
+            "hypradon512": lambda: wl.hypradon(9)}[name]()
 
 
 # ------------------------------------------------------------------ clocks
@@ -196,7 +199,7 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     spec = workload(args.workload)
-    nrhs = 1
+    nrhs = args.nrhs
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
 
@@ -213,7 +216,7 @@ def run_ours(args, rank, world, local_rank):
 
     prec = spec.precision
     plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec)
-    passes = plan.passes()
+    passes = plan.passes(nrhs)
     g_np = wl.source_values(spec, nrhs, plan.cdtype, seed=spec.seed + rank)
     g = torch.from_numpy(g_np).to(dev)
     f = torch.empty_like(g)
@@ -358,6 +361,8 @@ def run_ours(args, rank, world, local_rank):
     plan.close()
     if rank != 0:
         return None
+    csize = 8 if prec != "fp64" else 16
+    weight_gb = 2 * max(len(passes) - 1, 1) * spec.npts * spec.r * csize * nrhs / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64" if prec == "mixed" else "c128",
@@ -365,7 +370,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": spec.name, "d": spec.d, "N": spec.N, "q": spec.q, "r": spec.r,
                        "phase": spec.phase, "precision": prec, "nrhs": nrhs, "switch_level": spec.switch_level,
                        "passes": len(passes), "fuse_levels": plan_fuse(passes),
-                       "l2": "no flush: each step streams ~1.7 GB of weights through the 129 MB L2",
+                       "l2": f"no flush: each step streams {weight_gb:.1f} GB of weights through the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "fp64_gpu": fp64, "sfu_sincos": sfu, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * len(passes), "clocks": clocks}
@@ -427,7 +432,7 @@ def run_batched(args, rank, world, local_rank):
         t = torch.tensor([ms], dtype=torch.float64, device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    launches = sum(p.info()["launches"] for p in plans)
+    launches = sum(p.launches(k) for p, k in zip(plans, nr))
     acc = None
     if rank == 0 and not args.no_accuracy:
         # problem 0 (N = 128) against the oracle butterfly, all outputs, every RHS
@@ -464,6 +469,7 @@ def run_cg(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     spec = wl.genradon2d()
     plan = bf.Plan.from_spec(spec, precision="mixed")
+    launches = plan.launches(1)
     mt = torch.from_numpy(wl.sparse_spikes(spec, 0.01)).to(dev)
     d = plan.apply(mt)
     iters = 20
@@ -489,7 +495,7 @@ def run_cg(args, rank, world, local_rank):
             "config": {"workload": "cg20_genradon2d_N1024_q5", "iterations": iters, "applies": applies,
                        "m_true": "1% spikes, N(0,1) amplitudes", "precision": "mixed"},
             "residual_history": [round(h / hist[0], 6) for h in hist],
-            "gpu_launches": applies * len(bf.Plan.from_spec(spec, precision="mixed").passes()),
+            "gpu_launches": applies * launches,
             "clocks": clk.summary()}
 
 

@@ -140,15 +140,20 @@ bf_status bf_last_cuda_error(bf_plan plan, int *cuda_err);
 bf_status bf_plan_info(bf_plan plan, int *d, int64_t *N, int *q, int *m, int *fuse_levels,
                        int *launches_per_apply, int64_t *workspace_bytes);
 
-/* Instrumentation.  An apply is a fixed schedule of kernel passes (see
- * bf_plan_info: launches_per_apply).  bf_apply_pass runs pass i of that schedule
- * only, with the same arguments as bf_apply; running passes 0 .. n-1 in order on
- * one stream is exactly bf_apply.  Used to time individual kernels with events
- * recorded between passes.  bf_pass_info describes pass i: kind (0 column pass
- * with optional init/switch, 1 row pass with optional final), first level l0,
- * number of fused levels k, flags (1 init, 2 switch, 4 final). */
+/* Instrumentation.  An apply of nrhs right-hand sides is a fixed schedule of kernel
+ * passes: the single-RHS passes for nrhs = 1 (and for FP64 plans), the multi-RHS
+ * passes, which evaluate every phase factor once for up to 16 right-hand sides, for
+ * nrhs >= 2.  bf_pass_count gives the number of passes of that schedule (= kernel
+ * launches of one bf_apply).  bf_apply_pass runs pass i of the schedule only, with
+ * the same arguments as bf_apply; running passes 0 .. count-1 in order on one stream
+ * is exactly bf_apply.  Used to time individual kernels with events recorded between
+ * passes.  bf_pass_info describes pass i of the schedule for nrhs: kind (0 column
+ * pass with optional init/switch, 1 row pass with optional final), first level l0,
+ * number of fused levels k, flags (1 init, 2 switch, 4 final).  nrhs must lie in
+ * 1..max_nrhs, i in 0..count-1 (else BF_ERR_INVALID_ARG). */
+bf_status bf_pass_count(bf_plan plan, int nrhs, int *count);
 bf_status bf_apply_pass(bf_plan plan, int i, const void *g_dev, void *f_dev, int nrhs, void *stream);
-bf_status bf_pass_info(bf_plan plan, int i, int *kind, int *l0, int *k, int *flags);
+bf_status bf_pass_info(bf_plan plan, int nrhs, int i, int *kind, int *l0, int *k, int *flags);
 
 /* Self-checks of the mixed-precision arithmetic on the current device (they
  * allocate and free a few bytes of device memory and synchronise).

@@ -22,7 +22,7 @@ STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_E
 
 EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_apply_host",
            "bf_apply_batched", "bf_destroy", "bf_status_string", "bf_last_cuda_error", "bf_plan_info",
-           "bf_apply_pass", "bf_pass_info", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate"]
+           "bf_apply_pass", "bf_pass_info", "bf_pass_count", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate"]
 
 
 class BfError(RuntimeError):
@@ -66,8 +66,9 @@ def load():
                                      ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i64)]
         lib.bf_apply_pass.argtypes = [vp, i32, vp, vp, i32, vp]
-        lib.bf_pass_info.argtypes = [vp, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+        lib.bf_pass_info.argtypes = [vp, i32, i32, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                      ctypes.POINTER(i32)]
+        lib.bf_pass_count.argtypes = [vp, i32, ctypes.POINTER(i32)]
         lib.bf_selfcheck_sincos.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_selfcheck_phase.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_measure_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
@@ -192,12 +193,19 @@ class Plan:
         """Run pass i of the apply schedule only (instrumentation)."""
         _check(load().bf_apply_pass(self._h, i, g_ptr, f_ptr, nrhs, stream_ptr), "bf_apply_pass", self._h)
 
-    def passes(self) -> list[dict]:
+    def launches(self, nrhs: int = 1) -> int:
+        """Kernel launches (passes) of one apply of nrhs right-hand sides."""
+        n = ctypes.c_int()
+        _check(load().bf_pass_count(self._h, nrhs, ctypes.byref(n)), "bf_pass_count")
+        return n.value
+
+    def passes(self, nrhs: int = 1) -> list[dict]:
+        """The pass schedule bf_apply runs for nrhs right-hand sides."""
         i32 = ctypes.c_int
         out = []
-        for i in range(self.info()["launches"]):
+        for i in range(self.launches(nrhs)):
             kind, l0, k, fl = i32(), i32(), i32(), i32()
-            _check(load().bf_pass_info(self._h, i, ctypes.byref(kind), ctypes.byref(l0), ctypes.byref(k),
+            _check(load().bf_pass_info(self._h, nrhs, i, ctypes.byref(kind), ctypes.byref(l0), ctypes.byref(k),
                                        ctypes.byref(fl)), "bf_pass_info")
             out.append(dict(kind="row" if kind.value else "col", l0=l0.value, k=k.value,
                             init=bool(fl.value & 1), switch=bool(fl.value & 2), final=bool(fl.value & 4)))

@@ -39,7 +39,8 @@ struct bf_plan_s {
     size_t csize = 8;          // bytes per complex number
     int64_t ws_bytes = 0;
     std::vector<Pass> passes;
-    std::vector<Pass> passes_rb;   // schedule of the multi-RHS kernels (empty if not compiled)
+    std::vector<Pass> passes_mr;   // schedule of the multi-RHS kernels (empty if not compiled)
+    int mr_rc = 1;                 // right-hand sides per scratch chunk of the multi-RHS kernels
     std::vector<Pass> passes_adj;  // schedule whose reverse is the adjoint (fits the row caches)
     const bfl::PassFns *fns = nullptr;
     int last_cuda = 0;
@@ -204,6 +205,13 @@ size_t row_adj_cache_smem(const bf_plan_s *p, const Pass &ps)
            (size_t)p->fns->tsize;
 }
 
+// multi-RHS pass: nr right-hand sides of T 2^{dk} pairs, scratch for rc of them, a phase cache
+// of 5 r factors per pair (bf_mr.cuh)
+size_t mr_smem(const bf_plan_s *p, const Pass &ps, int nr, int rc)
+{
+    return (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (size_t)p->r * p->csize * (size_t)(nr + 2 * rc + 5);
+}
+
 // A CTA owns np pairs (2^{d kmax} of the instantiation, fewer for tiny problems):
 // T = np / 2^{dk} tiles of a k-level pass.
 Pass make_pass(const bf_plan_s *p, int64_t np_cta, int row, int l0, int k, int flags)
@@ -277,20 +285,22 @@ void fill_args(const bf_plan_s *p, bfk::KArgs<P> &a)
 // Run passes [first, last) of the forward schedule.  Pass i reads workspace
 // buffer i % 2 (or g when it initialises) and writes buffer (i + 1) % 2 (or f
 // when it evaluates the targets).
-// Multi-RHS forward: every CTA keeps rb_count right-hand sides of its tiles and
-// evaluates each phase once for all of them.
+// Multi-RHS forward: every CTA keeps up to mr_max right-hand sides of its tiles and
+// evaluates each phase factor once for all of them.
 template <class P>
-bf_status run_forward_rb(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s)
+bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last)
 {
     bfk::KArgs<P> a;
     fill_args<P>(p, a);
     a.g = static_cast<const typename P::C *>(g);
     a.f = static_cast<typename P::C *>(f);
     a.nrhs = nrhs;
-    const int rb = p->fns->rb_count;
+    const int mx = p->fns->mr_max;
+    const int nr = nrhs < mx ? nrhs : mx;
+    a.rc = p->mr_rc < nr ? p->mr_rc : nr;
     void *buf[2] = {p->w0, p->w1};
-    for (size_t i = 0; i < p->passes_rb.size(); ++i) {
-        const Pass &ps = p->passes_rb[i];
+    for (int i = first; i < last; ++i) {
+        const Pass &ps = p->passes_mr[i];
         a.l0 = ps.l0;
         a.k = ps.k;
         a.flags = ps.flags;
@@ -298,8 +308,8 @@ bf_status run_forward_rb(bf_plan p, const void *g, void *f, int nrhs, cudaStream
         a.win = static_cast<const typename P::C *>(buf[i & 1]);
         a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
         const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
-        const size_t smem = (size_t)rb * pass_smem(p, ps);
-        cudaError_t e = (ps.row ? p->fns->row_rb : p->fns->col_rb)(&a, (unsigned)ctas, (unsigned)((nrhs + rb - 1) / rb),
+        const size_t smem = mr_smem(p, ps, nr, a.rc);
+        cudaError_t e = (ps.row ? p->fns->row_mr : p->fns->col_mr)(&a, (unsigned)ctas, (unsigned)((nrhs + mx - 1) / mx),
                                                                    smem, s);
         if (e != cudaSuccess) return cuda_fail(p, e);
     }
@@ -388,6 +398,11 @@ double phase_bound(int d, int kind, const bf_params *p)
     }
     return std::fabs(p->phase_scale) * b;
 }
+
+// the multi-RHS schedule serves nrhs >= 2 where it is compiled (mixed precisions, d = 2)
+bool use_mr(const bf_plan_s *p, int nrhs) { return nrhs >= 2 && p->prec != BF_PREC_FP64 && !p->passes_mr.empty(); }
+
+const std::vector<Pass> &schedule_for(const bf_plan_s *p, int nrhs) { return use_mr(p, nrhs) ? p->passes_mr : p->passes; }
 
 bool supported_q(int d, int q) { return bfl::get_fns(d, q, 1, 0) != nullptr && bfl::get_fns(d, q, 0, 0) != nullptr; }
 
@@ -488,9 +503,27 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     const int kreq = prm->fuse_levels > 0 ? prm->fuse_levels : kfit;
     p->kc = p->kr = kreq < kfit ? kreq : kfit;
     p->passes = schedule(p, p->kc, p->fns->np);
-    if (p->fns->col_rb) {
-        const int krb = kreq < p->fns->kmax_rb ? kreq : p->fns->kmax_rb;
-        p->passes_rb = schedule(p, krb, p->fns->np_rb);
+    if (p->fns->col_mr) {
+        // 2 fused levels, as many pairs per CTA as one switch round covers (at least one tile);
+        // scratch for enough right-hand sides to give every thread an item, fewer if the
+        // shared memory of one CTA does not hold them
+        const int kmr = kreq < 2 ? kreq : 2;
+        const int nr = p->max_nrhs < p->fns->mr_max ? p->max_nrhs : p->fns->mr_max;
+        const int64_t ppr = p->fns->mr_nthreads / p->r;
+        p->passes_mr = schedule(p, kmr, ppr);
+        int64_t npr = 0;
+        for (const Pass &ps : p->passes_mr)
+            if (((int64_t)ps.T << (d * ps.k)) > npr) npr = (int64_t)ps.T << (d * ps.k);
+        int rc = (int)(p->fns->mr_nthreads / (npr * q));
+        rc = rc < 1 ? 1 : (rc > nr ? nr : rc);
+        bool fits = false;
+        for (; rc >= 1 && !fits; --rc) {
+            fits = true;
+            for (const Pass &ps : p->passes_mr)
+                if (mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
+            if (fits) p->mr_rc = rc;
+        }
+        if (!fits) p->passes_mr.clear();
     }
     // the adjoint's row passes also hold target-feature caches: fuse fewer levels, then put
     // fewer tiles in a CTA, until every pass fits the shared memory of one CTA
@@ -553,33 +586,47 @@ bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
     if (!g || !f) return BF_ERR_INVALID_ARG;
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int n = (int)p->passes.size();
+    const int n = (int)schedule_for(p, nrhs).size();
     if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n);
     if (p->prec == BF_PREC_MIXED_SFU) {
-        if (nrhs >= 2 && !p->passes_rb.empty()) return run_forward_rb<bfk::PMIXF>(p, g, f, nrhs, s);
+        if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, 0, n);
         return run_forward<bfk::PMIXF>(p, g, f, nrhs, s, 0, n);
     }
-    if (nrhs >= 2 && !p->passes_rb.empty()) return run_forward_rb<bfk::PMIX>(p, g, f, nrhs, s);
+    if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
     return run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
+}
+
+bf_status bf_pass_count(bf_plan p, int nrhs, int *count)
+{
+    if (!p || !count || nrhs < 1 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
+    *count = (int)schedule_for(p, nrhs).size();
+    return BF_OK;
 }
 
 bf_status bf_apply_pass(bf_plan p, int i, const void *g, void *f, int nrhs, void *stream)
 {
-    if (!p || i < 0 || i >= (int)p->passes.size()) return BF_ERR_INVALID_ARG;
+    if (!p) return BF_ERR_INVALID_ARG;
     if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
     if (nrhs == 0) return BF_OK;
+    if (i < 0 || i >= (int)schedule_for(p, nrhs).size()) return BF_ERR_INVALID_ARG;
     if (!g || !f) return BF_ERR_INVALID_ARG;
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, i, i + 1);
-    if (p->prec == BF_PREC_MIXED_SFU) return run_forward<bfk::PMIXF>(p, g, f, nrhs, s, i, i + 1);
+    if (p->prec == BF_PREC_MIXED_SFU) {
+        if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, i, i + 1);
+        return run_forward<bfk::PMIXF>(p, g, f, nrhs, s, i, i + 1);
+    }
+    if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, i, i + 1);
     return run_forward<bfk::PMIX>(p, g, f, nrhs, s, i, i + 1);
 }
 
-bf_status bf_pass_info(bf_plan p, int i, int *kind, int *l0, int *k, int *flags)
+bf_status bf_pass_info(bf_plan p, int nrhs, int i, int *kind, int *l0, int *k, int *flags)
 {
-    if (!p || i < 0 || i >= (int)p->passes.size()) return BF_ERR_INVALID_ARG;
-    const Pass &ps = p->passes[i];
+    if (!p || nrhs < 1 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
+    const std::vector<Pass> &sc = schedule_for(p, nrhs);
+    if (i < 0 || i >= (int)sc.size()) return BF_ERR_INVALID_ARG;
+    const Pass &ps = sc[i];
     if (kind) *kind = ps.row;
     if (l0) *l0 = ps.l0;
     if (k) *k = ps.k;

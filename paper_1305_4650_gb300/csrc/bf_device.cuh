@@ -216,6 +216,7 @@ struct KArgs {
     int L, l0, k, flags, kind;
     int T;                            // tiles per CTA (T * 2^{dk} pairs)
     int nrhs;                         // right-hand sides of the launch (multi-RHS kernels)
+    int rc;                           // right-hand sides per scratch chunk (multi-RHS kernels)
     const void *ctab;                 // target features at box centres, levels 0..ctab_levels (or null)
     int ctab_levels;
 };
@@ -626,7 +627,7 @@ struct Tile {
         const int ctr[DMAX] = {Q, Q, Q};
         const typename PH::T tX = tpoint<P, D, Q, K>(a, 0, cX, ctr);   // centre of X
         for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) {
-            const int t = it % RR, b = (it / RR) % n, tau = it / (RR * n);
+            const int t = it % RR, b = (it / RR) & (n - 1), tau = (it / RR) >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const uint32_t B = (Bstar << (D * k)) + b;
@@ -675,8 +676,8 @@ struct Tile {
             const int tq = it % Q;
             const int chi = (it / Q) & 1;
             const int alpha = (it / (2 * Q)) % NC;
-            const int beta = (it / (2 * Q * NC)) % nblk;
-            const int tau = it / (2 * Q * NC * nblk);
+            const int beta = (it / (2 * Q * NC)) & (nblk - 1);
+            const int tau = (it / (2 * Q * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -685,7 +686,6 @@ struct Tile {
             int ca[DMAX], cbq[DMAX];
             morton_decode<D>(Aa, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
-            const int ctr[DMAX] = {Q, Q, Q};
             const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
             const C *Wtau = Wt + tau * n * RR;
             C acc[QD1];
@@ -742,8 +742,8 @@ struct Tile {
         for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
             const int tl = it % QD1;
             const int alpha = (it / QD1) % NC;
-            const int beta = (it / (QD1 * NC)) % nblk;
-            const int tau = it / (QD1 * NC * nblk);
+            const int beta = (it / (QD1 * NC)) & (nblk - 1);
+            const int tau = (it / (QD1 * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -752,7 +752,6 @@ struct Tile {
             int ca[DMAX], cbq[DMAX];
             morton_decode<D>(Aa, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
-            const int ctr[DMAX] = {Q, Q, Q};
             const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
             C acc[Q];
 #pragma unroll
@@ -794,8 +793,8 @@ struct Tile {
         const int L = a.L;
         for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
             const int sh = it % QD1;
-            const int sl = (it / QD1) % n;
-            const int tau = it / (QD1 * n);
+            const int sl = (it / QD1) & (n - 1);
+            const int tau = (it / QD1) >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
@@ -855,7 +854,7 @@ struct Tile {
         const int L = a.L;
         const int nbox = 1 << (D * i);
         for (int j = threadIdx.x; j < a.T * nbox * RR; j += blockDim.x) {
-            const int t = j % RR, aloc = (j / RR) % nbox, tau = j / (RR * nbox);
+            const int t = j % RR, aloc = (j / RR) & (nbox - 1), tau = (j / RR) >> (D * i);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             int ca[DMAX], tk[DMAX], tt = t;
@@ -871,8 +870,8 @@ struct Tile {
         for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
             const int th = it % QD1;
             const int c = (it / QD1) % NC;
-            const int beta = (it / (QD1 * NC)) % nblk;
-            const int tau = it / (QD1 * NC * nblk);
+            const int beta = (it / (QD1 * NC)) & (nblk - 1);
+            const int tau = (it / (QD1 * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -907,8 +906,8 @@ struct Tile {
         for (int it = threadIdx.x; it < a.T * nblk * NC * Q; it += blockDim.x) {
             const int s0 = it % Q;
             const int alpha = (it / Q) % NC;
-            const int beta = (it / (Q * NC)) % nblk;
-            const int tau = it / (Q * NC * nblk);
+            const int beta = (it / (Q * NC)) & (nblk - 1);
+            const int tau = (it / (Q * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -1002,7 +1001,7 @@ struct Tile {
         const int ctr[DMAX] = {Q, Q, Q};
         const typename PH::S sY = spoint<P, D, Q, K>(a, L, cY, ctr);      // centre of Y
         for (int it = threadIdx.x; it < a.T * n; it += blockDim.x) {
-            const int sl = it % n, tau = it / n;
+            const int sl = it & (n - 1), tau = it >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
@@ -1044,8 +1043,8 @@ struct Tile {
         for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
             const int th = it % QD1;
             const int alpha = (it / QD1) % NC;
-            const int beta = (it / (QD1 * NC)) % nblk;
-            const int tau = it / (QD1 * NC * nblk);
+            const int beta = (it / (QD1 * NC)) & (nblk - 1);
+            const int tau = (it / (QD1 * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -1053,7 +1052,6 @@ struct Tile {
             int ca[DMAX], cbq[DMAX];
             morton_decode<D>((Apg << D) + alpha, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
-            const int ctr[DMAX] = {Q, Q, Q};
             const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, (Apg << D) + alpha, ca);
             int tk[DMAX];
             {
@@ -1087,8 +1085,8 @@ struct Tile {
         for (int it = threadIdx.x; it < a.T * nblk * NC * Q; it += blockDim.x) {
             const int s0 = it % Q;
             const int c = (it / Q) % NC;
-            const int beta = (it / (Q * NC)) % nblk;
-            const int tau = it / (Q * NC * nblk);
+            const int beta = (it / (Q * NC)) & (nblk - 1);
+            const int tau = (it / (Q * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -1106,7 +1104,6 @@ struct Tile {
             for (int alpha = 0; alpha < NC; ++alpha) {
                 int ca[DMAX];
                 morton_decode<D>((Apg << D) + alpha, l + 1, ca);
-                const int ctr[DMAX] = {Q, Q, Q};
                 const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, (Apg << D) + alpha, ca);
                 const typename PH::Part p0 = PH::part(tA, e0, 0);
                 const C *si = S + ((tau * nblk + beta) * NC + alpha) * QD1 * 2 * Q + c0 * Q + s0;   // [t_{>=1}] stride 2Q
@@ -1173,8 +1170,8 @@ struct Tile {
         for (int j = threadIdx.x; j < a.T * (nb1 + nb0) * RR; j += blockDim.x) {
             const bool child = j < a.T * nb1 * RR;
             const int jj = child ? j : j - a.T * nb1 * RR;
-            const int nb = child ? nb1 : nb0;
-            const int t = jj % RR, aloc = (jj / RR) % nb, tau = jj / (RR * nb);
+            const int nb = child ? nb1 : nb0, lgb = child ? D * (i + 1) : D * i;
+            const int t = jj % RR, aloc = (jj / RR) & (nb - 1), tau = (jj / RR) >> lgb;
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             int ca[DMAX], tk[DMAX], tt = t;
@@ -1192,8 +1189,8 @@ struct Tile {
             const int sq = it % Q;
             const int ahi = (it / Q) & 1;
             const int c = (it / (2 * Q)) % NC;
-            const int beta = (it / (2 * Q * NC)) % nblk;
-            const int tau = it / (2 * Q * NC * nblk);
+            const int beta = (it / (2 * Q * NC)) & (nblk - 1);
+            const int tau = (it / (2 * Q * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -1252,8 +1249,8 @@ struct Tile {
         for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
             const int tl = it % QD1;
             const int c = (it / QD1) % NC;
-            const int beta = (it / (QD1 * NC)) % nblk;
-            const int tau = it / (QD1 * NC * nblk);
+            const int beta = (it / (QD1 * NC)) & (nblk - 1);
+            const int tau = (it / (QD1 * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -1300,8 +1297,8 @@ struct Tile {
         const int L = a.L;
         for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
             const int th = it % QD1;
-            const int sl = (it / QD1) % n;
-            const int tau = it / (QD1 * n);
+            const int sl = (it / QD1) & (n - 1);
+            const int tau = (it / QD1) >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
@@ -1354,7 +1351,7 @@ struct Tile {
         const int ctr[DMAX] = {Q, Q, Q};
         const typename PH::T tX = tpoint<P, D, Q, K>(a, 0, cX, ctr);
         for (int it = threadIdx.x; it < a.T * n; it += blockDim.x) {
-            const int b = it % n, tau = it / n;
+            const int b = it & (n - 1), tau = it >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             int cb[DMAX];
@@ -1388,7 +1385,7 @@ struct Tile {
         const int ctr[DMAX] = {Q, Q, Q};
         const typename PH::S sY = spoint<P, D, Q, K>(a, L, cY, ctr);
         for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) {
-            const int t = it % RR, sl = (it / RR) % n, tau = it / (RR * n);
+            const int t = it % RR, sl = (it / RR) & (n - 1), tau = (it / RR) >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
@@ -1422,7 +1419,7 @@ struct Tile {
         const int64_t Sstar = 1LL << (D * (a.L - a.l0 - k));
         const C *src = a.win + (int64_t)rhs * a.wstride;
         for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) {
-            const int t = j % RR, sl = (j / RR) % n, tau = j / (RR * n);
+            const int t = j % RR, sl = (j / RR) & (n - 1), tau = (j / RR) >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const int64_t pair = ((int64_t)(((int64_t)Ap << (D * k)) + digit_rev<D>(sl, k))) * Sstar + Bstar;
@@ -1453,7 +1450,7 @@ struct Tile {
         const int64_t Sstar = 1LL << (D * (a.L - a.l0 - k));
         C *dst = a.wout + (int64_t)rhs * a.wstride;
         for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) {
-            const int t = j % RR, sl = (j / RR) % n, tau = j / (RR * n);
+            const int t = j % RR, sl = (j / RR) & (n - 1), tau = (j / RR) >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const int64_t pair = ((int64_t)(((int64_t)Ap << (D * k)) + digit_rev<D>(sl, k))) * Sstar + Bstar;
@@ -1543,446 +1540,6 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pa
     __syncthreads();
     for (int i = a.k - 1; i >= 0; --i) TL::row_level_adj(a, Wt, S, TC, a.l0 + i, i);
     TL::store_contig(a, Wt, rhs);
-}
-
-// ====================================================================== multi-RHS
-// Forward passes for d = 2 that keep RB right-hand sides of a tile in shared
-// memory: every phase factor is evaluated once and applied to all of them (the
-// phases depend only on the geometry).  Same items, stages and accumulation order
-// as Tile<2,...>, so results equal the single-RHS kernels bit for bit.
-
-constexpr int kmax_rb(int RR, int CS, int Q, int RB)
-{
-    int k = 1;
-    while (k < 4 && 3 * RB * (1 << (2 * (k + 1))) * RR * CS <= 200 * 1024 && (1 << (2 * (k + 1))) * Q <= 512) ++k;
-    return k;
-}
-
-template <int Q, class P, int RB>
-struct CfgRB {
-    static constexpr int RR = Q * Q;
-    static constexpr int KMAX = kmax_rb(RR, (int)sizeof(typename P::C), Q, RB);
-    static constexpr int NP = 1 << (2 * KMAX);
-    static constexpr int NT = NP * Q;
-};
-
-template <int Q, class P, int K, int RB>
-struct TileRB {
-    static constexpr int D = 2;
-    using R = typename P::R;
-    using C = typename P::C;
-    using TL = Tile<2, Q, P, K>;
-    using PH = Ph<P, 2, K>;
-    static constexpr int NC = 4;
-    static constexpr int RR = Q * Q;
-    static constexpr int QD1 = Q;
-
-    // number of right-hand sides of this CTA
-    static __device__ __forceinline__ int nrb(const KArgs<P> &a) { return min(RB, a.nrhs - (int)blockIdx.y * RB); }
-
-    static __device__ void init(const KArgs<P> &a, C *Wt, int WS)
-    {
-        const int k = a.k, n = 1 << (D * k), L = a.L, nr = nrb(a), rhs0 = blockIdx.y * RB;
-        const int cX[DMAX] = {0, 0, 0};
-        const int ctr[DMAX] = {Q, Q, Q};
-        const typename PH::T tX = tpoint<P, D, Q, K>(a, 0, cX, ctr);
-        for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) {
-            const int t = it % RR, b = (it / RR) % n, tau = it / (RR * n);
-            uint32_t Ap, Bstar;
-            TL::tile_of(a, tau, Ap, Bstar);
-            int cb[DMAX];
-            morton_decode<D>((Bstar << (D * k)) + b, L, cb);
-            R lag = R(1);
-            int tk[DMAX], tt = t;
-#pragma unroll
-            for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.lsrc[tk[j]]; }
-            if (lag != R(0)) {
-                int64_t flat = 0;
-#pragma unroll
-                for (int j = 0; j < D; ++j) flat = (flat << L) + cb[j];
-                const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
-                const C e1 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, pslot));
-                const C e0 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, tk));
-#pragma unroll 1
-                for (int rb = 0; rb < nr; ++rb) {
-                    const C gv = a.g[(int64_t)(rhs0 + rb) * a.npts + flat];
-                    C v = cjmul(e0, cmul(e1, gv));
-                    v.x = lag * v.x;
-                    v.y = lag * v.y;
-                    Wt[rb * WS + it] = v;
-                }
-            } else {
-#pragma unroll 1
-                for (int rb = 0; rb < nr; ++rb) Wt[rb * WS + it] = czero<C>();
-            }
-        }
-    }
-
-    static __device__ void col_level(const KArgs<P> &a, C *Wt, C *S, int WS, int SS, int l, int i)
-    {
-        const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, nr = nrb(a);
-        for (int it = threadIdx.x; it < a.T * nblk * NC * 2 * Q; it += blockDim.x) {
-            const int tq = it % Q;
-            const int chi = (it / Q) & 1;
-            const int alpha = (it / (2 * Q)) % NC;
-            const int beta = (it / (2 * Q * NC)) % nblk;
-            const int tau = it / (2 * Q * NC * nblk);
-            uint32_t Ap, Bstar, Apg, Bq;
-            int base;
-            TL::tile_of(a, tau, Ap, Bstar);
-            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            int ca[DMAX], cbq[DMAX];
-            morton_decode<D>((Apg << D) + alpha, l + 1, ca);
-            morton_decode<D>(Bq, L - l - 1, cbq);
-            const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, (Apg << D) + alpha, ca);
-            C ph[2][Q];
-#pragma unroll
-            for (int cl = 0; cl < 2; ++cl) {
-                const int c = cl | (chi << 1);
-                typename PH::S sp;
-                PH::src1(sp, 1, sget<P, Q>(a, 1, l, 2 * cbq[1] + chi, tq));
-#pragma unroll
-                for (int t0p = 0; t0p < Q; ++t0p) {
-                    PH::src1(sp, 0, sget<P, Q>(a, 0, l, 2 * cbq[0] + (c & 1), t0p));
-                    ph[cl][t0p] = expphase<P, D, K>(a, tA, sp);
-                }
-            }
-            C *so0 = S + ((((tau * nblk + beta) * NC + alpha) * 2 + chi) * Q + tq) * QD1;
-#pragma unroll 1
-            for (int rb = 0; rb < nr; ++rb) {
-                C acc[Q];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
-#pragma unroll
-                for (int cl = 0; cl < 2; ++cl) {
-                    const int c = cl | (chi << 1);
-                    const C *win = Wt + rb * WS + tau * n * RR + (base + (c << (D * i))) * RR;
-#pragma unroll
-                    for (int t0p = 0; t0p < Q; ++t0p) {
-                        const C u = cmul(ph[cl][t0p], win[t0p + Q * tq]);
-#pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[c & 1][t0][t0p], u);
-                    }
-                }
-                C *so = so0 + rb * SS;
-#pragma unroll
-                for (int j = 0; j < Q; ++j) so[j] = acc[j];
-            }
-        }
-        __syncthreads();
-        for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
-            const int tl = it % QD1;
-            const int alpha = (it / QD1) % NC;
-            const int beta = (it / (QD1 * NC)) % nblk;
-            const int tau = it / (QD1 * NC * nblk);
-            uint32_t Ap, Bstar, Apg, Bq;
-            int base;
-            TL::tile_of(a, tau, Ap, Bstar);
-            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            int ca[DMAX], cbq[DMAX];
-            morton_decode<D>((Apg << D) + alpha, l + 1, ca);
-            morton_decode<D>(Bq, L - l - 1, cbq);
-            const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, (Apg << D) + alpha, ca);
-            C ph[Q];
-            {
-                typename PH::S sp;
-                PH::src1(sp, 0, sget<P, Q>(a, 0, l + 1, cbq[0], tl));
-#pragma unroll
-                for (int tq = 0; tq < Q; ++tq) {
-                    PH::src1(sp, 1, sget<P, Q>(a, 1, l + 1, cbq[1], tq));
-                    ph[tq] = expphase<P, D, K>(a, tA, sp);
-                }
-            }
-#pragma unroll 1
-            for (int rb = 0; rb < nr; ++rb) {
-                C acc[Q];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
-#pragma unroll
-                for (int chi = 0; chi < 2; ++chi) {
-                    const C *si = S + rb * SS + ((((tau * nblk + beta) * NC + alpha) * 2 + chi) * Q) * QD1 + tl;
-#pragma unroll
-                    for (int tqp = 0; tqp < Q; ++tqp) {
-                        const C v = si[tqp * QD1];
-#pragma unroll
-                        for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], a.M[chi][tq][tqp], v);
-                    }
-                }
-                C *wo = Wt + rb * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + tl;
-#pragma unroll
-                for (int tq = 0; tq < Q; ++tq) wo[tq * QD1] = cjmul(ph[tq], acc[tq]);
-            }
-        }
-        __syncthreads();
-    }
-
-    static __device__ void switch_tiles(const KArgs<P> &a, C *Wt, C *S, int WS, int SS, int l)
-    {
-        const int k = a.k, n = 1 << (D * k), L = a.L, nr = nrb(a);
-        for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
-            const int sh = it % QD1;
-            const int sl = (it / QD1) % n;
-            const int tau = it / (QD1 * n);
-            uint32_t Ap, Bstar;
-            TL::tile_of(a, tau, Ap, Bstar);
-            int ca[DMAX], cb[DMAX];
-            morton_decode<D>((Ap << (D * k)) + digit_rev<D>(sl, k), l, ca);
-            morton_decode<D>(Bstar, L - l, cb);
-            typename PH::T tS[Q];
-            C acc[RB][Q];
-#pragma unroll
-            for (int s0 = 0; s0 < Q; ++s0) {
-                const int sk[DMAX] = {s0, sh, 0};
-                tS[s0] = tpoint<P, D, Q, K>(a, l, ca, sk);
-#pragma unroll
-                for (int rb = 0; rb < RB; ++rb) acc[rb][s0] = czero<C>();
-            }
-            const C *u = Wt + (tau * n + sl) * RR;
-#pragma unroll 1
-            for (int th = 0; th < QD1; ++th) {
-                typename PH::Part hp[Q];
-#pragma unroll
-                for (int s0 = 0; s0 < Q; ++s0) hp[s0] = PH::part(tS[s0], sget<P, Q>(a, 1, l, cb[1], th), 1);
-#pragma unroll
-                for (int t0 = 0; t0 < Q; ++t0) {
-                    const typename P::SE e0 = sget<P, Q>(a, 0, l, cb[0], t0);
-                    C e[Q];
-#pragma unroll
-                    for (int s0 = 0; s0 < Q; ++s0)
-                        e[s0] = expphase_part<P, D, K>(a, tS[s0], PH::add(PH::part(tS[s0], e0, 0), hp[s0]));
-#pragma unroll
-                    for (int rb = 0; rb < RB; ++rb) {
-                        if (rb < nr) {
-                            const C ut = u[rb * WS + t0 + Q * th];
-#pragma unroll
-                            for (int s0 = 0; s0 < Q; ++s0) cmac(acc[rb][s0], e[s0], ut);
-                        }
-                    }
-                }
-            }
-#pragma unroll
-            for (int rb = 0; rb < RB; ++rb) {
-                if (rb < nr) {
-                    C *w = S + rb * SS + (tau * n + sl) * RR + sh * Q;
-#pragma unroll
-                    for (int s0 = 0; s0 < Q; ++s0) w[s0] = acc[rb][s0];
-                }
-            }
-        }
-        __syncthreads();
-        for (int rb = 0; rb < nr; ++rb)
-            for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) Wt[rb * WS + j] = S[rb * SS + j];
-        __syncthreads();
-    }
-
-    static __device__ void row_level(const KArgs<P> &a, C *Wt, C *S, int WS, int SS, int l, int i)
-    {
-        const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, nr = nrb(a);
-        for (int it = threadIdx.x; it < a.T * nblk * NC * QD1; it += blockDim.x) {
-            const int th = it % QD1;
-            const int c = (it / QD1) % NC;
-            const int beta = (it / (QD1 * NC)) % nblk;
-            const int tau = it / (QD1 * NC * nblk);
-            uint32_t Ap, Bstar, Apg, Bq;
-            int base;
-            TL::tile_of(a, tau, Ap, Bstar);
-            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            int ca[DMAX], cbq[DMAX], cb[DMAX];
-            morton_decode<D>(Apg, l, ca);
-            morton_decode<D>(Bq, L - l - 1, cbq);
-#pragma unroll
-            for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
-            const int ctr[DMAX] = {Q, Q, Q};
-            const typename PH::S sc = spoint<P, D, Q, K>(a, l, cb, ctr);
-            C ph[Q];
-#pragma unroll
-            for (int t0 = 0; t0 < Q; ++t0) {
-                const int tk[DMAX] = {t0, th, 0};
-                ph[t0] = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l, ca, tk), sc);
-            }
-#pragma unroll 1
-            for (int rb = 0; rb < nr; ++rb) {
-                const C *win = Wt + rb * WS + tau * n * RR + (base + (c << (D * i))) * RR + th * Q;
-                C z[2][Q];
-#pragma unroll
-                for (int s0 = 0; s0 < Q; ++s0) { z[0][s0] = czero<C>(); z[1][s0] = czero<C>(); }
-#pragma unroll
-                for (int t0 = 0; t0 < Q; ++t0) {
-                    const C u = cjmul(ph[t0], win[t0]);
-#pragma unroll
-                    for (int s0 = 0; s0 < Q; ++s0) {
-                        cfma(z[0][s0], a.M[0][t0][s0], u);
-                        cfma(z[1][s0], a.M[1][t0][s0], u);
-                    }
-                }
-                C *so = S + rb * SS + (((tau * nblk + beta) * NC + c) * QD1 + th) * 2 * Q;
-#pragma unroll
-                for (int s0 = 0; s0 < Q; ++s0) { so[s0] = z[0][s0]; so[Q + s0] = z[1][s0]; }
-            }
-        }
-        __syncthreads();
-        for (int it = threadIdx.x; it < a.T * nblk * NC * Q; it += blockDim.x) {
-            const int s0 = it % Q;
-            const int alpha = (it / Q) % NC;
-            const int beta = (it / (Q * NC)) % nblk;
-            const int tau = it / (Q * NC * nblk);
-            uint32_t Ap, Bstar, Apg, Bq;
-            int base;
-            TL::tile_of(a, tau, Ap, Bstar);
-            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            int ca[DMAX], cbq[DMAX];
-            morton_decode<D>((Apg << D) + alpha, l + 1, ca);
-            morton_decode<D>(Bq, L - l - 1, cbq);
-            const int a0 = alpha & 1, a1 = (alpha >> 1) & 1;
-            C ph[NC][Q];
-            {
-                typename PH::S sc[NC];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    int cb[DMAX], ctr[DMAX] = {Q, Q, Q};
-#pragma unroll
-                    for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
-                    sc[c] = spoint<P, D, Q, K>(a, l, cb, ctr);
-                }
-#pragma unroll
-                for (int s1 = 0; s1 < Q; ++s1) {
-                    const int sk[DMAX] = {s0, s1, 0};
-                    const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) ph[c][s1] = expphase<P, D, K>(a, tS, sc[c]);
-                }
-            }
-#pragma unroll 1
-            for (int rb = 0; rb < nr; ++rb) {
-                const C *Sblk = S + rb * SS + ((tau * nblk + beta) * NC) * QD1 * 2 * Q;
-                C acc[Q];
-#pragma unroll
-                for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
-                C v[NC][Q];
-#pragma unroll
-                for (int c = 0; c < NC; ++c) {
-                    const C *si = Sblk + c * QD1 * 2 * Q + a0 * Q + s0;
-#pragma unroll
-                    for (int s1 = 0; s1 < Q; ++s1) v[c][s1] = czero<C>();
-#pragma unroll
-                    for (int t1 = 0; t1 < Q; ++t1) {
-                        const C zz = si[t1 * 2 * Q];
-#pragma unroll
-                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[c][s1], a.M[a1][t1][s1], zz);
-                    }
-                }
-#pragma unroll
-                for (int s1 = 0; s1 < Q; ++s1)
-#pragma unroll
-                    for (int c = 0; c < NC; ++c) acc[s1] = TL::cadd(acc[s1], cmul(ph[c][s1], v[c][s1]));
-                C *wo = Wt + rb * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
-#pragma unroll
-                for (int sh = 0; sh < Q; ++sh) wo[sh * Q] = acc[sh];
-            }
-        }
-        __syncthreads();
-    }
-
-    static __device__ void final_eval(const KArgs<P> &a, const C *Wt, int WS)
-    {
-        const int k = a.k, n = 1 << (D * k), L = a.L, nr = nrb(a), rhs0 = blockIdx.y * RB;
-        const int cY[DMAX] = {0, 0, 0};
-        const int ctr[DMAX] = {Q, Q, Q};
-        const typename PH::S sY = spoint<P, D, Q, K>(a, L, cY, ctr);
-        for (int it = threadIdx.x; it < a.T * n; it += blockDim.x) {
-            const int sl = it % n, tau = it / n;
-            uint32_t Ap, Bstar;
-            TL::tile_of(a, tau, Ap, Bstar);
-            int ca[DMAX];
-            morton_decode<D>((Ap << (D * k)) + digit_rev<D>(sl, k), L, ca);
-            C acc[RB];
-#pragma unroll
-            for (int rb = 0; rb < RB; ++rb) acc[rb] = czero<C>();
-            for (int t = 0; t < RR; ++t) {
-                R lag = R(1);
-                int tk[DMAX], tt = t;
-#pragma unroll
-                for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.ltgt[tk[j]]; }
-                if (lag == R(0)) continue;
-                const C e = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, tk), sY);
-#pragma unroll
-                for (int rb = 0; rb < RB; ++rb)
-                    if (rb < nr) cfma(acc[rb], lag, cjmul(e, Wt[rb * WS + it * RR + t]));
-            }
-            const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
-            const C e = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, pslot), sY);
-            int64_t flat = 0;
-#pragma unroll
-            for (int j = 0; j < D; ++j) flat = (flat << L) + ca[j];
-#pragma unroll
-            for (int rb = 0; rb < RB; ++rb)
-                if (rb < nr) a.f[(int64_t)(rhs0 + rb) * a.npts + flat] = cmul(e, acc[rb]);
-        }
-    }
-
-    static __device__ void load(const KArgs<P> &a, C *Wt, int WS)
-    {
-        const int nr = nrb(a), rhs0 = blockIdx.y * RB;
-        for (int rb = 0; rb < nr; ++rb) {
-            const C *src = a.win + (int64_t)(rhs0 + rb) * a.wstride + (int64_t)blockIdx.x * WS;
-            for (int j = threadIdx.x; j < WS; j += blockDim.x) Wt[rb * WS + j] = src[j];
-        }
-    }
-
-    static __device__ void store(const KArgs<P> &a, const C *Wt, int WS)
-    {
-        const int k = a.k, n = 1 << (D * k), nr = nrb(a), rhs0 = blockIdx.y * RB;
-        const int64_t Sstar = 1LL << (D * (a.L - a.l0 - k));
-        for (int rb = 0; rb < nr; ++rb) {
-            C *dst = a.wout + (int64_t)(rhs0 + rb) * a.wstride;
-            for (int j = threadIdx.x; j < WS; j += blockDim.x) {
-                const int t = j % RR, sl = (j / RR) % n, tau = j / (RR * n);
-                uint32_t Ap, Bstar;
-                TL::tile_of(a, tau, Ap, Bstar);
-                const int64_t pair = ((int64_t)(((int64_t)Ap << (D * k)) + digit_rev<D>(sl, k))) * Sstar + Bstar;
-                dst[pair * RR + t] = Wt[rb * WS + j];
-            }
-        }
-    }
-};
-
-template <int Q, class P, int K, int RB>
-__global__ void __launch_bounds__(CfgRB<Q, P, RB>::NT, 1) k_col_pass_rb(const KArgs<P> a)
-{
-    using C = typename P::C;
-    using TR = TileRB<Q, P, K, RB>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int WS = a.T * (1 << (2 * a.k)) * TR::RR, SS = 2 * WS;
-    C *Wt = reinterpret_cast<C *>(smem_raw);
-    C *S = Wt + RB * WS;
-    if (a.flags & F_INIT)
-        TR::init(a, Wt, WS);
-    else
-        TR::load(a, Wt, WS);
-    __syncthreads();
-    for (int i = 0; i < a.k; ++i) TR::col_level(a, Wt, S, WS, SS, a.l0 + i, i);
-    if (a.flags & F_SWITCH) TR::switch_tiles(a, Wt, S, WS, SS, a.l0 + a.k);
-    TR::store(a, Wt, WS);
-}
-
-template <int Q, class P, int K, int RB>
-__global__ void __launch_bounds__(CfgRB<Q, P, RB>::NT, 1) k_row_pass_rb(const KArgs<P> a)
-{
-    using C = typename P::C;
-    using TR = TileRB<Q, P, K, RB>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int WS = a.T * (1 << (2 * a.k)) * TR::RR, SS = 2 * WS;
-    C *Wt = reinterpret_cast<C *>(smem_raw);
-    C *S = Wt + RB * WS;
-    TR::load(a, Wt, WS);
-    __syncthreads();
-    for (int i = 0; i < a.k; ++i) TR::row_level(a, Wt, S, WS, SS, a.l0 + i, i);
-    if (a.flags & F_FINAL)
-        TR::final_eval(a, Wt, WS);
-    else
-        TR::store(a, Wt, WS);
 }
 
 }  // namespace bfk

@@ -2,6 +2,7 @@
 #pragma once
 
 #include "bf_device.cuh"
+#include "bf_mr.cuh"
 #include "bf_launch.h"
 
 namespace bfl {
@@ -67,27 +68,25 @@ cudaError_t launch_row_adj(const void *kargs, unsigned gx, unsigned gy, size_t s
     return cudaGetLastError();
 }
 
-template <int Q, class P, int K, int RB>
-cudaError_t launch_col_rb(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+template <int Q, class P, int K>
+cudaError_t launch_col_mr(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
 {
     static size_t granted[64] = {0};
-    cudaError_t e = prepare(bfk::k_col_pass_rb<Q, P, K, RB>, smem, granted);
+    cudaError_t e = prepare(bfk::k_col_pass_mr<Q, P, K>, smem, granted);
     if (e != cudaSuccess) return e;
-    bfk::k_col_pass_rb<Q, P, K, RB><<<dim3(gx, gy), bfk::CfgRB<Q, P, RB>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    bfk::k_col_pass_mr<Q, P, K><<<dim3(gx, gy), bfk::CfgMR<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
     return cudaGetLastError();
 }
 
-template <int Q, class P, int K, int RB>
-cudaError_t launch_row_rb(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+template <int Q, class P, int K>
+cudaError_t launch_row_mr(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
 {
     static size_t granted[64] = {0};
-    cudaError_t e = prepare(bfk::k_row_pass_rb<Q, P, K, RB>, smem, granted);
+    cudaError_t e = prepare(bfk::k_row_pass_mr<Q, P, K>, smem, granted);
     if (e != cudaSuccess) return e;
-    bfk::k_row_pass_rb<Q, P, K, RB><<<dim3(gx, gy), bfk::CfgRB<Q, P, RB>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    bfk::k_row_pass_mr<Q, P, K><<<dim3(gx, gy), bfk::CfgMR<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
     return cudaGetLastError();
 }
-
-constexpr int kRB = 4;   // right-hand sides per CTA in the multi-RHS kernels
 
 template <int D, int Q, class P, int K>
 cudaError_t launch_ctab(const void *kargs, void *out, int levels)
@@ -104,15 +103,14 @@ const PassFns *fns_for()
 {
     using CF = bfk::Cfg<D, Q, P>;
     if constexpr (D == 2 && !P::is_f64) {
-        using CR = bfk::CfgRB<Q, P, kRB>;
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT,
-                                  launch_col_rb<Q, P, K, kRB>, launch_row_rb<Q, P, K, kRB>, CR::KMAX, CR::NP, kRB,
+                                  launch_col_mr<Q, P, K>, launch_row_mr<Q, P, K>, bfk::MRMAX, bfk::CfgMR<Q>::NT,
                                   launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
         return &f;
     } else {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
-                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, nullptr, nullptr, 0, 0, 1,
+                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, nullptr, nullptr, 0, 0,
                                   launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
         return &f;
     }

@@ -15,8 +15,9 @@ struct PassFns {
     int kmax;                    // most levels one pass fuses
     int np;                      // pairs per CTA (2^{d kmax})
     int nthreads;                // threads per CTA
-    pass_fn col_rb, row_rb;      // forward passes sharing phases over rb_count RHS (null if absent)
-    int kmax_rb, np_rb, rb_count;
+    pass_fn col_mr, row_mr;      // multi-RHS forward passes with a phase cache (null if absent)
+    int mr_max;                  // right-hand sides one multi-RHS CTA holds
+    int mr_nthreads;             // threads per multi-RHS CTA
     cudaError_t (*center_table)(const void *kargs, void *out, int levels);   // target features at box centres
     int tsize;                   // bytes of one target-feature record
 };

@@ -1,0 +1,498 @@
+// Multi-RHS forward passes for d = 2 (the batched right-hand sides of Section 1:
+// one operator, several source vectors g).
+//
+// The phase factors of every step depend only on the geometry, not on g, so a CTA
+// keeps up to MRMAX right-hand sides of its tiles in shared memory and splits each
+// merge stage in two: all threads first evaluate the stage's phase factors once
+// into a shared-memory cache, then apply them to every right-hand side.  The two
+// interpolation stages of a merge exchange partial results through scratch; they
+// run over the right-hand sides in chunks of rc, so the scratch holds rc of them.
+// The switch keeps one accumulator per right-hand side in registers and evaluates
+// each entry of the r x r phase matrix once.
+//
+// Shared memory (complex numbers, npr = pairs of the CTA):
+//   W  [nr][npr][r]       weights of every right-hand side (in place, as in Tile)
+//   S  [rc][2 npr r]      stage scratch
+//   PC [5 r npr]          phase cache of the current stage
+// Stage items, scratch layouts and the order of every accumulation follow Tile<2,...>.
+#pragma once
+
+#include "bf_device.cuh"
+
+namespace bfk {
+
+constexpr int MRMAX = 16;   // right-hand sides held by one CTA
+
+// pairs per switch round and threads per CTA: the switch runs one thread per (pair, s)
+template <int Q>
+struct CfgMR {
+    static constexpr int RR = Q * Q;
+    static constexpr int PPR = RR <= 32 ? 16 : (RR <= 64 ? 8 : 4);
+    static constexpr int NT = PPR * RR;
+    static constexpr int MINB = RR <= 32 ? 2 : 1;   // CTAs per SM the register budget is cut for
+};
+
+template <int Q, class P, int K>
+struct TileMR {
+    static constexpr int D = 2, NC = 4, RR = Q * Q, NT = CfgMR<Q>::NT;
+    using R = typename P::R;
+    using C = typename P::C;
+    using PH = Ph<P, 2, K>;
+    using TL = Tile<2, Q, P, K>;
+
+    struct Ctx {
+        int tile0;   // first tile of the CTA
+        int rhs0;    // first right-hand side
+        int nr;      // right-hand sides held (1..MRMAX)
+        int npr;     // pairs held: T 2^{2k}
+        int rc;      // right-hand sides per scratch chunk
+        int lgp;     // log2(npr)
+    };
+
+    static __device__ __forceinline__ void tile_of(const KArgs<P> &a, const Ctx &x, int tau, uint32_t &Ap,
+                                                   uint32_t &Bstar)
+    {
+        const uint32_t tile = (uint32_t)x.tile0 + (uint32_t)tau;
+        const int sh = D * (a.L - a.l0 - a.k);
+        Ap = tile >> sh;
+        Bstar = tile & ((1u << sh) - 1u);
+    }
+
+    static __device__ __forceinline__ int block_base(int beta, int i)
+    {
+        const int ra = beta & ((1 << (D * i)) - 1);
+        return ((beta >> (D * i)) << (D * (i + 1))) + ra;
+    }
+
+    // ---- CTA input: npr consecutive pairs per right-hand side
+    static __device__ void load(const KArgs<P> &a, const Ctx &x, C *W)
+    {
+        const int WS = x.npr * RR;
+        const int64_t off = (int64_t)x.tile0 * ((int64_t)RR << (D * a.k));
+        for (int j = threadIdx.x; j < x.nr * WS; j += NT) {
+            const int rb = (j / RR) >> x.lgp, e = j - rb * WS;
+            W[j] = a.win[(int64_t)(x.rhs0 + rb) * a.wstride + off + e];
+        }
+    }
+
+    // ---- CTA output: tile slots are in digit-reversed order after k merges
+    static __device__ void store(const KArgs<P> &a, const Ctx &x, const C *W)
+    {
+        const int k = a.k, n = 1 << (D * k), WS = x.npr * RR;
+        const int64_t Sstar = 1LL << (D * (a.L - a.l0 - k));
+        for (int j = threadIdx.x; j < x.nr * WS; j += NT) {
+            const int rb = (j / RR) >> x.lgp, e = j - rb * WS;
+            const int t = e % RR, sl = (e / RR) & (n - 1), tau = (e / RR) >> (D * k);
+            uint32_t Ap, Bstar;
+            tile_of(a, x, tau, Ap, Bstar);
+            const int64_t pair = ((int64_t)(((int64_t)Ap << (D * k)) + digit_rev<D>(sl, k))) * Sstar + Bstar;
+            a.wout[(int64_t)(x.rhs0 + rb) * a.wstride + pair * RR + t] = W[j];
+        }
+    }
+
+    // ---- init: PC[pair][t] = l_t(y) e^{-2pi i Phi(x0(X), y_t^B)} e^{2pi i Phi(x0(X), y)}, then W = PC g(y)
+    static __device__ void init(const KArgs<P> &a, const Ctx &x, C *W, C *PC)
+    {
+        const int k = a.k, n = 1 << (D * k), L = a.L, WS = x.npr * RR;
+        const int cX[DMAX] = {0, 0, 0};
+        const int ctr[DMAX] = {Q, Q, Q};
+        const typename PH::T tX = tpoint<P, D, Q, K>(a, 0, cX, ctr);
+        for (int it = threadIdx.x; it < WS; it += NT) {
+            const int t = it % RR, pr = it / RR;
+            const int tk[DMAX] = {t % Q, t / Q, 0};
+            const R lag = a.lsrc[tk[0]] * a.lsrc[tk[1]];
+            C e = czero<C>();
+            if (lag != R(0)) {
+                uint32_t Ap, Bstar;
+                tile_of(a, x, pr >> (D * k), Ap, Bstar);
+                int cb[DMAX];
+                morton_decode<D>((Bstar << (D * k)) + (pr & (n - 1)), L, cb);
+                const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
+                const C e1 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, pslot));
+                const C e0 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, tk));
+                e = cjmul(e0, e1);
+                e.x *= lag;
+                e.y *= lag;
+            }
+            PC[it] = e;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < x.nr * WS; j += NT) {
+            const int rb = (j / RR) >> x.lgp, it = j - rb * WS;
+            const int t = it % RR, pr = it / RR;
+            C v = czero<C>();
+            if (a.lsrc[t % Q] * a.lsrc[t / Q] != R(0)) {
+                uint32_t Ap, Bstar;
+                tile_of(a, x, pr >> (D * k), Ap, Bstar);
+                int cb[DMAX];
+                morton_decode<D>((Bstar << (D * k)) + (pr & (n - 1)), L, cb);
+                const int64_t flat = ((int64_t)cb[0] << L) + cb[1];
+                v = cmul(PC[it], a.g[(int64_t)(x.rhs0 + rb) * a.npts + flat]);
+            }
+            W[j] = v;
+        }
+        __syncthreads();
+    }
+
+    // ---- one column-form merge level (l -> l+1)
+    static __device__ void col_level(const KArgs<P> &a, const Ctx &x, C *W, C *S, C *PC, int l, int i)
+    {
+        const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
+        C *PA = PC;                  // [pA][chi][cl][tq][t0']  modulation of the inputs
+        C *PB = PC + nout * 4 * RR;  // [pA][tq][tl]            demodulation of the output
+        for (int it = threadIdx.x; it < nout * 4 * Q; it += NT) {
+            const int tq = it % Q, cl = (it / Q) & 1, chi = (it / (2 * Q)) & 1, pA = it / (4 * Q);
+            const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, x, tau, Ap, Bstar);
+            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            const uint32_t Aa = (Apg << D) + alpha;
+            int ca[DMAX], cbq[DMAX];
+            morton_decode<D>(Aa, l + 1, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+            const int c = cl | (chi << 1);
+            const typename PH::Part p1 = PH::part(tA, sget<P, Q>(a, 1, l, 2 * cbq[1] + chi, tq), 1);
+            C *o = PA + it * Q;
+#pragma unroll
+            for (int t0p = 0; t0p < Q; ++t0p) {
+                const typename PH::Part pt =
+                    PH::add(PH::part(tA, sget<P, Q>(a, 0, l, 2 * cbq[0] + (c & 1), t0p), 0), p1);
+                o[t0p] = expphase_part<P, D, K>(a, tA, pt);
+            }
+        }
+        for (int it = threadIdx.x; it < nout * RR; it += NT) {
+            const int tl = it % Q, tq = (it / Q) % Q, pA = it / RR;
+            const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, x, tau, Ap, Bstar);
+            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            const uint32_t Aa = (Apg << D) + alpha;
+            int ca[DMAX], cbq[DMAX];
+            morton_decode<D>(Aa, l + 1, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+            const typename PH::Part pl = PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], tl), 0);
+            const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 1, l + 1, cbq[1], tq), 1), pl);
+            PB[it] = expphase_part<P, D, K>(a, tA, pt);
+        }
+        __syncthreads();
+        for (int r0 = 0; r0 < x.nr; r0 += x.rc) {
+            const int nrc = min(x.rc, x.nr - r0);
+            // stage A: items (rb, pA, chi, tq): modulate the inputs, contract dimension 0
+            for (int it = threadIdx.x; it < nrc * nout * 2 * Q; it += NT) {
+                const int tq = it % Q, chi = (it / Q) & 1, pA = (it / (2 * Q)) & (nout - 1), rbl = (it / (2 * Q)) >> x.lgp;
+                const int beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
+                const int base = block_base(beta, i);
+                const C *Wr = W + (r0 + rbl) * WS + tau * n * RR;
+                const C *ph = PA + (pA * 2 + chi) * 2 * RR + tq * Q;
+                C acc[Q];
+#pragma unroll
+                for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
+#pragma unroll
+                for (int cl = 0; cl < 2; ++cl) {
+                    const int c = cl | (chi << 1);
+                    const C *win = Wr + (base + (c << (D * i))) * RR + Q * tq;
+#pragma unroll
+                    for (int t0p = 0; t0p < Q; ++t0p) {
+                        const C u = cmul(ph[cl * RR + t0p], win[t0p]);
+#pragma unroll
+                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[c & 1][t0][t0p], u);
+                    }
+                }
+                C *so = S + rbl * 2 * WS + ((pA * 2 + chi) * Q + tq) * Q;
+#pragma unroll
+                for (int j = 0; j < Q; ++j) so[j] = acc[j];
+            }
+            __syncthreads();
+            // stage B: items (rb, pA, tl): contract dimension 1 and the child bit, demodulate
+            for (int it = threadIdx.x; it < nrc * nout * Q; it += NT) {
+                const int tl = it % Q, pA = (it / Q) & (nout - 1), rbl = (it / Q) >> x.lgp;
+                const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
+                const int base = block_base(beta, i);
+                C acc[Q];
+#pragma unroll
+                for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
+#pragma unroll
+                for (int chi = 0; chi < 2; ++chi) {
+                    const C *si = S + rbl * 2 * WS + ((pA * 2 + chi) * Q) * Q + tl;
+#pragma unroll
+                    for (int tqp = 0; tqp < Q; ++tqp) {
+                        const C v = si[tqp * Q];
+#pragma unroll
+                        for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], a.M[chi][tq][tqp], v);
+                    }
+                }
+                C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + tl;
+                const C *ph = PB + pA * RR + tl;
+#pragma unroll
+                for (int tq = 0; tq < Q; ++tq) wo[tq * Q] = cjmul(ph[tq * Q], acc[tq]);
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- switch at level l: one thread per (pair, s), one accumulator per right-hand side;
+    // rounds of whole pairs, results written back after every thread of the round has read
+    static __device__ void switch_tiles(const KArgs<P> &a, const Ctx &x, C *W, int l)
+    {
+        const int k = a.k, n = 1 << (D * k), L = a.L, WS = x.npr * RR;
+        const int G = CfgMR<Q>::PPR;
+        for (int p0 = 0; p0 < x.npr; p0 += G) {
+            const int pl = p0 + (int)threadIdx.x / RR, s = (int)threadIdx.x % RR;
+            const bool act = (int)threadIdx.x < G * RR && pl < x.npr;
+            C acc[MRMAX];
+#pragma unroll
+            for (int rb = 0; rb < MRMAX; ++rb) acc[rb] = czero<C>();
+            if (act) {
+                uint32_t Ap, Bstar;
+                tile_of(a, x, pl >> (D * k), Ap, Bstar);
+                const uint32_t A = (Ap << (D * k)) + digit_rev<D>(pl & (n - 1), k);
+                int ca[DMAX], cb[DMAX];
+                morton_decode<D>(A, l, ca);
+                morton_decode<D>(Bstar, L - l, cb);
+                const int sk[DMAX] = {s % Q, s / Q, 0};
+                const typename PH::T tS = tpoint<P, D, Q, K>(a, l, ca, sk);
+                const C *u = W + pl * RR;
+#pragma unroll 1
+                for (int th = 0; th < Q; ++th) {
+                    const typename PH::Part hp = PH::part(tS, sget<P, Q>(a, 1, l, cb[1], th), 1);
+#pragma unroll
+                    for (int t0 = 0; t0 < Q; ++t0) {
+                        const C e = expphase_part<P, D, K>(
+                            a, tS, PH::add(PH::part(tS, sget<P, Q>(a, 0, l, cb[0], t0), 0), hp));
+#pragma unroll
+                        for (int rb = 0; rb < MRMAX; ++rb)
+                            if (rb < x.nr) cmac(acc[rb], e, u[rb * WS + t0 + Q * th]);
+                    }
+                }
+            }
+            __syncthreads();
+            if (act) {
+#pragma unroll
+                for (int rb = 0; rb < MRMAX; ++rb)
+                    if (rb < x.nr) W[rb * WS + pl * RR + s] = acc[rb];
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- one row-form merge level (l -> l+1)
+    static __device__ void row_level(const KArgs<P> &a, const Ctx &x, C *W, C *S, C *PC, int l, int i)
+    {
+        const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
+        C *PA = PC;              // [pin][th][t0]     pre-modulation at the parent's nodes
+        C *PB = PC + nout * RR;  // [pA][c][s1][s0]   post-modulation at the child's nodes
+        for (int it = threadIdx.x; it < nout * RR; it += NT) {
+            const int t0 = it % Q, th = (it / Q) % Q, pin = it / RR;
+            const int c = pin & (NC - 1), beta = (pin >> D) & (nblk - 1), tau = pin >> (D * k);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, x, tau, Ap, Bstar);
+            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            int ca[DMAX], cbq[DMAX], cb[DMAX];
+            morton_decode<D>(Apg, l, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+#pragma unroll
+            for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+            const int ctr[DMAX] = {Q, Q, Q};
+            const int tk[DMAX] = {t0, th, 0};
+            PA[it] = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l, ca, tk), spoint<P, D, Q, K>(a, l, cb, ctr));
+        }
+        for (int it = threadIdx.x; it < nout * RR; it += NT) {
+            const int s0 = it % Q, s1 = (it / Q) % Q, pA = it / RR;
+            const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, x, tau, Ap, Bstar);
+            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            int ca[DMAX], cbq[DMAX];
+            morton_decode<D>((Apg << D) + alpha, l + 1, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+            const int sk[DMAX] = {s0, s1, 0};
+            const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
+            typename PH::Part q0[2], q1[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                q0[h] = PH::part(tS, sget<P, Q>(a, 0, l, 2 * cbq[0] + h, Q), 0);
+                q1[h] = PH::part(tS, sget<P, Q>(a, 1, l, 2 * cbq[1] + h, Q), 1);
+            }
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+                PB[((pA * NC + c) * Q + s1) * Q + s0] = expphase_part<P, D, K>(a, tS, PH::add(q0[c & 1], q1[c >> 1]));
+        }
+        __syncthreads();
+        for (int r0 = 0; r0 < x.nr; r0 += x.rc) {
+            const int nrc = min(x.rc, x.nr - r0);
+            // stage A: items (rb, pin, th): pre-modulate input c, contract dimension 0 for both alpha_0
+            for (int it = threadIdx.x; it < nrc * nout * Q; it += NT) {
+                const int th = it % Q, pin = (it / Q) & (nout - 1), rbl = (it / Q) >> x.lgp;
+                const int c = pin & (NC - 1), beta = (pin >> D) & (nblk - 1), tau = pin >> (D * k);
+                const int base = block_base(beta, i);
+                const C *win = W + (r0 + rbl) * WS + tau * n * RR + (base + (c << (D * i))) * RR + th * Q;
+                const C *ph = PA + (pin * Q + th) * Q;
+                C z[2][Q];
+#pragma unroll
+                for (int s0 = 0; s0 < Q; ++s0) {
+                    z[0][s0] = czero<C>();
+                    z[1][s0] = czero<C>();
+                }
+#pragma unroll
+                for (int t0 = 0; t0 < Q; ++t0) {
+                    const C u = cjmul(ph[t0], win[t0]);
+#pragma unroll
+                    for (int s0 = 0; s0 < Q; ++s0) {
+                        cfma(z[0][s0], a.M[0][t0][s0], u);
+                        cfma(z[1][s0], a.M[1][t0][s0], u);
+                    }
+                }
+                C *so = S + rbl * 2 * WS + (pin * Q + th) * 2 * Q;
+#pragma unroll
+                for (int s0 = 0; s0 < Q; ++s0) {
+                    so[s0] = z[0][s0];
+                    so[Q + s0] = z[1][s0];
+                }
+            }
+            __syncthreads();
+            // stage B: items (rb, pA, s0): contract dimension 1 per child, post-modulate, sum over c
+            for (int it = threadIdx.x; it < nrc * nout * Q; it += NT) {
+                const int s0 = it % Q, pA = (it / Q) & (nout - 1), rbl = (it / Q) >> x.lgp;
+                const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
+                const int base = block_base(beta, i);
+                const int a0 = alpha & 1, a1 = alpha >> 1;
+                const C *Sblk = S + rbl * 2 * WS + (pA - alpha) * Q * 2 * Q;
+                C v[NC][Q];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const C *si = Sblk + c * Q * 2 * Q + a0 * Q + s0;
+#pragma unroll
+                    for (int s1 = 0; s1 < Q; ++s1) v[c][s1] = czero<C>();
+#pragma unroll
+                    for (int t1 = 0; t1 < Q; ++t1) {
+                        const C zz = si[t1 * 2 * Q];
+#pragma unroll
+                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[c][s1], a.M[a1][t1][s1], zz);
+                    }
+                }
+                C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
+                const C *ph = PB + pA * NC * RR + s0;
+#pragma unroll
+                for (int s1 = 0; s1 < Q; ++s1) {
+                    C acc = czero<C>();
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc = TL::cadd(acc, cmul(ph[(c * Q + s1) * Q], v[c][s1]));
+                    wo[s1 * Q] = acc;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // ---- final evaluation: PC[pair][t] = l_t(x) conj(e^{2pi i Phi(x_t, y0(Y))}), PC[pair][r] = e^{2pi i Phi(x, y0(Y))}
+    static __device__ void final_eval(const KArgs<P> &a, const Ctx &x, const C *W, C *PC)
+    {
+        const int k = a.k, n = 1 << (D * k), L = a.L, WS = x.npr * RR;
+        const int cY[DMAX] = {0, 0, 0};
+        const int ctr[DMAX] = {Q, Q, Q};
+        const typename PH::S sY = spoint<P, D, Q, K>(a, L, cY, ctr);
+        for (int it = threadIdx.x; it < x.npr * (RR + 1); it += NT) {
+            const int t = it % (RR + 1), pl = it / (RR + 1);
+            C e = czero<C>();
+            const R lag = t < RR ? a.ltgt[t % Q] * a.ltgt[t / Q] : R(1);
+            if (lag != R(0)) {
+                uint32_t Ap, Bstar;
+                tile_of(a, x, pl >> (D * k), Ap, Bstar);
+                int ca[DMAX];
+                morton_decode<D>((Ap << (D * k)) + digit_rev<D>(pl & (n - 1), k), L, ca);
+                const int tk[DMAX] = {t < RR ? t % Q : Q + 1, t < RR ? t / Q : Q + 1, 0};
+                const C e0 = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, tk), sY);
+                if (t < RR) {
+                    e.x = lag * e0.x;
+                    e.y = -lag * e0.y;
+                } else {
+                    e = e0;
+                }
+            }
+            PC[it] = e;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < x.nr * x.npr; j += NT) {
+            const int pl = j & (x.npr - 1), rb = j >> x.lgp;
+            const C *pc = PC + pl * (RR + 1);
+            const C *w = W + rb * WS + pl * RR;
+            C acc = czero<C>();
+            for (int t = 0; t < RR; ++t)
+                if (a.ltgt[t % Q] * a.ltgt[t / Q] != R(0)) cmac(acc, pc[t], w[t]);
+            uint32_t Ap, Bstar;
+            tile_of(a, x, pl >> (D * k), Ap, Bstar);
+            int ca[DMAX];
+            morton_decode<D>((Ap << (D * k)) + digit_rev<D>(pl & (n - 1), k), L, ca);
+            const int64_t flat = ((int64_t)ca[0] << L) + ca[1];
+            a.f[(int64_t)(x.rhs0 + rb) * a.npts + flat] = cmul(pc[RR], acc);
+        }
+    }
+
+    // shared memory of one CTA, bytes
+    static __host__ __device__ size_t smem_bytes(int npr, int nr, int rc)
+    {
+        return (size_t)npr * RR * sizeof(C) * (size_t)(nr + 2 * rc + 5);
+    }
+
+    static __device__ __forceinline__ Ctx ctx(const KArgs<P> &a)
+    {
+        Ctx x;
+        x.tile0 = (int)blockIdx.x * a.T;
+        x.rhs0 = (int)blockIdx.y * MRMAX;
+        x.nr = min(MRMAX, a.nrhs - x.rhs0);
+        x.npr = a.T << (D * a.k);
+        x.rc = a.rc;
+        x.lgp = __ffs(x.npr) - 1;
+        return x;
+    }
+};
+
+template <int Q, class P, int K>
+__global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_col_pass_mr(const KArgs<P> a)
+{
+    using C = typename P::C;
+    using TM = TileMR<Q, P, K>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const typename TM::Ctx x = TM::ctx(a);
+    const int WS = x.npr * TM::RR;
+    C *W = reinterpret_cast<C *>(smem_raw);
+    C *S = W + x.nr * WS;
+    C *PC = S + x.rc * 2 * WS;
+    if (a.flags & F_INIT) {
+        TM::init(a, x, W, PC);
+    } else {
+        TM::load(a, x, W);
+        __syncthreads();
+    }
+    for (int i = 0; i < a.k; ++i) TM::col_level(a, x, W, S, PC, a.l0 + i, i);
+    if (a.flags & F_SWITCH) TM::switch_tiles(a, x, W, a.l0 + a.k);
+    TM::store(a, x, W);
+}
+
+template <int Q, class P, int K>
+__global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_row_pass_mr(const KArgs<P> a)
+{
+    using C = typename P::C;
+    using TM = TileMR<Q, P, K>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const typename TM::Ctx x = TM::ctx(a);
+    const int WS = x.npr * TM::RR;
+    C *W = reinterpret_cast<C *>(smem_raw);
+    C *S = W + x.nr * WS;
+    C *PC = S + x.rc * 2 * WS;
+    TM::load(a, x, W);
+    __syncthreads();
+    for (int i = 0; i < a.k; ++i) TM::row_level(a, x, W, S, PC, a.l0 + i, i);
+    if (a.flags & F_FINAL)
+        TM::final_eval(a, x, W, PC);
+    else
+        TM::store(a, x, W);
+}
+
+}  // namespace bfk
