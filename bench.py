@@ -267,6 +267,7 @@ def run_ours(args, rank, world, local_rank):
     all_ops = sum(work_ops(spec, pass_work(spec, p, nrhs)) for p in passes)
     roofline["apply_frac"] = round(all_ops / (ms * 1e-3) / 1e12 / peak, 4)
     roofline["measured_fma_tflops"] = {"fp32": round(bf.measure_fma_rate(False), 1),
+                                       "fp32_packed_pairs": round(bf.measure_fma_rate(packed=True), 1),
                                        "fp64": round(bf.measure_fma_rate(True), 3)}
 
     # ---- FP64 GPU butterfly on the same problem (the baseline of the speedup)

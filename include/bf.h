@@ -165,9 +165,17 @@ bf_status bf_pass_info(bf_plan plan, int nrhs, int i, int *kind, int *l0, int *k
  *     (BF_ERR_INVALID_ARG for an FP64 plan). */
 bf_status bf_selfcheck_sincos(int n, double *max_abs_err);
 /* Measured FMA rate of the current device in TFLOP/s (an FMA counts 2): fp64 = 0 for
- * FP32, 1 for FP64.  Independent dependent-FMA chains on every SM, timed with events;
- * the context for the FP32-issue roofline and for evaluating phases in double-float. */
+ * FP32, 1 for FP64, 2 for FP32 in packed pairs (one instruction, two FMAs).  Independent
+ * dependent-FMA chains on every SM, timed with events; the context for the FP32-issue
+ * roofline and for evaluating phases in double-float. */
 bf_status bf_measure_fma_rate(int fp64, double *tflops);
+/* Phase-evaluation rate of a mixed-precision d = 2 plan, in 10^9 phase factors per second:
+ * a compute-only kernel evaluates e^{2 pi i Phi} for (target node, source node) pairs of
+ * the plan's tables held in registers, one at a time (paired = 0) or two per float2
+ * (paired = 1).  The practical ceiling of the phase work (Section 1.4: every translation
+ * and the switch are dominated by these evaluations).  BF_ERR_INVALID_ARG for FP64 or
+ * d = 3 plans. */
+bf_status bf_measure_phase_rate(bf_plan plan, int paired, double *gphases_per_s);
 bf_status bf_selfcheck_phase(bf_plan plan, int n, double *max_err_cycles);
 
 /* Forward apply that allocates no device memory.  The paper has no counterpart:

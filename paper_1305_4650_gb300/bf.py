@@ -22,7 +22,8 @@ STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_E
 
 EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_apply_host",
            "bf_apply_batched", "bf_destroy", "bf_status_string", "bf_last_cuda_error", "bf_plan_info",
-           "bf_apply_pass", "bf_pass_info", "bf_pass_count", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate"]
+           "bf_apply_pass", "bf_pass_info", "bf_pass_count", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate",
+           "bf_measure_phase_rate"]
 
 
 class BfError(RuntimeError):
@@ -72,6 +73,7 @@ def load():
         lib.bf_selfcheck_sincos.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_selfcheck_phase.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_measure_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
+        lib.bf_measure_phase_rate.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         for name in EXPORTS:
             getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
         lib.bf_status_string.restype = ctypes.c_char_p
@@ -226,6 +228,13 @@ class Plan:
         _check(load().bf_selfcheck_phase(self._h, n, ctypes.byref(e)), "bf_selfcheck_phase", self._h)
         return e.value
 
+    def phase_rate(self, paired: bool = False) -> float:
+        """Measured phase factors per second (10^9) of this plan's phase, one or two per instruction stream."""
+        e = ctypes.c_double()
+        _check(load().bf_measure_phase_rate(self._h, 1 if paired else 0, ctypes.byref(e)), "bf_measure_phase_rate",
+               self._h)
+        return e.value
+
     def last_cuda_error(self) -> int:
         e = ctypes.c_int()
         _check(load().bf_last_cuda_error(self._h, ctypes.byref(e)), "bf_last_cuda_error")
@@ -250,10 +259,12 @@ def selfcheck_sincos(n: int = 1 << 22) -> float:
     return e.value
 
 
-def measure_fma_rate(fp64: bool = False) -> float:
-    """Measured FP32 (or FP64) FMA rate of the current device, TFLOP/s."""
+def measure_fma_rate(fp64: bool = False, packed: bool = False) -> float:
+    """Measured FMA rate of the current device, TFLOP/s: FP32, FP64 (fp64=True) or FP32 in
+    packed pairs (packed=True)."""
     e = ctypes.c_double()
-    _check(load().bf_measure_fma_rate(1 if fp64 else 0, ctypes.byref(e)), "bf_measure_fma_rate")
+    mode = 1 if fp64 else (2 if packed else 0)
+    _check(load().bf_measure_fma_rate(mode, ctypes.byref(e)), "bf_measure_fma_rate")
     return e.value
 
 

@@ -709,7 +709,7 @@ bf_status bf_selfcheck_sincos(int n, double *max_abs_err)
 
 bf_status bf_measure_fma_rate(int fp64, double *tflops)
 {
-    if (!tflops || (fp64 != 0 && fp64 != 1)) return BF_ERR_INVALID_ARG;
+    if (!tflops || fp64 < 0 || fp64 > 2) return BF_ERR_INVALID_ARG;
     return bfl::measure_fma(fp64, tflops) == cudaSuccess ? BF_OK : BF_ERR_CUDA;
 }
 
@@ -721,6 +721,17 @@ bf_status bf_selfcheck_phase(bf_plan p, int n, double *max_err_cycles)
     fill_args<bfk::PMIX>(p, am);
     fill_args<bfk::PF64>(p, ad);
     cudaError_t e = bfl::selfcheck_phase(&am, &ad, p->d, p->L, p->q, p->kind, n, max_err_cycles);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    return BF_OK;
+}
+
+bf_status bf_measure_phase_rate(bf_plan p, int paired, double *gphases_per_s)
+{
+    if (!p || !gphases_per_s || p->prec == BF_PREC_FP64 || p->d != 2 || (paired != 0 && paired != 1))
+        return BF_ERR_INVALID_ARG;
+    bfk::KArgs<bfk::PMIX> am;
+    fill_args<bfk::PMIX>(p, am);
+    cudaError_t e = bfl::phase_rate(&am, p->prec == BF_PREC_MIXED_SFU, p->L, p->q, p->kind, paired, gphases_per_s);
     if (e != cudaSuccess) return cuda_fail(p, e);
     return BF_OK;
 }

@@ -40,6 +40,7 @@ BFL_DECLARE(3, sfu, dot) BFL_DECLARE(3, sfu, genradon) BFL_DECLARE(3, sfu, separ
 // device self-checks and the FMA rate probe (bf_selfcheck.cu)
 cudaError_t measure_fma(int fp64, double *tflops);
 cudaError_t selfcheck_sincos(int n, double *max_err);
+cudaError_t phase_rate(const void *kargs_mix, int sfu, int L, int q, int kind, int paired, double *gphases);
 cudaError_t selfcheck_phase(const void *kargs_mix, const void *kargs_f64, int d, int L, int q, int kind, int n,
                             double *max_err);
 

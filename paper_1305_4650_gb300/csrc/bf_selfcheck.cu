@@ -7,6 +7,7 @@
 
 #include "bf_device.cuh"
 #include "bf_launch.h"
+#include "bf_pair.cuh"
 
 namespace {
 
@@ -87,6 +88,25 @@ __global__ void k_fma32(int iters, float *out)
     out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
+// packed pairs: one instruction does two FP32 FMAs (sm_100 and later)
+__global__ void k_fma32x2(int iters, float *out)
+{
+    const float f = threadIdx.x;
+    float2 a0 = make_float2(f, f + 1), a1 = make_float2(f + 2, f + 3), a2 = make_float2(f + 4, f + 5),
+           a3 = make_float2(f + 6, f + 7), a4 = make_float2(f + 8, f + 9), a5 = make_float2(f + 10, f + 11),
+           a6 = make_float2(f + 12, f + 13), a7 = make_float2(f + 14, f + 15);
+    const float2 b = make_float2(0.999f, 0.999f), c = make_float2(0.001f, 0.001f);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            a0 = __ffma2_rn(a0, b, c); a1 = __ffma2_rn(a1, b, c); a2 = __ffma2_rn(a2, b, c); a3 = __ffma2_rn(a3, b, c);
+            a4 = __ffma2_rn(a4, b, c); a5 = __ffma2_rn(a5, b, c); a6 = __ffma2_rn(a6, b, c); a7 = __ffma2_rn(a7, b, c);
+        }
+    }
+    out[blockIdx.x * blockDim.x + threadIdx.x] =
+        a0.x + a1.x + a2.x + a3.x + a4.x + a5.x + a6.x + a7.x + a0.y + a1.y + a2.y + a3.y + a4.y + a5.y + a6.y + a7.y;
+}
+
 __global__ void k_fma64(int iters, double *out)
 {
     double a0 = threadIdx.x, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
@@ -98,9 +118,125 @@ __global__ void k_fma64(int iters, double *out)
     out[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3;
 }
 
+// Phase-evaluation rate (d = 2): every thread holds two target nodes and 4 + 4
+// per-dimension source entries of a plan's tables and evaluates e^{2 pi i Phi} for
+// all 2 x 4 x 4 combinations per iteration, with the part of source coordinate 1
+// hoisted as in the kernels; every source entry moves every iteration (16 adds per
+// 32 phases) so nothing is loop invariant.  PAIRED = 1 evaluates the two targets in the lanes of a float2.
+template <class P, int K, int PAIRED>
+__global__ void k_phase_rate(const bfk::KArgs<P> a, int L, int q, int iters, float *out)
+{
+    using PH = bfk::Ph<P, 2, K>;
+    using PH2 = bfk::Ph2<P, 2, K>;
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t h = hash32(tid + 1);
+    const int lv = L / 2;
+    typename PH::T tg[2];
+    for (int j = 0; j < 2; ++j) {
+        typename P::TE e[2];
+        for (int k = 0; k < 2; ++k) {
+            h = hash32(h);
+            e[k] = a.tt[k][((1LL << lv) - 1) * (q + 2) + (int64_t)(h % (1u << lv)) * (q + 2) + (h >> 24) % q];
+        }
+        tg[j] = PH::tgt(a, e);
+    }
+    typename P::SE s0[4], s1[4];
+    for (int j = 0; j < 4; ++j) {
+        h = hash32(h);
+        const int64_t off = ((2LL << L) - (2LL << (L - lv))) * (q + 2);
+        s0[j] = a.st[0][off + (int64_t)(h % (1u << (L - lv))) * (q + 2) + (h >> 24) % q];
+        h = hash32(h);
+        s1[j] = a.st[1][off + (int64_t)(h % (1u << (L - lv))) * (q + 2) + (h >> 24) % q];
+    }
+    float2 acc = make_float2(0.f, 0.f);
+    const typename PH2::T t2 = PH2::pair(tg[0], tg[1]);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            s0[j].a.x = __fadd_rn(s0[j].a.x, 1e-3f);
+            s0[j].a.z = __fadd_rn(s0[j].a.z, 1e-3f);
+            s1[j].a.x = __fadd_rn(s1[j].a.x, 1e-3f);
+            s1[j].a.z = __fadd_rn(s1[j].a.z, 1e-3f);
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            if constexpr (PAIRED) {
+                const typename PH2::Part hp = PH2::part(t2, s1[j], s1[j], 1);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float2 e0, e1;
+                    bfk::expphase_part2<P, 2, K>(a, t2, PH2::add(PH2::part(t2, s0[i], s0[i], 0), hp), e0, e1);
+                    acc.x += e0.x + e1.x;
+                    acc.y += e0.y + e1.y;
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const typename PH::Part hp = PH::part(tg[u], s1[j], 1);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 e = bfk::expphase_part<P, 2, K>(a, tg[u], PH::add(PH::part(tg[u], s0[i], 0), hp));
+                        acc.x += e.x;
+                        acc.y += e.y;
+                    }
+                }
+            }
+        }
+    }
+    out[tid] = acc.x + acc.y;
+}
+
+template <class P>
+cudaError_t phase_rate_t(const void *kargs, int L, int q, int kind, int paired, double *gphases)
+{
+    const bfk::KArgs<P> &a = *static_cast<const bfk::KArgs<P> *>(kargs);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = sms * 8, threads = 256, iters = 200;
+    float *out = nullptr;
+    cudaError_t e = cudaMalloc(&out, (size_t)blocks * threads * sizeof(float));
+    if (e != cudaSuccess) return e;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto launch = [&](int n) {
+#define BF_PR(KK)                                                                                         \
+    (paired ? k_phase_rate<P, KK, 1><<<blocks, threads>>>(a, L, q, n, out)                                \
+            : k_phase_rate<P, KK, 0><<<blocks, threads>>>(a, L, q, n, out))
+        switch (kind) {
+        case bfk::KIND_DOT: BF_PR(bfk::KIND_DOT); break;
+        case bfk::KIND_GENRADON: BF_PR(bfk::KIND_GENRADON); break;
+        case bfk::KIND_HYPRADON: BF_PR(bfk::KIND_HYPRADON); break;
+        default: BF_PR(bfk::KIND_SEPARABLE); break;
+        }
+#undef BF_PR
+    };
+    launch(4);
+    cudaEventRecord(e0);
+    launch(iters);
+    cudaEventRecord(e1);
+    e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *gphases = (double)blocks * threads * iters * 32 / (ms * 1e-3) / 1e9;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e;
+}
+
 }  // namespace
 
 namespace bfl {
+
+cudaError_t phase_rate(const void *kargs, int sfu, int L, int q, int kind, int paired, double *gphases)
+{
+    return sfu ? phase_rate_t<bfk::PMIXF>(kargs, L, q, kind, paired, gphases)
+               : phase_rate_t<bfk::PMIX>(kargs, L, q, kind, paired, gphases);
+}
+
 
 cudaError_t measure_fma(int fp64, double *tflops)
 {
@@ -114,11 +250,13 @@ cudaError_t measure_fma(int fp64, double *tflops)
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int iters = fp64 ? 100 : 2000;
+    const int iters = fp64 == 1 ? 100 : 2000;
     for (int rep = 0; rep < 2; ++rep) {
         if (rep == 1) cudaEventRecord(e0);
-        if (fp64)
+        if (fp64 == 1)
             k_fma64<<<blocks, threads>>>(rep ? iters : 2, static_cast<double *>(out));
+        else if (fp64 == 2)
+            k_fma32x2<<<blocks, threads>>>(rep ? iters : 10, static_cast<float *>(out));
         else
             k_fma32<<<blocks, threads>>>(rep ? iters : 10, static_cast<float *>(out));
     }
@@ -126,7 +264,7 @@ cudaError_t measure_fma(int fp64, double *tflops)
     e = cudaEventSynchronize(e1);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    const double flops = 2.0 * blocks * threads * (double)iters * 16 * (fp64 ? 4 : 8);
+    const double flops = 2.0 * blocks * threads * (double)iters * 16 * (fp64 == 1 ? 4 : fp64 == 2 ? 16 : 8);
     *tflops = flops / (ms * 1e-3) / 1e12;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
