@@ -380,7 +380,9 @@ def run_ours(args, rank, world, local_rank):
 
 def run_batched(args, rank, world, local_rank):
     """48 hyperbolic Radon problems (16 each of N = 128, 256, 512; 1..16 RHS each, drawn from the
-    seed) applied by one bf_apply_batched call, captured once in a CUDA graph and replayed.
+    seed) applied by one persistent kernel launch per step (bf_batch_apply), captured once in a
+    CUDA graph and replayed; the same problems as one launch per pass (bf_apply_batched) are
+    timed beside it.
     Under torchrun the problems are dealt round-robin to the ranks (independent problems,
     no exchange); value = all ranks' points*RHS / max time."""
     import numpy as np
@@ -402,38 +404,52 @@ def run_batched(args, rank, world, local_rank):
         nr.append(k)
     pts_rhs_local = sum(s.npts * k for _, s, k in mine)
     pts_rhs = sum(s.npts * k for s, k in probs)
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        for _ in range(2):                               # kernel attributes set before capture
-            bf.apply_batched(plans, gs, fs, nr, stream=side)
-    torch.cuda.current_stream().wait_stream(side)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        bf.apply_batched(plans, gs, fs, nr)
-    for _ in range(args.warmup):
-        graph.replay()
-    torch.cuda.synchronize()
+    batch = bf.Batch(plans, nr)
+    binfo = batch.info()
     stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with Clocks(local_rank) as clk:
-        if world > 1:
-            dist.barrier()
+
+    def timed_graph(fn):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):                               # kernel attributes set before capture
+                fn(side)
+        torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(args.steps):
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            fn(None)
+        for _ in range(args.warmup):
             graph.replay()
-        e1.record(stream)
         torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with Clocks(local_rank) as clk:
+            if world > 1:
+                dist.barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            for _ in range(args.steps):
+                graph.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if world > 1:
+                dist.barrier()
+        t = e0.elapsed_time(e1) / args.steps
         if world > 1:
-            dist.barrier()
-    ms = e0.elapsed_time(e1) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    launches = sum(p.launches(k) for p, k in zip(plans, nr))
+            tt = torch.tensor([t], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t, clk.summary()
+
+    # headline: one persistent launch per step; comparison: one launch per pass of every problem
+    ms, clocks = timed_graph(lambda st: batch.apply(gs, fs, stream=st))
+    timed_out = batch.status()
+    waits = batch.wait_stats()
+    ms_seq, _ = timed_graph(lambda st: bf.apply_batched(plans, gs, fs, nr, stream=st))
+    batch.apply(gs, fs)
+    torch.cuda.synchronize()
+    launches = 1
+    seq_launches = sum(p.launches(k) for p, k in zip(plans, nr))
     acc = None
     if rank == 0 and not args.no_accuracy:
         # problem 0 (N = 128) against the oracle butterfly, all outputs, every RHS
@@ -444,6 +460,7 @@ def run_batched(args, rank, world, local_rank):
         out = fs[0].cpu().numpy()
         acc = {"rel_l2_vs_oracle_butterfly": float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
                "sample": f"problem {i0} (N={s0.N}, {k0} RHS), all outputs"}
+    batch.close()
     for p in plans:
         p.close()
     if rank != 0:
@@ -453,9 +470,16 @@ def run_batched(args, rank, world, local_rank):
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": "hypradon48_q5", "problems": len(probs), "N": [128, 256, 512],
                        "nrhs_total": int(sum(nr)) if world == 1 else None, "points_rhs": pts_rhs,
-                       "points_rhs_rank0": pts_rhs_local, "precision": "mixed", "graph": "one CUDA graph per step",
+                       "points_rhs_rank0": pts_rhs_local, "precision": "mixed",
+                       "launch": f"one persistent kernel per step (CUDA graph): {binfo['units']} work units in "
+                                 f"{binfo['jobs']} jobs on {binfo['grid']} CTAs",
                        "parallelism": f"problems round-robin over {world} rank(s)"},
-            "accuracy": acc, "gpu_launches": args.steps * launches, "clocks": clk.summary()}
+            "per_problem_passes": {"ms_per_step": round(ms_seq, 3), "value": pts_rhs / (ms_seq * 1e-3),
+                                   "launches_per_step": seq_launches},
+            "batch_wait_timed_out": timed_out,
+            "batch_dependency_waits": {"cta_ms_per_step": round(waits["wait_ms_total"], 3), "waits": waits["waits"],
+                                       "cta_slots": binfo["grid"]},
+            "accuracy": acc, "gpu_launches": args.steps * launches, "clocks": clocks}
 
 
 def run_cg(args, rank, world, local_rank):

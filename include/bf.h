@@ -124,6 +124,41 @@ bf_status bf_apply_host(bf_plan plan, const void *g_host, void *f_host, int nrhs
 bf_status bf_apply_batched(const bf_plan *plans, const void *const *g_dev, void *const *f_dev,
                            const int *nrhs, int count, void *stream);
 
+/* Persistent batches.  A batch fixes a list of independent problems (plans, d = 2,
+ * mixed precision, all with the same q, phase kind and precision) and their numbers
+ * of right-hand sides; bf_batch_apply then runs every pass of every problem in ONE
+ * kernel launch.  The launch keeps as many CTAs as fit on the device; they take
+ * work units (one CTA's tiles of one pass of one problem, for a block of up to 16
+ * right-hand sides) from a queue ordered by pass index, and a unit of pass j waits
+ * until the same problem's pass j-1 has finished (a counter in device memory).  The
+ * butterflies are independent (the many transforms of Section 3.1), so the queue
+ * fills the GPU across problems of uneven N.
+ *   bf_batch_create: plans[i] with nrhs[i] (1..max_nrhs) right-hand sides, count in
+ *     1..256, each plan at most once (its workspace serves one problem).  Allocates
+ *     the job table and counters (a few KB).  BF_ERR_UNSUPPORTED if the plans do not
+ *     qualify (use bf_apply_batched then).  The plans must outlive the batch.
+ *   bf_batch_apply: f_dev[i] = B_i g_dev[i], asynchronous on the stream (device
+ *     pointers, 16-byte aligned); one memset and one launch, capturable in a CUDA graph.
+ *   bf_batch_status: synchronises the device and reports whether a wait of the last
+ *     apply gave up (a dependency not met within 4 s; the unit and every later one are
+ *     then skipped, their outputs undefined) -- the kernel never waits unboundedly.
+ *   bf_batch_selftest_timeout: runs the batch with every wait's target one above what
+ *     can be reached and a 20 ms limit, synchronises, and reports the flag (1 expected;
+ *     outputs undefined); shows that a missed dependency ends in an error, not a hang.
+ *   bf_batch_info: jobs, work units, CTAs of the launch, shared memory per CTA.
+ *   bf_batch_wait_stats: synchronises the device; total time the CTAs of the last
+ *     apply spent waiting for dependencies (summed over CTAs, ms) and the number of
+ *     waits that did not find their dependency already met. */
+typedef struct bf_batch_s *bf_batch;
+bf_status bf_batch_create(const bf_plan *plans, const int *nrhs, int count, bf_batch *out);
+bf_status bf_batch_apply(bf_batch batch, const void *const *g_dev, void *const *f_dev, void *stream);
+bf_status bf_batch_status(bf_batch batch, int *timed_out);
+bf_status bf_batch_selftest_timeout(bf_batch batch, const void *const *g_dev, void *const *f_dev, void *stream,
+                                    int *timed_out);
+bf_status bf_batch_info(bf_batch batch, int *jobs, int *units, int *grid, int64_t *smem_bytes);
+bf_status bf_batch_wait_stats(bf_batch batch, double *wait_ms_total, int64_t *waits);
+bf_status bf_batch_destroy(bf_batch batch);
+
 /* Release the plan and its device memory.  bf_destroy(NULL) is a no-op.  The caller
  * must ensure no apply on this plan is still running. */
 bf_status bf_destroy(bf_plan plan);

@@ -23,7 +23,8 @@ STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_E
 EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint", "bf_apply_host",
            "bf_apply_batched", "bf_destroy", "bf_status_string", "bf_last_cuda_error", "bf_plan_info",
            "bf_apply_pass", "bf_pass_info", "bf_pass_count", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate",
-           "bf_measure_phase_rate"]
+           "bf_measure_phase_rate", "bf_batch_create", "bf_batch_apply", "bf_batch_status",
+           "bf_batch_selftest_timeout", "bf_batch_info", "bf_batch_wait_stats", "bf_batch_destroy"]
 
 
 class BfError(RuntimeError):
@@ -74,6 +75,14 @@ def load():
         lib.bf_selfcheck_phase.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_measure_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_measure_phase_rate.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+        lib.bf_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), i32, ctypes.POINTER(vp)]
+        lib.bf_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+        lib.bf_batch_status.argtypes = [vp, ctypes.POINTER(i32)]
+        lib.bf_batch_selftest_timeout.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp, ctypes.POINTER(i32)]
+        lib.bf_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                      ctypes.POINTER(i64)]
+        lib.bf_batch_destroy.argtypes = [vp]
+        lib.bf_batch_wait_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in EXPORTS:
             getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
         lib.bf_status_string.restype = ctypes.c_char_p
@@ -277,6 +286,69 @@ def apply_batched(plans, gs, fs, nrhs, stream=None) -> None:
     F = (vp * n)(*[f.data_ptr() for f in fs])
     R = (ctypes.c_int * n)(*nrhs)
     _check(load().bf_apply_batched(P, G, F, R, n, _stream_ptr(stream)), "bf_apply_batched")
+
+
+class Batch:
+    """Persistent batch: every pass of every problem in one kernel launch (bf_batch_*)."""
+
+    def __init__(self, plans, nrhs):
+        vp = ctypes.c_void_p
+        n = len(plans)
+        self.plans = list(plans)          # keep the plans alive
+        self.nrhs = list(nrhs)
+        P = (vp * n)(*[p.handle for p in plans])
+        R = (ctypes.c_int * n)(*nrhs)
+        h = vp()
+        _check(load().bf_batch_create(P, R, n, ctypes.byref(h)), "bf_batch_create")
+        self._h = h
+
+    def _ptrs(self, gs, fs):
+        vp = ctypes.c_void_p
+        n = len(self.plans)
+        if len(gs) != n or len(fs) != n:
+            raise ValueError("one g and one f per problem")
+        return (vp * n)(*[g.data_ptr() for g in gs]), (vp * n)(*[f.data_ptr() for f in fs])
+
+    def apply(self, gs, fs, stream=None) -> None:
+        G, F = self._ptrs(gs, fs)
+        _check(load().bf_batch_apply(self._h, G, F, _stream_ptr(stream)), "bf_batch_apply")
+
+    def status(self) -> bool:
+        """True if a wait of the last apply timed out (synchronises the device)."""
+        t = ctypes.c_int()
+        _check(load().bf_batch_status(self._h, ctypes.byref(t)), "bf_batch_status")
+        return bool(t.value)
+
+    def selftest_timeout(self, gs, fs, stream=None) -> bool:
+        G, F = self._ptrs(gs, fs)
+        t = ctypes.c_int()
+        _check(load().bf_batch_selftest_timeout(self._h, G, F, _stream_ptr(stream), ctypes.byref(t)),
+               "bf_batch_selftest_timeout")
+        return bool(t.value)
+
+    def info(self) -> dict:
+        i32, i64 = ctypes.c_int, ctypes.c_int64
+        j, u, g, sm = i32(), i32(), i32(), i64()
+        _check(load().bf_batch_info(self._h, ctypes.byref(j), ctypes.byref(u), ctypes.byref(g), ctypes.byref(sm)),
+               "bf_batch_info")
+        return dict(jobs=j.value, units=u.value, grid=g.value, smem_bytes=sm.value)
+
+    def wait_stats(self) -> dict:
+        """Dependency waits of the last apply: total CTA-milliseconds and count (synchronises)."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(load().bf_batch_wait_stats(self._h, ctypes.byref(ms), ctypes.byref(n)), "bf_batch_wait_stats")
+        return dict(wait_ms_total=ms.value, waits=n.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            load().bf_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def apply_noalloc(d: int, N: int, q: int, phase: str, g, f, precision: str = "mixed", scale: float = 1.0,

@@ -10,6 +10,8 @@
 #include "../../include/bf.h"
 #include "bf_device.cuh"
 #include "bf_launch.h"
+#include "bf_mr.cuh"
+#include <algorithm>
 
 namespace {
 
@@ -43,6 +45,19 @@ struct bf_plan_s {
     int mr_rc = 1;                 // right-hand sides per scratch chunk of the multi-RHS kernels
     std::vector<Pass> passes_adj;  // schedule whose reverse is the adjoint (fits the row caches)
     const bfl::PassFns *fns = nullptr;
+    int last_cuda = 0;
+};
+
+struct bf_batch_s {
+    int count = 0, njobs = 0, units = 0, prec = 0;
+    size_t smem = 0;
+    unsigned grid = 0;
+    const bfl::PassFns *fns = nullptr;
+    void *desc = nullptr;       // device: KArgs per (problem, pass)
+    void *jobs = nullptr;       // device: BatchJob per job, in queue order
+    void *state = nullptr;      // device: 2 x u64 wait statistics, then the counters below
+    unsigned *ctr = nullptr;    // device: [njobs] counters, [njobs] queue head, [njobs + 1] error flag
+    float M[2][bfk::QMAX][bfk::QMAX] = {};   // child->parent matrices shared by the problems
     int last_cuda = 0;
 };
 
@@ -408,6 +423,152 @@ bool supported_q(int d, int q) { return bfl::get_fns(d, q, 1, 0) != nullptr && b
 
 }  // namespace
 
+// ---------------------------------------------------------------- batches
+
+namespace {
+
+template <class P>
+bf_status batch_build(bf_batch b, const bf_plan *plans, const int *nrhs, int count)
+{
+    std::vector<bfk::KArgs<P>> desc;
+    struct J { bfk::BatchJob j; int pass; int key; };
+    std::vector<J> jobs;
+    std::vector<int> desc0(count);
+    size_t smem = 0;
+    for (int i = 0; i < count; ++i) {
+        const bf_plan p = plans[i];
+        const int nr = nrhs[i] < p->fns->mr_max ? nrhs[i] : p->fns->mr_max;
+        const int rc = p->mr_rc < nr ? p->mr_rc : nr;
+        const int ny = (nrhs[i] + p->fns->mr_max - 1) / p->fns->mr_max;
+        void *buf[2] = {p->w0, p->w1};
+        desc0[i] = (int)desc.size();
+        for (size_t j = 0; j < p->passes_mr.size(); ++j) {
+            const Pass &ps = p->passes_mr[j];
+            bfk::KArgs<P> a;
+            fill_args<P>(p, a);
+            a.l0 = ps.l0;
+            a.k = ps.k;
+            a.flags = ps.flags;
+            a.T = ps.T;
+            a.win = static_cast<const typename P::C *>(buf[j & 1]);
+            a.wout = static_cast<typename P::C *>(buf[(j + 1) & 1]);
+            a.nrhs = nrhs[i];
+            a.rc = rc;
+            desc.push_back(a);
+            const size_t sm = mr_smem(p, ps, nr, rc);
+            if (sm > smem) smem = sm;
+            const int ctas = (int)((p->npts >> (p->d * ps.k)) / ps.T);
+            for (int y = 0; y < ny; ++y) {
+                J jb{};
+                jb.j.prob = i;
+                jb.j.desc = desc0[i] + (int)j;
+                jb.j.y = y;
+                jb.j.ctas = ctas;
+                jb.j.row = ps.row;
+                jb.pass = (int)j;
+                jobs.push_back(jb);
+            }
+        }
+    }
+    // queue order: pass index first (a job's dependency is always earlier), larger jobs first
+    std::stable_sort(jobs.begin(), jobs.end(), [](const J &x, const J &y) {
+        if (x.pass != y.pass) return x.pass < y.pass;
+        return x.j.ctas > y.j.ctas;
+    });
+    // a work unit runs `per` consecutive CTAs of a job: about 512 units per CTA slot over the
+    // whole queue, so taking a unit (an atomic and a table search) costs a few percent at
+    // most while the last units still balance
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem_total = smem;
+    if (smem_total > 227 * 1024) return BF_ERR_UNSUPPORTED;
+    const int per_sm = b->fns->batch_ctas_per_sm(smem_total);
+    if (per_sm < 1) return BF_ERR_UNSUPPORTED;
+    int64_t all_ctas = 0;
+    for (const J &x : jobs) all_ctas += x.j.ctas;
+    const int64_t slots = (int64_t)sms * per_sm;
+    int64_t per = all_ctas / (slots * 512);
+    per = per < 1 ? 1 : (per > 16 ? 16 : per);
+    std::vector<bfk::BatchJob> hj(jobs.size());
+    int first = 0;
+    for (size_t n = 0; n < jobs.size(); ++n) {
+        hj[n] = jobs[n].j;
+        hj[n].per = (int)per;
+        hj[n].units = (int)((hj[n].ctas + per - 1) / per);
+        hj[n].first = first;
+        first += hj[n].units;
+        hj[n].dep = -1;
+        if (jobs[n].pass > 0)
+            for (size_t m = 0; m < n; ++m)
+                if (jobs[m].j.prob == jobs[n].j.prob && jobs[m].j.y == jobs[n].j.y && jobs[m].pass == jobs[n].pass - 1)
+                    hj[n].dep = (int)m;
+        if (jobs[n].pass > 0 && hj[n].dep < 0) return BF_ERR_INTERNAL;
+    }
+    b->njobs = (int)hj.size();
+    b->units = first;
+    b->smem = smem_total;
+    cudaError_t e = cudaMalloc(&b->desc, desc.size() * sizeof(bfk::KArgs<P>));
+    if (e == cudaSuccess) e = cudaMemcpy(b->desc, desc.data(), desc.size() * sizeof(bfk::KArgs<P>), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->jobs, hj.size() * sizeof(bfk::BatchJob));
+    if (e == cudaSuccess) e = cudaMemcpy(b->jobs, hj.data(), hj.size() * sizeof(bfk::BatchJob), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&b->state, 16 + (hj.size() + 2) * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemset(b->state, 0, 16 + (hj.size() + 2) * sizeof(unsigned));
+    b->ctr = reinterpret_cast<unsigned *>(static_cast<char *>(b->state) + 16);
+    for (int h = 0; h < 2; ++h)
+        for (int t = 0; t < bfk::QMAX; ++t)
+            for (int u = 0; u < bfk::QMAX; ++u) b->M[h][t][u] = (float)desc[0].M[h][t][u];
+    if (e != cudaSuccess) {
+        b->last_cuda = (int)e;
+        return e == cudaErrorMemoryAllocation ? BF_ERR_NOMEM : BF_ERR_CUDA;
+    }
+    const int64_t grid = slots;
+    b->grid = (unsigned)(grid < b->units ? grid : b->units);
+    return BF_OK;
+}
+
+template <class P>
+bf_status batch_launch(bf_batch b, const void *const *g, void *const *f, cudaStream_t s, unsigned long long wait_ns,
+                       int dep_extra)
+{
+    bfk::BatchArgs<P> a;
+    std::memset(&a, 0, sizeof(a));
+    a.desc = static_cast<const bfk::KArgs<P> *>(b->desc);
+    a.jobs = static_cast<const bfk::BatchJob *>(b->jobs);
+    a.njobs = b->njobs;
+    a.units = b->units;
+    a.ctr = b->ctr;
+    a.err = reinterpret_cast<int *>(b->ctr + b->njobs + 1);
+    a.stats = static_cast<unsigned long long *>(b->state);
+    std::memcpy(a.M, b->M, sizeof(a.M));
+    a.wait_ns = wait_ns;
+    a.dep_extra = dep_extra;
+    for (int i = 0; i < b->count; ++i) {
+        a.g[i] = static_cast<const typename P::C *>(g[i]);
+        a.f[i] = static_cast<typename P::C *>(f[i]);
+    }
+    cudaError_t e = cudaMemsetAsync(b->state, 0, 16 + (size_t)(b->njobs + 2) * sizeof(unsigned), s);
+    if (e == cudaSuccess) e = b->fns->batch(&a, b->grid, b->smem, s);
+    if (e != cudaSuccess) {
+        b->last_cuda = (int)e;
+        return BF_ERR_CUDA;
+    }
+    return BF_OK;
+}
+
+bf_status batch_apply(bf_batch b, const void *const *g, void *const *f, void *stream, unsigned long long wait_ns,
+                      int dep_extra)
+{
+    if (!b || !g || !f) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < b->count; ++i)
+        if (!g[i] || !f[i] || ((uintptr_t)g[i] & 15) || ((uintptr_t)f[i] & 15)) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (b->prec == BF_PREC_MIXED_SFU) return batch_launch<bfk::PMIXF>(b, g, f, s, wait_ns, dep_extra);
+    return batch_launch<bfk::PMIX>(b, g, f, s, wait_ns, dep_extra);
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *bf_status_string(bf_status s)
@@ -681,6 +842,103 @@ bf_status bf_apply_batched(const bf_plan *plans, const void *const *g, void *con
         bf_status st = bf_apply(plans[i], g[i], f[i], nrhs[i], stream);
         if (st != BF_OK) return st;
     }
+    return BF_OK;
+}
+
+bf_status bf_batch_create(const bf_plan *plans, const int *nrhs, int count, bf_batch *out)
+{
+    if (!out) return BF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!plans || !nrhs || count < 1 || count > bfk::BATCH_MAX) return BF_ERR_INVALID_ARG;
+    for (int i = 0; i < count; ++i)
+        if (!plans[i] || nrhs[i] < 1 || nrhs[i] > plans[i]->max_nrhs) return BF_ERR_INVALID_ARG;
+    const bf_plan p0 = plans[0];
+    for (int i = 0; i < count; ++i) {
+        const bf_plan p = plans[i];
+        if (p->d != 2 || p->prec == BF_PREC_FP64 || p->passes_mr.empty() || !p->fns->batch) return BF_ERR_UNSUPPORTED;
+        if (p->q != p0->q || p->kind != p0->kind || p->prec != p0->prec || p->node_kind != p0->node_kind)
+            return BF_ERR_UNSUPPORTED;
+        for (int j = 0; j < i; ++j)
+            if (plans[j] == p) return BF_ERR_INVALID_ARG;   // one workspace per problem
+    }
+    bf_batch b = new (std::nothrow) bf_batch_s();
+    if (!b) return BF_ERR_NOMEM;
+    b->count = count;
+    b->prec = p0->prec;
+    b->fns = p0->fns;
+    bf_status st = b->prec == BF_PREC_MIXED_SFU ? batch_build<bfk::PMIXF>(b, plans, nrhs, count)
+                                                : batch_build<bfk::PMIX>(b, plans, nrhs, count);
+    if (st != BF_OK) {
+        bf_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return BF_OK;
+}
+
+bf_status bf_batch_apply(bf_batch b, const void *const *g_dev, void *const *f_dev, void *stream)
+{
+    return batch_apply(b, g_dev, f_dev, stream, 4000000000ull, 0);
+}
+
+bf_status bf_batch_status(bf_batch b, int *timed_out)
+{
+    if (!b || !timed_out) return BF_ERR_INVALID_ARG;
+    int v = 0;
+    cudaError_t e = cudaMemcpy(&v, b->ctr + b->njobs + 1, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        b->last_cuda = (int)e;
+        return BF_ERR_CUDA;
+    }
+    *timed_out = v != 0;
+    return BF_OK;
+}
+
+bf_status bf_batch_selftest_timeout(bf_batch b, const void *const *g_dev, void *const *f_dev, void *stream,
+                                    int *timed_out)
+{
+    if (!timed_out) return BF_ERR_INVALID_ARG;
+    bf_status st = batch_apply(b, g_dev, f_dev, stream, 20000000ull, 1);
+    if (st != BF_OK) return st;
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        b->last_cuda = (int)e;
+        return BF_ERR_CUDA;
+    }
+    return bf_batch_status(b, timed_out);
+}
+
+bf_status bf_batch_info(bf_batch b, int *jobs, int *units, int *grid, int64_t *smem_bytes)
+{
+    if (!b) return BF_ERR_INVALID_ARG;
+    if (jobs) *jobs = b->njobs;
+    if (units) *units = b->units;
+    if (grid) *grid = (int)b->grid;
+    if (smem_bytes) *smem_bytes = (int64_t)b->smem;
+    return BF_OK;
+}
+
+bf_status bf_batch_wait_stats(bf_batch b, double *wait_ms_total, int64_t *waits)
+{
+    if (!b) return BF_ERR_INVALID_ARG;
+    unsigned long long v[2] = {0, 0};
+    cudaError_t e = cudaMemcpy(v, b->state, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        b->last_cuda = (int)e;
+        return BF_ERR_CUDA;
+    }
+    if (wait_ms_total) *wait_ms_total = (double)v[0] * 1e-6;
+    if (waits) *waits = (int64_t)v[1];
+    return BF_OK;
+}
+
+bf_status bf_batch_destroy(bf_batch b)
+{
+    if (!b) return BF_OK;
+    if (b->desc) cudaFree(b->desc);
+    if (b->jobs) cudaFree(b->jobs);
+    if (b->state) cudaFree(b->state);
+    delete b;
     return BF_OK;
 }
 

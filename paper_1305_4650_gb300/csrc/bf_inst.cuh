@@ -88,6 +88,27 @@ cudaError_t launch_row_mr(const void *kargs, unsigned gx, unsigned gy, size_t sm
     return cudaGetLastError();
 }
 
+template <int Q, class P, int K>
+cudaError_t launch_batch(const void *bargs, unsigned grid, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_batch_mr<Q, P, K>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_batch_mr<Q, P, K><<<grid, bfk::CfgMR<Q>::NT, smem, s>>>(*static_cast<const bfk::BatchArgs<P> *>(bargs));
+    return cudaGetLastError();
+}
+
+template <int Q, class P, int K>
+int batch_ctas_per_sm(size_t smem)
+{
+    static size_t granted[64] = {0};
+    if (prepare(bfk::k_batch_mr<Q, P, K>, smem, granted) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bfk::k_batch_mr<Q, P, K>, bfk::CfgMR<Q>::NT, smem) != cudaSuccess)
+        return 0;
+    return n;
+}
+
 template <int D, int Q, class P, int K>
 cudaError_t launch_ctab(const void *kargs, void *out, int levels)
 {
@@ -106,11 +127,12 @@ const PassFns *fns_for()
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT,
                                   launch_col_mr<Q, P, K>, launch_row_mr<Q, P, K>, bfk::MRMAX, bfk::CfgMR<Q>::NT,
+                                  launch_batch<Q, P, K>, batch_ctas_per_sm<Q, P, K>,
                                   launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
         return &f;
     } else {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
-                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, nullptr, nullptr, 0, 0,
+                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, nullptr, nullptr, 0, 0, nullptr, nullptr,
                                   launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
         return &f;
     }

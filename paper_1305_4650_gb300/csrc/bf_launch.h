@@ -18,6 +18,9 @@ struct PassFns {
     pass_fn col_mr, row_mr;      // multi-RHS forward passes with a phase cache (null if absent)
     int mr_max;                  // right-hand sides one multi-RHS CTA holds
     int mr_nthreads;             // threads per multi-RHS CTA
+    // persistent batch kernel (bf_mr.cuh): bargs points to a bfk::BatchArgs<P>
+    cudaError_t (*batch)(const void *bargs, unsigned grid, size_t smem, cudaStream_t s);
+    int (*batch_ctas_per_sm)(size_t smem);
     cudaError_t (*center_table)(const void *kargs, void *out, int levels);   // target features at box centres
     int tsize;                   // bytes of one target-feature record
 };

@@ -71,7 +71,7 @@ struct TileMR {
         const int64_t off = (int64_t)x.tile0 * ((int64_t)RR << (D * a.k));
         for (int j = threadIdx.x; j < x.nr * WS; j += NT) {
             const int rb = (j / RR) >> x.lgp, e = j - rb * WS;
-            W[j] = a.win[(int64_t)(x.rhs0 + rb) * a.wstride + off + e];
+            W[j] = __ldcg(a.win + (int64_t)(x.rhs0 + rb) * a.wstride + off + e);
         }
     }
 
@@ -91,7 +91,7 @@ struct TileMR {
     }
 
     // ---- init: PC[pair][t] = l_t(y) e^{-2pi i Phi(x0(X), y_t^B)} e^{2pi i Phi(x0(X), y)}, then W = PC g(y)
-    static __device__ void init(const KArgs<P> &a, const Ctx &x, C *W, C *PC)
+    static __device__ void init(const KArgs<P> &a, const Ctx &x, C *W, C *PC, const C *g)
     {
         const int k = a.k, n = 1 << (D * k), L = a.L, WS = x.npr * RR;
         const int cX[DMAX] = {0, 0, 0};
@@ -127,15 +127,16 @@ struct TileMR {
                 int cb[DMAX];
                 morton_decode<D>((Bstar << (D * k)) + (pr & (n - 1)), L, cb);
                 const int64_t flat = ((int64_t)cb[0] << L) + cb[1];
-                v = cmul(PC[it], a.g[(int64_t)(x.rhs0 + rb) * a.npts + flat]);
+                v = cmul(PC[it], g[(int64_t)(x.rhs0 + rb) * a.npts + flat]);
             }
             W[j] = v;
         }
         __syncthreads();
     }
 
-    // ---- one column-form merge level (l -> l+1)
-    static __device__ void col_level(const KArgs<P> &a, const Ctx &x, C *W, C *S, C *PC, int l, int i)
+    // ---- one column-form merge level (l -> l+1); ms.M holds the child->parent matrices
+    template <class MS>
+    static __device__ void col_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
         C *PA = PC;                  // [pA][chi][cl][tq][t0']  modulation of the inputs
@@ -199,7 +200,7 @@ struct TileMR {
                     for (int t0p = 0; t0p < Q; ++t0p) {
                         const C u = cmul(ph[cl * RR + t0p], win[t0p]);
 #pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[c & 1][t0][t0p], u);
+                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], ms.M[c & 1][t0][t0p], u);
                     }
                 }
                 C *so = S + rbl * 2 * WS + ((pA * 2 + chi) * Q + tq) * Q;
@@ -222,7 +223,7 @@ struct TileMR {
                     for (int tqp = 0; tqp < Q; ++tqp) {
                         const C v = si[tqp * Q];
 #pragma unroll
-                        for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], a.M[chi][tq][tqp], v);
+                        for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], ms.M[chi][tq][tqp], v);
                     }
                 }
                 C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + tl;
@@ -280,7 +281,8 @@ struct TileMR {
     }
 
     // ---- one row-form merge level (l -> l+1)
-    static __device__ void row_level(const KArgs<P> &a, const Ctx &x, C *W, C *S, C *PC, int l, int i)
+    template <class MS>
+    static __device__ void row_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
         C *PA = PC;              // [pin][th][t0]     pre-modulation at the parent's nodes
@@ -344,8 +346,8 @@ struct TileMR {
                     const C u = cjmul(ph[t0], win[t0]);
 #pragma unroll
                     for (int s0 = 0; s0 < Q; ++s0) {
-                        cfma(z[0][s0], a.M[0][t0][s0], u);
-                        cfma(z[1][s0], a.M[1][t0][s0], u);
+                        cfma(z[0][s0], ms.M[0][t0][s0], u);
+                        cfma(z[1][s0], ms.M[1][t0][s0], u);
                     }
                 }
                 C *so = S + rbl * 2 * WS + (pin * Q + th) * 2 * Q;
@@ -373,7 +375,7 @@ struct TileMR {
                     for (int t1 = 0; t1 < Q; ++t1) {
                         const C zz = si[t1 * 2 * Q];
 #pragma unroll
-                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[c][s1], a.M[a1][t1][s1], zz);
+                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[c][s1], ms.M[a1][t1][s1], zz);
                     }
                 }
                 C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
@@ -391,7 +393,7 @@ struct TileMR {
     }
 
     // ---- final evaluation: PC[pair][t] = l_t(x) conj(e^{2pi i Phi(x_t, y0(Y))}), PC[pair][r] = e^{2pi i Phi(x, y0(Y))}
-    static __device__ void final_eval(const KArgs<P> &a, const Ctx &x, const C *W, C *PC)
+    static __device__ void final_eval(const KArgs<P> &a, const Ctx &x, const C *W, C *PC, C *f)
     {
         const int k = a.k, n = 1 << (D * k), L = a.L, WS = x.npr * RR;
         const int cY[DMAX] = {0, 0, 0};
@@ -430,7 +432,7 @@ struct TileMR {
             int ca[DMAX];
             morton_decode<D>((Ap << (D * k)) + digit_rev<D>(pl & (n - 1), k), L, ca);
             const int64_t flat = ((int64_t)ca[0] << L) + ca[1];
-            a.f[(int64_t)(x.rhs0 + rb) * a.npts + flat] = cmul(pc[RR], acc);
+            f[(int64_t)(x.rhs0 + rb) * a.npts + flat] = cmul(pc[RR], acc);
         }
     }
 
@@ -453,46 +455,184 @@ struct TileMR {
     }
 };
 
-template <int Q, class P, int K>
-__global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_col_pass_mr(const KArgs<P> a)
+// pass bodies shared by the per-pass kernels and the persistent batch kernel; ms is a
+// kernel parameter holding M, so the interpolation reads its coefficients from the
+// constant bank
+template <int Q, class P, int K, class MS>
+__device__ __forceinline__ void col_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
+                                            unsigned char *sm, const typename P::C *g)
 {
     using C = typename P::C;
     using TM = TileMR<Q, P, K>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const typename TM::Ctx x = TM::ctx(a);
     const int WS = x.npr * TM::RR;
-    C *W = reinterpret_cast<C *>(smem_raw);
+    C *W = reinterpret_cast<C *>(sm);
     C *S = W + x.nr * WS;
     C *PC = S + x.rc * 2 * WS;
     if (a.flags & F_INIT) {
-        TM::init(a, x, W, PC);
+        TM::init(a, x, W, PC, g);
     } else {
         TM::load(a, x, W);
         __syncthreads();
     }
-    for (int i = 0; i < a.k; ++i) TM::col_level(a, x, W, S, PC, a.l0 + i, i);
+    for (int i = 0; i < a.k; ++i) TM::col_level(a, ms, x, W, S, PC, a.l0 + i, i);
     if (a.flags & F_SWITCH) TM::switch_tiles(a, x, W, a.l0 + a.k);
     TM::store(a, x, W);
+}
+
+template <int Q, class P, int K, class MS>
+__device__ __forceinline__ void row_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
+                                            unsigned char *sm, typename P::C *f)
+{
+    using C = typename P::C;
+    using TM = TileMR<Q, P, K>;
+    const int WS = x.npr * TM::RR;
+    C *W = reinterpret_cast<C *>(sm);
+    C *S = W + x.nr * WS;
+    C *PC = S + x.rc * 2 * WS;
+    TM::load(a, x, W);
+    __syncthreads();
+    for (int i = 0; i < a.k; ++i) TM::row_level(a, ms, x, W, S, PC, a.l0 + i, i);
+    if (a.flags & F_FINAL)
+        TM::final_eval(a, x, W, PC, f);
+    else
+        TM::store(a, x, W);
+}
+
+template <int Q, class P, int K>
+__global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_col_pass_mr(const KArgs<P> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    col_pass_mr<Q, P, K>(a, a, TileMR<Q, P, K>::ctx(a), smem_raw, a.g);
 }
 
 template <int Q, class P, int K>
 __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_row_pass_mr(const KArgs<P> a)
 {
-    using C = typename P::C;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    row_pass_mr<Q, P, K>(a, a, TileMR<Q, P, K>::ctx(a), smem_raw, a.f);
+}
+
+// ====================================================================== persistent batch
+// Many independent problems in one launch.  A job is one pass of one problem for one
+// block of up to MRMAX right-hand sides; its units are the pass's CTAs.  Jobs are
+// ordered by pass index, so a unit only ever waits for units that come earlier in the
+// queue: CTAs take units from a global counter in order, and before a unit of pass j
+// starts, the CTA waits until every unit of the same problem's pass j-1 (same RHS
+// block) has finished.  The unit that is earliest among the unfinished ones never
+// waits, so the queue always advances.  A wait gives up after a time limit, sets the
+// error flag and skips its unit; once the flag is set no unit waits or computes.
+
+constexpr int BATCH_MAX = 256;          // problems per batch
+
+struct BatchJob {
+    int prob, desc;      // problem, descriptor (problem, pass) of the job
+    int y;               // block of right-hand sides
+    int ctas;            // CTAs of the pass (tile groups of T tiles)
+    int per;             // CTAs per work unit, run one after another by one CTA
+    int units, first;    // units of the job and index of its first unit in the queue
+    int dep;             // job that must finish first (-1: none)
+    int row, pad0, pad1, pad2;   // 1: row pass
+};
+
+template <class P>
+struct BatchArgs {
+    typename P::R M[2][QMAX][QMAX];   // child->parent matrices (the same for every problem)
+    const KArgs<P> *__restrict__ desc;   // per (problem, pass); g and f come from the arrays below
+    const BatchJob *jobs;
+    int njobs, units;
+    unsigned *ctr;                 // [njobs] finished units per job, [njobs] queue head
+    int *err;                      // set when a wait times out
+    unsigned long long *stats;     // [0] nanoseconds spent waiting, [1] waits
+    unsigned long long wait_ns;    // time limit of one wait
+    int dep_extra;                 // added to every wait's target (0; 1 only in the time-out self-test)
+    const typename P::C *g[BATCH_MAX];
+    typename P::C *f[BATCH_MAX];
+};
+
+__device__ __forceinline__ uint64_t globaltimer_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// wait (one thread) until *ctr >= target; 1 if given up (time limit or error flag)
+__device__ __forceinline__ int wait_count(const unsigned *ctr, unsigned target, int *err, unsigned long long limit,
+                                          unsigned long long *stats)
+{
+    const uint64_t t0 = globaltimer_ns();
+    for (int n = 0;; ++n) {
+        unsigned v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(ctr) : "memory");
+        if (v >= target) {
+            if (n > 0) {
+                atomicAdd(&stats[0], (unsigned long long)(globaltimer_ns() - t0));
+                atomicAdd(&stats[1], 1ull);
+            }
+            return 0;
+        }
+        if (*reinterpret_cast<volatile int *>(err)) return 1;
+        if (globaltimer_ns() - t0 > limit) {
+            atomicExch(err, 1);
+            return 1;
+        }
+        __nanosleep(256);
+    }
+}
+
+template <int Q, class P, int K>
+__global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_batch_mr(const BatchArgs<P> b)
+{
     using TM = TileMR<Q, P, K>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const typename TM::Ctx x = TM::ctx(a);
-    const int WS = x.npr * TM::RR;
-    C *W = reinterpret_cast<C *>(smem_raw);
-    C *S = W + x.nr * WS;
-    C *PC = S + x.rc * 2 * WS;
-    TM::load(a, x, W);
-    __syncthreads();
-    for (int i = 0; i < a.k; ++i) TM::row_level(a, x, W, S, PC, a.l0 + i, i);
-    if (a.flags & F_FINAL)
-        TM::final_eval(a, x, W, PC);
-    else
-        TM::store(a, x, W);
+    __shared__ int s_unit, s_job, s_skip;
+    for (;;) {
+        if (threadIdx.x == 0) {
+            const int u = (int)atomicAdd(&b.ctr[b.njobs], 1u);
+            s_unit = u;
+            if (u < b.units) {
+                int lo = 0, hi = b.njobs - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(&b.jobs[mid].first) <= u) lo = mid; else hi = mid - 1;
+                }
+                s_job = lo;
+                int skip = *reinterpret_cast<volatile int *>(b.err);
+                const int dep = __ldg(&b.jobs[lo].dep);
+                if (!skip && dep >= 0)
+                    skip = wait_count(&b.ctr[dep], (unsigned)(__ldg(&b.jobs[dep].units) + b.dep_extra), b.err, b.wait_ns,
+                                      b.stats);
+                s_skip = skip;
+            }
+        }
+        __syncthreads();
+        const int u = s_unit;
+        if (u >= b.units) break;
+        const BatchJob jb = b.jobs[s_job];
+        if (!s_skip) {
+            // the pass's arguments stay in global memory (read-only for the whole launch)
+            const KArgs<P> &a = b.desc[jb.desc];
+            const int c0 = (u - jb.first) * jb.per;
+            const int c1 = min(c0 + jb.per, jb.ctas);
+            for (int c = c0; c < c1; ++c) {
+                typename TM::Ctx x;
+                x.tile0 = c * a.T;
+                x.rhs0 = jb.y * MRMAX;
+                x.nr = min(MRMAX, a.nrhs - x.rhs0);
+                x.npr = a.T << (2 * a.k);
+                x.rc = a.rc;
+                x.lgp = __ffs(x.npr) - 1;
+                if (jb.row)
+                    row_pass_mr<Q, P, K>(a, b, x, smem_raw, b.f[jb.prob]);
+                else
+                    col_pass_mr<Q, P, K>(a, b, x, smem_raw, b.g[jb.prob]);
+                __syncthreads();
+            }
+        }
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) atomicAdd(&b.ctr[s_job], 1u);
+    }
 }
 
 }  // namespace bfk
