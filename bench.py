@@ -73,6 +73,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile schedules")
     return ap.parse_args()
 
 
@@ -216,6 +217,7 @@ def run_ours(args, rank, world, local_rank):
 
     prec = spec.precision
     plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec)
+    tuned = None if args.no_autotune else round(plan.autotune(nrhs, reps=3), 4)   # plan time, not timed
     passes = plan.passes(nrhs)
     g_np = wl.source_values(spec, nrhs, plan.cdtype, seed=spec.seed + rank)
     g = torch.from_numpy(g_np).to(dev)
@@ -274,6 +276,8 @@ def run_ours(args, rank, world, local_rank):
     fp64 = None
     if prec != "fp64" and args.fp64_steps > 0:
         p64 = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="fp64")
+        if not args.no_autotune:
+            p64.autotune(nrhs, reps=1)
         g64 = g.to(torch.complex128)
         f64 = torch.empty_like(g64)
         p64.apply(g64, f64)
@@ -294,6 +298,8 @@ def run_ours(args, rank, world, local_rank):
     sfu = None
     if prec == "mixed":
         psf = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="mixed_sfu")
+        if not args.no_autotune:
+            psf.autotune(nrhs, reps=3)
         fsf = torch.empty_like(g)
         for _ in range(args.warmup):
             psf.apply(g, fsf)
@@ -371,6 +377,8 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": spec.name, "d": spec.d, "N": spec.N, "q": spec.q, "r": spec.r,
                        "phase": spec.phase, "precision": prec, "nrhs": nrhs, "switch_level": spec.switch_level,
                        "passes": len(passes), "fuse_levels": plan_fuse(passes),
+                       "schedule": [("col" if p["kind"] == "col" else "row") + str(p["k"]) for p in passes],
+                       "autotuned_ms": tuned,
                        "l2": f"no flush: each step streams {weight_gb:.1f} GB of weights through the 129 MB L2",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "fp64_gpu": fp64, "sfu_sincos": sfu, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
@@ -397,6 +405,8 @@ def run_batched(args, rank, world, local_rank):
     plans, gs, fs, nr = [], [], [], []
     for i, spec, k in mine:
         p = bf.Plan.from_spec(spec, max_nrhs=k, precision="mixed")
+        if not args.no_autotune:
+            p.autotune(k, reps=2)                            # plan time, not timed
         g = torch.from_numpy(wl.source_values(spec, k, np.complex64, seed=spec.seed + i)).to(dev)
         plans.append(p)
         gs.append(g)
@@ -450,6 +460,7 @@ def run_batched(args, rank, world, local_rank):
     torch.cuda.synchronize()
     launches = 1
     seq_launches = sum(p.launches(k) for p, k in zip(plans, nr))
+    weight_gb = sum(2 * (p.launches(k) - 1) * s.npts * s.r * 8 * k for p, (_, s, k) in zip(plans, mine)) / 1e9
     acc = None
     if rank == 0 and not args.no_accuracy:
         # problem 0 (N = 128) against the oracle butterfly, all outputs, every RHS
@@ -465,21 +476,24 @@ def run_batched(args, rank, world, local_rank):
         p.close()
     if rank != 0:
         return None
-    return {"metric": METRIC, "value": pts_rhs / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+    persistent = {"ms_per_step": round(ms, 3), "value": pts_rhs / (ms * 1e-3), "launches_per_step": 1,
+                  "work_units": binfo["units"], "jobs": binfo["jobs"], "ctas": binfo["grid"],
+                  "wait_timed_out": timed_out, "dependency_wait_cta_ms": round(waits["wait_ms_total"], 3),
+                  "dependency_waits": waits["waits"]}
+    per_pass = {"ms_per_step": round(ms_seq, 3), "value": pts_rhs / (ms_seq * 1e-3), "launches_per_step": seq_launches}
+    # the headline is the faster of the two launch forms; both are reported
+    best, how = (ms, "one persistent kernel per step") if ms <= ms_seq else (ms_seq, "one kernel per pass of every problem")
+    return {"metric": METRIC, "value": pts_rhs / (best * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(best, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
             "config": {"workload": "hypradon48_q5", "problems": len(probs), "N": [128, 256, 512],
                        "nrhs_total": int(sum(nr)) if world == 1 else None, "points_rhs": pts_rhs,
                        "points_rhs_rank0": pts_rhs_local, "precision": "mixed",
-                       "launch": f"one persistent kernel per step (CUDA graph): {binfo['units']} work units in "
-                                 f"{binfo['jobs']} jobs on {binfo['grid']} CTAs",
+                       "launch": how + " (CUDA graph)",
+                       "l2": f"no flush: each step streams {weight_gb:.0f} GB of weights through the 129 MB L2",
                        "parallelism": f"problems round-robin over {world} rank(s)"},
-            "per_problem_passes": {"ms_per_step": round(ms_seq, 3), "value": pts_rhs / (ms_seq * 1e-3),
-                                   "launches_per_step": seq_launches},
-            "batch_wait_timed_out": timed_out,
-            "batch_dependency_waits": {"cta_ms_per_step": round(waits["wait_ms_total"], 3), "waits": waits["waits"],
-                                       "cta_slots": binfo["grid"]},
-            "accuracy": acc, "gpu_launches": args.steps * launches, "clocks": clocks}
+            "persistent_launch": persistent, "per_pass_launches": per_pass,
+            "accuracy": acc, "gpu_launches": args.steps * (1 if best == ms else seq_launches), "clocks": clocks}
 
 
 def run_cg(args, rank, world, local_rank):
@@ -494,6 +508,8 @@ def run_cg(args, rank, world, local_rank):
     torch.cuda.set_device(dev)
     spec = wl.genradon2d()
     plan = bf.Plan.from_spec(spec, precision="mixed")
+    if not args.no_autotune:
+        plan.autotune(1, reps=3)
     launches = plan.launches(1)
     mt = torch.from_numpy(wl.sparse_spikes(spec, 0.01)).to(dev)
     d = plan.apply(mt)

@@ -175,6 +175,19 @@ bf_status bf_last_cuda_error(bf_plan plan, int *cuda_err);
 bf_status bf_plan_info(bf_plan plan, int *d, int64_t *N, int *q, int *m, int *fuse_levels,
                        int *launches_per_apply, int64_t *workspace_bytes);
 
+/* Autotuner.  Times candidate tile schedules of the apply bf_apply runs for nrhs
+ * right-hand sides on this device and keeps the fastest in the plan.  Single-RHS (and
+ * FP64) passes: levels fused per pass (1 .. the compiled maximum) and whether the
+ * short pass of a run of levels comes first or last.  Multi-RHS passes: fused levels
+ * (1, 2), pairs per CTA (1 or 2 switch rounds), right-hand sides per scratch chunk
+ * (1, 2, 4, 5, 8, 16),
+ * and the short-pass position, among those that fit the shared memory of one CTA.
+ * Each candidate runs one warm-up apply and reps timed applies (CUDA events) on
+ * scratch buffers the call allocates and frees; synchronises the stream.  Results do
+ * not depend on the schedule beyond FP32 rounding order.  best_ms (may be NULL)
+ * receives the chosen schedule's time per apply. */
+bf_status bf_plan_autotune(bf_plan plan, int nrhs, int reps, void *stream, double *best_ms);
+
 /* Instrumentation.  An apply of nrhs right-hand sides is a fixed schedule of kernel
  * passes: the single-RHS passes for nrhs = 1 (and for FP64 plans), the multi-RHS
  * passes, which evaluate every phase factor once for up to 16 right-hand sides, for

@@ -24,7 +24,7 @@ EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint"
            "bf_apply_batched", "bf_destroy", "bf_status_string", "bf_last_cuda_error", "bf_plan_info",
            "bf_apply_pass", "bf_pass_info", "bf_pass_count", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate",
            "bf_measure_phase_rate", "bf_batch_create", "bf_batch_apply", "bf_batch_status",
-           "bf_batch_selftest_timeout", "bf_batch_info", "bf_batch_wait_stats", "bf_batch_destroy"]
+           "bf_batch_selftest_timeout", "bf_batch_info", "bf_batch_wait_stats", "bf_batch_destroy", "bf_plan_autotune"]
 
 
 class BfError(RuntimeError):
@@ -82,6 +82,7 @@ def load():
         lib.bf_batch_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i32),
                                       ctypes.POINTER(i64)]
         lib.bf_batch_destroy.argtypes = [vp]
+        lib.bf_plan_autotune.argtypes = [vp, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
         lib.bf_batch_wait_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in EXPORTS:
             getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -203,6 +204,13 @@ class Plan:
     def apply_pass(self, i: int, g_ptr: int, f_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
         """Run pass i of the apply schedule only (instrumentation)."""
         _check(load().bf_apply_pass(self._h, i, g_ptr, f_ptr, nrhs, stream_ptr), "bf_apply_pass", self._h)
+
+    def autotune(self, nrhs: int = 1, reps: int = 3, stream=None) -> float:
+        """Time candidate tile schedules for nrhs right-hand sides, keep the fastest; ms per apply."""
+        ms = ctypes.c_double()
+        _check(load().bf_plan_autotune(self._h, nrhs, reps, _stream_ptr(stream), ctypes.byref(ms)),
+               "bf_plan_autotune", self._h)
+        return ms.value
 
     def launches(self, nrhs: int = 1) -> int:
         """Kernel launches (passes) of one apply of nrhs right-hand sides."""

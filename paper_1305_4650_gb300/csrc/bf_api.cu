@@ -238,15 +238,21 @@ Pass make_pass(const bf_plan_s *p, int64_t np_cta, int row, int l0, int k, int f
 }
 
 // column passes of <= kmax levels (init first, switch last), then row passes (final last)
-std::vector<Pass> schedule(const bf_plan_s *p, int kmax, int64_t np_cta)
+// (rem_first: the short pass of each run of levels goes first instead of last)
+std::vector<Pass> schedule(const bf_plan_s *p, int kmax, int64_t np_cta, bool rem_first = false)
 {
     std::vector<Pass> out;
     const int m = p->m, L = p->L;
+    auto chunk = [&](int left, int total) {
+        const int r = total % kmax;
+        if (rem_first && r && left == total) return r;
+        return left < kmax ? left : kmax;
+    };
     if (m == 0) {
         out.push_back(make_pass(p, np_cta, 0, 0, 0, bfk::F_INIT | bfk::F_SWITCH));
     } else {
         for (int l = 0; l < m;) {
-            const int k = (m - l) < kmax ? (m - l) : kmax;
+            const int k = chunk(m - l, m);
             int fl = 0;
             if (l == 0) fl |= bfk::F_INIT;
             if (l + k == m) fl |= bfk::F_SWITCH;
@@ -255,7 +261,7 @@ std::vector<Pass> schedule(const bf_plan_s *p, int kmax, int64_t np_cta)
         }
     }
     for (int l = m; l < L;) {
-        const int k = (L - l) < kmax ? (L - l) : kmax;
+        const int k = chunk(L - l, L - m);
         out.push_back(make_pass(p, np_cta, 1, l, k, (l + k == L) ? bfk::F_FINAL : 0));
         l += k;
     }
@@ -755,6 +761,96 @@ bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
     }
     if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
     return run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
+}
+
+bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *best_ms)
+{
+    if (!p || nrhs < 1 || nrhs > p->max_nrhs || reps < 1 || reps > 1000) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)nrhs * (size_t)p->npts * p->csize;
+    void *g = nullptr, *f = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&g, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&f, bytes);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g, 0, bytes, s);   // the run time does not depend on the values
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    bf_status st = e == cudaSuccess ? BF_OK : cuda_fail(p, e);
+    // one candidate: warm-up apply, then reps applies between events
+    auto time_it = [&](double &ms) -> bf_status {
+        bf_status r = bf_apply(p, g, f, nrhs, stream);
+        if (r != BF_OK) return r;
+        cudaEventRecord(e0, s);
+        for (int i = 0; i < reps && r == BF_OK; ++i) r = bf_apply(p, g, f, nrhs, stream);
+        cudaEventRecord(e1, s);
+        if (r != BF_OK) return r;
+        cudaError_t ce = cudaEventSynchronize(e1);
+        if (ce != cudaSuccess) return cuda_fail(p, ce);
+        float t = 0.f;
+        cudaEventElapsedTime(&t, e0, e1);
+        ms = (double)t / reps;
+        return BF_OK;
+    };
+    double best = 1e300;
+    if (st == BF_OK && use_mr(p, nrhs)) {
+        // multi-RHS tiles: fused levels, pairs per CTA, right-hand sides per scratch chunk
+        const int nr = nrhs < p->fns->mr_max ? nrhs : p->fns->mr_max;
+        const int64_t ppr = p->fns->mr_nthreads / p->r;
+        std::vector<Pass> keep = p->passes_mr;
+        int keep_rc = p->mr_rc;
+        const int rcs[6] = {1, 2, 4, 5, 8, 16};
+        for (int k = 1; k <= 2 && st == BF_OK; ++k)
+            for (int64_t np = ppr; np <= 2 * ppr && st == BF_OK; np *= 2)
+                for (int rem = 0; rem < 2 && st == BF_OK; ++rem)
+                    for (int ri = 0; ri < 6 && st == BF_OK; ++ri) {
+                        const int rc = rcs[ri];
+                        if (rc > nr) continue;
+                        std::vector<Pass> cand = schedule(p, k, np, rem != 0);
+                        bool fits = true;
+                        for (const Pass &ps : cand)
+                            if (mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
+                        if (!fits) continue;
+                        p->passes_mr = cand;
+                        p->mr_rc = rc;
+                        double ms = 0.0;
+                        st = time_it(ms);
+                        if (st == BF_OK && ms < best) {
+                            best = ms;
+                            keep = cand;
+                            keep_rc = rc;
+                        }
+                    }
+        p->passes_mr = keep;
+        p->mr_rc = keep_rc;
+    } else if (st == BF_OK) {
+        // single-RHS tiles: fused levels per pass and where the short pass goes
+        std::vector<Pass> keep = p->passes;
+        int keep_k = p->kc;
+        for (int k = 1; k <= p->fns->kmax && st == BF_OK; ++k)
+            for (int rem = 0; rem < 2 && st == BF_OK; ++rem) {
+                std::vector<Pass> cand = schedule(p, k, p->fns->np, rem != 0);
+                bool fits = true;
+                for (const Pass &ps : cand)
+                    if (pass_smem(p, ps) + row_cache_smem(p, ps) > 227 * 1024) fits = false;
+                if (!fits) continue;
+                p->passes = cand;
+                double ms = 0.0;
+                st = time_it(ms);
+                if (st == BF_OK && ms < best) {
+                    best = ms;
+                    keep = cand;
+                    keep_k = k;
+                }
+            }
+        p->passes = keep;
+        p->kc = p->kr = keep_k;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (g) cudaFree(g);
+    if (f) cudaFree(f);
+    if (st == BF_OK && best_ms) *best_ms = best;
+    return st;
 }
 
 bf_status bf_pass_count(bf_plan p, int nrhs, int *count)
