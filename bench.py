@@ -38,10 +38,10 @@ FP32_LANES_PER_SM = 128
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each pass of the default
 # workload, from one ncu capture of `python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-accuracy
-# --fp64-steps 0`.  They describe the kernels as built from sources with the recorded hash; after any
-# change to those sources the figure is dropped (traffic: null) until it is captured again.
-TRAFFIC = {"genradon2d": {"src_sha256": "1b14f90c3ba41a40250ddc3c991cecf83b95b6285a61c9db3beefc18846bac1d",
-                          "bytes": [160105984, 379043328, 369424384, 216444672]}}
+# --fp64-steps 0 --no-autotune`.  They describe the kernels as built from sources with the recorded hash
+# and the recorded pass schedule; otherwise the figure is dropped (traffic: null) until captured again.
+TRAFFIC = {"genradon2d": {"src_sha256": "@SHA@", "schedule": ["col2", "col3", "row2", "row3"],
+                          "bytes": None}}
 TRAFFIC_SRC = ("bf_device.cuh", "bf_inst.cuh", "bf_launch.h", "bf_api.cu")
 
 
@@ -54,9 +54,10 @@ def kernel_src_sha256():
     return h.hexdigest()
 
 
-def recorded_traffic(workload_name, pass_index):
+def recorded_traffic(workload_name, schedule, pass_index):
     rec = TRAFFIC.get(workload_name)
-    if rec is None or rec["src_sha256"] != kernel_src_sha256() or pass_index >= len(rec["bytes"]):
+    if (rec is None or rec["bytes"] is None or rec["src_sha256"] != kernel_src_sha256()
+            or rec["schedule"] != schedule or pass_index >= len(rec["bytes"])):
         return None
     return rec["bytes"][pass_index]
 
@@ -254,12 +255,13 @@ def run_ours(args, rank, world, local_rank):
         for i in range(len(passes)):
             tpass[i] += evs[i].elapsed_time(evs[i + 1]) / args.steps
     dom = max(range(len(passes)), key=lambda i: tpass[i])
+    sched = [("col" if p["kind"] == "col" else "row") + str(p["k"]) for p in passes]
     wdom = pass_work(spec, passes[dom], nrhs)
     ops = work_ops(spec, wdom)
     peak = SM_COUNT * FP32_LANES_PER_SM * 2.07e9 / 1e12       # FP32-pipe Tops/s at the 2070 MHz max clock
     achieved = ops / (tpass[dom] * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "Tops/s",
-                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, dom),
+                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, sched, dom),
                 "kernel": f"pass{dom}:{passes[dom]['kind']} l0={passes[dom]['l0']} k={passes[dom]['k']}"
                           + (" +init" if passes[dom]["init"] else "") + (" +switch" if passes[dom]["switch"] else "")
                           + (" +final" if passes[dom]["final"] else ""),
@@ -377,7 +379,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": spec.name, "d": spec.d, "N": spec.N, "q": spec.q, "r": spec.r,
                        "phase": spec.phase, "precision": prec, "nrhs": nrhs, "switch_level": spec.switch_level,
                        "passes": len(passes), "fuse_levels": plan_fuse(passes),
-                       "schedule": [("col" if p["kind"] == "col" else "row") + str(p["k"]) for p in passes],
+                       "schedule": sched,
                        "autotuned_ms": tuned,
                        "l2": f"no flush: each step streams {weight_gb:.1f} GB of weights through the 129 MB L2",
                        "parallelism": f"replicas x{world}"},

@@ -669,7 +669,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     const int kfit = p->fns->kmax;
     const int kreq = prm->fuse_levels > 0 ? prm->fuse_levels : kfit;
     p->kc = p->kr = kreq < kfit ? kreq : kfit;
-    p->passes = schedule(p, p->kc, p->fns->np);
+    p->passes = schedule(p, p->kc, p->fns->np, true);
     if (p->fns->col_mr) {
         // 2 fused levels, as many pairs per CTA as one switch round covers (at least one tile);
         // scratch for enough right-hand sides to give every thread an item, fewer if the
@@ -677,7 +677,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         const int kmr = kreq < 2 ? kreq : 2;
         const int nr = p->max_nrhs < p->fns->mr_max ? p->max_nrhs : p->fns->mr_max;
         const int64_t ppr = p->fns->mr_nthreads / p->r;
-        p->passes_mr = schedule(p, kmr, ppr);
+        p->passes_mr = schedule(p, kmr, ppr, true);
         int64_t npr = 0;
         for (const Pass &ps : p->passes_mr)
             if (((int64_t)ps.T << (d * ps.k)) > npr) npr = (int64_t)ps.T << (d * ps.k);
