@@ -846,6 +846,93 @@ struct Tile {
         __syncthreads();
     }
 
+    // ---- switch for a phase that is a sum over dimensions, Phi = sum_k phi_k(x_k, y_k)
+    // (Fourier, and the separable test phase): e^{2pi i Phi(x_s, y_t)} is the product of the
+    // d factors e^{2pi i phi_k(x_{s_k}, y_{t_k})}, so the r x r switch is d sweeps of q x q
+    // matrices, one per node digit -- O(d q^{d+1}) work per pair instead of O(r^2) (the
+    // tensor-product case of Section 1.4).  ADJ applies the conjugate transpose (each sweep
+    // conjugate-transposed; the sweeps commute).  Items (tau, slot, output digit, D-2 other
+    // digits); each evaluates its q phases once and sweeps the last digit.  Results go
+    // Wt -> S -> Wt (-> S, copied back for odd d).
+    template <bool ADJ>
+    static __device__ void switch_sep(const KArgs<P> &a, C *Wt, C *S, int l)
+    {
+        const int k = a.k, n = 1 << (D * k);
+        const int L = a.L;
+        C *src = Wt, *dst = S;
+#pragma unroll
+        for (int dim = 0; dim < D; ++dim) {
+            int oth[DMAX - 1];
+            {
+                int j = 0;
+#pragma unroll
+                for (int e = 0; e < D; ++e)
+                    if (e != dim) oth[j++] = e;
+            }
+            int pw[DMAX];
+            pw[0] = 1;
+#pragma unroll
+            for (int e = 1; e < D; ++e) pw[e] = pw[e - 1] * Q;
+            for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
+                const int rest = it % QD1;
+                const int sl = (it / QD1) & (n - 1);
+                const int tau = (it / QD1) >> (D * k);
+                uint32_t Ap, Bstar;
+                tile_of(a, tau, Ap, Bstar);
+                const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
+                int ca[DMAX], cb[DMAX];
+                morton_decode<D>(A, l, ca);
+                morton_decode<D>(Bstar, L - l, cb);
+                const int sd = rest % Q;                        // output digit of dimension dim
+                const int o1 = D == 3 ? rest / Q : 0;            // digit of oth[0] (d = 3)
+                C e[Q];
+                if constexpr (!ADJ) {
+                    int sk[DMAX] = {Q, Q, Q};
+                    sk[dim] = sd;
+                    const typename PH::T tS = tpoint<P, D, Q, K>(a, l, ca, sk);
+#pragma unroll
+                    for (int u = 0; u < Q; ++u)
+                        e[u] = expphase_part<P, D, K>(a, tS, PH::part(tS, sget<P, Q>(a, dim, l, cb[dim], u), dim));
+                } else {
+                    const typename P::SE ys = sget<P, Q>(a, dim, l, cb[dim], sd);
+#pragma unroll
+                    for (int u = 0; u < Q; ++u) {
+                        int sk[DMAX] = {Q, Q, Q};
+                        sk[dim] = u;
+                        const typename PH::T tS = tpoint<P, D, Q, K>(a, l, ca, sk);
+                        e[u] = expphase_part<P, D, K>(a, tS, PH::part(tS, ys, dim));
+                    }
+                }
+                const int base = (tau * n + sl) * RR + (D == 3 ? o1 * pw[oth[0]] : 0);
+                const int last = oth[D - 2];
+                const C *in = src + base;
+                C *out = dst + base;
+#pragma unroll 1
+                for (int oi = 0; oi < Q; ++oi) {
+                    const int off = oi * pw[last];
+                    C acc = czero<C>();
+#pragma unroll
+                    for (int u = 0; u < Q; ++u) {
+                        const C v = in[off + u * pw[dim]];
+                        if constexpr (ADJ)
+                            acc = cadd(acc, cjmul(e[u], v));
+                        else
+                            cmac(acc, e[u], v);
+                    }
+                    out[off + sd * pw[dim]] = acc;
+                }
+            }
+            __syncthreads();
+            C *t = src;
+            src = dst;
+            dst = t;
+        }
+        if (src != Wt) {
+            for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) Wt[j] = src[j];
+            __syncthreads();
+        }
+    }
+
     // ---- one row-form merge level (l -> l+1) on all tiles of the CTA.  TC caches the
     // target features of the parents' nodes (T * 2^{Di} boxes x q^d nodes) for stage A.
     static __device__ void row_level(const KArgs<P> &a, C *Wt, C *S, typename PH::T *TC, int l, int i)
@@ -1477,7 +1564,12 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pa
         TL::load(a, Wt, rhs);
     __syncthreads();
     for (int i = 0; i < a.k; ++i) TL::col_level(a, Wt, S, a.l0 + i, i);
-    if (a.flags & F_SWITCH) TL::switch_tiles(a, Wt, S, a.l0 + a.k);
+    if (a.flags & F_SWITCH) {
+        if constexpr (K == KIND_DOT || K == KIND_SEPARABLE)
+            TL::template switch_sep<false>(a, Wt, S, a.l0 + a.k);
+        else
+            TL::switch_tiles(a, Wt, S, a.l0 + a.k);
+    }
     TL::store(a, Wt, rhs);
 }
 
@@ -1514,7 +1606,12 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pa
     const int rhs = blockIdx.y;
     TL::load_strided(a, Wt, rhs);
     __syncthreads();
-    if (a.flags & F_SWITCH) TL::switch_adj(a, Wt, S, a.l0 + a.k);
+    if (a.flags & F_SWITCH) {
+        if constexpr (K == KIND_DOT || K == KIND_SEPARABLE)
+            TL::template switch_sep<true>(a, Wt, S, a.l0 + a.k);
+        else
+            TL::switch_adj(a, Wt, S, a.l0 + a.k);
+    }
     for (int i = a.k - 1; i >= 0; --i) TL::col_level_adj(a, Wt, S, a.l0 + i, i);
     if (a.flags & F_INIT)
         TL::init_adj(a, Wt, rhs);
