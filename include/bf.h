@@ -86,8 +86,23 @@ typedef struct {
     int32_t node_kind;        /* 0 Chebyshev-Lobatto cos(j pi/(q-1))/2, 1 first kind        */
     int32_t max_nrhs;         /* largest nrhs an apply may use (>= 1)                       */
     int32_t fuse_levels;      /* levels fused per kernel pass; 0 selects the default        */
-    int32_t reserved[7];      /* must be zero                                               */
+    int32_t phase_tables;     /* 1: evaluate every phase factor once, at plan creation      */
+    int32_t reserved[6];      /* must be zero                                               */
 } bf_params;
+
+/* Phase tables (phase_tables = 1; mixed precisions, d = 2): the precompute trade-off of
+ * Section 1.4.  bf_plan_create evaluates every phase factor of the apply -- the 5 r
+ * modulation factors per pair and level, the r x r switch matrices, init and final --
+ * once into device memory (5 r L + r^2 + 2 r + 1 complex64 numbers per point: 16.2 GB at
+ * d = 2, N = 1024, q = 5; BF_ERR_NOMEM if it does not fit), and every bf_apply, for any
+ * nrhs, reads them instead of evaluating Phi: the apply streams the table instead of
+ * being bound by instruction issue.  The factors are the ones the evaluating kernels
+ * compute, so results are the same.  The apply kernels fetch each CTA's table blocks with
+ * bulk copies (the TMA engine, cp.async.bulk) into two shared-memory buffers two blocks
+ * ahead of use.  Needs q <= 5.  bf_plan_table_info reports the table's bytes, the time
+ * its construction took and (synchronising the device; timed_out may be NULL) whether a
+ * wait for a copy ever gave up (results undefined then).  The adjoint and persistent
+ * batches evaluate phases as without tables. */
 
 /* Defaults for the problem classes of Section 3: X = [0,1)^d, Y = [-N/2, N/2)^d
  * (integer frequencies), s = 1, points at the lower corner of their leaf boxes,
@@ -174,6 +189,7 @@ bf_status bf_last_cuda_error(bf_plan plan, int *cuda_err);
  *   launches per apply (per right-hand-side batch), bytes of device workspace. */
 bf_status bf_plan_info(bf_plan plan, int *d, int64_t *N, int *q, int *m, int *fuse_levels,
                        int *launches_per_apply, int64_t *workspace_bytes);
+bf_status bf_plan_table_info(bf_plan plan, int64_t *table_bytes, double *build_ms, int *timed_out);
 
 /* Autotuner.  Times candidate tile schedules of the apply bf_apply runs for nrhs
  * right-hand sides on this device and keeps the fastest in the plan.  Single-RHS (and

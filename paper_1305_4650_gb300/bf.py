@@ -24,7 +24,8 @@ EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint"
            "bf_apply_batched", "bf_destroy", "bf_status_string", "bf_last_cuda_error", "bf_plan_info",
            "bf_apply_pass", "bf_pass_info", "bf_pass_count", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate",
            "bf_measure_phase_rate", "bf_batch_create", "bf_batch_apply", "bf_batch_status",
-           "bf_batch_selftest_timeout", "bf_batch_info", "bf_batch_wait_stats", "bf_batch_destroy", "bf_plan_autotune"]
+           "bf_batch_selftest_timeout", "bf_batch_info", "bf_batch_wait_stats", "bf_batch_destroy", "bf_plan_autotune",
+           "bf_plan_table_info"]
 
 
 class BfError(RuntimeError):
@@ -38,7 +39,8 @@ class BfParams(ctypes.Structure):
                 ("y_lo", ctypes.c_double * 3), ("y_w", ctypes.c_double * 3),
                 ("phase_scale", ctypes.c_double), ("tgt_off", ctypes.c_double), ("src_off", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("switch_level", ctypes.c_int32), ("node_kind", ctypes.c_int32),
-                ("max_nrhs", ctypes.c_int32), ("fuse_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 7)]
+                ("max_nrhs", ctypes.c_int32), ("fuse_levels", ctypes.c_int32), ("phase_tables", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 6)]
 
 
 _lib = None
@@ -83,6 +85,8 @@ def load():
                                       ctypes.POINTER(i64)]
         lib.bf_batch_destroy.argtypes = [vp]
         lib.bf_plan_autotune.argtypes = [vp, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.bf_plan_table_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(i32)]
         lib.bf_batch_wait_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
         for name in EXPORTS:
             getattr(lib, name).restype = getattr(lib, name).restype or ctypes.c_int
@@ -112,7 +116,8 @@ class Plan:
 
     def __init__(self, d: int, N: int, q: int, phase: str, precision: str = "mixed", scale: float = 1.0,
                  x_lo=None, x_w=None, y_lo=None, y_w=None, tgt_off: float = 0.0, src_off: float = 0.0,
-                 switch_level: int = -1, node_kind: int = 0, max_nrhs: int = 1, fuse_levels: int = 0):
+                 switch_level: int = -1, node_kind: int = 0, max_nrhs: int = 1, fuse_levels: int = 0,
+                 phase_tables: bool = False):
         lib = load()
         p = BfParams()
         _check(lib.bf_params_default(d, N, ctypes.byref(p)), "bf_params_default")
@@ -128,6 +133,7 @@ class Plan:
         p.node_kind = node_kind
         p.max_nrhs = max_nrhs
         p.fuse_levels = fuse_levels
+        p.phase_tables = 1 if phase_tables else 0
         h = ctypes.c_void_p()
         _check(lib.bf_plan_create(d, N, q, PHASE[phase], ctypes.byref(p), ctypes.byref(h)), "bf_plan_create")
         self._h = h
@@ -136,11 +142,12 @@ class Plan:
         self.cdtype = np.complex128 if precision == "fp64" else np.complex64
 
     @classmethod
-    def from_spec(cls, spec, max_nrhs: int = 1, precision: str | None = None, fuse_levels: int = 0) -> "Plan":
+    def from_spec(cls, spec, max_nrhs: int = 1, precision: str | None = None, fuse_levels: int = 0,
+                  phase_tables: bool = False) -> "Plan":
         x_lo, x_w, y_lo, y_w = spec.domain()
         return cls(spec.d, spec.N, spec.q, spec.phase, precision or spec.precision, spec.scale,
                    x_lo, x_w, y_lo, y_w, spec.tgt_off, spec.src_off, spec.switch_level, spec.node_kind,
-                   max_nrhs, fuse_levels)
+                   max_nrhs, fuse_levels, phase_tables)
 
     @property
     def handle(self) -> int:
@@ -204,6 +211,14 @@ class Plan:
     def apply_pass(self, i: int, g_ptr: int, f_ptr: int, nrhs: int, stream_ptr: int = 0) -> None:
         """Run pass i of the apply schedule only (instrumentation)."""
         _check(load().bf_apply_pass(self._h, i, g_ptr, f_ptr, nrhs, stream_ptr), "bf_apply_pass", self._h)
+
+    def table_info(self) -> dict:
+        """Bytes of the plan's phase table (0 without), the milliseconds its construction took, and
+        whether a wait for a table copy ever gave up (synchronises the device)."""
+        b, ms, t = ctypes.c_int64(), ctypes.c_double(), ctypes.c_int()
+        _check(load().bf_plan_table_info(self._h, ctypes.byref(b), ctypes.byref(ms), ctypes.byref(t)),
+               "bf_plan_table_info")
+        return dict(bytes=b.value, build_ms=ms.value, timed_out=bool(t.value))
 
     def autotune(self, nrhs: int = 1, reps: int = 3, stream=None) -> float:
         """Time candidate tile schedules for nrhs right-hand sides, keep the fastest; ms per apply."""

@@ -42,6 +42,11 @@ struct bf_plan_s {
     int64_t ws_bytes = 0;
     std::vector<Pass> passes;
     std::vector<Pass> passes_mr;   // schedule of the multi-RHS kernels (empty if not compiled)
+    void *ptab = nullptr;          // phase table of the multi-RHS schedule (bf_params.phase_tables)
+    int *errflag = nullptr;        // device flag of the table stream's bounded waits
+    int64_t ptab_bytes = 0;
+    std::vector<int64_t> ptab_off, ptab_cta;   // per pass: offset and per-CTA size, complex numbers
+    float ptab_build_ms = 0.f;
     int mr_rc = 1;                 // right-hand sides per scratch chunk of the multi-RHS kernels
     std::vector<Pass> passes_adj;  // schedule whose reverse is the adjoint (fits the row caches)
     const bfl::PassFns *fns = nullptr;
@@ -227,6 +232,15 @@ size_t mr_smem(const bf_plan_s *p, const Pass &ps, int nr, int rc)
     return (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (size_t)p->r * p->csize * (size_t)(nr + 2 * rc + 5);
 }
 
+// multi-RHS pass reading a phase table: stream control and two table-block buffers, then
+// the weights and scratch (no phase cache)
+size_t mr_smem_table(const bf_plan_s *p, const Pass &ps, int nr, int rc)
+{
+    const size_t npr = (size_t)ps.T << (p->d * ps.k);
+    const size_t blk = (size_t)(p->q > 5 ? p->q : 5) * (size_t)p->r * npr;
+    return (size_t)bfk::TABCTL_BYTES + 2 * blk * p->csize + npr * (size_t)p->r * p->csize * (size_t)(nr + 2 * rc);
+}
+
 // A CTA owns np pairs (2^{d kmax} of the instantiation, fewer for tiny problems):
 // T = np / 2^{dk} tiles of a k-level pass.
 Pass make_pass(const bf_plan_s *p, int64_t np_cta, int row, int l0, int k, int flags)
@@ -320,6 +334,7 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
     const int nr = nrhs < mx ? nrhs : mx;
     a.rc = p->mr_rc < nr ? p->mr_rc : nr;
     void *buf[2] = {p->w0, p->w1};
+    const int mode = p->ptab ? bfk::PM_TABLE : bfk::PM_COMPUTE;
     for (int i = first; i < last; ++i) {
         const Pass &ps = p->passes_mr[i];
         a.l0 = ps.l0;
@@ -328,10 +343,23 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
         a.T = ps.T;
         a.win = static_cast<const typename P::C *>(buf[i & 1]);
         a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
+        a.ptab = p->ptab ? static_cast<typename P::C *>(p->ptab) + p->ptab_off[i] : nullptr;
+        a.ptab_cta = p->ptab ? p->ptab_cta[i] : 0;
+        a.err = p->errflag;
         const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
-        const size_t smem = mr_smem(p, ps, nr, a.rc);
-        cudaError_t e = (ps.row ? p->fns->row_mr : p->fns->col_mr)(&a, (unsigned)ctas, (unsigned)((nrhs + mx - 1) / mx),
-                                                                   smem, s);
+        a.ncta = (int)ctas;
+        const size_t smem = p->ptab ? mr_smem_table(p, ps, nr, a.rc) : mr_smem(p, ps, nr, a.rc);
+        int64_t grid = ctas;
+        if (p->ptab) {   // as many CTAs as fit; each streams the table of several tile groups
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int per_sm = p->fns->mr_table_occupancy(ps.row, smem);
+            if (per_sm < 1) return BF_ERR_UNSUPPORTED;
+            if ((int64_t)sms * per_sm < grid) grid = (int64_t)sms * per_sm;
+        }
+        cudaError_t e = (ps.row ? p->fns->row_mr : p->fns->col_mr)[mode](&a, (unsigned)grid,
+                                                                         (unsigned)((nrhs + mx - 1) / mx), smem, s);
         if (e != cudaSuccess) return cuda_fail(p, e);
     }
     return BF_OK;
@@ -421,7 +449,66 @@ double phase_bound(int d, int kind, const bf_params *p)
 }
 
 // the multi-RHS schedule serves nrhs >= 2 where it is compiled (mixed precisions, d = 2)
-bool use_mr(const bf_plan_s *p, int nrhs) { return nrhs >= 2 && p->prec != BF_PREC_FP64 && !p->passes_mr.empty(); }
+bool use_mr(const bf_plan_s *p, int nrhs)
+{
+    return (nrhs >= 2 || p->ptab) && p->prec != BF_PREC_FP64 && !p->passes_mr.empty();
+}
+
+// Phase table of the multi-RHS schedule: per pass and CTA, the init factors, 5 r per pair for
+// each level, the r x r switch matrices and the final factors, in the order the kernels read them.
+template <class P>
+bf_status build_phase_table(bf_plan p)
+{
+    const int64_t r = p->r;
+    int64_t total = 0;
+    p->ptab_off.clear();
+    p->ptab_cta.clear();
+    for (const Pass &ps : p->passes_mr) {
+        const int64_t npr = (int64_t)ps.T << (p->d * ps.k), ctas = (p->npts >> (p->d * ps.k)) / ps.T;
+        int64_t per = ps.k * 5 * r * npr;
+        if (ps.flags & bfk::F_INIT) per += r * npr;
+        if (ps.flags & bfk::F_SWITCH) per += r * r * npr;
+        if (ps.flags & bfk::F_FINAL) per += (r + 1) * npr;
+        p->ptab_off.push_back(total);
+        p->ptab_cta.push_back(per);
+        total += per * ctas;
+    }
+    p->ptab_bytes = total * (int64_t)sizeof(typename P::C);
+    cudaError_t e = cudaMalloc(&p->ptab, (size_t)p->ptab_bytes);
+    if (e != cudaSuccess) {
+        p->ptab = nullptr;
+        return cuda_fail(p, e);
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventRecord(e0);
+    bfk::KArgs<P> a;
+    fill_args<P>(p, a);
+    a.nrhs = 1;
+    a.rc = 1;
+    for (size_t i = 0; i < p->passes_mr.size() && e == cudaSuccess; ++i) {
+        const Pass &ps = p->passes_mr[i];
+        a.l0 = ps.l0;
+        a.k = ps.k;
+        a.flags = ps.flags;
+        a.T = ps.T;
+        a.ptab = static_cast<typename P::C *>(p->ptab) + p->ptab_off[i];
+        a.ptab_cta = p->ptab_cta[i];
+        const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
+        a.ncta = (int)ctas;
+        e = (ps.row ? p->fns->row_mr : p->fns->col_mr)[bfk::PM_BUILD](&a, (unsigned)ctas, 1u, mr_smem(p, ps, 1, 1), 0);
+    }
+    cudaEventRecord(e1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    p->ptab_build_ms = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    return BF_OK;
+}
 
 const std::vector<Pass> &schedule_for(const bf_plan_s *p, int nrhs) { return use_mr(p, nrhs) ? p->passes_mr : p->passes; }
 
@@ -460,6 +547,7 @@ bf_status batch_build(bf_batch b, const bf_plan *plans, const int *nrhs, int cou
             a.wout = static_cast<typename P::C *>(buf[(j + 1) & 1]);
             a.nrhs = nrhs[i];
             a.rc = rc;
+            a.ncta = (int)((p->npts >> (p->d * ps.k)) / ps.T);
             desc.push_back(a);
             const size_t sm = mr_smem(p, ps, nr, rc);
             if (sm > smem) smem = sm;
@@ -636,8 +724,10 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     if (prm->node_kind != 0 && prm->node_kind != 1) return BF_ERR_INVALID_ARG;
     if (prm->max_nrhs < 1 || prm->max_nrhs > 65535) return BF_ERR_INVALID_ARG;
     if (prm->fuse_levels < 0 || prm->fuse_levels > 8) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 7; ++i)
+    for (int i = 0; i < 6; ++i)
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
+    if (prm->phase_tables != 0 && prm->phase_tables != 1) return BF_ERR_INVALID_ARG;
+    if (prm->phase_tables && (prm->precision == BF_PREC_FP64 || d != 2 || q > 5)) return BF_ERR_UNSUPPORTED;
 
     bf_plan p = new (std::nothrow) bf_plan_s();
     if (!p) return BF_ERR_NOMEM;
@@ -730,12 +820,22 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         else
             p->ctab_levels = lv;
     }
+    if (st == BF_OK && prm->phase_tables) {
+        cudaError_t e = cudaMalloc(&p->errflag, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->errflag, 0, sizeof(int));
+        if (e != cudaSuccess)
+            st = cuda_fail(p, e);
+        else if (p->passes_mr.empty())
+            st = BF_ERR_UNSUPPORTED;
+        else
+            st = p->prec == BF_PREC_MIXED_SFU ? build_phase_table<bfk::PMIXF>(p) : build_phase_table<bfk::PMIX>(p);
+    }
     if (st == BF_OK) {
         const size_t wbytes = (size_t)p->max_nrhs * (size_t)p->npts * (size_t)p->r * p->csize;
         cudaError_t e = cudaMalloc(&p->w0, wbytes);
         if (e == cudaSuccess) e = cudaMalloc(&p->w1, wbytes);
         if (e != cudaSuccess) st = cuda_fail(p, e);
-        p->ws_bytes = (int64_t)(2 * wbytes);
+        p->ws_bytes = (int64_t)(2 * wbytes) + p->ptab_bytes;
     }
     if (st != BF_OK) {
         bf_destroy(p);
@@ -792,7 +892,9 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
         return BF_OK;
     };
     double best = 1e300;
-    if (st == BF_OK && use_mr(p, nrhs)) {
+    if (st == BF_OK && p->ptab) {
+        st = time_it(best);          // the phase table fixes the multi-RHS schedule
+    } else if (st == BF_OK && use_mr(p, nrhs)) {
         // multi-RHS tiles: fused levels, pairs per CTA, right-hand sides per scratch chunk
         const int nr = nrhs < p->fns->mr_max ? nrhs : p->fns->mr_max;
         const int64_t ppr = p->fns->mr_nthreads / p->r;
@@ -1048,6 +1150,8 @@ bf_status bf_destroy(bf_plan p)
     if (p->w0) cudaFree(p->w0);
     if (p->w1) cudaFree(p->w1);
     if (p->ctab) cudaFree(p->ctab);
+    if (p->ptab) cudaFree(p->ptab);
+    if (p->errflag) cudaFree(p->errflag);
     if (p->gstage) cudaFree(p->gstage);
     if (p->fstage) cudaFree(p->fstage);
     delete p;
@@ -1087,6 +1191,22 @@ bf_status bf_measure_phase_rate(bf_plan p, int paired, double *gphases_per_s)
     fill_args<bfk::PMIX>(p, am);
     cudaError_t e = bfl::phase_rate(&am, p->prec == BF_PREC_MIXED_SFU, p->L, p->q, p->kind, paired, gphases_per_s);
     if (e != cudaSuccess) return cuda_fail(p, e);
+    return BF_OK;
+}
+
+bf_status bf_plan_table_info(bf_plan p, int64_t *bytes, double *build_ms, int *timed_out)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (bytes) *bytes = p->ptab_bytes;
+    if (build_ms) *build_ms = p->ptab_build_ms;
+    if (timed_out) {
+        int v = 0;
+        if (p->errflag) {
+            cudaError_t e = cudaMemcpy(&v, p->errflag, sizeof(int), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(p, e);
+        }
+        *timed_out = v != 0;
+    }
     return BF_OK;
 }
 

@@ -219,6 +219,10 @@ struct KArgs {
     int rc;                           // right-hand sides per scratch chunk (multi-RHS kernels)
     const void *ctab;                 // target features at box centres, levels 0..ctab_levels (or null)
     int ctab_levels;
+    C *ptab;                          // phase table of the pass (multi-RHS passes with tables) or null
+    int64_t ptab_cta;                 // phase-table complex numbers per CTA of the pass
+    int *err;                         // set by a bounded wait that gave up (or null)
+    int ncta;                         // CTAs (tile groups of T tiles) of the pass (multi-RHS kernels)
 };
 
 // --------------------------------------------------------- index helpers

@@ -68,24 +68,44 @@ cudaError_t launch_row_adj(const void *kargs, unsigned gx, unsigned gy, size_t s
     return cudaGetLastError();
 }
 
-template <int Q, class P, int K>
+template <int Q, class P, int K, int PM>
 cudaError_t launch_col_mr(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
 {
     static size_t granted[64] = {0};
-    cudaError_t e = prepare(bfk::k_col_pass_mr<Q, P, K>, smem, granted);
+    cudaError_t e = prepare(bfk::k_col_pass_mr<Q, P, K, PM>, smem, granted);
     if (e != cudaSuccess) return e;
-    bfk::k_col_pass_mr<Q, P, K><<<dim3(gx, gy), bfk::CfgMR<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    bfk::k_col_pass_mr<Q, P, K, PM><<<dim3(gx, gy), bfk::CfgMR<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
     return cudaGetLastError();
 }
 
-template <int Q, class P, int K>
+template <int Q, class P, int K, int PM>
 cudaError_t launch_row_mr(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
 {
     static size_t granted[64] = {0};
-    cudaError_t e = prepare(bfk::k_row_pass_mr<Q, P, K>, smem, granted);
+    cudaError_t e = prepare(bfk::k_row_pass_mr<Q, P, K, PM>, smem, granted);
     if (e != cudaSuccess) return e;
-    bfk::k_row_pass_mr<Q, P, K><<<dim3(gx, gy), bfk::CfgMR<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    bfk::k_row_pass_mr<Q, P, K, PM><<<dim3(gx, gy), bfk::CfgMR<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
     return cudaGetLastError();
+}
+
+// CTAs per SM of the table-reading multi-RHS passes with `smem` bytes of shared memory
+template <int Q, class P, int K>
+int mr_table_occupancy(int row, size_t smem)
+{
+    static size_t granted_c[64] = {0}, granted_r[64] = {0};
+    int n = 0;
+    if (row) {
+        if (prepare(bfk::k_row_pass_mr<Q, P, K, bfk::PM_TABLE>, smem, granted_r) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bfk::k_row_pass_mr<Q, P, K, bfk::PM_TABLE>,
+                                                          bfk::CfgMR<Q>::NT, smem) != cudaSuccess)
+            return 0;
+    } else {
+        if (prepare(bfk::k_col_pass_mr<Q, P, K, bfk::PM_TABLE>, smem, granted_c) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bfk::k_col_pass_mr<Q, P, K, bfk::PM_TABLE>,
+                                                          bfk::CfgMR<Q>::NT, smem) != cudaSuccess)
+            return 0;
+    }
+    return n;
 }
 
 template <int Q, class P, int K>
@@ -126,13 +146,18 @@ const PassFns *fns_for()
     if constexpr (D == 2 && !P::is_f64) {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT,
-                                  launch_col_mr<Q, P, K>, launch_row_mr<Q, P, K>, bfk::MRMAX, bfk::CfgMR<Q>::NT,
-                                  launch_batch<Q, P, K>, batch_ctas_per_sm<Q, P, K>,
+                                  {launch_col_mr<Q, P, K, bfk::PM_COMPUTE>, launch_col_mr<Q, P, K, bfk::PM_BUILD>,
+                                   launch_col_mr<Q, P, K, bfk::PM_TABLE>},
+                                  {launch_row_mr<Q, P, K, bfk::PM_COMPUTE>, launch_row_mr<Q, P, K, bfk::PM_BUILD>,
+                                   launch_row_mr<Q, P, K, bfk::PM_TABLE>},
+                                  bfk::MRMAX, bfk::CfgMR<Q>::NT,
+                                  launch_batch<Q, P, K>, batch_ctas_per_sm<Q, P, K>, mr_table_occupancy<Q, P, K>,
                                   launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
         return &f;
     } else {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
-                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, nullptr, nullptr, 0, 0, nullptr, nullptr,
+                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, {nullptr, nullptr, nullptr},
+                                  {nullptr, nullptr, nullptr}, 0, 0, nullptr, nullptr, nullptr,
                                   launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
         return &f;
     }

@@ -15,12 +15,15 @@ struct PassFns {
     int kmax;                    // most levels one pass fuses
     int np;                      // pairs per CTA (2^{d kmax})
     int nthreads;                // threads per CTA
-    pass_fn col_mr, row_mr;      // multi-RHS forward passes with a phase cache (null if absent)
+    // multi-RHS forward passes with a phase cache (null if absent), per phase mode:
+    // [0] evaluate, [1] build the plan's phase table, [2] read the phase table
+    pass_fn col_mr[3], row_mr[3];
     int mr_max;                  // right-hand sides one multi-RHS CTA holds
     int mr_nthreads;             // threads per multi-RHS CTA
     // persistent batch kernel (bf_mr.cuh): bargs points to a bfk::BatchArgs<P>
     cudaError_t (*batch)(const void *bargs, unsigned grid, size_t smem, cudaStream_t s);
     int (*batch_ctas_per_sm)(size_t smem);
+    int (*mr_table_occupancy)(int row, size_t smem);   // CTAs per SM of the table-reading passes
     cudaError_t (*center_table)(const void *kargs, void *out, int levels);   // target features at box centres
     int tsize;                   // bytes of one target-feature record
 };

@@ -15,6 +15,13 @@
 //   S  [rc][2 npr r]      stage scratch
 //   PC [5 r npr]          phase cache of the current stage
 // Stage items, scratch layouts and the order of every accumulation follow Tile<2,...>.
+//
+// Phase tables (the precompute trade-off of Section 1.4).  A plan may keep every phase
+// factor of its apply in device memory: PM_BUILD runs the phase stages only and writes
+// each stage's cache (and the switch matrices) to the table, in the order PM_TABLE reads
+// them back; PM_TABLE copies them into the cache instead of evaluating Phi, which turns
+// the instruction-bound apply into a stream over the table.  The values are those the
+// computing kernels (PM_COMPUTE) would produce, so the results are identical.
 #pragma once
 
 #include "bf_device.cuh"
@@ -22,6 +29,67 @@
 namespace bfk {
 
 constexpr int MRMAX = 16;   // right-hand sides held by one CTA
+
+enum { PM_COMPUTE = 0, PM_BUILD = 1, PM_TABLE = 2 };
+
+// ---- bulk copies (TMA engine) into shared memory, completed on an mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
+{
+    uint32_t ok;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(ok)
+                 : "r"(smem_u32(bar)), "r"(parity)
+                 : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// wait for phase `parity` of an mbarrier; false after `limit` polls (the caller flags the error)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity, int limit)
+{
+    for (int i = 0; i < limit; ++i)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+constexpr int TS_MAXB = 16;          // table blocks per CTA and pass
+constexpr int TS_POLLS = 1 << 16;    // polls of one wait before it is flagged
+
+// Phase-table stream of a CTA (PM_TABLE): block j of the pass's table arrives in buffer
+// j & 1 by one bulk copy, issued two blocks ahead of its use.
+struct TabCtl {
+    uint64_t bar[2];
+    int64_t off[TS_MAXB + 1];   // block j of a tile group = complex numbers [off[j], off[j+1]) of its table
+    int nblk;                   // blocks per tile group
+    int total;                  // blocks of all the CTA's tile groups
+};
+
+template <class C>
+struct TS {
+    C *tb;          // PM_BUILD: write cursor; PM_TABLE: the pass's table in global memory
+    C *buf[2];      // PM_TABLE: shared-memory buffers
+    TabCtl *ctl;
+    int j;          // PM_TABLE: next block to use
+    int *err;       // set when a wait gives up
+    int c0, cstep;  // PM_TABLE: the CTA's tile groups are c0, c0 + cstep, ...
+    int64_t cstride;   // table complex numbers per tile group
+};
 
 // pairs per switch round and threads per CTA: the switch runs one thread per (pair, s)
 template <int Q>
@@ -64,6 +132,76 @@ struct TileMR {
         return ((beta >> (D * i)) << (D * (i + 1))) + ra;
     }
 
+    // ---- phase-table stream (PM_TABLE)
+    static __device__ void ts_issue(TS<C> &ts, int j)
+    {
+        TabCtl *c = ts.ctl;
+        const int g = j / c->nblk, jj = j - g * c->nblk;
+        const unsigned bytes = (unsigned)((c->off[jj + 1] - c->off[jj]) * (int64_t)sizeof(C));
+        const C *src = ts.tb + (int64_t)(ts.c0 + g * ts.cstep) * ts.cstride + c->off[jj];
+        mbar_expect_tx(&c->bar[j & 1], bytes);
+        bulk_g2s(ts.buf[j & 1], src, bytes, &c->bar[j & 1]);
+    }
+    // block list of a tile group (sizes in complex numbers), barriers, the first two copies
+    // of the stream over all the CTA's tile groups
+    static __device__ void ts_setup(TS<C> &ts, const KArgs<P> &a, const Ctx &x, bool row)
+    {
+        if (threadIdx.x == 0) {
+            TabCtl *c = ts.ctl;
+            const int64_t npr = x.npr, r5 = 5 * RR * npr;
+            int nb = 0;
+            int64_t o = 0;
+            auto add = [&](int64_t n) { c->off[nb++] = o; o += n; };
+            if (!row) {
+                if (a.flags & F_INIT) add(RR * npr);
+                for (int i = 0; i < a.k; ++i) add(r5);
+                if (a.flags & F_SWITCH)
+                    for (int th = 0; th < Q; ++th) add((int64_t)Q * RR * npr);
+            } else {
+                for (int i = 0; i < a.k; ++i) add(r5);
+                if (a.flags & F_FINAL) add((RR + 1) * npr);
+            }
+            c->off[nb] = o;
+            c->nblk = nb;
+            c->total = nb * ((a.ncta - ts.c0 + ts.cstep - 1) / ts.cstep);
+            mbar_init(&c->bar[0], 1);
+            mbar_init(&c->bar[1], 1);
+            mbar_init_fence();
+            for (int j = 0; j < 2 && j < c->total; ++j) ts_issue(ts, j);
+        }
+        ts.j = 0;
+        __syncthreads();
+    }
+    // wait for the next block; a wait that gives up is flagged and waited for once more,
+    // so no copy is left in flight (the results are then undefined, never a hang)
+    static __device__ C *ts_acquire(TS<C> &ts)
+    {
+        const int j = ts.j;
+        uint64_t *bar = &ts.ctl->bar[j & 1];
+        if (!mbar_wait(bar, (unsigned)((j >> 1) & 1), TS_POLLS)) {
+            if (ts.err) atomicExch(ts.err, 1);
+            mbar_wait(bar, (unsigned)((j >> 1) & 1), TS_POLLS);
+        }
+        return ts.buf[j & 1];
+    }
+    // after the block's last reader (callers sync first): refill its buffer two blocks ahead
+    static __device__ void ts_release(TS<C> &ts)
+    {
+        const int j = ts.j++;
+        if (threadIdx.x == 0 && j + 2 < ts.ctl->total) {
+            fence_proxy_async();
+            ts_issue(ts, j + 2);
+        }
+    }
+
+    // ---- phase-table store of n complex numbers (PM_BUILD; n even, 16-byte aligned blocks)
+    static __device__ __forceinline__ void tab_store(C *dst, const C *src, int n)
+    {
+        const float4 *s4 = reinterpret_cast<const float4 *>(src);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);
+        for (int j = threadIdx.x; j < (n >> 1); j += NT) __stcs(d4 + j, s4[j]);
+    }
+
     // ---- CTA input: npr consecutive pairs per right-hand side
     static __device__ void load(const KArgs<P> &a, const Ctx &x, C *W)
     {
@@ -91,13 +229,15 @@ struct TileMR {
     }
 
     // ---- init: PC[pair][t] = l_t(y) e^{-2pi i Phi(x0(X), y_t^B)} e^{2pi i Phi(x0(X), y)}, then W = PC g(y)
-    static __device__ void init(const KArgs<P> &a, const Ctx &x, C *W, C *PC, const C *g)
+    template <int PM>
+    static __device__ void init(const KArgs<P> &a, const Ctx &x, C *W, C *PC, const C *g, TS<C> &ts)
     {
         const int k = a.k, n = 1 << (D * k), L = a.L, WS = x.npr * RR;
         const int cX[DMAX] = {0, 0, 0};
         const int ctr[DMAX] = {Q, Q, Q};
         const typename PH::T tX = tpoint<P, D, Q, K>(a, 0, cX, ctr);
-        for (int it = threadIdx.x; it < WS; it += NT) {
+        if constexpr (PM == PM_TABLE) PC = ts_acquire(ts);
+        for (int it = threadIdx.x; PM != PM_TABLE && it < WS; it += NT) {
             const int t = it % RR, pr = it / RR;
             const int tk[DMAX] = {t % Q, t / Q, 0};
             const R lag = a.lsrc[tk[0]] * a.lsrc[tk[1]];
@@ -117,7 +257,12 @@ struct TileMR {
             PC[it] = e;
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < x.nr * WS; j += NT) {
+        if constexpr (PM == PM_BUILD) {   // build: store the factors; no weights are touched
+            tab_store(ts.tb, PC, WS);
+            ts.tb += WS;
+            __syncthreads();
+        }
+        for (int j = threadIdx.x; PM != PM_BUILD && j < x.nr * WS; j += NT) {
             const int rb = (j / RR) >> x.lgp, it = j - rb * WS;
             const int t = it % RR, pr = it / RR;
             C v = czero<C>();
@@ -132,16 +277,19 @@ struct TileMR {
             W[j] = v;
         }
         __syncthreads();
+        if constexpr (PM == PM_TABLE) ts_release(ts);
     }
 
     // ---- one column-form merge level (l -> l+1); ms.M holds the child->parent matrices
-    template <class MS>
-    static __device__ void col_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i)
+    template <int PM, class MS>
+    static __device__ void col_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i,
+                                     TS<C> &ts)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
+        if constexpr (PM == PM_TABLE) PC = ts_acquire(ts);
         C *PA = PC;                  // [pA][chi][cl][tq][t0']  modulation of the inputs
         C *PB = PC + nout * 4 * RR;  // [pA][tq][tl]            demodulation of the output
-        for (int it = threadIdx.x; it < nout * 4 * Q; it += NT) {
+        for (int it = threadIdx.x; PM != PM_TABLE && it < nout * 4 * Q; it += NT) {
             const int tq = it % Q, cl = (it / Q) & 1, chi = (it / (2 * Q)) & 1, pA = it / (4 * Q);
             const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
             uint32_t Ap, Bstar, Apg, Bq;
@@ -163,7 +311,7 @@ struct TileMR {
                 o[t0p] = expphase_part<P, D, K>(a, tA, pt);
             }
         }
-        for (int it = threadIdx.x; it < nout * RR; it += NT) {
+        for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
             const int tl = it % Q, tq = (it / Q) % Q, pA = it / RR;
             const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
             uint32_t Ap, Bstar, Apg, Bq;
@@ -180,7 +328,12 @@ struct TileMR {
             PB[it] = expphase_part<P, D, K>(a, tA, pt);
         }
         __syncthreads();
-        for (int r0 = 0; r0 < x.nr; r0 += x.rc) {
+        if constexpr (PM == PM_BUILD) {   // build: store the factors; no weights are touched
+            tab_store(ts.tb, PC, 5 * RR * nout);
+            ts.tb += 5 * RR * nout;
+            __syncthreads();
+        }
+        for (int r0 = 0; PM != PM_BUILD && r0 < x.nr; r0 += x.rc) {
             const int nrc = min(x.rc, x.nr - r0);
             // stage A: items (rb, pA, chi, tq): modulate the inputs, contract dimension 0
             for (int it = threadIdx.x; it < nrc * nout * 2 * Q; it += NT) {
@@ -233,11 +386,15 @@ struct TileMR {
             }
             __syncthreads();
         }
+        if constexpr (PM == PM_TABLE) ts_release(ts);
     }
 
     // ---- switch at level l: one thread per (pair, s), one accumulator per right-hand side;
-    // rounds of whole pairs, results written back after every thread of the round has read
-    static __device__ void switch_tiles(const KArgs<P> &a, const Ctx &x, C *W, int l)
+    // rounds of whole pairs, results written back after every thread of the round has read.
+    // Phase-table layout: q chunks (one per source digit t_1), each [pair][t_0][s], so a
+    // chunk is one contiguous block (PM_TABLE plans have one round: npr <= PPR).
+    template <int PM>
+    static __device__ void switch_tiles(const KArgs<P> &a, const Ctx &x, C *W, int l, TS<C> &ts)
     {
         const int k = a.k, n = 1 << (D * k), L = a.L, WS = x.npr * RR;
         const int G = CfgMR<Q>::PPR;
@@ -247,47 +404,71 @@ struct TileMR {
             C acc[MRMAX];
 #pragma unroll
             for (int rb = 0; rb < MRMAX; ++rb) acc[rb] = czero<C>();
-            if (act) {
+            typename PH::T tS;
+            int cb[DMAX] = {0, 0, 0};
+            if (PM != PM_TABLE && act) {
                 uint32_t Ap, Bstar;
                 tile_of(a, x, pl >> (D * k), Ap, Bstar);
                 const uint32_t A = (Ap << (D * k)) + digit_rev<D>(pl & (n - 1), k);
-                int ca[DMAX], cb[DMAX];
+                int ca[DMAX];
                 morton_decode<D>(A, l, ca);
                 morton_decode<D>(Bstar, L - l, cb);
                 const int sk[DMAX] = {s % Q, s / Q, 0};
-                const typename PH::T tS = tpoint<P, D, Q, K>(a, l, ca, sk);
-                const C *u = W + pl * RR;
+                tS = tpoint<P, D, Q, K>(a, l, ca, sk);
+            }
+            const C *u = W + pl * RR;
 #pragma unroll 1
-                for (int th = 0; th < Q; ++th) {
-                    const typename PH::Part hp = PH::part(tS, sget<P, Q>(a, 1, l, cb[1], th), 1);
+            for (int th = 0; th < Q; ++th) {
+                const C *chunk = nullptr;
+                if constexpr (PM == PM_TABLE) chunk = ts_acquire(ts);
+                if (act) {
+                    typename PH::Part hp;
+                    if constexpr (PM != PM_TABLE) hp = PH::part(tS, sget<P, Q>(a, 1, l, cb[1], th), 1);
 #pragma unroll
                     for (int t0 = 0; t0 < Q; ++t0) {
-                        const C e = expphase_part<P, D, K>(
-                            a, tS, PH::add(PH::part(tS, sget<P, Q>(a, 0, l, cb[0], t0), 0), hp));
+                        C e;
+                        if constexpr (PM == PM_TABLE)
+                            e = chunk[(pl * Q + t0) * RR + s];
+                        else
+                            e = expphase_part<P, D, K>(
+                                a, tS, PH::add(PH::part(tS, sget<P, Q>(a, 0, l, cb[0], t0), 0), hp));
+                        if constexpr (PM == PM_BUILD) {
+                            __stcs(ts.tb + ((int64_t)th * x.npr * Q + pl * Q + t0) * RR + s, e);
+                        } else {
 #pragma unroll
-                        for (int rb = 0; rb < MRMAX; ++rb)
-                            if (rb < x.nr) cmac(acc[rb], e, u[rb * WS + t0 + Q * th]);
+                            for (int rb = 0; rb < MRMAX; ++rb)
+                                if (rb < x.nr) cmac(acc[rb], e, u[rb * WS + t0 + Q * th]);
+                        }
                     }
                 }
+                if constexpr (PM == PM_TABLE) {
+                    __syncthreads();
+                    ts_release(ts);
+                }
             }
-            __syncthreads();
-            if (act) {
+            if constexpr (PM != PM_BUILD) {
+                __syncthreads();
+                if (act) {
 #pragma unroll
-                for (int rb = 0; rb < MRMAX; ++rb)
-                    if (rb < x.nr) W[rb * WS + pl * RR + s] = acc[rb];
+                    for (int rb = 0; rb < MRMAX; ++rb)
+                        if (rb < x.nr) W[rb * WS + pl * RR + s] = acc[rb];
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
+        if constexpr (PM == PM_BUILD) ts.tb += (int64_t)x.npr * RR * RR;
     }
 
     // ---- one row-form merge level (l -> l+1)
-    template <class MS>
-    static __device__ void row_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i)
+    template <int PM, class MS>
+    static __device__ void row_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i,
+                                     TS<C> &ts)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
+        if constexpr (PM == PM_TABLE) PC = ts_acquire(ts);
         C *PA = PC;              // [pin][th][t0]     pre-modulation at the parent's nodes
         C *PB = PC + nout * RR;  // [pA][c][s1][s0]   post-modulation at the child's nodes
-        for (int it = threadIdx.x; it < nout * RR; it += NT) {
+        for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
             const int t0 = it % Q, th = (it / Q) % Q, pin = it / RR;
             const int c = pin & (NC - 1), beta = (pin >> D) & (nblk - 1), tau = pin >> (D * k);
             uint32_t Ap, Bstar, Apg, Bq;
@@ -303,7 +484,7 @@ struct TileMR {
             const int tk[DMAX] = {t0, th, 0};
             PA[it] = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l, ca, tk), spoint<P, D, Q, K>(a, l, cb, ctr));
         }
-        for (int it = threadIdx.x; it < nout * RR; it += NT) {
+        for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
             const int s0 = it % Q, s1 = (it / Q) % Q, pA = it / RR;
             const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
             uint32_t Ap, Bstar, Apg, Bq;
@@ -326,7 +507,12 @@ struct TileMR {
                 PB[((pA * NC + c) * Q + s1) * Q + s0] = expphase_part<P, D, K>(a, tS, PH::add(q0[c & 1], q1[c >> 1]));
         }
         __syncthreads();
-        for (int r0 = 0; r0 < x.nr; r0 += x.rc) {
+        if constexpr (PM == PM_BUILD) {   // build: store the factors; no weights are touched
+            tab_store(ts.tb, PC, 5 * RR * nout);
+            ts.tb += 5 * RR * nout;
+            __syncthreads();
+        }
+        for (int r0 = 0; PM != PM_BUILD && r0 < x.nr; r0 += x.rc) {
             const int nrc = min(x.rc, x.nr - r0);
             // stage A: items (rb, pin, th): pre-modulate input c, contract dimension 0 for both alpha_0
             for (int it = threadIdx.x; it < nrc * nout * Q; it += NT) {
@@ -390,16 +576,19 @@ struct TileMR {
             }
             __syncthreads();
         }
+        if constexpr (PM == PM_TABLE) ts_release(ts);
     }
 
     // ---- final evaluation: PC[pair][t] = l_t(x) conj(e^{2pi i Phi(x_t, y0(Y))}), PC[pair][r] = e^{2pi i Phi(x, y0(Y))}
-    static __device__ void final_eval(const KArgs<P> &a, const Ctx &x, const C *W, C *PC, C *f)
+    template <int PM>
+    static __device__ void final_eval(const KArgs<P> &a, const Ctx &x, const C *W, C *PC, C *f, TS<C> &ts)
     {
         const int k = a.k, n = 1 << (D * k), L = a.L, WS = x.npr * RR;
         const int cY[DMAX] = {0, 0, 0};
         const int ctr[DMAX] = {Q, Q, Q};
         const typename PH::S sY = spoint<P, D, Q, K>(a, L, cY, ctr);
-        for (int it = threadIdx.x; it < x.npr * (RR + 1); it += NT) {
+        if constexpr (PM == PM_TABLE) PC = ts_acquire(ts);
+        for (int it = threadIdx.x; PM != PM_TABLE && it < x.npr * (RR + 1); it += NT) {
             const int t = it % (RR + 1), pl = it / (RR + 1);
             C e = czero<C>();
             const R lag = t < RR ? a.ltgt[t % Q] * a.ltgt[t / Q] : R(1);
@@ -420,7 +609,12 @@ struct TileMR {
             PC[it] = e;
         }
         __syncthreads();
-        for (int j = threadIdx.x; j < x.nr * x.npr; j += NT) {
+        if constexpr (PM == PM_BUILD) {   // build: store the factors; no weights are touched
+            tab_store(ts.tb, PC, x.npr * (RR + 1));
+            ts.tb += x.npr * (RR + 1);
+            __syncthreads();
+        }
+        for (int j = threadIdx.x; PM != PM_BUILD && j < x.nr * x.npr; j += NT) {
             const int pl = j & (x.npr - 1), rb = j >> x.lgp;
             const C *pc = PC + pl * (RR + 1);
             const C *w = W + rb * WS + pl * RR;
@@ -434,6 +628,10 @@ struct TileMR {
             const int64_t flat = ((int64_t)ca[0] << L) + ca[1];
             f[(int64_t)(x.rhs0 + rb) * a.npts + flat] = cmul(pc[RR], acc);
         }
+        if constexpr (PM == PM_TABLE) {   // the stream continues with the CTA's next tile group
+            __syncthreads();
+            ts_release(ts);
+        }
     }
 
     // shared memory of one CTA, bytes
@@ -442,10 +640,10 @@ struct TileMR {
         return (size_t)npr * RR * sizeof(C) * (size_t)(nr + 2 * rc + 5);
     }
 
-    static __device__ __forceinline__ Ctx ctx(const KArgs<P> &a)
+    static __device__ __forceinline__ Ctx ctx(const KArgs<P> &a, int cta)
     {
         Ctx x;
-        x.tile0 = (int)blockIdx.x * a.T;
+        x.tile0 = cta * a.T;
         x.rhs0 = (int)blockIdx.y * MRMAX;
         x.nr = min(MRMAX, a.nrhs - x.rhs0);
         x.npr = a.T << (D * a.k);
@@ -457,10 +655,10 @@ struct TileMR {
 
 // pass bodies shared by the per-pass kernels and the persistent batch kernel; ms is a
 // kernel parameter holding M, so the interpolation reads its coefficients from the
-// constant bank
-template <int Q, class P, int K, class MS>
+// constant bank; ts carries the phase table (PM_BUILD, PM_TABLE)
+template <int Q, class P, int K, int PM, class MS>
 __device__ __forceinline__ void col_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
-                                            unsigned char *sm, const typename P::C *g)
+                                            unsigned char *sm, const typename P::C *g, TS<typename P::C> &ts)
 {
     using C = typename P::C;
     using TM = TileMR<Q, P, K>;
@@ -469,19 +667,19 @@ __device__ __forceinline__ void col_pass_mr(const KArgs<P> &a, const MS &ms, con
     C *S = W + x.nr * WS;
     C *PC = S + x.rc * 2 * WS;
     if (a.flags & F_INIT) {
-        TM::init(a, x, W, PC, g);
-    } else {
+        TM::template init<PM>(a, x, W, PC, g, ts);
+    } else if (PM != PM_BUILD) {
         TM::load(a, x, W);
         __syncthreads();
     }
-    for (int i = 0; i < a.k; ++i) TM::col_level(a, ms, x, W, S, PC, a.l0 + i, i);
-    if (a.flags & F_SWITCH) TM::switch_tiles(a, x, W, a.l0 + a.k);
-    TM::store(a, x, W);
+    for (int i = 0; i < a.k; ++i) TM::template col_level<PM>(a, ms, x, W, S, PC, a.l0 + i, i, ts);
+    if (a.flags & F_SWITCH) TM::template switch_tiles<PM>(a, x, W, a.l0 + a.k, ts);
+    if (PM != PM_BUILD) TM::store(a, x, W);
 }
 
-template <int Q, class P, int K, class MS>
+template <int Q, class P, int K, int PM, class MS>
 __device__ __forceinline__ void row_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
-                                            unsigned char *sm, typename P::C *f)
+                                            unsigned char *sm, typename P::C *f, TS<typename P::C> &ts)
 {
     using C = typename P::C;
     using TM = TileMR<Q, P, K>;
@@ -489,27 +687,74 @@ __device__ __forceinline__ void row_pass_mr(const KArgs<P> &a, const MS &ms, con
     C *W = reinterpret_cast<C *>(sm);
     C *S = W + x.nr * WS;
     C *PC = S + x.rc * 2 * WS;
-    TM::load(a, x, W);
-    __syncthreads();
-    for (int i = 0; i < a.k; ++i) TM::row_level(a, ms, x, W, S, PC, a.l0 + i, i);
+    if (PM != PM_BUILD) {
+        TM::load(a, x, W);
+        __syncthreads();
+    }
+    for (int i = 0; i < a.k; ++i) TM::template row_level<PM>(a, ms, x, W, S, PC, a.l0 + i, i, ts);
     if (a.flags & F_FINAL)
-        TM::final_eval(a, x, W, PC, f);
-    else
+        TM::template final_eval<PM>(a, x, W, PC, f, ts);
+    else if (PM != PM_BUILD)
         TM::store(a, x, W);
 }
 
-template <int Q, class P, int K>
+constexpr int TABCTL_BYTES = (int)((sizeof(TabCtl) + 15) / 16 * 16);
+
+// largest table block of a pass (a level's 5 r factors per pair, or a switch chunk)
+template <int Q>
+__host__ __device__ constexpr int tab_blk_factor() { return Q > 5 ? Q : 5; }
+
+// shared memory of a CTA: PM_TABLE puts the stream control and two block buffers first
+template <int Q, class P, int K, int PM>
+__device__ __forceinline__ unsigned char *mr_setup(const KArgs<P> &a, const typename TileMR<Q, P, K>::Ctx &x,
+                                                   unsigned char *smem, TS<typename P::C> &ts, bool row)
+{
+    using C = typename P::C;
+    ts.tb = nullptr;
+    ts.ctl = nullptr;
+    ts.buf[0] = ts.buf[1] = nullptr;
+    ts.j = 0;
+    ts.err = a.err;
+    ts.c0 = (int)blockIdx.x;
+    ts.cstep = (int)gridDim.x;
+    ts.cstride = a.ptab_cta;
+    if constexpr (PM != PM_TABLE) return smem;
+    ts.tb = a.ptab;
+    const int blk = tab_blk_factor<Q>() * Q * Q * x.npr;
+    ts.ctl = reinterpret_cast<TabCtl *>(smem);
+    ts.buf[0] = reinterpret_cast<C *>(smem + TABCTL_BYTES);
+    ts.buf[1] = ts.buf[0] + blk;
+    TileMR<Q, P, K>::ts_setup(ts, a, x, row);
+    return reinterpret_cast<unsigned char *>(ts.buf[1] + blk);
+}
+
+// Per-pass kernels.  A CTA runs tile groups blockIdx.x, blockIdx.x + gridDim.x, ... < a.ncta
+// (one with a full grid; PM_TABLE launches as many CTAs as fit and streams the table of
+// all its tile groups through one pipeline).
+template <int Q, class P, int K, int PM>
 __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_col_pass_mr(const KArgs<P> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    col_pass_mr<Q, P, K>(a, a, TileMR<Q, P, K>::ctx(a), smem_raw, a.g);
+    TS<typename P::C> ts;
+    unsigned char *work = mr_setup<Q, P, K, PM>(a, TileMR<Q, P, K>::ctx(a, blockIdx.x), smem_raw, ts, false);
+    for (int c = blockIdx.x; c < a.ncta; c += gridDim.x) {
+        if constexpr (PM == PM_BUILD) ts.tb = a.ptab + (int64_t)c * a.ptab_cta;
+        col_pass_mr<Q, P, K, PM>(a, a, TileMR<Q, P, K>::ctx(a, c), work, a.g, ts);
+        __syncthreads();
+    }
 }
 
-template <int Q, class P, int K>
+template <int Q, class P, int K, int PM>
 __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_row_pass_mr(const KArgs<P> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    row_pass_mr<Q, P, K>(a, a, TileMR<Q, P, K>::ctx(a), smem_raw, a.f);
+    TS<typename P::C> ts;
+    unsigned char *work = mr_setup<Q, P, K, PM>(a, TileMR<Q, P, K>::ctx(a, blockIdx.x), smem_raw, ts, true);
+    for (int c = blockIdx.x; c < a.ncta; c += gridDim.x) {
+        if constexpr (PM == PM_BUILD) ts.tb = a.ptab + (int64_t)c * a.ptab_cta;
+        row_pass_mr<Q, P, K, PM>(a, a, TileMR<Q, P, K>::ctx(a, c), work, a.f, ts);
+        __syncthreads();
+    }
 }
 
 // ====================================================================== persistent batch
@@ -622,10 +867,11 @@ __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_batch_mr(const
                 x.npr = a.T << (2 * a.k);
                 x.rc = a.rc;
                 x.lgp = __ffs(x.npr) - 1;
+                TS<typename P::C> ts{};
                 if (jb.row)
-                    row_pass_mr<Q, P, K>(a, b, x, smem_raw, b.f[jb.prob]);
+                    row_pass_mr<Q, P, K, PM_COMPUTE>(a, b, x, smem_raw, b.f[jb.prob], ts);
                 else
-                    col_pass_mr<Q, P, K>(a, b, x, smem_raw, b.g[jb.prob]);
+                    col_pass_mr<Q, P, K, PM_COMPUTE>(a, b, x, smem_raw, b.g[jb.prob], ts);
                 __syncthreads();
             }
         }

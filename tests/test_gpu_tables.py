@@ -1,0 +1,80 @@
+"""Phase tables (bf_params.phase_tables): every phase factor evaluated once at plan
+creation and read back by the apply.  The factors are the ones the evaluating kernels
+compute, so the apply equals the evaluating multi-RHS apply bit for bit, and the oracle
+to the mixed tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_4650_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_4650_gb300 import build, bf as bfmod
+    build.build()
+    return bfmod
+
+
+def _table_bytes(plan, spec):
+    # r (5 per pair and level, init, final) + r^2 at the switch, complex64, per point
+    r, L = spec.r, spec.L
+    return 8 * spec.npts * (r * 5 * L + r + (r + 1) + r * r)
+
+
+@pytest.mark.parametrize("spec,nrhs,prec", [(wl.genradon2d(L=6), 3, "mixed"), (wl.hypradon(7), 16, "mixed"),
+                                            (wl.hypradon(5), 19, "mixed_sfu"), (wl.genradon2d(L=3).with_(q=4), 2, "mixed"),
+                                            (wl.dft64().with_(precision="mixed"), 5, "mixed")])
+def test_tables_equal_evaluated_phases(bf, spec, nrhs, prec):
+    import torch
+    pt = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec, phase_tables=True)
+    pc = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec)
+    info = pt.table_info()
+    assert info["bytes"] == _table_bytes(pt, spec) and info["build_ms"] > 0
+    assert pc.table_info()["bytes"] == 0
+    g = torch.from_numpy(wl.source_values(spec, nrhs, np.complex64, seed=61)).cuda()
+    ft, fc = pt.apply(g), pc.apply(g)
+    torch.cuda.synchronize()
+    assert not pt.table_info()["timed_out"]
+    assert torch.equal(ft, fc)
+    ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.cpu().numpy().astype(np.complex128))
+    tol = 1e-5 if prec == "mixed" else 2e-5
+    out = ft.cpu().numpy()
+    assert np.linalg.norm(out - ref) <= tol * np.linalg.norm(ref)
+    pt.close()
+    pc.close()
+
+
+def test_tables_one_rhs_and_autotune(bf):
+    # one right-hand side goes through the table kernels too; autotune keeps the schedule
+    import torch
+    spec = wl.genradon2d(L=7)
+    pt = bf.Plan.from_spec(spec, precision="mixed", phase_tables=True)
+    before = pt.passes(1)
+    assert pt.autotune(1, reps=2) > 0
+    assert pt.passes(1) == before
+    g = torch.from_numpy(wl.source_values(spec, 1, np.complex64, seed=62)).cuda()
+    out = pt.apply(g)
+    single = bf.Plan.from_spec(spec, precision="mixed").apply(g)
+    torch.cuda.synchronize()
+    assert (torch.linalg.vector_norm(out - single) / torch.linalg.vector_norm(single)).item() < 2e-6
+    ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.cpu().numpy().astype(np.complex128))
+    assert np.linalg.norm(out.cpu().numpy() - ref) <= 1e-5 * np.linalg.norm(ref)
+    pt.close()
+
+
+def test_tables_refused_where_not_built(bf):
+    with pytest.raises(bf.BfError) as e:
+        bf.Plan.from_spec(wl.hypradon(5).with_(q=6), precision="mixed", phase_tables=True)
+    assert e.value.code == 2
+    with pytest.raises(bf.BfError) as e:
+        bf.Plan.from_spec(wl.hypradon(5), precision="fp64", phase_tables=True)
+    assert e.value.code == 2
+    with pytest.raises(bf.BfError) as e:
+        bf.Plan.from_spec(wl.genradon3d(L=3), precision="mixed", phase_tables=True)
+    assert e.value.code == 2
