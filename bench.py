@@ -72,6 +72,7 @@ def parse():
     ap.add_argument("--workload", default="genradon2d",
                     choices=["genradon2d", "genradon3d", "dft64", "hypradon512", "hypradon48", "cg1024"])
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per apply (single-problem workloads)")
+    ap.add_argument("--L", type=int, default=0, help="override log2 N of a single-problem workload (small cases)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
@@ -80,8 +81,12 @@ def parse():
     return ap.parse_args()
 
 
-def workload(name):
+def workload(name, L=0):
     from paper_1305_4650_gb300 import workloads as wl
+    if L:   # a smaller (or larger) case of the same family, e.g. for profiling
+        return {"genradon2d": lambda: wl.genradon2d(L), "genradon3d": lambda: wl.genradon3d(L),
+                "dft64": lambda: wl.dft64().with_(L=L, name=f"dft_N{1 << L}_q5"),
+                "hypradon512": lambda: wl.hypradon(L)}[name]()
     return {"genradon2d": wl.genradon2d, "genradon3d": wl.genradon3d, "dft64": wl.dft64,
             "hypradon512": lambda: wl.hypradon(9)}[name]()
 
@@ -206,7 +211,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    spec = workload(args.workload)
+    spec = workload(args.workload, args.L)
     nrhs = args.nrhs
     stream = torch.cuda.current_stream()
     sptr = stream.cuda_stream
@@ -272,7 +277,7 @@ def run_ours(args, rank, world, local_rank):
         peak_basis = "measured FP64 FMA rate (bf_measure_fma_rate), one FP64 op per FMA"
     achieved = ops / (tpass[dom] * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "Tops/s",
-                "frac": round(achieved / peak, 4), "traffic": recorded_traffic(args.workload, sched, dom),
+                "frac": round(achieved / peak, 4), "traffic": None if args.L else recorded_traffic(args.workload, sched, dom),
                 "kernel": f"pass{dom}:{passes[dom]['kind']} l0={passes[dom]['l0']} k={passes[dom]['k']}"
                           + (" +init" if passes[dom]["init"] else "") + (" +switch" if passes[dom]["switch"] else "")
                           + (" +final" if passes[dom]["final"] else ""),
