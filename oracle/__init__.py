@@ -12,6 +12,9 @@ Contents (all in ``bf_oracle.c``, plain C99 + OpenMP, FP64):
 * ``butterfly``   -- Algorithm 1 with the analytic Chebyshev interpolation of
   Section 1.4 (column space, middle switch, row space);
 * ``butterfly_adjoint`` -- the exact conjugate transpose of ``butterfly``;
+* ``direct_sum_points`` / ``butterfly_points`` -- the same for arbitrary source and
+  target point sets (init sums the sources of each leaf box, final evaluates the
+  leaf box's interpolant at each target);
 * ``cheb_nodes`` / ``lagrange1`` / ``phi`` -- the building blocks, exposed so the
   tests can pin them.
 
@@ -71,6 +74,8 @@ def _bind(path: str):
     lib.orc_direct_sum.argtypes = [P, cp, ctypes.c_int64, cp, cp]
     lib.orc_butterfly.argtypes = [P, cp, cp, ctypes.c_int, ctypes.c_int64]
     lib.orc_butterfly_adjoint.argtypes = [P, cp, cp]
+    lib.orc_direct_sum_points.argtypes = [P, ctypes.c_int64, cp, cp, ctypes.c_int64, cp, cp]
+    lib.orc_butterfly_points.argtypes = [P, ctypes.c_int64, cp, cp, ctypes.c_int64, cp, cp]
     lib.orc_phi.argtypes = [P, cp, cp]
     lib.orc_phi.restype = ctypes.c_double
     lib.orc_cheb_nodes.argtypes = [ctypes.c_int, ctypes.c_int, cp]
@@ -187,6 +192,55 @@ def butterfly_adjoint(P: Problem, f: np.ndarray) -> np.ndarray:
         _check(lib.orc_butterfly_adjoint(ctypes.byref(pc), fi.ctypes.data, out[i].ctypes.data),
                "butterfly_adjoint")
     return out.reshape(f.shape)
+
+
+def _points(P: Problem, pts) -> np.ndarray:
+    a = np.ascontiguousarray(pts, dtype=np.float64)
+    if a.ndim != 2 or a.shape[1] != P.d:
+        raise ValueError("points must be an (n, d) array")
+    return a
+
+
+def direct_sum_points(P: Problem, y, g: np.ndarray, x) -> np.ndarray:
+    """f_i = sum_j exp(2 pi i Phi(x_i, y_j)) g_j for arbitrary points; g: (nsrc,) or (nrhs, nsrc)."""
+    lib = _load()
+    y, x = _points(P, y), _points(P, x)
+    g = _c128(g)
+    batch = g.reshape(-1, y.shape[0])
+    out = np.zeros((batch.shape[0], x.shape[0]), np.complex128)
+    pc = P._c()
+    for i in range(batch.shape[0]):
+        gi = np.ascontiguousarray(batch[i])
+        _check(lib.orc_direct_sum_points(ctypes.byref(pc), y.shape[0], y.ctypes.data, gi.ctypes.data, x.shape[0],
+                                         x.ctypes.data, out[i].ctypes.data), "direct_sum_points")
+    return out.reshape(g.shape[:-1] + (x.shape[0],)) if g.ndim > 1 else out[0]
+
+
+def butterfly_points(P: Problem, y, g: np.ndarray, x) -> np.ndarray:
+    """CPU butterfly for arbitrary sources y (nsrc, d) and targets x (ntgt, d)."""
+    lib = _load()
+    y, x = _points(P, y), _points(P, x)
+    g = _c128(g)
+    batch = g.reshape(-1, y.shape[0])
+    out = np.zeros((batch.shape[0], x.shape[0]), np.complex128)
+    pc = P._c()
+    for i in range(batch.shape[0]):
+        gi = np.ascontiguousarray(batch[i])
+        _check(lib.orc_butterfly_points(ctypes.byref(pc), y.shape[0], y.ctypes.data, gi.ctypes.data, x.shape[0],
+                                        x.ctypes.data, out[i].ctypes.data), "butterfly_points")
+    return out.reshape(g.shape[:-1] + (x.shape[0],)) if g.ndim > 1 else out[0]
+
+
+def grid_points(P: Problem, is_src: bool) -> np.ndarray:
+    """The uniform grid points of the plan, row-major flat order: (N^d, d)."""
+    N = 1 << P.L
+    y_lo = P.y_lo if P.y_lo is not None else (-N / 2,) * 3
+    y_w = P.y_w if P.y_w is not None else (float(N),) * 3
+    lo = y_lo if is_src else P.x_lo
+    w = y_w if is_src else P.x_w
+    off = P.src_off if is_src else P.tgt_off
+    idx = np.indices((N,) * P.d).reshape(P.d, -1).T
+    return np.stack([lo[k] + (idx[:, k] + off) * (w[k] / N) for k in range(P.d)], axis=1)
 
 
 def restricted_targets(P: Problem, level: int, box: int) -> np.ndarray:

@@ -332,48 +332,16 @@ static int tgt_active(int d, int l, int64_t A, int rl, int64_t R)
 }
 
 /*
- * Forward butterfly, Algorithm 1.  g: N^d source values (row-major);
- * f: N^d outputs.  If rl >= 0 only target boxes on the path to box R at level
- * rl are computed (a restriction of the same arithmetic: outputs for targets
- * inside R are identical to the unrestricted run, other outputs are zero).
+ * The log2 N stages of Algorithm 1 (and the switch at level m) on the level-0 weights
+ * in *W; *W holds the level-L weights afterwards (*Wn is scratch; the two may be swapped).
  */
-int orc_butterfly(const orc_problem *P, const cplx *g, cplx *f, int rl, int64_t R)
+static void stages(const orc_problem *P, cplx **Wp, cplx **Wnp, int rl, int64_t R, const double *z)
 {
-    if (check(P)) return ORC_ERR_ARG;
-    if (rl > P->L) return ORC_ERR_ARG;
     const int d = P->d, L = P->L, q = P->q, m = P->m;
     const int r = (int)ipow(q, d);
     const int nc = 1 << d;
     const int64_t Nd = ipow(1LL << L, d);
-    double z[16];
-    orc_cheb_nodes(q, P->node_kind, z);
-
-    cplx *W = calloc((size_t)Nd * r, sizeof(cplx));
-    cplx *Wn = calloc((size_t)Nd * r, sizeof(cplx));
-    if (!W || !Wn) {
-        free(W);
-        free(Wn);
-        return ORC_ERR_NOMEM;
-    }
-
-    /* init: A = X, one source per leaf box B (pair index = B) */
-    {
-        double x0[3], wx[3];
-        tbox(P, 0, 0, x0, wx);
-#pragma omp parallel for schedule(static)
-        for (int64_t j = 0; j < Nd; ++j) {
-            double y[3], cb[3], wb[3], yt[3];
-            int64_t B;
-            point(P, 1, j, y, &B);
-            sbox(P, 0, B, cb, wb);
-            cplx src = kern(P, x0, y) * g[j];
-            for (int t = 0; t < r; ++t) {
-                node(d, q, z, cb, wb, t, yt);
-                W[B * r + t] = conj(kern(P, x0, yt)) * lag(d, q, z, cb, wb, t, y) * src;
-            }
-        }
-    }
-
+    cplx *W = *Wp, *Wn = *Wnp;
     for (int l = 0; l < L; ++l) {
         if (l == m) { /* switch to row-space interpolation at level m */
             const int64_t SB = ipow(1LL << (L - l), d);
@@ -477,6 +445,54 @@ int orc_butterfly(const orc_problem *P, const cplx *g, cplx *f, int rl, int64_t 
             for (int s = 0; s < r; ++s) W[A * r + s] = tmp[s];
         }
     }
+
+    *Wp = W;
+    *Wnp = Wn;
+}
+
+/*
+ * Forward butterfly, Algorithm 1.  g: N^d source values (row-major);
+ * f: N^d outputs.  If rl >= 0 only target boxes on the path to box R at level
+ * rl are computed (a restriction of the same arithmetic: outputs for targets
+ * inside R are identical to the unrestricted run, other outputs are zero).
+ */
+int orc_butterfly(const orc_problem *P, const cplx *g, cplx *f, int rl, int64_t R)
+{
+    if (check(P)) return ORC_ERR_ARG;
+    if (rl > P->L) return ORC_ERR_ARG;
+    const int d = P->d, L = P->L, q = P->q;
+    const int r = (int)ipow(q, d);
+    const int64_t Nd = ipow(1LL << L, d);
+    double z[16];
+    orc_cheb_nodes(q, P->node_kind, z);
+
+    cplx *W = calloc((size_t)Nd * r, sizeof(cplx));
+    cplx *Wn = calloc((size_t)Nd * r, sizeof(cplx));
+    if (!W || !Wn) {
+        free(W);
+        free(Wn);
+        return ORC_ERR_NOMEM;
+    }
+
+    /* init: A = X, one source per leaf box B (pair index = B) */
+    {
+        double x0[3], wx[3];
+        tbox(P, 0, 0, x0, wx);
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < Nd; ++j) {
+            double y[3], cb[3], wb[3], yt[3];
+            int64_t B;
+            point(P, 1, j, y, &B);
+            sbox(P, 0, B, cb, wb);
+            cplx src = kern(P, x0, y) * g[j];
+            for (int t = 0; t < r; ++t) {
+                node(d, q, z, cb, wb, t, yt);
+                W[B * r + t] = conj(kern(P, x0, yt)) * lag(d, q, z, cb, wb, t, y) * src;
+            }
+        }
+    }
+
+    stages(P, &W, &Wn, rl, R, z);
 
     /* final: B = Y, one target per leaf box A (pair index = A) */
     {
@@ -650,6 +666,101 @@ int orc_butterfly_adjoint(const orc_problem *P, const cplx *f, cplx *g)
 }
 
 /* flat row-major index of the target in leaf box with Morton index mi */
+/* ------------------------------------------------ arbitrary point sets */
+
+/* Leaf box (Morton index) of a point of the source (is_src) or target domain: the box
+ * whose half-open extent holds it; points on the upper face belong to the last box. */
+static int64_t leaf_of(const orc_problem *P, int is_src, const double *p)
+{
+    const int d = P->d;
+    const int64_t N = 1LL << P->L;
+    int64_t c[3];
+    for (int k = 0; k < d; ++k) {
+        const double lo = is_src ? P->y_lo[k] : P->x_lo[k], w = is_src ? P->y_w[k] : P->x_w[k];
+        int64_t ck = (int64_t)floor((p[k] - lo) / (w / (double)N));
+        c[k] = ck < 0 ? 0 : (ck >= N ? N - 1 : ck);
+    }
+    return morton_encode(d, P->L, c);
+}
+
+/* f[i] = sum_j K(x_i, y_j) g[j] for arbitrary points (rows of x: ntgt x d, y: nsrc x d). */
+int orc_direct_sum_points(const orc_problem *P, int64_t nsrc, const double *y, const cplx *g, int64_t ntgt,
+                          const double *x, cplx *f)
+{
+    if (check(P) || nsrc < 0 || ntgt < 0) return ORC_ERR_ARG;
+    const int d = P->d;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t i = 0; i < ntgt; ++i) {
+        cplx acc = 0.0;
+        for (int64_t j = 0; j < nsrc; ++j) acc += kern(P, x + i * d, y + j * d) * g[j];
+        f[i] = acc;
+    }
+    return ORC_OK;
+}
+
+/*
+ * Butterfly for arbitrary sources and targets (the field of Section 1.4 evaluated
+ * anywhere; sparse and clustered point sets of the future-work discussion).  Only
+ * the first and last steps change: init sums over the sources that lie in each leaf
+ * box, final evaluates the interpolant of the target's leaf box at the target.  Points
+ * must lie in their domains (the box of a point outside is its nearest one).
+ */
+int orc_butterfly_points(const orc_problem *P, int64_t nsrc, const double *y, const cplx *g, int64_t ntgt,
+                         const double *x, cplx *f)
+{
+    if (check(P) || nsrc < 0 || ntgt < 0) return ORC_ERR_ARG;
+    const int d = P->d, L = P->L, q = P->q;
+    const int r = (int)ipow(q, d);
+    const int64_t Nd = ipow(1LL << L, d);
+    double z[16];
+    orc_cheb_nodes(q, P->node_kind, z);
+    cplx *W = calloc((size_t)Nd * r, sizeof(cplx));
+    cplx *Wn = calloc((size_t)Nd * r, sizeof(cplx));
+    if (!W || !Wn) {
+        free(W);
+        free(Wn);
+        return ORC_ERR_NOMEM;
+    }
+    /* init: every source adds its interpolation weights to its leaf box (sources in order) */
+    {
+        double x0[3], wx[3];
+        tbox(P, 0, 0, x0, wx);
+        for (int64_t j = 0; j < nsrc; ++j) {
+            const double *yj = y + j * d;
+            double cb[3], wb[3], yt[3];
+            const int64_t B = leaf_of(P, 1, yj);
+            sbox(P, 0, B, cb, wb);
+            cplx src = kern(P, x0, yj) * g[j];
+            for (int t = 0; t < r; ++t) {
+                node(d, q, z, cb, wb, t, yt);
+                W[B * r + t] += conj(kern(P, x0, yt)) * lag(d, q, z, cb, wb, t, yj) * src;
+            }
+        }
+    }
+    stages(P, &W, &Wn, -1, 0, z);
+    /* final: each target from the weights of its leaf box */
+    {
+        double y0[3], wy[3];
+        sbox(P, L, 0, y0, wy);
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < ntgt; ++i) {
+            const double *xi = x + i * d;
+            double ca[3], wa[3], xt[3];
+            const int64_t A = leaf_of(P, 0, xi);
+            tbox(P, L, A, ca, wa);
+            cplx acc = 0.0;
+            for (int t = 0; t < r; ++t) {
+                node(d, q, z, ca, wa, t, xt);
+                acc += lag(d, q, z, ca, wa, t, xi) * conj(kern(P, xt, y0)) * W[A * r + t];
+            }
+            f[i] = kern(P, xi, y0) * acc;
+        }
+    }
+    free(W);
+    free(Wn);
+    return ORC_OK;
+}
+
 int64_t orc_flat_from_morton(const orc_problem *P, int64_t mi) { return flat_from_morton(P, mi); }
 
 int orc_num_threads(void)
