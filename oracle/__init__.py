@@ -206,7 +206,7 @@ def direct_sum_points(P: Problem, y, g: np.ndarray, x) -> np.ndarray:
     lib = _load()
     y, x = _points(P, y), _points(P, x)
     g = _c128(g)
-    batch = g.reshape(-1, y.shape[0])
+    batch = g.reshape((1 if g.ndim == 1 else g.shape[0]), y.shape[0])
     out = np.zeros((batch.shape[0], x.shape[0]), np.complex128)
     pc = P._c()
     for i in range(batch.shape[0]):
@@ -221,7 +221,7 @@ def butterfly_points(P: Problem, y, g: np.ndarray, x) -> np.ndarray:
     lib = _load()
     y, x = _points(P, y), _points(P, x)
     g = _c128(g)
-    batch = g.reshape(-1, y.shape[0])
+    batch = g.reshape((1 if g.ndim == 1 else g.shape[0]), y.shape[0])
     out = np.zeros((batch.shape[0], x.shape[0]), np.complex128)
     pc = P._c()
     for i in range(batch.shape[0]):
