@@ -174,6 +174,25 @@ bf_status bf_batch_info(bf_batch batch, int *jobs, int *units, int *grid, int64_
 bf_status bf_batch_wait_stats(bf_batch batch, double *wait_ms_total, int64_t *waits);
 bf_status bf_batch_destroy(bf_batch batch);
 
+/* Arbitrary point sets (Section 1.4: the interpolant of a pair can be evaluated anywhere
+ * in its target box, so only the first and last steps see the points; sparse and
+ * non-uniform sets are the paper's closing suggestion).  bf_plan_create_points builds a
+ * plan as bf_plan_create does for the same (d, N, q, phase, params) -- N fixes the depth
+ * of the box trees, N^d leaf boxes per domain -- with nsrc sources src[j*d + k] in the
+ * source domain and ntgt targets tgt[i*d + k] in the target domain (host FP64 arrays,
+ * copied; a point outside its domain joins the nearest leaf box; a leaf box may hold
+ * any number of points, including none).  bf_apply then reads g as nrhs x nsrc values
+ * and writes f as nrhs x ntgt values, both in the caller's point order (bf_apply_host
+ * and bf_apply_batched likewise).  The per-point Lagrange values and phase factors are
+ * computed in FP64 when the plan is made, the leaf boxes' node factors by an FP64 kernel;
+ * the merges are the uniform-grid kernels.  bf_apply_adjoint, bf_plan_autotune,
+ * bf_apply_pass, bf_pass_info, persistent batches and phase tables return
+ * BF_ERR_UNSUPPORTED for such plans.  bf_plan_points_info: 1 and the point counts for
+ * them, 0 and N^d, N^d for grid plans. */
+bf_status bf_plan_create_points(int d, int64_t N, int q, bf_phase_kind phase, const bf_params *p, int64_t nsrc,
+                                const double *src, int64_t ntgt, const double *tgt, bf_plan *out);
+bf_status bf_plan_points_info(bf_plan plan, int *is_points, int64_t *nsrc, int64_t *ntgt);
+
 /* Release the plan and its device memory.  bf_destroy(NULL) is a no-op.  The caller
  * must ensure no apply on this plan is still running. */
 bf_status bf_destroy(bf_plan plan);

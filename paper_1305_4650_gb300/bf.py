@@ -25,7 +25,7 @@ EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint"
            "bf_apply_pass", "bf_pass_info", "bf_pass_count", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate",
            "bf_measure_phase_rate", "bf_batch_create", "bf_batch_apply", "bf_batch_status",
            "bf_batch_selftest_timeout", "bf_batch_info", "bf_batch_wait_stats", "bf_batch_destroy", "bf_plan_autotune",
-           "bf_plan_table_info"]
+           "bf_plan_table_info", "bf_plan_create_points", "bf_plan_points_info"]
 
 
 class BfError(RuntimeError):
@@ -85,6 +85,9 @@ def load():
                                       ctypes.POINTER(i64)]
         lib.bf_batch_destroy.argtypes = [vp]
         lib.bf_plan_autotune.argtypes = [vp, i32, i32, vp, ctypes.POINTER(ctypes.c_double)]
+        lib.bf_plan_create_points.argtypes = [i32, i64, i32, i32, ctypes.POINTER(BfParams), i64, vp, i64, vp,
+                                              ctypes.POINTER(vp)]
+        lib.bf_plan_points_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.bf_plan_table_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(i32)]
         lib.bf_batch_wait_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
@@ -117,7 +120,7 @@ class Plan:
     def __init__(self, d: int, N: int, q: int, phase: str, precision: str = "mixed", scale: float = 1.0,
                  x_lo=None, x_w=None, y_lo=None, y_w=None, tgt_off: float = 0.0, src_off: float = 0.0,
                  switch_level: int = -1, node_kind: int = 0, max_nrhs: int = 1, fuse_levels: int = 0,
-                 phase_tables: bool = False):
+                 phase_tables: bool = False, sources=None, targets=None):
         lib = load()
         p = BfParams()
         _check(lib.bf_params_default(d, N, ctypes.byref(p)), "bf_params_default")
@@ -135,7 +138,17 @@ class Plan:
         p.fuse_levels = fuse_levels
         p.phase_tables = 1 if phase_tables else 0
         h = ctypes.c_void_p()
-        _check(lib.bf_plan_create(d, N, q, PHASE[phase], ctypes.byref(p), ctypes.byref(h)), "bf_plan_create")
+        if sources is None and targets is None:
+            _check(lib.bf_plan_create(d, N, q, PHASE[phase], ctypes.byref(p), ctypes.byref(h)), "bf_plan_create")
+            self.nsrc = self.ntgt = N ** d
+        else:
+            ys = np.ascontiguousarray(np.asarray(sources, dtype=np.float64).reshape(-1, d))
+            xs = np.ascontiguousarray(np.asarray(targets, dtype=np.float64).reshape(-1, d))
+            _check(lib.bf_plan_create_points(d, N, q, PHASE[phase], ctypes.byref(p), ys.shape[0],
+                                             ys.ctypes.data if ys.size else None, xs.shape[0],
+                                             xs.ctypes.data if xs.size else None, ctypes.byref(h)),
+                   "bf_plan_create_points")
+            self.nsrc, self.ntgt = ys.shape[0], xs.shape[0]
         self._h = h
         self.d, self.N, self.q, self.precision, self.max_nrhs = d, N, q, precision, max_nrhs
         self.npts = N ** d
@@ -143,11 +156,12 @@ class Plan:
 
     @classmethod
     def from_spec(cls, spec, max_nrhs: int = 1, precision: str | None = None, fuse_levels: int = 0,
-                  phase_tables: bool = False) -> "Plan":
+                  phase_tables: bool = False, sources=None, targets=None) -> "Plan":
+        """Plan for a workload spec; sources / targets ((n, d) arrays) make a point-set plan."""
         x_lo, x_w, y_lo, y_w = spec.domain()
         return cls(spec.d, spec.N, spec.q, spec.phase, precision or spec.precision, spec.scale,
                    x_lo, x_w, y_lo, y_w, spec.tgt_off, spec.src_off, spec.switch_level, spec.node_kind,
-                   max_nrhs, fuse_levels, phase_tables)
+                   max_nrhs, fuse_levels, phase_tables, sources, targets)
 
     @property
     def handle(self) -> int:
@@ -157,34 +171,36 @@ class Plan:
         import torch
         return torch.complex128 if self.precision == "fp64" else torch.complex64
 
-    def _nrhs(self, t) -> int:
+    def _nrhs(self, t, n=None) -> int:
         import torch
+        n = self.npts if n is None else n
         if not isinstance(t, torch.Tensor) or not t.is_cuda:
             raise TypeError("expected a CUDA tensor")
         if t.dtype != self.torch_dtype():
             raise TypeError(f"expected dtype {self.torch_dtype()}, got {t.dtype}")
-        if not t.is_contiguous() or t.numel() % self.npts:
-            raise ValueError("expected a contiguous tensor of nrhs x N^d elements")
-        return t.numel() // self.npts
+        if not t.is_contiguous() or (n and t.numel() % n) or (not n and t.numel()):
+            raise ValueError("expected a contiguous tensor of nrhs x points elements")
+        return t.numel() // n if n else (t.shape[0] if t.dim() > 1 else 1)
 
     def apply(self, g, f=None, stream=None):
-        """f = B g for CUDA tensors of shape (N^d,) or (nrhs, N^d)."""
+        """f = B g for CUDA tensors of shape (nsrc,) or (nrhs, nsrc); f: (nrhs, ntgt)
+        (nsrc = ntgt = N^d for grid plans)."""
         import torch
-        n = self._nrhs(g)
+        n = self._nrhs(g, self.nsrc)
         if f is None:
-            f = torch.empty_like(g)
-        elif self._nrhs(f) != n:
+            f = torch.empty((n, self.ntgt) if g.dim() > 1 else (self.ntgt,), dtype=g.dtype, device=g.device)
+        elif self._nrhs(f, self.ntgt) != n:
             raise ValueError("g and f differ in size")
         _check(load().bf_apply(self._h, g.data_ptr(), f.data_ptr(), n, _stream_ptr(stream)), "bf_apply", self._h)
         return f
 
     def apply_adjoint(self, f, g=None, stream=None):
-        """g = B^H f."""
+        """g = B^H f (grid plans)."""
         import torch
-        n = self._nrhs(f)
+        n = self._nrhs(f, self.ntgt)
         if g is None:
-            g = torch.empty_like(f)
-        elif self._nrhs(g) != n:
+            g = torch.empty((n, self.nsrc) if f.dim() > 1 else (self.nsrc,), dtype=f.dtype, device=f.device)
+        elif self._nrhs(g, self.nsrc) != n:
             raise ValueError("f and g differ in size")
         _check(load().bf_apply_adjoint(self._h, f.data_ptr(), g.data_ptr(), n, _stream_ptr(stream)),
                "bf_apply_adjoint", self._h)
@@ -193,11 +209,11 @@ class Plan:
     def apply_host(self, g: np.ndarray, f: np.ndarray | None = None, stream=None) -> np.ndarray:
         """Host-buffer apply: H2D copy, butterfly, D2H copy, stream synchronised."""
         g = np.ascontiguousarray(g, dtype=self.cdtype)
-        if g.size % self.npts:
-            raise ValueError("g must hold nrhs x N^d values")
+        if (self.nsrc and g.size % self.nsrc) or (not self.nsrc and g.size):
+            raise ValueError("g must hold nrhs x nsrc values")
+        n = g.size // self.nsrc if self.nsrc else (g.shape[0] if g.ndim > 1 else 1)
         if f is None:
-            f = np.empty_like(g)
-        n = g.size // self.npts
+            f = np.empty((n, self.ntgt) if g.ndim > 1 else (self.ntgt,), dtype=self.cdtype)
         st = 0 if stream is None else _stream_ptr(stream)
         _check(load().bf_apply_host(self._h, g.ctypes.data, f.ctypes.data, n, st), "bf_apply_host", self._h)
         return f

@@ -47,6 +47,13 @@ struct bf_plan_s {
     int64_t ptab_bytes = 0;
     std::vector<int64_t> ptab_off, ptab_cta;   // per pass: offset and per-CTA size, complex numbers
     float ptab_build_ms = 0.f;
+    // arbitrary point sets (bf_plan_create_points): per-point data and the forward passes
+    // without init and final, which the point kernels replace
+    int points = 0;
+    int64_t nsrc = 0, ntgt = 0;
+    bfl::PointsData pd{};
+    std::vector<void *> pts_mem;
+    std::vector<Pass> passes_pts;
     int mr_rc = 1;                 // right-hand sides per scratch chunk of the multi-RHS kernels
     std::vector<Pass> passes_adj;  // schedule whose reverse is the adjoint (fits the row caches)
     const bfl::PassFns *fns = nullptr;
@@ -451,7 +458,205 @@ double phase_bound(int d, int kind, const bf_params *p)
 // the multi-RHS schedule serves nrhs >= 2 where it is compiled (mixed precisions, d = 2)
 bool use_mr(const bf_plan_s *p, int nrhs)
 {
-    return (nrhs >= 2 || p->ptab) && p->prec != BF_PREC_FP64 && !p->passes_mr.empty();
+    return (nrhs >= 2 || p->ptab) && p->prec != BF_PREC_FP64 && !p->passes_mr.empty() && !p->points;
+}
+
+// ------------------------------------------------------------ point sets
+
+// Phi in FP64 (cycles) from coordinates, the phase kinds of bf.h
+double phi_host(int kind, int d, double s, const double *x, const double *y)
+{
+    switch (kind) {
+    case BF_PHASE_DOT: {
+        double v = 0.0;
+        for (int k = 0; k < d; ++k) v += x[k] * y[k];
+        return s * v;
+    }
+    case BF_PHASE_GENRADON: {
+        double xy = 0.0, q2 = 0.0;
+        for (int k = 0; k < d; ++k) xy += x[k] * y[k];
+        if (d == 2) {
+            const double a0 = (2.0 + std::sin(2 * kPi * x[0]) * std::sin(2 * kPi * x[1])) / 3.0;
+            const double a1 = (2.0 + std::cos(2 * kPi * x[0]) * std::cos(2 * kPi * x[1])) / 3.0;
+            q2 = a0 * a0 * y[0] * y[0] + a1 * a1 * y[1] * y[1];
+        } else {
+            for (int k = 0; k < d; ++k) {
+                const double a = (2.0 + std::sin(2 * kPi * x[k]) * std::cos(2 * kPi * x[(k + 1) % d])) / 3.0;
+                q2 += a * a * y[k] * y[k];
+            }
+        }
+        return s * (xy + std::sqrt(q2));
+    }
+    case BF_PHASE_HYPRADON:
+        return s * x[0] * std::sqrt(y[0] * y[0] + y[1] * y[1] * x[1] * x[1]);
+    default: {
+        double v = 0.0;
+        for (int k = 0; k < d; ++k) v += std::sin(2 * kPi * (x[k] + (k + 1) / 7.0)) + y[k] * y[k] / (k + 2.0);
+        return s * v;
+    }
+    }
+}
+
+// leaf box (Morton) of a point and its Lagrange values l_t(xi_k) in that box, [d][q]
+int64_t leaf_and_lagrange(const bf_plan_s *p, bool src, const double *pt, double *lag)
+{
+    const int d = p->d, q = p->q;
+    int64_t c[3] = {0, 0, 0}, mort = 0;
+    for (int k = 0; k < d; ++k) {
+        const double lo = src ? p->prm.y_lo[k] : p->prm.x_lo[k];
+        const double w = (src ? p->prm.y_w[k] : p->prm.x_w[k]) / (double)p->N;
+        int64_t ck = (int64_t)std::floor((pt[k] - lo) / w);
+        ck = ck < 0 ? 0 : (ck >= p->N ? p->N - 1 : ck);
+        c[k] = ck;
+        const double xi = (pt[k] - (lo + ((double)ck + 0.5) * w)) / w;
+        for (int t = 0; t < q; ++t) lag[k * q + t] = lagrange1(q, p->z, t, xi);
+    }
+    for (int j = 0; j < p->L; ++j)
+        for (int k = 0; k < d; ++k) mort |= ((c[k] >> j) & 1) << (j * d + k);
+    return mort;
+}
+
+template <class T>
+bf_status pts_upload(bf_plan p, const std::vector<T> &h, const void **dst)
+{
+    void *ptr = nullptr;
+    if (h.empty()) {
+        *dst = nullptr;
+        return BF_OK;
+    }
+    bf_status st = upload(p, h, &ptr);
+    if (ptr) p->pts_mem.push_back(ptr);
+    *dst = ptr;
+    return st;
+}
+
+template <class R, class C>
+bf_status setup_points_t(bf_plan p, int64_t nsrc, const double *src, int64_t ntgt, const double *tgt)
+{
+    const int d = p->d, q = p->q;
+    const int64_t nbox = p->npts;
+    double x0[3], y0[3];
+    for (int k = 0; k < d; ++k) {
+        x0[k] = p->prm.x_lo[k] + 0.5 * p->prm.x_w[k];
+        y0[k] = p->prm.y_lo[k] + 0.5 * p->prm.y_w[k];
+    }
+    auto cexp = [](double th) {
+        const double f = th - std::nearbyint(th);
+        C e;
+        e.x = (R)std::cos(2 * kPi * f);
+        e.y = (R)std::sin(2 * kPi * f);
+        return e;
+    };
+    // sources: leaf boxes, counting sort (stable), Lagrange values and phase factors in sorted order
+    std::vector<int64_t> box(nsrc), off(nbox + 1, 0), perm(nsrc);
+    std::vector<double> lagd((size_t)nsrc * d * q);
+    for (int64_t j = 0; j < nsrc; ++j) {
+        box[j] = leaf_and_lagrange(p, true, src + j * d, &lagd[(size_t)j * d * q]);
+        ++off[box[j] + 1];
+    }
+    for (int64_t b = 0; b < nbox; ++b) off[b + 1] += off[b];
+    {
+        std::vector<int64_t> fill(off.begin(), off.end() - 1);
+        for (int64_t j = 0; j < nsrc; ++j) perm[fill[box[j]]++] = j;
+    }
+    std::vector<R> slag((size_t)nsrc * d * q);
+    std::vector<C> se(nsrc);
+    for (int64_t i = 0; i < nsrc; ++i) {
+        const int64_t j = perm[i];
+        for (int e = 0; e < d * q; ++e) slag[(size_t)i * d * q + e] = (R)lagd[(size_t)j * d * q + e];
+        se[i] = cexp(phi_host(p->kind, d, p->prm.phase_scale, x0, src + j * d));
+    }
+    // targets in the caller's order
+    std::vector<int64_t> tbox(ntgt);
+    std::vector<R> tlag((size_t)ntgt * d * q);
+    std::vector<C> te(ntgt);
+    std::vector<double> tl(d * q);
+    for (int64_t i = 0; i < ntgt; ++i) {
+        tbox[i] = leaf_and_lagrange(p, false, tgt + i * d, tl.data());
+        for (int e = 0; e < d * q; ++e) tlag[(size_t)i * d * q + e] = (R)tl[e];
+        te[i] = cexp(phi_host(p->kind, d, p->prm.phase_scale, tgt + i * d, y0));
+    }
+    bfl::PointsData &pd = p->pd;
+    pd.d = d;
+    pd.q = q;
+    pd.nbox = nbox;
+    pd.nsrc = nsrc;
+    pd.ntgt = ntgt;
+    pd.wstride = p->npts * p->r;
+    bf_status st = BF_OK;
+    const void *ptr = nullptr;
+    if ((st = pts_upload(p, off, &ptr)) != BF_OK) return st;
+    pd.src_off = static_cast<const int64_t *>(ptr);
+    if ((st = pts_upload(p, perm, &ptr)) != BF_OK) return st;
+    pd.src_perm = static_cast<const int64_t *>(ptr);
+    if ((st = pts_upload(p, slag, &pd.src_lag)) != BF_OK) return st;
+    if ((st = pts_upload(p, se, &pd.src_e)) != BF_OK) return st;
+    if ((st = pts_upload(p, tbox, &ptr)) != BF_OK) return st;
+    pd.tgt_box = static_cast<const int64_t *>(ptr);
+    if ((st = pts_upload(p, tlag, &pd.tgt_lag)) != BF_OK) return st;
+    if ((st = pts_upload(p, te, &pd.tgt_e)) != BF_OK) return st;
+    // node factors of every leaf box
+    void *ni = nullptr, *nf = nullptr;
+    cudaError_t e = cudaMalloc(&ni, (size_t)nbox * p->r * sizeof(C));
+    if (ni) p->pts_mem.push_back(ni);
+    if (e == cudaSuccess) e = cudaMalloc(&nf, (size_t)nbox * p->r * sizeof(C));
+    if (nf) p->pts_mem.push_back(nf);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    bfl::PointsGeom geo{};
+    geo.d = d;
+    geo.L = p->L;
+    geo.q = q;
+    geo.kind = p->kind;
+    geo.s = p->prm.phase_scale;
+    for (int k = 0; k < 3; ++k) {
+        geo.x_lo[k] = p->prm.x_lo[k];
+        geo.x_w[k] = p->prm.x_w[k];
+        geo.y_lo[k] = p->prm.y_lo[k];
+        geo.y_w[k] = p->prm.y_w[k];
+    }
+    for (int t = 0; t < q; ++t) geo.z[t] = p->z[t];
+    e = bfl::points_nodes(geo, sizeof(R) == 8, ni, nf);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    pd.node_init = ni;
+    pd.node_final = nf;
+    // the grid schedule without its init and final steps
+    p->passes_pts = p->passes;
+    p->passes_pts.front().flags &= ~bfk::F_INIT;
+    p->passes_pts.back().flags &= ~bfk::F_FINAL;
+    p->points = 1;
+    p->nsrc = nsrc;
+    p->ntgt = ntgt;
+    return BF_OK;
+}
+
+template <class P>
+bf_status run_points(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s)
+{
+    const int fp64 = P::is_f64 ? 1 : 0;
+    void *buf[2] = {p->w0, p->w1};
+    cudaError_t e = p->nsrc ? bfl::points_init(p->pd, fp64, p->r, g, buf[0], nrhs, s)
+                            : cudaMemsetAsync(buf[0], 0, (size_t)nrhs * p->npts * p->r * p->csize, s);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    bfk::KArgs<P> a;
+    fill_args<P>(p, a);
+    const int n = (int)p->passes_pts.size();
+    for (int i = 0; i < n; ++i) {
+        const Pass &ps = p->passes_pts[i];
+        a.l0 = ps.l0;
+        a.k = ps.k;
+        a.flags = ps.flags;
+        a.T = ps.T;
+        a.win = static_cast<const typename P::C *>(buf[i & 1]);
+        a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
+        const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
+        const size_t smem = pass_smem(p, ps) + row_cache_smem(p, ps);
+        e = (ps.row ? p->fns->row : p->fns->col)(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
+        if (e != cudaSuccess) return cuda_fail(p, e);
+    }
+    e = bfl::points_final(p->pd, fp64, p->r, buf[n & 1], f, nrhs, s);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    return BF_OK;
 }
 
 // Phase table of the multi-RHS schedule: per pass and CTA, the init factors, 5 r per pair for
@@ -760,7 +965,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     const int kreq = prm->fuse_levels > 0 ? prm->fuse_levels : kfit;
     p->kc = p->kr = kreq < kfit ? kreq : kfit;
     p->passes = schedule(p, p->kc, p->fns->np, true);
-    if (p->fns->col_mr) {
+    if (p->fns->col_mr[0]) {
         // 2 fused levels, as many pairs per CTA as one switch round covers (at least one tile);
         // scratch for enough right-hand sides to give every thread an item, fewer if the
         // shared memory of one CTA does not hold them
@@ -845,14 +1050,54 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     return BF_OK;
 }
 
+bf_status bf_plan_create_points(int d, int64_t N, int q, bf_phase_kind phase, const bf_params *prm, int64_t nsrc,
+                                const double *src, int64_t ntgt, const double *tgt, bf_plan *out)
+{
+    if (!out) return BF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!prm || nsrc < 0 || ntgt < 0 || (nsrc > 0 && !src) || (ntgt > 0 && !tgt)) return BF_ERR_INVALID_ARG;
+    if (nsrc > ((int64_t)1 << 40) || ntgt > ((int64_t)1 << 40)) return BF_ERR_INVALID_ARG;
+    if (prm->phase_tables) return BF_ERR_UNSUPPORTED;
+    for (int64_t i = 0; i < nsrc * (int64_t)(d > 0 ? d : 0); ++i)
+        if (!std::isfinite(src[i])) return BF_ERR_INVALID_ARG;
+    for (int64_t i = 0; i < ntgt * (int64_t)(d > 0 ? d : 0); ++i)
+        if (!std::isfinite(tgt[i])) return BF_ERR_INVALID_ARG;
+    bf_plan p = nullptr;
+    bf_status st = bf_plan_create(d, N, q, phase, prm, &p);
+    if (st != BF_OK) return st;
+    st = p->prec == BF_PREC_FP64 ? setup_points_t<double, double2>(p, nsrc, src, ntgt, tgt)
+                                 : setup_points_t<float, float2>(p, nsrc, src, ntgt, tgt);
+    if (st != BF_OK) {
+        bf_destroy(p);
+        return st;
+    }
+    *out = p;
+    return BF_OK;
+}
+
+bf_status bf_plan_points_info(bf_plan p, int *is_points, int64_t *nsrc, int64_t *ntgt)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (is_points) *is_points = p->points;
+    if (nsrc) *nsrc = p->points ? p->nsrc : p->npts;
+    if (ntgt) *ntgt = p->points ? p->ntgt : p->npts;
+    return BF_OK;
+}
+
 bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
 {
     if (!p) return BF_ERR_INVALID_ARG;
     if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
     if (nrhs == 0) return BF_OK;
-    if (!g || !f) return BF_ERR_INVALID_ARG;
+    // (an empty point set needs no buffer)
+    if ((!g && !(p->points && p->nsrc == 0)) || (!f && !(p->points && p->ntgt == 0))) return BF_ERR_INVALID_ARG;
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (p->points) {
+        if (p->prec == BF_PREC_FP64) return run_points<bfk::PF64>(p, g, f, nrhs, s);
+        if (p->prec == BF_PREC_MIXED_SFU) return run_points<bfk::PMIXF>(p, g, f, nrhs, s);
+        return run_points<bfk::PMIX>(p, g, f, nrhs, s);
+    }
     const int n = (int)schedule_for(p, nrhs).size();
     if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n);
     if (p->prec == BF_PREC_MIXED_SFU) {
@@ -866,6 +1111,7 @@ bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
 bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *best_ms)
 {
     if (!p || nrhs < 1 || nrhs > p->max_nrhs || reps < 1 || reps > 1000) return BF_ERR_INVALID_ARG;
+    if (p->points) return BF_ERR_UNSUPPORTED;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = (size_t)nrhs * (size_t)p->npts * p->csize;
     void *g = nullptr, *f = nullptr;
@@ -958,7 +1204,7 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
 bf_status bf_pass_count(bf_plan p, int nrhs, int *count)
 {
     if (!p || !count || nrhs < 1 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
-    *count = (int)schedule_for(p, nrhs).size();
+    *count = p->points ? (int)p->passes_pts.size() + 2 : (int)schedule_for(p, nrhs).size();
     return BF_OK;
 }
 
@@ -967,6 +1213,7 @@ bf_status bf_apply_pass(bf_plan p, int i, const void *g, void *f, int nrhs, void
     if (!p) return BF_ERR_INVALID_ARG;
     if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
     if (nrhs == 0) return BF_OK;
+    if (p->points) return BF_ERR_UNSUPPORTED;
     if (i < 0 || i >= (int)schedule_for(p, nrhs).size()) return BF_ERR_INVALID_ARG;
     if (!g || !f) return BF_ERR_INVALID_ARG;
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
@@ -983,6 +1230,7 @@ bf_status bf_apply_pass(bf_plan p, int i, const void *g, void *f, int nrhs, void
 bf_status bf_pass_info(bf_plan p, int nrhs, int i, int *kind, int *l0, int *k, int *flags)
 {
     if (!p || nrhs < 1 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
+    if (p->points) return BF_ERR_UNSUPPORTED;
     const std::vector<Pass> &sc = schedule_for(p, nrhs);
     if (i < 0 || i >= (int)sc.size()) return BF_ERR_INVALID_ARG;
     const Pass &ps = sc[i];
@@ -996,6 +1244,7 @@ bf_status bf_pass_info(bf_plan p, int nrhs, int i, int *kind, int *l0, int *k, i
 bf_status bf_apply_adjoint(bf_plan p, const void *f, void *g, int nrhs, void *stream)
 {
     if (!p) return BF_ERR_INVALID_ARG;
+    if (p->points) return BF_ERR_UNSUPPORTED;
     if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
     if (nrhs == 0) return BF_OK;
     if (!g || !f) return BF_ERR_INVALID_ARG;
@@ -1012,18 +1261,18 @@ bf_status bf_apply_host(bf_plan p, const void *g_host, void *f_host, int nrhs, v
     if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
     if (nrhs == 0) return BF_OK;
     if (!g_host || !f_host) return BF_ERR_INVALID_ARG;
-    const size_t bytes = (size_t)p->max_nrhs * (size_t)p->npts * p->csize;
+    const int64_t ng = p->points ? p->nsrc : p->npts, nf = p->points ? p->ntgt : p->npts;
     cudaError_t e;
-    if (!p->gstage) {
-        if ((e = cudaMalloc(&p->gstage, bytes)) != cudaSuccess) return cuda_fail(p, e);
-        if ((e = cudaMalloc(&p->fstage, bytes)) != cudaSuccess) return cuda_fail(p, e);
+    if (!p->gstage) {   // 16 bytes at least, so that empty point sets still get valid pointers
+        if ((e = cudaMalloc(&p->gstage, (size_t)p->max_nrhs * ng * p->csize + 16)) != cudaSuccess) return cuda_fail(p, e);
+        if ((e = cudaMalloc(&p->fstage, (size_t)p->max_nrhs * nf * p->csize + 16)) != cudaSuccess) return cuda_fail(p, e);
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const size_t n = (size_t)nrhs * (size_t)p->npts * p->csize;
-    if ((e = cudaMemcpyAsync(p->gstage, g_host, n, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(p, e);
+    const size_t bg = (size_t)nrhs * ng * p->csize, bfo = (size_t)nrhs * nf * p->csize;
+    if (bg && (e = cudaMemcpyAsync(p->gstage, g_host, bg, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(p, e);
     bf_status st = bf_apply(p, p->gstage, p->fstage, nrhs, stream);
     if (st != BF_OK) return st;
-    if ((e = cudaMemcpyAsync(f_host, p->fstage, n, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(p, e);
+    if (bfo && (e = cudaMemcpyAsync(f_host, p->fstage, bfo, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(p, e);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(p, e);
     return BF_OK;
 }
@@ -1053,7 +1302,8 @@ bf_status bf_batch_create(const bf_plan *plans, const int *nrhs, int count, bf_b
     const bf_plan p0 = plans[0];
     for (int i = 0; i < count; ++i) {
         const bf_plan p = plans[i];
-        if (p->d != 2 || p->prec == BF_PREC_FP64 || p->passes_mr.empty() || !p->fns->batch) return BF_ERR_UNSUPPORTED;
+        if (p->d != 2 || p->prec == BF_PREC_FP64 || p->passes_mr.empty() || !p->fns->batch || p->points)
+            return BF_ERR_UNSUPPORTED;
         if (p->q != p0->q || p->kind != p0->kind || p->prec != p0->prec || p->node_kind != p0->node_kind)
             return BF_ERR_UNSUPPORTED;
         for (int j = 0; j < i; ++j)
@@ -1152,6 +1402,7 @@ bf_status bf_destroy(bf_plan p)
     if (p->ctab) cudaFree(p->ctab);
     if (p->ptab) cudaFree(p->ptab);
     if (p->errflag) cudaFree(p->errflag);
+    for (void *m : p->pts_mem) cudaFree(m);
     if (p->gstage) cudaFree(p->gstage);
     if (p->fstage) cudaFree(p->fstage);
     delete p;

@@ -43,6 +43,30 @@ BFL_DECLARE(3, sfu, dot) BFL_DECLARE(3, sfu, genradon) BFL_DECLARE(3, sfu, separ
 #undef BFL_DECLARE
 
 
+// arbitrary point sets (bf_points.cu)
+struct PointsGeom {
+    int d, L, q, kind;
+    double s;
+    double x_lo[3], x_w[3], y_lo[3], y_w[3];
+    double z[8];                  // Chebyshev nodes on [-1/2, 1/2]
+};
+struct PointsData {
+    int d, q;
+    int64_t nbox, nsrc, ntgt, wstride;
+    const int64_t *src_off;       // [nbox + 1] sources of leaf box B: sorted positions src_off[B] .. src_off[B+1]-1
+    const int64_t *src_perm;      // [nsrc] caller's index of each sorted source
+    const void *src_lag;          // [nsrc][d][q] Lagrange values in the leaf box (R)
+    const void *src_e;            // [nsrc] e^{2 pi i Phi(x0(X), y)} (C)
+    const int64_t *tgt_box;       // [ntgt] leaf box of each target (caller's order)
+    const void *tgt_lag;          // [ntgt][d][q] (R)
+    const void *tgt_e;            // [ntgt] e^{2 pi i Phi(x, y0(Y))} (C)
+    const void *node_init;        // [nbox][r] conj(e^{2 pi i Phi(x0(X), y_t^B)}) (C)
+    const void *node_final;       // [nbox][r] conj(e^{2 pi i Phi(x_t^A, y0(Y))}) (C)
+};
+cudaError_t points_nodes(const PointsGeom &geo, int fp64, void *node_init, void *node_final);
+cudaError_t points_init(const PointsData &pd, int fp64, int r, const void *g, void *w0, int nrhs, cudaStream_t s);
+cudaError_t points_final(const PointsData &pd, int fp64, int r, const void *wl, void *f, int nrhs, cudaStream_t s);
+
 // device self-checks and the FMA rate probe (bf_selfcheck.cu)
 cudaError_t measure_fma(int fp64, double *tflops);
 cudaError_t selfcheck_sincos(int n, double *max_err);
