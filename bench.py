@@ -70,7 +70,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="genradon2d",
-                    choices=["genradon2d", "genradon3d", "dft64", "hypradon512", "hypradon48", "cg1024"])
+                    choices=["genradon2d", "genradon3d", "dft64", "hypradon512", "hypradon48", "cg1024",
+                             "genradon2d_points"])
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per apply (single-problem workloads)")
     ap.add_argument("--L", type=int, default=0, help="override log2 N of a single-problem workload (small cases)")
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -585,6 +586,69 @@ def run_cg(args, rank, world, local_rank):
             "clocks": clk.summary()}
 
 
+def run_points(args, rank, world, local_rank):
+    """2^20 sources and 2^20 targets at random positions (70% of each clustered in a small
+    square, so many leaf boxes are empty and some crowded) for the generalized Radon phase
+    with the N = 1024 box trees, q = 5, mixed.  value = 2^20 targets x RHS / time; error of
+    32 sampled targets against the direct sum over all sources."""
+    import numpy as np
+    import torch
+    from paper_1305_4650_gb300 import bf, workloads as wl
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    spec = wl.genradon2d(args.L or 10)
+    n = spec.npts
+    rng = np.random.default_rng(spec.seed + 7)
+    x_lo, x_w, y_lo, y_w = spec.domain()
+
+    def pts(lo, w):
+        u = rng.random((n, 2))
+        u = np.where(rng.random((n, 1)) < 0.7, 0.4 + 0.05 * u, u)
+        return np.asarray(lo[:2]) + u * np.asarray(w[:2])
+
+    y, x = pts(y_lo, y_w), pts(x_lo, x_w)
+    t0 = time.perf_counter()
+    plan = bf.Plan.from_spec(spec, precision="mixed", sources=y, targets=x)
+    plan_s = time.perf_counter() - t0
+    g_np = wl.source_values(spec, 1, np.complex64, seed=spec.seed + rank)
+    g = torch.from_numpy(g_np).to(dev)
+    f = plan.apply(g)
+    for _ in range(args.warmup):
+        plan.apply(g, f)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            plan.apply(g, f)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    acc = None
+    if rank == 0 and not args.no_accuracy:
+        import oracle
+        P = oracle.Problem(**spec.oracle_kwargs())
+        samp = rng.choice(n, 32, replace=False)
+        ref = oracle.direct_sum_points(P, y, g_np[0].astype(np.complex128), x[samp])
+        out = f.cpu().numpy()[0][samp]
+        acc = {"rel_l2_vs_direct_sum": float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
+               "sample": "32 random targets, direct sum over all 2^20 sources"}
+    launches = plan.launches(1)
+    plan.close()
+    if rank != 0:
+        return None
+    return {"metric": METRIC, "value": n * world / (ms * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+            "config": {"workload": f"genradon2d_points_{n}", "d": 2, "tree_N": spec.N, "q": 5, "sources": n,
+                       "targets": n, "placement": "70% clustered in 5% of each domain's width, rest uniform",
+                       "precision": "mixed", "plan_s": round(plan_s, 2),
+                       "parallelism": f"replicas x{world}"},
+            "accuracy": acc, "gpu_launches": args.steps * launches, "clocks": clk.summary()}
+
+
 def plan_fuse(passes):
     return max(p["k"] for p in passes)
 
@@ -664,7 +728,8 @@ def main():
             import torch.distributed as dist
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl")
-        runner = {"hypradon48": run_batched, "cg1024": run_cg}.get(args.workload, run_ours)
+        runner = {"hypradon48": run_batched, "cg1024": run_cg, "genradon2d_points": run_points}.get(args.workload,
+                                                                                                   run_ours)
         line = runner(args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist
