@@ -40,9 +40,9 @@ FP32_LANES_PER_SM = 128
 # workload, from one ncu capture of `python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-accuracy
 # --fp64-steps 0 --no-autotune`.  They describe the kernels as built from sources with the recorded hash
 # and the recorded pass schedule; otherwise the figure is dropped (traffic: null) until captured again.
-TRAFFIC = {"genradon2d": {"src_sha256": "5c62f68458489cff66c21315a6b52d925d6cacbc347ec613ccfbab7220f47e15",
+TRAFFIC = {"genradon2d": {"src_sha256": "e73ec132d5ff0e3f1a400b6c5dc53e3946582f680c210941759c68d9a648eadf",
                           "schedule": ["col2", "col3", "row2", "row3"],
-                          "bytes": [157957888, 378126080, 370089728, 216272128]}}
+                          "bytes": [157750272, 378383360, 370278912, 216414208]}}
 TRAFFIC_SRC = ("bf_device.cuh", "bf_inst.cuh", "bf_launch.h", "bf_api.cu")
 
 
