@@ -299,7 +299,10 @@ void fill_args(const bf_plan_s *p, bfk::KArgs<P> &a)
     }
     for (int h = 0; h < 2; ++h)
         for (int t = 0; t < p->q; ++t)
-            for (int u = 0; u < p->q; ++u) a.M[h][t][u] = (typename P::R)p->M[h][t][u];
+            for (int u = 0; u < p->q; ++u) {
+                a.M[h][t][u] = (typename P::R)p->M[h][t][u];
+                a.M2[h][t][u].x = a.M2[h][t][u].y = a.M[h][t][u];
+            }
     for (int t = 0; t < p->q; ++t) {
         a.lsrc[t] = (typename P::R)p->lsrc[t];
         a.ltgt[t] = (typename P::R)p->ltgt[t];

@@ -183,13 +183,22 @@ __device__ __forceinline__ void sincos2pi_sfu(float f, float &s, float &c)
     __sincosf(__fmul_rn(r, 6.28318530717958647692f), &s, &c);
 }
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(__fmaf_rn(a.x, b.x, -(a.y * b.y)), __fmaf_rn(a.x, b.y, a.y * b.x));
+}
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 // conj(a) * b
-__device__ __forceinline__ float2 cjmul(float2 a, float2 b) { return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
+__device__ __forceinline__ float2 cjmul(float2 a, float2 b)
+{
+    return make_float2(__fmaf_rn(a.x, b.x, a.y * b.y), __fmaf_rn(a.x, b.y, -(a.y * b.x)));
+}
 __device__ __forceinline__ double2 cjmul(double2 a, double2 b) { return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }
 __device__ __forceinline__ void cfma(float2 &acc, float m, float2 v) { acc.x = fmaf(m, v.x, acc.x); acc.y = fmaf(m, v.y, acc.y); }
 __device__ __forceinline__ void cfma(double2 &acc, double m, double2 v) { acc.x = fma(m, v.x, acc.x); acc.y = fma(m, v.y, acc.y); }
+// acc += m v with m given twice (m2 = (m, m)): one packed FMA on sm_100+, the same roundings as cfma
+__device__ __forceinline__ void cfma2(float2 &acc, float2 m2, float2 v) { acc = __ffma2_rn(m2, v, acc); }
+__device__ __forceinline__ void cfma2(double2 &acc, double2 m2, double2 v) { acc.x = fma(m2.x, v.x, acc.x); acc.y = fma(m2.y, v.y, acc.y); }
 template <class C> __device__ __forceinline__ C czero();
 template <> __device__ __forceinline__ float2 czero<float2>() { return make_float2(0.f, 0.f); }
 template <> __device__ __forceinline__ double2 czero<double2>() { return make_double2(0.0, 0.0); }
@@ -211,6 +220,7 @@ struct KArgs {
     int64_t wstride;                  // per-rhs stride of weights, in complex numbers
     int64_t npts;                     // N^d
     R M[2][QMAX][QMAX];               // M[h][t][t'] = l_t((z_t' + h - 1/2)/2)
+    C M2[2][QMAX][QMAX];              // the same, each value twice (operand of a packed FMA)
     R lsrc[QMAX], ltgt[QMAX];         // l_t(off - 1/2): Lagrange values of the grid point in its leaf box
     typename P::Sc sc;
     int L, l0, k, flags, kind;
@@ -712,7 +722,7 @@ struct Tile {
                         const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], t0p), 0), p1);
                         const C u = cmul(expphase_part<P, D, K>(a, tA, pt), win[t0p + Q * tq]);
 #pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[c0][t0][t0p], u);
+                        for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0], a.M2[c0][t0][t0p], u);
                     }
                 } else {
                     const int c0 = c & 1, c1 = (c >> 1) & 1;
@@ -727,12 +737,12 @@ struct Tile {
                             PH::src1(sp, 0, sget<P, Q>(a, 0, l, cb[0], t0p));
                             const C u = cmul(expphase<P, D, K>(a, tA, sp), win[t0p + Q * t1p + Q * Q * tq]);
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) cfma(tmp[t0], a.M[c0][t0][t0p], u);
+                            for (int t0 = 0; t0 < Q; ++t0) cfma2(tmp[t0], a.M2[c0][t0][t0p], u);
                         }
 #pragma unroll
                         for (int t1 = 0; t1 < Q; ++t1)
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0 + Q * t1], a.M[c1][t1][t1p], tmp[t0]);
+                            for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0 + Q * t1], a.M2[c1][t1][t1p], tmp[t0]);
                     }
                 }
             }
@@ -767,7 +777,7 @@ struct Tile {
                 for (int tqp = 0; tqp < Q; ++tqp) {
                     const C v = si[tqp * QD1];
 #pragma unroll
-                    for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], a.M[chi][tq][tqp], v);
+                    for (int tq = 0; tq < Q; ++tq) cfma2(acc[tq], a.M2[chi][tq][tqp], v);
                 }
             }
             int tk[DMAX];
@@ -983,8 +993,8 @@ struct Tile {
                 const C u = cjmul(expphase<P, D, K>(a, tn[t0], sc), win[t0]);
 #pragma unroll
                 for (int s0 = 0; s0 < Q; ++s0) {
-                    cfma(z[0][s0], a.M[0][t0][s0], u);
-                    cfma(z[1][s0], a.M[1][t0][s0], u);
+                    cfma2(z[0][s0], a.M2[0][t0][s0], u);
+                    cfma2(z[1][s0], a.M2[1][t0][s0], u);
                 }
             }
             C *so = S + (((tau * nblk + beta) * NC + c) * QD1 + th) * 2 * Q;
@@ -1030,7 +1040,7 @@ struct Tile {
                     for (int t1 = 0; t1 < Q; ++t1) {
                         const C zz = si[t1 * 2 * Q];
 #pragma unroll
-                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[c][s1], a.M[a1][t1][s1], zz);
+                        for (int s1 = 0; s1 < Q; ++s1) cfma2(v[c][s1], a.M2[a1][t1][s1], zz);
                     }
                 }
 #pragma unroll
@@ -1061,7 +1071,7 @@ struct Tile {
                         for (int t1 = 0; t1 < Q; ++t1) {
                             const C zz = si[(t1 + Q * t2) * 2 * Q];
 #pragma unroll
-                            for (int s2 = 0; s2 < Q; ++s2) cfma(w[t1 * Q + s2], a.M[a2][t2][s2], zz);
+                            for (int s2 = 0; s2 < Q; ++s2) cfma2(w[t1 * Q + s2], a.M2[a2][t2][s2], zz);
                         }
 #pragma unroll
                     for (int s2 = 0; s2 < Q; ++s2)
@@ -1069,7 +1079,7 @@ struct Tile {
                         for (int s1 = 0; s1 < Q; ++s1) {
                             C v = czero<C>();
 #pragma unroll
-                            for (int t1 = 0; t1 < Q; ++t1) cfma(v, a.M[a1][t1][s1], w[t1 * Q + s2]);
+                            for (int t1 = 0; t1 < Q; ++t1) cfma2(v, a.M2[a1][t1][s1], w[t1 * Q + s2]);
                             const int sk[DMAX] = {s0, s1, s2};
                             const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
                             acc[s1 + Q * s2] = cadd(acc[s1 + Q * s2], cmul(expphase<P, D, K>(a, tS, sc), v));
@@ -1162,8 +1172,8 @@ struct Tile {
                 const C u = cmul(e, wi[t0]);
 #pragma unroll
                 for (int s0 = 0; s0 < Q; ++s0) {
-                    cfma(z[0][s0], a.M[0][t0][s0], u);
-                    cfma(z[1][s0], a.M[1][t0][s0], u);
+                    cfma2(z[0][s0], a.M2[0][t0][s0], u);
+                    cfma2(z[1][s0], a.M2[1][t0][s0], u);
                 }
             }
             C *so = S + (((tau * nblk + beta) * NC + alpha) * QD1 + th) * 2 * Q;
@@ -1207,7 +1217,7 @@ struct Tile {
                     for (int t1 = 0; t1 < Q; ++t1) {
                         const C zz = si[t1 * 2 * Q];
 #pragma unroll
-                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[s1], a.M[c1][t1][s1], zz);
+                        for (int s1 = 0; s1 < Q; ++s1) cfma2(v[s1], a.M2[c1][t1][s1], zz);
                     }
 #pragma unroll
                     for (int s1 = 0; s1 < Q; ++s1) {
@@ -1225,7 +1235,7 @@ struct Tile {
                         for (int t1 = 0; t1 < Q; ++t1) {
                             const C zz = si[(t1 + Q * t2) * 2 * Q];
 #pragma unroll
-                            for (int s2 = 0; s2 < Q; ++s2) cfma(w[t1 * Q + s2], a.M[c2][t2][s2], zz);
+                            for (int s2 = 0; s2 < Q; ++s2) cfma2(w[t1 * Q + s2], a.M2[c2][t2][s2], zz);
                         }
 #pragma unroll
                     for (int s2 = 0; s2 < Q; ++s2) {
@@ -1234,7 +1244,7 @@ struct Tile {
                         for (int s1 = 0; s1 < Q; ++s1) {
                             C v = czero<C>();
 #pragma unroll
-                            for (int t1 = 0; t1 < Q; ++t1) cfma(v, a.M[c1][t1][s1], w[t1 * Q + s2]);
+                            for (int t1 = 0; t1 < Q; ++t1) cfma2(v, a.M2[c1][t1][s1], w[t1 * Q + s2]);
                             const C e = expphase_part<P, D, K>(a, tA, PH::add(p2, PH::part(tA, sget<P, Q>(a, 1, l, cb[1], s1), 1)));
                             acc[s1 + Q * s2] = cadd(acc[s1 + Q * s2], cjmul(e, v));
                         }
@@ -1307,7 +1317,7 @@ struct Tile {
                         const C e = expphase<P, D, K>(a, tn[s0 + Q * sq], sc);
                         const C u = cjmul(e, wi[s0 + Q * sq]);
 #pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], a.M[a0][t0][s0], u);
+                        for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0], a.M2[a0][t0][s0], u);
                     }
                 } else {
                     const int a0 = alpha & 1, a1 = (alpha >> 1) & 1;
@@ -1321,12 +1331,12 @@ struct Tile {
                             const C e = expphase<P, D, K>(a, tn[s0 + Q * s1 + Q * Q * sq], sc);
                             const C u = cjmul(e, wi[s0 + Q * s1 + Q * Q * sq]);
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) cfma(tmp[t0], a.M[a0][t0][s0], u);
+                            for (int t0 = 0; t0 < Q; ++t0) cfma2(tmp[t0], a.M2[a0][t0][s0], u);
                         }
 #pragma unroll
                         for (int t1 = 0; t1 < Q; ++t1)
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0 + Q * t1], a.M[a1][t1][s1], tmp[t0]);
+                            for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0 + Q * t1], a.M2[a1][t1][s1], tmp[t0]);
                     }
                 }
             }
@@ -1363,7 +1373,7 @@ struct Tile {
                 for (int sq = 0; sq < Q; ++sq) {
                     const C v = si[sq * QD1];
 #pragma unroll
-                    for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], a.M[ahi][tq][sq], v);
+                    for (int tq = 0; tq < Q; ++tq) cfma2(acc[tq], a.M2[ahi][tq][sq], v);
                 }
             }
             int tk[DMAX];

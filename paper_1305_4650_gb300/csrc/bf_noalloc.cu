@@ -156,7 +156,10 @@ bf_status run(int d, int L, int q, int kind, const bf_params *prm, const void *g
     void *w1 = base + off;
     for (int h = 0; h < 2; ++h)
         for (int t = 0; t < q; ++t)
-            for (int u = 0; u < q; ++u) a.M[h][t][u] = (typename P::R)lagrange1(q, z, t, (z[u] + h - 0.5) / 2.0);
+            for (int u = 0; u < q; ++u) {
+                a.M[h][t][u] = (typename P::R)lagrange1(q, z, t, (z[u] + h - 0.5) / 2.0);
+                a.M2[h][t][u].x = a.M2[h][t][u].y = a.M[h][t][u];
+            }
     for (int t = 0; t < q; ++t) {
         a.lsrc[t] = (typename P::R)lagrange1(q, z, t, prm->src_off - 0.5);
         a.ltgt[t] = (typename P::R)lagrange1(q, z, t, prm->tgt_off - 0.5);
