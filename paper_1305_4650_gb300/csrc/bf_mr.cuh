@@ -216,15 +216,20 @@ struct TileMR {
     // ---- CTA output: tile slots are in digit-reversed order after k merges
     static __device__ void store(const KArgs<P> &a, const Ctx &x, const C *W)
     {
+        // destination of each slot's pair, once per CTA (slots are in digit-reversed order)
+        __shared__ int64_t poff[64];
         const int k = a.k, n = 1 << (D * k), WS = x.npr * RR;
         const int64_t Sstar = 1LL << (D * (a.L - a.l0 - k));
+        for (int pl = threadIdx.x; pl < x.npr; pl += NT) {
+            uint32_t Ap, Bstar;
+            tile_of(a, x, pl >> (D * k), Ap, Bstar);
+            poff[pl] = ((((int64_t)Ap << (D * k)) + digit_rev<D>(pl & (n - 1), k)) * Sstar + Bstar) * RR;
+        }
+        __syncthreads();
         for (int j = threadIdx.x; j < x.nr * WS; j += NT) {
             const int rb = (j / RR) >> x.lgp, e = j - rb * WS;
-            const int t = e % RR, sl = (e / RR) & (n - 1), tau = (e / RR) >> (D * k);
-            uint32_t Ap, Bstar;
-            tile_of(a, x, tau, Ap, Bstar);
-            const int64_t pair = ((int64_t)(((int64_t)Ap << (D * k)) + digit_rev<D>(sl, k))) * Sstar + Bstar;
-            a.wout[(int64_t)(x.rhs0 + rb) * a.wstride + pair * RR + t] = W[j];
+            const int pl = e / RR, t = e - pl * RR;
+            a.wout[(int64_t)(x.rhs0 + rb) * a.wstride + poff[pl] + t] = W[j];
         }
     }
 
@@ -262,19 +267,30 @@ struct TileMR {
             ts.tb += WS;
             __syncthreads();
         }
-        for (int j = threadIdx.x; PM != PM_BUILD && j < x.nr * WS; j += NT) {
-            const int rb = (j / RR) >> x.lgp, it = j - rb * WS;
-            const int t = it % RR, pr = it / RR;
-            C v = czero<C>();
-            if (a.lsrc[t % Q] * a.lsrc[t / Q] != R(0)) {
+        if constexpr (PM != PM_BUILD) {
+            // the grid point of a leaf box has a non-zero Lagrange value at few nodes (one
+            // for points at box corners): zero the weights, then fill those nodes only
+            __shared__ int nzt[QMAX * QMAX];
+            __shared__ int nnz;
+            if (threadIdx.x == 0) {
+                int m = 0;
+                for (int t = 0; t < RR; ++t)
+                    if (a.lsrc[t % Q] * a.lsrc[t / Q] != R(0)) nzt[m++] = t;
+                nnz = m;
+            }
+            float4 *w4 = reinterpret_cast<float4 *>(W);
+            for (int j = threadIdx.x; j < (x.nr * WS * (int)sizeof(C)) / 16; j += NT) w4[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            __syncthreads();
+            for (int j = threadIdx.x; j < x.nr * x.npr * nnz; j += NT) {
+                const int z = j % nnz, pr = (j / nnz) & (x.npr - 1), rb = (j / nnz) >> x.lgp;
+                const int it = pr * RR + nzt[z];
                 uint32_t Ap, Bstar;
                 tile_of(a, x, pr >> (D * k), Ap, Bstar);
                 int cb[DMAX];
                 morton_decode<D>((Bstar << (D * k)) + (pr & (n - 1)), L, cb);
                 const int64_t flat = ((int64_t)cb[0] << L) + cb[1];
-                v = cmul(PC[it], g[(int64_t)(x.rhs0 + rb) * a.npts + flat]);
+                W[rb * WS + it] = cmul(PC[it], g[(int64_t)(x.rhs0 + rb) * a.npts + flat]);
             }
-            W[j] = v;
         }
         __syncthreads();
         if constexpr (PM == PM_TABLE) ts_release(ts);
