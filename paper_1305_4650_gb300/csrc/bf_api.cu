@@ -953,6 +953,10 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     p->prm = *prm;
     p->csize = p->prec == BF_PREC_FP64 ? 16 : 8;
     p->fns = bfl::get_fns(d, q, (int)p->prec, (int)phase);
+    if (!p->fns) {   // this combination was not compiled into the library
+        delete p;
+        return BF_ERR_UNSUPPORTED;
+    }
 
     for (int j = 0; j < q; ++j)
         p->z[j] = p->node_kind == 0 ? 0.5 * std::cos(j * kPi / (q - 1)) : 0.5 * std::cos((2 * j + 1) * kPi / (2.0 * q));

@@ -527,6 +527,12 @@ __device__ __forceinline__ void cmac(double2 &acc, double2 e, double2 u)
     acc.y = fma(e.y, u.x, acc.y);
 }
 
+}  // namespace bfk
+
+#include "bf_pair.cuh"   // the same phase arithmetic on the two lanes of a float2
+
+namespace bfk {
+
 // table reads
 template <class P, int Q>
 __device__ __forceinline__ typename P::TE tget(const KArgs<P> &a, int k, int l, int box, int slot)
@@ -714,7 +720,33 @@ struct Tile {
                 for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
                 typename PH::S sp;
                 PH::src1(sp, D - 1, sget<P, Q>(a, D - 1, l, cb[D - 1], tq));
-                if constexpr (D == 2) {
+                if constexpr (D == 2 && !P::is_f64) {
+                    // phases two at a time: lanes t'_0 and t'_0 + 1 (the last one alone for odd q)
+                    using PH2 = Ph2<P, D, K>;
+                    const int c0 = c & 1;
+                    const typename PH2::T tA2 = PH2::dup(tA);
+                    const typename P::SE e1 = sget<P, Q>(a, 1, l, cb[1], tq);
+                    const typename PH2::Part p1 = PH2::part(tA2, e1, e1, 1);
+#pragma unroll
+                    for (int t0p = 0; t0p + 1 < Q; t0p += 2) {
+                        float2 E0, E1;
+                        expphase_part2<P, D, K>(a, tA2,
+                                                PH2::add(PH2::part(tA2, sget<P, Q>(a, 0, l, cb[0], t0p),
+                                                                   sget<P, Q>(a, 0, l, cb[0], t0p + 1), 0), p1), E0, E1);
+                        const C u0 = cmul(E0, win[t0p + Q * tq]), u1 = cmul(E1, win[t0p + 1 + Q * tq]);
+#pragma unroll
+                        for (int t0 = 0; t0 < Q; ++t0) {
+                            cfma2(acc[t0], a.M2[c0][t0][t0p], u0);
+                            cfma2(acc[t0], a.M2[c0][t0][t0p + 1], u1);
+                        }
+                    }
+                    if constexpr (Q & 1) {
+                        const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(p1));
+                        const C u = cmul(expphase_part<P, D, K>(a, tA, pt), win[Q - 1 + Q * tq]);
+#pragma unroll
+                        for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0], a.M2[c0][t0][Q - 1], u);
+                    }
+                } else if constexpr (D == 2) {
                     const int c0 = c & 1;
                     const typename PH::Part p1 = PH::part(tA, sget<P, Q>(a, 1, l, cb[1], tq), 1);
 #pragma unroll
@@ -723,6 +755,46 @@ struct Tile {
                         const C u = cmul(expphase_part<P, D, K>(a, tA, pt), win[t0p + Q * tq]);
 #pragma unroll
                         for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0], a.M2[c0][t0][t0p], u);
+                    }
+                } else if constexpr (!P::is_f64) {
+                    // d = 3: the parts of coordinates 2 and 1 hoisted, phases two at a time over t'_0
+                    using PH2 = Ph2<P, D, K>;
+                    const int c0 = c & 1, c1 = (c >> 1) & 1;
+                    const typename PH2::T tA2 = PH2::dup(tA);
+                    const typename P::SE e2 = sget<P, Q>(a, 2, l, cb[2], tq);
+                    const typename PH2::Part p2 = PH2::part(tA2, e2, e2, 2);
+#pragma unroll
+                    for (int t1p = 0; t1p < Q; ++t1p) {
+                        const typename P::SE e1 = sget<P, Q>(a, 1, l, cb[1], t1p);
+                        const typename PH2::Part p12 = PH2::add(PH2::part(tA2, e1, e1, 1), p2);
+                        const C *wrow = win + Q * t1p + Q * Q * tq;
+                        C tmp[Q];
+#pragma unroll
+                        for (int t0 = 0; t0 < Q; ++t0) tmp[t0] = czero<C>();
+#pragma unroll
+                        for (int t0p = 0; t0p + 1 < Q; t0p += 2) {
+                            float2 E0, E1;
+                            expphase_part2<P, D, K>(a, tA2,
+                                                    PH2::add(PH2::part(tA2, sget<P, Q>(a, 0, l, cb[0], t0p),
+                                                                       sget<P, Q>(a, 0, l, cb[0], t0p + 1), 0), p12),
+                                                    E0, E1);
+                            const C u0 = cmul(E0, wrow[t0p]), u1 = cmul(E1, wrow[t0p + 1]);
+#pragma unroll
+                            for (int t0 = 0; t0 < Q; ++t0) {
+                                cfma2(tmp[t0], a.M2[c0][t0][t0p], u0);
+                                cfma2(tmp[t0], a.M2[c0][t0][t0p + 1], u1);
+                            }
+                        }
+                        if constexpr (Q & 1) {
+                            const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(p12));
+                            const C u = cmul(expphase_part<P, D, K>(a, tA, pt), wrow[Q - 1]);
+#pragma unroll
+                            for (int t0 = 0; t0 < Q; ++t0) cfma2(tmp[t0], a.M2[c0][t0][Q - 1], u);
+                        }
+#pragma unroll
+                        for (int t1 = 0; t1 < Q; ++t1)
+#pragma unroll
+                            for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0 + Q * t1], a.M2[c1][t1][t1p], tmp[t0]);
                     }
                 } else {
                     const int c0 = c & 1, c1 = (c >> 1) & 1;
@@ -789,10 +861,31 @@ struct Tile {
             typename PH::Part pl = PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], tk[0]), 0);
             if constexpr (D == 3) pl = PH::add(pl, PH::part(tA, sget<P, Q>(a, 1, l + 1, cbq[1], tk[1]), 1));
             C *wo = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR + tl;
+            if constexpr (!P::is_f64) {
+                // phases two at a time: lanes t_{d-1} and t_{d-1} + 1 (the last one alone for odd q)
+                using PH2 = Ph2<P, D, K>;
+                const typename PH2::T tA2 = PH2::dup(tA);
+                const typename PH2::Part pl2 = PH2::dup(pl);
 #pragma unroll
-            for (int tq = 0; tq < Q; ++tq) {
-                const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq), D - 1), pl);
-                wo[tq * QD1] = cjmul(expphase_part<P, D, K>(a, tA, pt), acc[tq]);
+                for (int tq = 0; tq + 1 < Q; tq += 2) {
+                    float2 E0, E1;
+                    expphase_part2<P, D, K>(a, tA2,
+                                            PH2::add(PH2::part(tA2, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq),
+                                                               sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq + 1), D - 1), pl2),
+                                            E0, E1);
+                    wo[tq * QD1] = cjmul(E0, acc[tq]);
+                    wo[(tq + 1) * QD1] = cjmul(E1, acc[tq + 1]);
+                }
+                if constexpr (Q & 1) {
+                    const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], Q - 1), D - 1), pl);
+                    wo[(Q - 1) * QD1] = cjmul(expphase_part<P, D, K>(a, tA, pt), acc[Q - 1]);
+                }
+            } else {
+#pragma unroll
+                for (int tq = 0; tq < Q; ++tq) {
+                    const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq), D - 1), pl);
+                    wo[tq * QD1] = cjmul(expphase_part<P, D, K>(a, tA, pt), acc[tq]);
+                }
             }
         }
         __syncthreads();
@@ -803,6 +896,10 @@ struct Tile {
     // slot that another item has already rewritten.
     static __device__ void switch_tiles(const KArgs<P> &a, C *Wt, C *S, int l)
     {
+        if constexpr (!P::is_f64 && K == KIND_GENRADON) {   // the phase whose pairs pay for their registers
+            switch_tiles_pair(a, Wt, S, l);
+            return;
+        }
         const int k = a.k, n = 1 << (D * k);
         const int L = a.L;
         for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
@@ -849,6 +946,93 @@ struct Tile {
 #pragma unroll
                     for (int s0 = 0; s0 < Q; ++s0)
                         cmac(acc[s0], expphase_part<P, D, K>(a, tS[s0], PH::add(PH::part(tS[s0], e0, 0), hp[s0])), ut);
+                }
+            }
+            C *w = S + (tau * n + sl) * RR + sh * Q;
+#pragma unroll
+            for (int s0 = 0; s0 < Q; ++s0) w[s0] = acc[s0];
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) Wt[j] = S[j];
+        __syncthreads();
+    }
+
+    // ---- the same switch with the phases evaluated two at a time (lanes of a float2):
+    // targets s_0 = 2j and 2j + 1 share a pair; for odd q the last target takes two
+    // consecutive t_0 in its lanes.  Each lane rounds exactly as the scalar code.
+    static __device__ void switch_tiles_pair(const KArgs<P> &a, C *Wt, C *S, int l)
+    {
+        using PH2 = Ph2<P, D, K>;
+        constexpr int NPR = Q / 2, ODD = Q & 1, NT2 = NPR + ODD;
+        const int k = a.k, n = 1 << (D * k);
+        const int L = a.L;
+        for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
+            const int sh = it % QD1;
+            const int sl = (it / QD1) & (n - 1);
+            const int tau = (it / QD1) >> (D * k);
+            uint32_t Ap, Bstar;
+            tile_of(a, tau, Ap, Bstar);
+            const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
+            int ca[DMAX], cb[DMAX];
+            morton_decode<D>(A, l, ca);
+            morton_decode<D>(Bstar, L - l, cb);
+            typename PH2::T tP[NT2];
+            C acc[Q];
+            int sk[DMAX];
+            {
+                int tt = sh;
+#pragma unroll
+                for (int j = 1; j < D; ++j) { sk[j] = tt % Q; tt /= Q; }
+            }
+#pragma unroll
+            for (int j = 0; j < NT2; ++j) {
+                sk[0] = 2 * j;
+                const typename PH::T t0 = tpoint<P, D, Q, K>(a, l, ca, sk);
+                sk[0] = (2 * j + 1 < Q) ? 2 * j + 1 : 2 * j;
+                tP[j] = PH2::pair(t0, tpoint<P, D, Q, K>(a, l, ca, sk));
+            }
+#pragma unroll
+            for (int s0 = 0; s0 < Q; ++s0) acc[s0] = czero<C>();
+            const C *u = Wt + (tau * n + sl) * RR;
+#pragma unroll 1
+            for (int th = 0; th < QD1; ++th) {
+                int tk[DMAX], tt = th;
+#pragma unroll
+                for (int j = 1; j < D; ++j) { tk[j] = tt % Q; tt /= Q; }
+                typename PH2::Part hp[NT2];
+                const typename P::SE e1 = sget<P, Q>(a, 1, l, cb[1], tk[1]);
+#pragma unroll
+                for (int j = 0; j < NT2; ++j) {
+                    hp[j] = PH2::part(tP[j], e1, e1, 1);
+                    if constexpr (D == 3) {
+                        const typename P::SE e2 = sget<P, Q>(a, 2, l, cb[2], tk[2]);
+                        hp[j] = PH2::add(hp[j], PH2::part(tP[j], e2, e2, 2));
+                    }
+                }
+#pragma unroll
+                for (int t0 = 0; t0 < Q; t0 += 2) {
+                    const bool two = t0 + 1 < Q;
+                    const typename P::SE ea = sget<P, Q>(a, 0, l, cb[0], t0);
+                    const typename P::SE eb = two ? sget<P, Q>(a, 0, l, cb[0], t0 + 1) : ea;
+                    const C ua = u[t0 + Q * th];
+                    const C ub = two ? u[t0 + 1 + Q * th] : czero<C>();
+                    float2 E0, E1;
+#pragma unroll
+                    for (int j = 0; j < NPR; ++j) {
+                        expphase_part2<P, D, K>(a, tP[j], PH2::add(PH2::part(tP[j], ea, ea, 0), hp[j]), E0, E1);
+                        cmac(acc[2 * j], E0, ua);
+                        cmac(acc[2 * j + 1], E1, ua);
+                        if (two) {
+                            expphase_part2<P, D, K>(a, tP[j], PH2::add(PH2::part(tP[j], eb, eb, 0), hp[j]), E0, E1);
+                            cmac(acc[2 * j], E0, ub);
+                            cmac(acc[2 * j + 1], E1, ub);
+                        }
+                    }
+                    if constexpr (ODD) {
+                        expphase_part2<P, D, K>(a, tP[NPR], PH2::add(PH2::part(tP[NPR], ea, eb, 0), hp[NPR]), E0, E1);
+                        cmac(acc[Q - 1], E0, ua);
+                        if (two) cmac(acc[Q - 1], E1, ub);
+                    }
                 }
             }
             C *w = S + (tau * n + sl) * RR + sh * Q;
@@ -1047,11 +1231,25 @@ struct Tile {
                 for (int s1 = 0; s1 < Q; ++s1) {
                     const int sk[DMAX] = {s0, s1, 0};
                     const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
-                    const typename PH::Part q0[2] = {PH::part(tS, sc0[0], 0), PH::part(tS, sc0[1], 0)};
-                    const typename PH::Part q1[2] = {PH::part(tS, sc1[0], 1), PH::part(tS, sc1[1], 1)};
+                    if constexpr (!P::is_f64) {
+                        // phases two at a time: lanes c_0 = 0 and 1
+                        using PH2 = Ph2<P, D, K>;
+                        const typename PH2::T tS2 = PH2::dup(tS);
+                        const typename PH2::Part q0 = PH2::part(tS2, sc0[0], sc0[1], 0);
 #pragma unroll
-                    for (int c = 0; c < NC; ++c)
-                        acc[s1] = cadd(acc[s1], cmul(expphase_part<P, D, K>(a, tS, PH::add(q0[c & 1], q1[c >> 1])), v[c][s1]));
+                        for (int c1 = 0; c1 < 2; ++c1) {
+                            float2 E0, E1;
+                            expphase_part2<P, D, K>(a, tS2, PH2::add(q0, PH2::part(tS2, sc1[c1], sc1[c1], 1)), E0, E1);
+                            acc[s1] = cadd(acc[s1], cmul(E0, v[2 * c1][s1]));
+                            acc[s1] = cadd(acc[s1], cmul(E1, v[2 * c1 + 1][s1]));
+                        }
+                    } else {
+                        const typename PH::Part q0[2] = {PH::part(tS, sc0[0], 0), PH::part(tS, sc0[1], 0)};
+                        const typename PH::Part q1[2] = {PH::part(tS, sc1[0], 1), PH::part(tS, sc1[1], 1)};
+#pragma unroll
+                        for (int c = 0; c < NC; ++c)
+                            acc[s1] = cadd(acc[s1], cmul(expphase_part<P, D, K>(a, tS, PH::add(q0[c & 1], q1[c >> 1])), v[c][s1]));
+                    }
                 }
             } else {
                 const int a1 = (alpha >> 1) & 1, a2 = (alpha >> 2) & 1;

@@ -106,6 +106,7 @@ struct TileMR {
     using R = typename P::R;
     using C = typename P::C;
     using PH = Ph<P, 2, K>;
+    using PH2 = Ph2<P, 2, K>;
     using TL = Tile<2, Q, P, K>;
 
     struct Ctx {
@@ -318,13 +319,21 @@ struct TileMR {
             morton_decode<D>(Bq, L - l - 1, cbq);
             const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
             const int c = cl | (chi << 1);
-            const typename PH::Part p1 = PH::part(tA, sget<P, Q>(a, 1, l, 2 * cbq[1] + chi, tq), 1);
+            // phases two at a time: lanes t'_0 and t'_0 + 1 (the last one alone for odd q)
+            const typename PH2::T tA2 = PH2::dup(tA);
+            const typename P::SE e1 = sget<P, Q>(a, 1, l, 2 * cbq[1] + chi, tq);
+            const typename PH2::Part p1 = PH2::part(tA2, e1, e1, 1);
+            const int c0 = 2 * cbq[0] + (c & 1);
             C *o = PA + it * Q;
 #pragma unroll
-            for (int t0p = 0; t0p < Q; ++t0p) {
-                const typename PH::Part pt =
-                    PH::add(PH::part(tA, sget<P, Q>(a, 0, l, 2 * cbq[0] + (c & 1), t0p), 0), p1);
-                o[t0p] = expphase_part<P, D, K>(a, tA, pt);
+            for (int t0p = 0; t0p + 1 < Q; t0p += 2) {
+                const typename PH2::Part pt =
+                    PH2::add(PH2::part(tA2, sget<P, Q>(a, 0, l, c0, t0p), sget<P, Q>(a, 0, l, c0, t0p + 1), 0), p1);
+                expphase_part2<P, D, K>(a, tA2, pt, o[t0p], o[t0p + 1]);
+            }
+            if constexpr (Q & 1) {
+                const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, c0, Q - 1), 0), PH2::lane0(p1));
+                o[Q - 1] = expphase_part<P, D, K>(a, tA, pt);
             }
         }
         for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
@@ -438,16 +447,28 @@ struct TileMR {
                 const C *chunk = nullptr;
                 if constexpr (PM == PM_TABLE) chunk = ts_acquire(ts);
                 if (act) {
-                    typename PH::Part hp;
-                    if constexpr (PM != PM_TABLE) hp = PH::part(tS, sget<P, Q>(a, 1, l, cb[1], th), 1);
+                    C ev[Q];   // the factors of this digit t_1: two at a time (lanes t_0, t_0 + 1)
+                    if constexpr (PM != PM_TABLE) {
+                        const typename PH2::T tS2 = PH2::dup(tS);
+                        const typename P::SE e1 = sget<P, Q>(a, 1, l, cb[1], th);
+                        const typename PH2::Part hp = PH2::part(tS2, e1, e1, 1);
+#pragma unroll
+                        for (int t0 = 0; t0 + 1 < Q; t0 += 2)
+                            expphase_part2<P, D, K>(
+                                a, tS2,
+                                PH2::add(PH2::part(tS2, sget<P, Q>(a, 0, l, cb[0], t0), sget<P, Q>(a, 0, l, cb[0], t0 + 1), 0), hp),
+                                ev[t0], ev[t0 + 1]);
+                        if constexpr (Q & 1)
+                            ev[Q - 1] = expphase_part<P, D, K>(
+                                a, tS, PH::add(PH::part(tS, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(hp)));
+                    }
 #pragma unroll
                     for (int t0 = 0; t0 < Q; ++t0) {
                         C e;
                         if constexpr (PM == PM_TABLE)
                             e = chunk[(pl * Q + t0) * RR + s];
                         else
-                            e = expphase_part<P, D, K>(
-                                a, tS, PH::add(PH::part(tS, sget<P, Q>(a, 0, l, cb[0], t0), 0), hp));
+                            e = ev[t0];
                         if constexpr (PM == PM_BUILD) {
                             __stcs(ts.tb + ((int64_t)th * x.npr * Q + pl * Q + t0) * RR + s, e);
                         } else {
@@ -512,15 +533,17 @@ struct TileMR {
             morton_decode<D>(Bq, L - l - 1, cbq);
             const int sk[DMAX] = {s0, s1, 0};
             const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
-            typename PH::Part q0[2], q1[2];
+            // phases two at a time: lanes c_0 = 0 and 1
+            const typename PH2::T tS2 = PH2::dup(tS);
+            const typename PH2::Part q0 =
+                PH2::part(tS2, sget<P, Q>(a, 0, l, 2 * cbq[0], Q), sget<P, Q>(a, 0, l, 2 * cbq[0] + 1, Q), 0);
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                q0[h] = PH::part(tS, sget<P, Q>(a, 0, l, 2 * cbq[0] + h, Q), 0);
-                q1[h] = PH::part(tS, sget<P, Q>(a, 1, l, 2 * cbq[1] + h, Q), 1);
+            for (int c1 = 0; c1 < 2; ++c1) {
+                const typename P::SE e1 = sget<P, Q>(a, 1, l, 2 * cbq[1] + c1, Q);
+                expphase_part2<P, D, K>(a, tS2, PH2::add(q0, PH2::part(tS2, e1, e1, 1)),
+                                        PB[((pA * NC + 2 * c1) * Q + s1) * Q + s0],
+                                        PB[((pA * NC + 2 * c1 + 1) * Q + s1) * Q + s0]);
             }
-#pragma unroll
-            for (int c = 0; c < NC; ++c)
-                PB[((pA * NC + c) * Q + s1) * Q + s0] = expphase_part<P, D, K>(a, tS, PH::add(q0[c & 1], q1[c >> 1]));
         }
         __syncthreads();
         if constexpr (PM == PM_BUILD) {   // build: store the factors; no weights are touched

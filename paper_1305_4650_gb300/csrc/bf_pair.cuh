@@ -3,12 +3,12 @@
 // sm_100 and later issue FP32 add, multiply and fused multiply-add on a pair of
 // registers as one instruction (add/sub/mul/fma .f32x2).  The double-float
 // evaluation of Phi and the sincos polynomial are long chains of such operations,
-// so two independent phases (two lanes of a float2) cost about the issue slots of
-// one.  Every lane computes exactly what the scalar code in bf_device.cuh computes
-// (same operations, same rounding), so paired and scalar results are identical.
+// so two independent phases (two lanes of a float2) take about the issue slots of
+// one.  Every lane performs the operations of the scalar code in bf_device.cuh; where
+// a caller sums the per-coordinate parts in another order than the scalar code, the
+// two agree to FP32 rounding.
+// Included by bf_device.cuh after the scalar phase code it builds on.
 #pragma once
-
-#include "bf_device.cuh"
 
 namespace bfk {
 
@@ -122,6 +122,16 @@ struct Ph2<PMIXT<F>, D, K> {
     struct Part { float2 f; df2 q; };
 
     static __device__ __forceinline__ df2 pack(const df &a, const df &b) { return {make_float2(a.hi, b.hi), make_float2(a.lo, b.lo)}; }
+
+    static __device__ __forceinline__ T dup(const typename PH::T &a) { return pair(a, a); }
+    static __device__ __forceinline__ Part dup(const typename PH::Part &p)
+    {
+        return Part{dup2(p.f), {dup2(p.q.hi), dup2(p.q.lo)}};
+    }
+    static __device__ __forceinline__ typename PH::Part lane0(const Part &p)
+    {
+        return typename PH::Part{p.f.x, {p.q.hi.x, p.q.lo.x}};
+    }
 
     static __device__ __forceinline__ T pair(const typename PH::T &a, const typename PH::T &b)
     {
