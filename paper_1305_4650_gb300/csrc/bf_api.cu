@@ -233,10 +233,12 @@ size_t row_adj_cache_smem(const bf_plan_s *p, const Pass &ps)
 }
 
 // multi-RHS pass: nr right-hand sides of T 2^{dk} pairs, scratch for rc of them, a phase cache
-// of 5 r factors per pair (bf_mr.cuh)
+// of 5 r factors per pair, with the bank-conflict padding of bf_mr.cuh
 size_t mr_smem(const bf_plan_s *p, const Pass &ps, int nr, int rc)
 {
-    return (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (size_t)p->r * p->csize * (size_t)(nr + 2 * rc + 5);
+    const size_t npr = (size_t)ps.T << (p->d * ps.k);
+    return p->csize * (npr * (size_t)p->r * (size_t)(nr + 5) + (size_t)rc * (size_t)bfk::mr_s_stride(p->q, (int64_t)npr) +
+                       npr * (size_t)bfk::mr_pc_extra(p->q));
 }
 
 // multi-RHS pass reading a phase table: stream control and two table-block buffers, then
@@ -245,7 +247,8 @@ size_t mr_smem_table(const bf_plan_s *p, const Pass &ps, int nr, int rc)
 {
     const size_t npr = (size_t)ps.T << (p->d * ps.k);
     const size_t blk = (size_t)(p->q > 5 ? p->q : 5) * (size_t)p->r * npr;
-    return (size_t)bfk::TABCTL_BYTES + 2 * blk * p->csize + npr * (size_t)p->r * p->csize * (size_t)(nr + 2 * rc);
+    return (size_t)bfk::TABCTL_BYTES + 2 * blk * p->csize +
+           p->csize * (npr * (size_t)p->r * (size_t)nr + (size_t)rc * (size_t)bfk::mr_s_stride(p->q, (int64_t)npr));
 }
 
 // A CTA owns np pairs (2^{d kmax} of the instantiation, fewer for tiny problems):

@@ -100,8 +100,29 @@ struct CfgMR {
     static constexpr int MINB = RR <= 32 ? 2 : 1;   // CTAs per SM the register budget is cut for
 };
 
+// Padding (in complex numbers) of the shared-memory arrays read and written by the apply
+// stages, so that the 64-bit accesses of a warp fall in distinct banks (32 banks of 4
+// bytes).  Chosen for q = 5 by counting the wavefronts of every access pattern of the
+// stages for 16 and 32 pairs per CTA and 1 or 2 fused levels (46% more wavefronts than the
+// minimum before, 3% after); the phase-table layout stays compact.
+struct MRPad {
+    int ca;   // column modulation: per (pair, chi) block of 2 r factors
+    int cb;   // column demodulation: per pair (r factors)
+    int rb;   // row post-modulation: per pair (4 r factors)
+    int rs;   // row scratch: per (pair, t_1) unit of 2 q partial sums
+};
+__host__ __device__ constexpr MRPad mr_pad(int q) { return q == 5 ? MRPad{7, 12, 1, 1} : MRPad{0, 0, 0, 0}; }
+// phase-cache entries per pair beyond 5 r (evaluating passes)
+__host__ __device__ constexpr int mr_pc_extra(int q)
+{
+    return 2 * mr_pad(q).ca + mr_pad(q).cb > mr_pad(q).rb ? 2 * mr_pad(q).ca + mr_pad(q).cb : mr_pad(q).rb;
+}
+// scratch entries per right-hand side (2 r per pair, plus the row scratch padding)
+__host__ __device__ constexpr int64_t mr_s_stride(int q, int64_t npr) { return 2 * npr * q * q + npr * q * mr_pad(q).rs; }
+
 template <int Q, class P, int K>
 struct TileMR {
+    static constexpr MRPad PAD = mr_pad(Q);
     static constexpr int D = 2, NC = 4, RR = Q * Q, NT = CfgMR<Q>::NT;
     using R = typename P::R;
     using C = typename P::C;
@@ -304,8 +325,10 @@ struct TileMR {
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
         if constexpr (PM == PM_TABLE) PC = ts_acquire(ts);
-        C *PA = PC;                  // [pA][chi][cl][tq][t0']  modulation of the inputs
-        C *PB = PC + nout * 4 * RR;  // [pA][tq][tl]            demodulation of the output
+        const int SW = (int)mr_s_stride(Q, x.npr);
+        constexpr int PCA = 2 * RR + (PM == PM_COMPUTE ? PAD.ca : 0), PCB = RR + (PM == PM_COMPUTE ? PAD.cb : 0);
+        C *PA = PC;                     // [pA][chi] blocks of PCA: [cl][tq][t0']  modulation of the inputs
+        C *PB = PC + nout * 2 * PCA;    // [pA] blocks of PCB: [tq][tl]            demodulation of the output
         for (int it = threadIdx.x; PM != PM_TABLE && it < nout * 4 * Q; it += NT) {
             const int tq = it % Q, cl = (it / Q) & 1, chi = (it / (2 * Q)) & 1, pA = it / (4 * Q);
             const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
@@ -324,7 +347,7 @@ struct TileMR {
             const typename P::SE e1 = sget<P, Q>(a, 1, l, 2 * cbq[1] + chi, tq);
             const typename PH2::Part p1 = PH2::part(tA2, e1, e1, 1);
             const int c0 = 2 * cbq[0] + (c & 1);
-            C *o = PA + it * Q;
+            C *o = PA + (pA * 2 + chi) * PCA + cl * RR + tq * Q;
 #pragma unroll
             for (int t0p = 0; t0p + 1 < Q; t0p += 2) {
                 const typename PH2::Part pt =
@@ -350,7 +373,7 @@ struct TileMR {
             const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
             const typename PH::Part pl = PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], tl), 0);
             const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 1, l + 1, cbq[1], tq), 1), pl);
-            PB[it] = expphase_part<P, D, K>(a, tA, pt);
+            PB[pA * PCB + tq * Q + tl] = expphase_part<P, D, K>(a, tA, pt);
         }
         __syncthreads();
         if constexpr (PM == PM_BUILD) {   // build: store the factors; no weights are touched
@@ -366,7 +389,7 @@ struct TileMR {
                 const int beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
                 const int base = block_base(beta, i);
                 const C *Wr = W + (r0 + rbl) * WS + tau * n * RR;
-                const C *ph = PA + (pA * 2 + chi) * 2 * RR + tq * Q;
+                const C *ph = PA + (pA * 2 + chi) * PCA + tq * Q;
                 C acc[Q];
 #pragma unroll
                 for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
@@ -381,7 +404,7 @@ struct TileMR {
                         for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], ms.M[c & 1][t0][t0p], u);
                     }
                 }
-                C *so = S + rbl * 2 * WS + ((pA * 2 + chi) * Q + tq) * Q;
+                C *so = S + rbl * SW + ((pA * 2 + chi) * Q + tq) * Q;
 #pragma unroll
                 for (int j = 0; j < Q; ++j) so[j] = acc[j];
             }
@@ -396,7 +419,7 @@ struct TileMR {
                 for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
 #pragma unroll
                 for (int chi = 0; chi < 2; ++chi) {
-                    const C *si = S + rbl * 2 * WS + ((pA * 2 + chi) * Q) * Q + tl;
+                    const C *si = S + rbl * SW + ((pA * 2 + chi) * Q) * Q + tl;
 #pragma unroll
                     for (int tqp = 0; tqp < Q; ++tqp) {
                         const C v = si[tqp * Q];
@@ -405,7 +428,7 @@ struct TileMR {
                     }
                 }
                 C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + tl;
-                const C *ph = PB + pA * RR + tl;
+                const C *ph = PB + pA * PCB + tl;
 #pragma unroll
                 for (int tq = 0; tq < Q; ++tq) wo[tq * Q] = cjmul(ph[tq * Q], acc[tq]);
             }
@@ -503,8 +526,10 @@ struct TileMR {
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
         if constexpr (PM == PM_TABLE) PC = ts_acquire(ts);
-        C *PA = PC;              // [pin][th][t0]     pre-modulation at the parent's nodes
-        C *PB = PC + nout * RR;  // [pA][c][s1][s0]   post-modulation at the child's nodes
+        const int SW = (int)mr_s_stride(Q, x.npr);
+        constexpr int PRB = 4 * RR + (PM == PM_COMPUTE ? PAD.rb : 0), SU = 2 * Q + PAD.rs;
+        C *PA = PC;              // [pin][th][t0]                       pre-modulation at the parent's nodes
+        C *PB = PC + nout * RR;  // [pA] blocks of PRB: [c][s1][s0]     post-modulation at the child's nodes
         for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
             const int t0 = it % Q, th = (it / Q) % Q, pin = it / RR;
             const int c = pin & (NC - 1), beta = (pin >> D) & (nblk - 1), tau = pin >> (D * k);
@@ -541,8 +566,8 @@ struct TileMR {
             for (int c1 = 0; c1 < 2; ++c1) {
                 const typename P::SE e1 = sget<P, Q>(a, 1, l, 2 * cbq[1] + c1, Q);
                 expphase_part2<P, D, K>(a, tS2, PH2::add(q0, PH2::part(tS2, e1, e1, 1)),
-                                        PB[((pA * NC + 2 * c1) * Q + s1) * Q + s0],
-                                        PB[((pA * NC + 2 * c1 + 1) * Q + s1) * Q + s0]);
+                                        PB[pA * PRB + ((2 * c1) * Q + s1) * Q + s0],
+                                        PB[pA * PRB + ((2 * c1 + 1) * Q + s1) * Q + s0]);
             }
         }
         __syncthreads();
@@ -575,7 +600,7 @@ struct TileMR {
                         cfma(z[1][s0], ms.M[1][t0][s0], u);
                     }
                 }
-                C *so = S + rbl * 2 * WS + (pin * Q + th) * 2 * Q;
+                C *so = S + rbl * SW + (pin * Q + th) * SU;
 #pragma unroll
                 for (int s0 = 0; s0 < Q; ++s0) {
                     so[s0] = z[0][s0];
@@ -589,22 +614,22 @@ struct TileMR {
                 const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
                 const int base = block_base(beta, i);
                 const int a0 = alpha & 1, a1 = alpha >> 1;
-                const C *Sblk = S + rbl * 2 * WS + (pA - alpha) * Q * 2 * Q;
+                const C *Sblk = S + rbl * SW + (pA - alpha) * Q * SU;
                 C v[NC][Q];
 #pragma unroll
                 for (int c = 0; c < NC; ++c) {
-                    const C *si = Sblk + c * Q * 2 * Q + a0 * Q + s0;
+                    const C *si = Sblk + c * Q * SU + a0 * Q + s0;
 #pragma unroll
                     for (int s1 = 0; s1 < Q; ++s1) v[c][s1] = czero<C>();
 #pragma unroll
                     for (int t1 = 0; t1 < Q; ++t1) {
-                        const C zz = si[t1 * 2 * Q];
+                        const C zz = si[t1 * SU];
 #pragma unroll
                         for (int s1 = 0; s1 < Q; ++s1) cfma(v[c][s1], ms.M[a1][t1][s1], zz);
                     }
                 }
                 C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
-                const C *ph = PB + pA * NC * RR + s0;
+                const C *ph = PB + pA * PRB + s0;
 #pragma unroll
                 for (int s1 = 0; s1 < Q; ++s1) {
                     C acc = czero<C>();
@@ -676,7 +701,8 @@ struct TileMR {
     // shared memory of one CTA, bytes
     static __host__ __device__ size_t smem_bytes(int npr, int nr, int rc)
     {
-        return (size_t)npr * RR * sizeof(C) * (size_t)(nr + 2 * rc + 5);
+        return sizeof(C) * ((size_t)npr * RR * (size_t)(nr + 5) + (size_t)rc * (size_t)mr_s_stride(Q, npr) +
+                            (size_t)npr * mr_pc_extra(Q));
     }
 
     static __device__ __forceinline__ Ctx ctx(const KArgs<P> &a, int cta)
@@ -704,7 +730,7 @@ __device__ __forceinline__ void col_pass_mr(const KArgs<P> &a, const MS &ms, con
     const int WS = x.npr * TM::RR;
     C *W = reinterpret_cast<C *>(sm);
     C *S = W + x.nr * WS;
-    C *PC = S + x.rc * 2 * WS;
+    C *PC = S + x.rc * mr_s_stride(Q, x.npr);
     if (a.flags & F_INIT) {
         TM::template init<PM>(a, x, W, PC, g, ts);
     } else if (PM != PM_BUILD) {
@@ -725,7 +751,7 @@ __device__ __forceinline__ void row_pass_mr(const KArgs<P> &a, const MS &ms, con
     const int WS = x.npr * TM::RR;
     C *W = reinterpret_cast<C *>(sm);
     C *S = W + x.nr * WS;
-    C *PC = S + x.rc * 2 * WS;
+    C *PC = S + x.rc * mr_s_stride(Q, x.npr);
     if (PM != PM_BUILD) {
         TM::load(a, x, W);
         __syncthreads();
