@@ -153,17 +153,19 @@ def phase_ops(phase: str, d: int, q: int) -> float:
     """FP32-pipe operations of one e^{2 pi i Phi} in the mixed path, counted from the
     double-float formulas with the per-dimension split of Phi: the part of source
     coordinate 0 (evaluated per phase), the parts of coordinates >= 1 (shared by the q
-    phases of a node row), the two-sum that adds parts, the final sqrt / mod-1 step,
-    and 22 for the quadrant-reduced sincos (setup 5, sin 5, cos 5, quadrant 7)."""
-    sincos, add = 22, 9
+    phases of a node row), the sum of parts (an ordered fast two-sum where the parts are
+    non-negative), the final sqrt / mod-1 step, and 22 for the quadrant-reduced sincos
+    (setup 5, sin 5, cos 5, quadrant 7).  The frac of a double-float product costs 5
+    (two FMAs for the nearest integer and the remainder, two for the cross terms)."""
+    sincos = 22
     if phase == "dot":
-        part, fin = 8, 0
+        part, add, fin = 5, 1, 0
     elif phase == "genradon":
-        part, fin = 12, 12
+        part, add, fin = 9, 8, 12
     elif phase == "hypradon":
-        part, fin = 4, 15
+        part, add, fin = 4, 8, 12
     else:
-        part, fin = 11, 4
+        part, add, fin = 11, 9, 4
     return part + (d - 1) * part / q + add + fin + sincos
 
 

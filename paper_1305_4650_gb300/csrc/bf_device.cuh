@@ -108,11 +108,16 @@ __device__ __forceinline__ df df_sqrt_u(df x)
 // x - nearest integer (|x| < 2^22), one float in about [-0.5, 0.5]
 __device__ __forceinline__ float df_frac(df x) { return __fadd_rn(__fsub_rn(x.hi, fround(x.hi)), x.lo); }
 
-// frac of a product x*y with both factors double-float (the product itself may be large)
+// frac of a product x*y with both factors double-float, |x y| < 2^22: one FMA against
+// 1.5 * 2^23 gives the integer n nearest to x.hi*y.hi, a second FMA the remainder
+// x.hi*y.hi - n (|.| <= 1/2, one rounding), and two more add the cross terms (the
+// x.lo*y.lo term is below FP32 resolution); the result lies in (-1, 1)
 __device__ __forceinline__ float df_mul_frac(df x, df y)
 {
-    df p = df_mul_u(x, y);
-    return __fadd_rn(__fsub_rn(p.hi, fround(p.hi)), p.lo);
+    const float M = 12582912.0f;
+    const float n = __fsub_rn(__fmaf_rn(x.hi, y.hi, M), M);
+    const float f = __fmaf_rn(x.hi, y.hi, -n);
+    return __fmaf_rn(x.hi, y.lo, __fmaf_rn(x.lo, y.hi, f));
 }
 
 // ------------------------------------------------------- precision traits
@@ -356,7 +361,14 @@ struct Ph<PMIXT<F>, D, K> {
     }
     static __device__ __forceinline__ Part add(const Part &u, const Part &v)
     {
-        const df s = two_sum(u.q.hi, v.q.hi);
+        df s;
+        if constexpr (K == KIND_GENRADON || K == KIND_HYPRADON) {
+            // both parts are sums of squares times non-negative factors: with the larger one
+            // first the fast two-sum is exact (the same s and error term as the two-sum)
+            s = fast_two_sum(fmaxf(u.q.hi, v.q.hi), fminf(u.q.hi, v.q.hi));
+        } else {
+            s = two_sum(u.q.hi, v.q.hi);
+        }
         return Part{u.f + v.f, {s.hi, __fadd_rn(__fadd_rn(u.q.lo, v.q.lo), s.lo)}};
     }
     static __device__ __forceinline__ float fin(const KArgs<PMIXT<F>> &a, const T &t, const Part &p)
@@ -390,7 +402,7 @@ struct Ph<PMIXT<F>, D, K> {
 #pragma unroll
             for (int k = 1; k < D; ++k) {
                 df pk = df_mul_u(t.A[k], s.y2[k]);
-                df sk = two_sum(hi, pk.hi);
+                df sk = fast_two_sum(fmaxf(hi, pk.hi), fminf(hi, pk.hi));   // both non-negative
                 hi = sk.hi;
                 lo = __fadd_rn(lo, __fadd_rn(pk.lo, sk.lo));
             }

@@ -82,8 +82,10 @@ __device__ __forceinline__ float2 df_frac2(const df2 &x) { return add2(sub2(x.hi
 
 __device__ __forceinline__ float2 df_mul_frac2(const df2 &x, const df2 &y)
 {
-    const df2 p = df_mul_u2(x, y);
-    return add2(sub2(p.hi, fround2(p.hi)), p.lo);
+    const float2 M = dup2(12582912.0f);
+    const float2 n = sub2(fma2(x.hi, y.hi, M), M);
+    const float2 f = fma2(x.hi, y.hi, neg2(n));
+    return fma2(x.hi, y.lo, fma2(x.lo, y.hi, f));
 }
 
 // the polynomial sincos of bf_device.cuh on both lanes
@@ -164,7 +166,12 @@ struct Ph2<PMIXT<F>, D, K> {
     }
     static __device__ __forceinline__ Part add(const Part &u, const Part &v)
     {
-        const df2 s = two_sum2(u.q.hi, v.q.hi);
+        df2 s;
+        if constexpr (K == KIND_GENRADON || K == KIND_HYPRADON)   // non-negative parts, larger first
+            s = fast_two_sum2(make_float2(fmaxf(u.q.hi.x, v.q.hi.x), fmaxf(u.q.hi.y, v.q.hi.y)),
+                              make_float2(fminf(u.q.hi.x, v.q.hi.x), fminf(u.q.hi.y, v.q.hi.y)));
+        else
+            s = two_sum2(u.q.hi, v.q.hi);
         return Part{add2(u.f, v.f), {s.hi, add2(add2(u.q.lo, v.q.lo), s.lo)}};
     }
     static __device__ __forceinline__ float2 fin(const KArgs<PMIXT<F>> &a, const T &t, const Part &p)
