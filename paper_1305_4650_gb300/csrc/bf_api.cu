@@ -224,9 +224,13 @@ size_t row_cache_smem(const bf_plan_s *p, const Pass &ps)
     return (size_t)ps.T * ((size_t)1 << (p->d * (ps.k - 1))) * (size_t)p->r * (size_t)p->fns->tsize;
 }
 
-// the adjoint row pass caches children's and parents' node features (T (2^{dk} + 2^{d(k-1)}) boxes x r)
+// the adjoint row pass caches children's and parents' node features (T (2^{dk} + 2^{d(k-1)}) boxes x r);
+// the adjoint column pass with the (unfactorised, d = 2) switch caches the features of every
+// (pair, node) of its tiles (T 2^{dk} pairs x r)
 size_t row_adj_cache_smem(const bf_plan_s *p, const Pass &ps)
 {
+    if (!ps.row && (ps.flags & bfk::F_SWITCH) && p->d == 2 && p->kind != BF_PHASE_DOT && p->kind != BF_PHASE_SEPARABLE)
+        return (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (size_t)p->r * (size_t)p->fns->tsize;
     if (!ps.row || ps.k < 1) return 0;
     return (size_t)ps.T * (((size_t)1 << (p->d * ps.k)) + ((size_t)1 << (p->d * (ps.k - 1)))) * (size_t)p->r *
            (size_t)p->fns->tsize;

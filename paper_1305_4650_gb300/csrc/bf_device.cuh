@@ -1376,14 +1376,46 @@ struct Tile {
             C z[2][Q];
 #pragma unroll
             for (int s0 = 0; s0 < Q; ++s0) { z[0][s0] = czero<C>(); z[1][s0] = czero<C>(); }
+            if constexpr (!P::is_f64) {
+                // phases two at a time: lanes t_0 and t_0 + 1 (the last one alone for odd q)
+                using PH2 = Ph2<P, D, K>;
+                const typename PH2::T tA2 = PH2::dup(tA);
+                const typename PH2::Part hp2 = PH2::dup(hp);
 #pragma unroll
-            for (int t0 = 0; t0 < Q; ++t0) {
-                const C e = expphase_part<P, D, K>(a, tA, PH::add(PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], t0), 0), hp));
-                const C u = cmul(e, wi[t0]);
+                for (int t0 = 0; t0 + 1 < Q; t0 += 2) {
+                    float2 E0, E1;
+                    expphase_part2<P, D, K>(a, tA2,
+                                            PH2::add(PH2::part(tA2, sget<P, Q>(a, 0, l + 1, cbq[0], t0),
+                                                               sget<P, Q>(a, 0, l + 1, cbq[0], t0 + 1), 0), hp2),
+                                            E0, E1);
+                    const C u0 = cmul(E0, wi[t0]), u1 = cmul(E1, wi[t0 + 1]);
 #pragma unroll
-                for (int s0 = 0; s0 < Q; ++s0) {
-                    cfma2(z[0][s0], a.M2[0][t0][s0], u);
-                    cfma2(z[1][s0], a.M2[1][t0][s0], u);
+                    for (int s0 = 0; s0 < Q; ++s0) {
+                        cfma2(z[0][s0], a.M2[0][t0][s0], u0);
+                        cfma2(z[1][s0], a.M2[1][t0][s0], u0);
+                        cfma2(z[0][s0], a.M2[0][t0 + 1][s0], u1);
+                        cfma2(z[1][s0], a.M2[1][t0 + 1][s0], u1);
+                    }
+                }
+                if constexpr (Q & 1) {
+                    const C e = expphase_part<P, D, K>(a, tA, PH::add(PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], Q - 1), 0), hp));
+                    const C u = cmul(e, wi[Q - 1]);
+#pragma unroll
+                    for (int s0 = 0; s0 < Q; ++s0) {
+                        cfma2(z[0][s0], a.M2[0][Q - 1][s0], u);
+                        cfma2(z[1][s0], a.M2[1][Q - 1][s0], u);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int t0 = 0; t0 < Q; ++t0) {
+                    const C e = expphase_part<P, D, K>(a, tA, PH::add(PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], t0), 0), hp));
+                    const C u = cmul(e, wi[t0]);
+#pragma unroll
+                    for (int s0 = 0; s0 < Q; ++s0) {
+                        cfma2(z[0][s0], a.M2[0][t0][s0], u);
+                        cfma2(z[1][s0], a.M2[1][t0][s0], u);
+                    }
                 }
             }
             C *so = S + (((tau * nblk + beta) * NC + alpha) * QD1 + th) * 2 * Q;
@@ -1429,10 +1461,31 @@ struct Tile {
 #pragma unroll
                         for (int s1 = 0; s1 < Q; ++s1) cfma2(v[s1], a.M2[c1][t1][s1], zz);
                     }
+                    if constexpr (!P::is_f64) {
+                        // phases two at a time: lanes s_1 and s_1 + 1 (the last one alone for odd q)
+                        using PH2 = Ph2<P, D, K>;
+                        const typename PH2::T tA2 = PH2::dup(tA);
+                        const typename PH2::Part p02 = PH2::dup(p0);
 #pragma unroll
-                    for (int s1 = 0; s1 < Q; ++s1) {
-                        const C e = expphase_part<P, D, K>(a, tA, PH::add(p0, PH::part(tA, sget<P, Q>(a, 1, l, cb[1], s1), 1)));
-                        acc[s1] = cadd(acc[s1], cjmul(e, v[s1]));
+                        for (int s1 = 0; s1 + 1 < Q; s1 += 2) {
+                            float2 E0, E1;
+                            expphase_part2<P, D, K>(a, tA2,
+                                                    PH2::add(p02, PH2::part(tA2, sget<P, Q>(a, 1, l, cb[1], s1),
+                                                                            sget<P, Q>(a, 1, l, cb[1], s1 + 1), 1)),
+                                                    E0, E1);
+                            acc[s1] = cadd(acc[s1], cjmul(E0, v[s1]));
+                            acc[s1 + 1] = cadd(acc[s1 + 1], cjmul(E1, v[s1 + 1]));
+                        }
+                        if constexpr (Q & 1) {
+                            const C e = expphase_part<P, D, K>(a, tA, PH::add(p0, PH::part(tA, sget<P, Q>(a, 1, l, cb[1], Q - 1), 1)));
+                            acc[Q - 1] = cadd(acc[Q - 1], cjmul(e, v[Q - 1]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int s1 = 0; s1 < Q; ++s1) {
+                            const C e = expphase_part<P, D, K>(a, tA, PH::add(p0, PH::part(tA, sget<P, Q>(a, 1, l, cb[1], s1), 1)));
+                            acc[s1] = cadd(acc[s1], cjmul(e, v[s1]));
+                        }
                     }
                 } else {
                     const int c1 = (c >> 1) & 1, c2 = (c >> 2) & 1;
@@ -1601,11 +1654,26 @@ struct Tile {
     }
 
     // ---- adjoint of the switch at level l: u(t) = sum_s e^{-2pi i Phi(x_s^A, y_t^B)} v(s);
-    // items (tau, slot, t_{>=1}), the q values of t_0 accumulated together
-    static __device__ void switch_adj(const KArgs<P> &a, C *Wt, C *S, int l)
+    // items (tau, slot, t_{>=1}), the q values of t_0 accumulated together.  For d = 2 the
+    // target features of every (pair, s) are computed once into TC (the q^{d-1} items of a
+    // pair share them); the mixed precision evaluates the phases of t_0, t_0 + 1 in pairs.
+    static __device__ void switch_adj(const KArgs<P> &a, C *Wt, C *S, typename PH::T *TC, int l)
     {
         const int k = a.k, n = 1 << (D * k);
         const int L = a.L;
+        if constexpr (D == 2) {
+            for (int j = threadIdx.x; j < a.T * n * RR; j += blockDim.x) {
+                const int s = j % RR, pr = j / RR;
+                const int sl = pr & (n - 1), tau = pr >> (D * k);
+                uint32_t Ap, Bstar;
+                tile_of(a, tau, Ap, Bstar);
+                int ca[DMAX];
+                morton_decode<D>((Ap << (D * k)) + digit_rev<D>(sl, k), l, ca);
+                const int sk[DMAX] = {s % Q, s / Q, 0};
+                TC[j] = tpoint<P, D, Q, K>(a, l, ca, sk);
+            }
+            __syncthreads();
+        }
         for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
             const int th = it % QD1;
             const int sl = (it / QD1) & (n - 1);
@@ -1630,18 +1698,47 @@ struct Tile {
 #pragma unroll
             for (int t0 = 0; t0 < Q; ++t0) acc[t0] = czero<C>();
             const C *v = Wt + (tau * n + sl) * RR;
+            const typename PH::T *tc = TC + (tau * n + sl) * RR;
+            // d = 2: q targets per iteration of the outer loop (more independent work per iteration)
+            constexpr int SI = D == 2 ? Q : 1;
 #pragma unroll 1
-            for (int s = 0; s < RR; ++s) {
-                int sk[DMAX], ss = s;
+            for (int s1 = 0; s1 < RR; s1 += SI)
 #pragma unroll
-                for (int j = 0; j < D; ++j) { sk[j] = ss % Q; ss /= Q; }
-                const typename PH::T tS = tpoint<P, D, Q, K>(a, l, ca, sk);
-                typename PH::Part hp = PH::part(tS, eh[1], 1);
-                if constexpr (D == 3) hp = PH::add(hp, PH::part(tS, eh[2], 2));
+            for (int s0 = 0; s0 < SI; ++s0) {
+                const int s = s1 + s0;
+                typename PH::T tS;
+                if constexpr (D == 2) {
+                    tS = tc[s];
+                } else {
+                    int sk[DMAX], ss = s;
+#pragma unroll
+                    for (int j = 0; j < D; ++j) { sk[j] = ss % Q; ss /= Q; }
+                    tS = tpoint<P, D, Q, K>(a, l, ca, sk);
+                }
                 const C vs = v[s];
+                if constexpr (!P::is_f64) {
+                    using PH2 = Ph2<P, D, K>;
+                    const typename PH2::T tS2 = PH2::dup(tS);
+                    typename PH2::Part hp = PH2::part(tS2, eh[1], eh[1], 1);
+                    if constexpr (D == 3) hp = PH2::add(hp, PH2::part(tS2, eh[2], eh[2], 2));
 #pragma unroll
-                for (int t0 = 0; t0 < Q; ++t0)
-                    acc[t0] = cadd(acc[t0], cjmul(expphase_part<P, D, K>(a, tS, PH::add(PH::part(tS, e0[t0], 0), hp)), vs));
+                    for (int t0 = 0; t0 + 1 < Q; t0 += 2) {
+                        float2 E0, E1;
+                        expphase_part2<P, D, K>(a, tS2, PH2::add(PH2::part(tS2, e0[t0], e0[t0 + 1], 0), hp), E0, E1);
+                        acc[t0] = cadd(acc[t0], cjmul(E0, vs));
+                        acc[t0 + 1] = cadd(acc[t0 + 1], cjmul(E1, vs));
+                    }
+                    if constexpr (Q & 1)
+                        acc[Q - 1] = cadd(acc[Q - 1], cjmul(expphase_part<P, D, K>(
+                                                                a, tS, PH::add(PH::part(tS, e0[Q - 1], 0), PH2::lane0(hp))),
+                                                            vs));
+                } else {
+                    typename PH::Part hp = PH::part(tS, eh[1], 1);
+                    if constexpr (D == 3) hp = PH::add(hp, PH::part(tS, eh[2], 2));
+#pragma unroll
+                    for (int t0 = 0; t0 < Q; ++t0)
+                        acc[t0] = cadd(acc[t0], cjmul(expphase_part<P, D, K>(a, tS, PH::add(PH::part(tS, e0[t0], 0), hp)), vs));
+                }
             }
             C *w = S + (tau * n + sl) * RR + th * Q;
 #pragma unroll
@@ -1695,8 +1792,24 @@ struct Tile {
         const int cY[DMAX] = {0, 0, 0};
         const int ctr[DMAX] = {Q, Q, Q};
         const typename PH::S sY = spoint<P, D, Q, K>(a, L, cY, ctr);
-        for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) {
-            const int t = it % RR, sl = (it / RR) & (n - 1), tau = (it / RR) >> (D * k);
+        // the nodes whose Lagrange value at the target point is non-zero (the same in every
+        // leaf box); the other weights are zero
+        __shared__ int nzt[RR];
+        __shared__ int nnz;
+        if (threadIdx.x == 0) {
+            int c = 0;
+            for (int t = 0; t < RR; ++t) {
+                R lag = R(1);
+                for (int j = 0, tt = t; j < D; ++j, tt /= Q) lag *= a.ltgt[tt % Q];
+                if (lag != R(0)) nzt[c++] = t;
+            }
+            nnz = c;
+        }
+        for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) Wt[it] = czero<C>();
+        __syncthreads();
+        for (int it = threadIdx.x; it < a.T * n * nnz; it += blockDim.x) {
+            const int pr = it / nnz, t = nzt[it - pr * nnz];
+            const int sl = pr & (n - 1), tau = pr >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const uint32_t A = (Ap << (D * k)) + digit_rev<D>(sl, k);
@@ -1706,20 +1819,18 @@ struct Tile {
             int tk[DMAX], tt = t;
 #pragma unroll
             for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.ltgt[tk[j]]; }
-            C out = czero<C>();
-            if (lag != R(0)) {
-                int64_t flat = 0;
+            int64_t flat = 0;
 #pragma unroll
-                for (int j = 0; j < D; ++j) flat = (flat << L) + ca[j];
-                const C fv = a.fadj[(int64_t)rhs * a.npts + flat];
-                const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
-                const C ex = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, pslot), sY);
-                const C et = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, tk), sY);
-                const C v = cmul(et, cjmul(ex, fv));
-                out.x = lag * v.x;
-                out.y = lag * v.y;
-            }
-            Wt[it] = out;
+            for (int j = 0; j < D; ++j) flat = (flat << L) + ca[j];
+            const C fv = a.fadj[(int64_t)rhs * a.npts + flat];
+            const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
+            const C ex = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, pslot), sY);
+            const C et = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, L, ca, tk), sY);
+            const C v = cmul(et, cjmul(ex, fv));
+            C out;
+            out.x = lag * v.x;
+            out.y = lag * v.y;
+            Wt[pr * RR + t] = out;
         }
     }
 
@@ -1827,6 +1938,7 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pa
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *Wt = reinterpret_cast<C *>(smem_raw);
     C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
+    typename TL::PH::T *TC = reinterpret_cast<typename TL::PH::T *>(S + 2 * a.T * (1 << (D * a.k)) * TL::RR);
     const int rhs = blockIdx.y;
     TL::load_strided(a, Wt, rhs);
     __syncthreads();
@@ -1834,7 +1946,7 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pa
         if constexpr (K == KIND_DOT || K == KIND_SEPARABLE)
             TL::template switch_sep<true>(a, Wt, S, a.l0 + a.k);
         else
-            TL::switch_adj(a, Wt, S, a.l0 + a.k);
+            TL::switch_adj(a, Wt, S, TC, a.l0 + a.k);
     }
     for (int i = a.k - 1; i >= 0; --i) TL::col_level_adj(a, Wt, S, a.l0 + i, i);
     if (a.flags & F_INIT)
