@@ -47,6 +47,8 @@ struct bf_plan_s {
     int64_t ptab_bytes = 0;
     std::vector<int64_t> ptab_off, ptab_cta;   // per pass: offset and per-CTA size, complex numbers
     float ptab_build_ms = 0.f;
+    float *ftab = nullptr;         // reduced-phase table of the single-RHS schedule (plans with max_nrhs = 1)
+    std::vector<int64_t> ftab_off, ftab_cta;   // per pass: offset and per-CTA size, floats
     // arbitrary point sets (bf_plan_create_points): per-point data and the forward passes
     // without init and final, which the point kernels replace
     int points = 0;
@@ -390,6 +392,8 @@ bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t 
     a.g = static_cast<const typename P::C *>(g);
     a.f = static_cast<typename P::C *>(f);
     void *buf[2] = {p->w0, p->w1};
+    const bool tab = p->ftab && nrhs == 1;   // read the phases from the plan's table
+    a.err = p->errflag;
     for (int i = first; i < last; ++i) {
         const Pass &ps = p->passes[i];
         a.l0 = ps.l0;
@@ -398,9 +402,12 @@ bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t 
         a.T = ps.T;
         a.win = static_cast<const typename P::C *>(buf[i & 1]);
         a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
+        a.ftab = tab ? p->ftab + p->ftab_off[i] : nullptr;
+        a.ftab_cta = tab ? p->ftab_cta[i] : 0;
         const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
         const size_t smem = pass_smem(p, ps) + row_cache_smem(p, ps);
-        cudaError_t e = (ps.row ? p->fns->row : p->fns->col)(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
+        const bfl::pass_fn fn = tab ? (ps.row ? p->fns->row_tab : p->fns->col_tab)[1] : (ps.row ? p->fns->row : p->fns->col);
+        cudaError_t e = fn(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
         if (e != cudaSuccess) return cuda_fail(p, e);
     }
     return BF_OK;
@@ -725,6 +732,74 @@ bf_status build_phase_table(bf_plan p)
     return BF_OK;
 }
 
+// Reduced-phase table of the single-RHS schedule: the build passes run the evaluating
+// kernels on zero input and record, per CTA and stage, the reduced phase of every factor
+// (floats, [phase of an item][item]); the apply reads them instead of evaluating Phi.
+// The switch of the factorised kinds keeps evaluating (d q^2 phases per pair).
+template <class P>
+bf_status build_tile_table(bf_plan p)
+{
+    const int64_t r = p->r;
+    const bool tab_switch = p->kind != BF_PHASE_DOT && p->kind != BF_PHASE_SEPARABLE;
+    int64_t total = 0;
+    p->ftab_off.clear();
+    p->ftab_cta.clear();
+    for (const Pass &ps : p->passes) {
+        const int64_t npr = (int64_t)ps.T << (p->d * ps.k), ctas = (p->npts >> (p->d * ps.k)) / ps.T;
+        int64_t per = ps.k * 5 * r * npr;
+        if (!ps.row && (ps.flags & bfk::F_SWITCH) && tab_switch) per += r * r * npr;
+        p->ftab_off.push_back(total);
+        p->ftab_cta.push_back(per);
+        total += per * ctas;
+    }
+    p->ptab_bytes = total * (int64_t)sizeof(float);
+    cudaError_t e = cudaMalloc(&p->ftab, (size_t)p->ptab_bytes);
+    if (e != cudaSuccess) {
+        p->ftab = nullptr;
+        return cuda_fail(p, e);
+    }
+    void *gz = nullptr, *fz = nullptr;
+    const size_t vbytes = (size_t)p->npts * p->csize;
+    e = cudaMalloc(&gz, vbytes);
+    if (e == cudaSuccess) e = cudaMalloc(&fz, vbytes);
+    if (e == cudaSuccess) e = cudaMemset(gz, 0, vbytes);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaEventRecord(e0);
+    bfk::KArgs<P> a;
+    fill_args<P>(p, a);
+    a.g = static_cast<const typename P::C *>(gz);
+    a.f = static_cast<typename P::C *>(fz);
+    a.err = p->errflag;
+    void *buf[2] = {p->w0, p->w1};
+    for (size_t i = 0; i < p->passes.size() && e == cudaSuccess; ++i) {
+        const Pass &ps = p->passes[i];
+        a.l0 = ps.l0;
+        a.k = ps.k;
+        a.flags = ps.flags;
+        a.T = ps.T;
+        a.win = static_cast<const typename P::C *>(buf[i & 1]);
+        a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
+        a.ftab = p->ftab + p->ftab_off[i];
+        a.ftab_cta = p->ftab_cta[i];
+        const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
+        const size_t smem = pass_smem(p, ps) + row_cache_smem(p, ps);
+        e = (ps.row ? p->fns->row_tab : p->fns->col_tab)[0](&a, (unsigned)ctas, 1u, smem, 0);
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+    p->ptab_build_ms = ms;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (gz) cudaFree(gz);
+    if (fz) cudaFree(fz);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    return BF_OK;
+}
+
 const std::vector<Pass> &schedule_for(const bf_plan_s *p, int nrhs) { return use_mr(p, nrhs) ? p->passes_mr : p->passes; }
 
 bool supported_q(int d, int q) { return bfl::get_fns(d, q, 1, 0) != nullptr && bfl::get_fns(d, q, 0, 0) != nullptr; }
@@ -1039,11 +1114,16 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         else
             p->ctab_levels = lv;
     }
+    // phase tables: the single-RHS schedule's reduced phases for plans of one right-hand side,
+    // the multi-RHS schedule's factors otherwise
+    const bool tile_table = prm->phase_tables && p->max_nrhs == 1 && p->fns->col_tab[0];
     if (st == BF_OK && prm->phase_tables) {
         cudaError_t e = cudaMalloc(&p->errflag, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->errflag, 0, sizeof(int));
         if (e != cudaSuccess)
             st = cuda_fail(p, e);
+        else if (tile_table)
+            ;   // built below, once the weight buffers exist
         else if (p->passes_mr.empty())
             st = BF_ERR_UNSUPPORTED;
         else
@@ -1054,6 +1134,8 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         cudaError_t e = cudaMalloc(&p->w0, wbytes);
         if (e == cudaSuccess) e = cudaMalloc(&p->w1, wbytes);
         if (e != cudaSuccess) st = cuda_fail(p, e);
+        if (st == BF_OK && tile_table)
+            st = p->prec == BF_PREC_MIXED_SFU ? build_tile_table<bfk::PMIXF>(p) : build_tile_table<bfk::PMIX>(p);
         p->ws_bytes = (int64_t)(2 * wbytes) + p->ptab_bytes;
     }
     if (st != BF_OK) {
@@ -1152,8 +1234,8 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
         return BF_OK;
     };
     double best = 1e300;
-    if (st == BF_OK && p->ptab) {
-        st = time_it(best);          // the phase table fixes the multi-RHS schedule
+    if (st == BF_OK && (p->ptab || p->ftab)) {
+        st = time_it(best);          // the phase table fixes the schedule
     } else if (st == BF_OK && use_mr(p, nrhs)) {
         // multi-RHS tiles: fused levels, pairs per CTA, right-hand sides per scratch chunk
         const int nr = nrhs < p->fns->mr_max ? nrhs : p->fns->mr_max;
@@ -1415,6 +1497,7 @@ bf_status bf_destroy(bf_plan p)
     if (p->w1) cudaFree(p->w1);
     if (p->ctab) cudaFree(p->ctab);
     if (p->ptab) cudaFree(p->ptab);
+    if (p->ftab) cudaFree(p->ftab);
     if (p->errflag) cudaFree(p->errflag);
     for (void *m : p->pts_mem) cudaFree(m);
     if (p->gstage) cudaFree(p->gstage);

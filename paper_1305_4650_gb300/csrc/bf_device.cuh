@@ -39,6 +39,10 @@ constexpr int DMAX = 3;
 enum { KIND_DOT = 0, KIND_GENRADON = 1, KIND_HYPRADON = 2, KIND_SEPARABLE = 3 };
 enum { F_INIT = 1, F_SWITCH = 2, F_FINAL = 4 };
 
+// Where a kernel's phase factors come from: evaluated (PM_COMPUTE), evaluated and recorded
+// in the plan's phase table (PM_BUILD, at plan creation), or read from it (PM_TABLE)
+enum { PM_COMPUTE = 0, PM_BUILD = 1, PM_TABLE = 2 };
+
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
 // ------------------------------------------------------------ double-float
@@ -236,7 +240,9 @@ struct KArgs {
     int ctab_levels;
     C *ptab;                          // phase table of the pass (multi-RHS passes with tables) or null
     int64_t ptab_cta;                 // phase-table complex numbers per CTA of the pass
-    int *err;                         // set by a bounded wait that gave up (or null)
+    int *err;                         // set by a bounded wait that gave up, or a table-size mismatch (or null)
+    float *ftab;                      // reduced-phase table of a single-RHS pass (PM_BUILD, PM_TABLE) or null
+    int64_t ftab_cta;                 // floats of that table per CTA
     int ncta;                         // CTAs (tile groups of T tiles) of the pass (multi-RHS kernels)
 };
 
@@ -638,6 +644,97 @@ struct Tile {
     static constexpr int RR = ipow(Q, D);
     static constexpr int QD1 = ipow(Q, D - 1);
 
+    // ---- reduced-phase table of a single-RHS pass (d = 2, mixed precisions).  The block of
+    // one stage is [phase j of an item][item], so one phase index over a warp's items is one
+    // coalesced access.  The table holds the reduced phase that the evaluating kernel feeds
+    // to its sincos, so reading it gives the evaluating kernel's results exactly.
+    struct FT {
+        float *p;   // the stage's block
+        int n;      // items of the stage
+        __device__ __forceinline__ float *at(int j, int it) const { return p + (int64_t)j * n + it; }
+    };
+    // items of the stages that evaluate phases, and phases per item
+    static __device__ __forceinline__ int n_col_a(const KArgs<P> &a) { return a.T * ((1 << (D * a.k)) >> D) * NC * 2 * Q; }
+    static __device__ __forceinline__ int n_col_b(const KArgs<P> &a) { return a.T * ((1 << (D * a.k)) >> D) * NC * QD1; }
+    static __device__ __forceinline__ int n_switch(const KArgs<P> &a) { return a.T * (1 << (D * a.k)) * QD1; }
+    static __device__ __forceinline__ int n_row_a(const KArgs<P> &a) { return a.T * ((1 << (D * a.k)) >> D) * NC * QD1; }
+    static __device__ __forceinline__ int n_row_b(const KArgs<P> &a) { return a.T * ((1 << (D * a.k)) >> D) * NC * Q; }
+    static constexpr int PH_COL_A = 2 * Q, PH_COL_B = Q, PH_SWITCH = Q * RR, PH_ROW_A = Q, PH_ROW_B = Q * NC;
+    // floats of the table one CTA of this pass reads (the phases of the switch of the
+    // factorised kinds are evaluated, not tabled)
+    static __device__ __forceinline__ int64_t table_floats(const KArgs<P> &a, bool row)
+    {
+        int64_t f = row ? (int64_t)n_row_a(a) * PH_ROW_A + (int64_t)n_row_b(a) * PH_ROW_B
+                        : (int64_t)n_col_a(a) * PH_COL_A + (int64_t)n_col_b(a) * PH_COL_B;
+        f *= a.k;
+        if (!row && (a.flags & F_SWITCH) && K != KIND_DOT && K != KIND_SEPARABLE) f += (int64_t)n_switch(a) * PH_SWITCH;
+        return f;
+    }
+    static __device__ __forceinline__ C cis(R fr)
+    {
+        R sn, cs;
+        if constexpr (P::sfu)
+            sincos2pi_sfu(fr, sn, cs);
+        else
+            sincos2pi(fr, sn, cs);
+        C e;
+        e.x = cs;
+        e.y = sn;
+        return e;
+    }
+    // one factor from its reduced phase (summed parts): evaluated, evaluated and recorded, or read
+    template <int PM>
+    static __device__ __forceinline__ C ph(const KArgs<P> &a, const typename PH::T &t, const typename PH::Part &pt, float *q)
+    {
+        R fr;
+        if constexpr (PM == PM_TABLE) {
+            fr = __ldcs(q);
+        } else {
+            fr = PH::fin(a, t, pt);
+            if constexpr (PM == PM_BUILD) __stcs(q, fr);
+        }
+        return cis(fr);
+    }
+    // the same from the whole source point
+    template <int PM>
+    static __device__ __forceinline__ C phs(const KArgs<P> &a, const typename PH::T &t, const typename PH::S &sv, float *q)
+    {
+        R fr;
+        if constexpr (PM == PM_TABLE) {
+            fr = __ldcs(q);
+        } else {
+            fr = PH::frac(a, t, sv);
+            if constexpr (PM == PM_BUILD) __stcs(q, fr);
+        }
+        return cis(fr);
+    }
+    // two factors in the lanes of a float2 (bf_pair.cuh); q1 null: lane 1 is not recorded or read
+    template <int PM, class T2, class Part2>
+    static __device__ __forceinline__ void ph2(const KArgs<P> &a, const T2 &t, const Part2 &pt, float *q0, float *q1,
+                                               float2 &e0, float2 &e1)
+    {
+        float2 fr;
+        if constexpr (PM == PM_TABLE) {
+            fr.x = __ldcs(q0);
+            fr.y = q1 ? __ldcs(q1) : 0.0f;
+        } else {
+            fr = Ph2<P, D, K>::fin(a, t, pt);
+            if constexpr (PM == PM_BUILD) {
+                __stcs(q0, fr.x);
+                if (q1) __stcs(q1, fr.y);
+            }
+        }
+        float2 sn, cs;
+        if constexpr (P::sfu) {
+            sincos2pi_sfu(fr.x, sn.x, cs.x);
+            sincos2pi_sfu(fr.y, sn.y, cs.y);
+        } else {
+            sincos2pi2(fr, sn, cs);
+        }
+        e0 = make_float2(cs.x, sn.x);
+        e1 = make_float2(cs.y, sn.y);
+    }
+
     static __device__ __forceinline__ float2 cadd(float2 x, float2 y) { return make_float2(x.x + y.x, x.y + y.y); }
     static __device__ __forceinline__ double2 cadd(double2 x, double2 y) { return make_double2(x.x + y.x, x.y + y.y); }
 
@@ -699,10 +796,16 @@ struct Tile {
     }
 
     // ---- one column-form merge level (l -> l+1) on all tiles of the CTA
-    static __device__ void col_level(const KArgs<P> &a, C *Wt, C *S, int l, int i)
+    template <int PM = PM_COMPUTE>
+    static __device__ void col_level(const KArgs<P> &a, C *Wt, C *S, int l, int i, float *&tb)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D;
         const int L = a.L;
+        FT fa{tb, n_col_a(a)}, fb{tb, n_col_b(a)};
+        if constexpr (PM != PM_COMPUTE) {
+            fb.p = tb + (int64_t)fa.n * PH_COL_A;
+            tb = fb.p + (int64_t)fb.n * PH_COL_B;
+        }
         // stage A: items (tau, block, alpha, c_{D-1}, t'_{D-1}): modulate and contract dims 0..D-2
         for (int it = threadIdx.x; it < a.T * nblk * NC * 2 * Q; it += blockDim.x) {
             const int tq = it % Q;
@@ -742,9 +845,9 @@ struct Tile {
 #pragma unroll
                     for (int t0p = 0; t0p + 1 < Q; t0p += 2) {
                         float2 E0, E1;
-                        expphase_part2<P, D, K>(a, tA2,
-                                                PH2::add(PH2::part(tA2, sget<P, Q>(a, 0, l, cb[0], t0p),
-                                                                   sget<P, Q>(a, 0, l, cb[0], t0p + 1), 0), p1), E0, E1);
+                        ph2<PM>(a, tA2,
+                                PH2::add(PH2::part(tA2, sget<P, Q>(a, 0, l, cb[0], t0p), sget<P, Q>(a, 0, l, cb[0], t0p + 1), 0), p1),
+                                fa.at(cl * Q + t0p, it), fa.at(cl * Q + t0p + 1, it), E0, E1);
                         const C u0 = cmul(E0, win[t0p + Q * tq]), u1 = cmul(E1, win[t0p + 1 + Q * tq]);
 #pragma unroll
                         for (int t0 = 0; t0 < Q; ++t0) {
@@ -754,7 +857,7 @@ struct Tile {
                     }
                     if constexpr (Q & 1) {
                         const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(p1));
-                        const C u = cmul(expphase_part<P, D, K>(a, tA, pt), win[Q - 1 + Q * tq]);
+                        const C u = cmul(ph<PM>(a, tA, pt, fa.at(cl * Q + Q - 1, it)), win[Q - 1 + Q * tq]);
 #pragma unroll
                         for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0], a.M2[c0][t0][Q - 1], u);
                     }
@@ -881,16 +984,16 @@ struct Tile {
 #pragma unroll
                 for (int tq = 0; tq + 1 < Q; tq += 2) {
                     float2 E0, E1;
-                    expphase_part2<P, D, K>(a, tA2,
-                                            PH2::add(PH2::part(tA2, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq),
-                                                               sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq + 1), D - 1), pl2),
-                                            E0, E1);
+                    ph2<PM>(a, tA2,
+                            PH2::add(PH2::part(tA2, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq),
+                                               sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], tq + 1), D - 1), pl2),
+                            fb.at(tq, it), fb.at(tq + 1, it), E0, E1);
                     wo[tq * QD1] = cjmul(E0, acc[tq]);
                     wo[(tq + 1) * QD1] = cjmul(E1, acc[tq + 1]);
                 }
                 if constexpr (Q & 1) {
                     const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, D - 1, l + 1, cbq[D - 1], Q - 1), D - 1), pl);
-                    wo[(Q - 1) * QD1] = cjmul(expphase_part<P, D, K>(a, tA, pt), acc[Q - 1]);
+                    wo[(Q - 1) * QD1] = cjmul(ph<PM>(a, tA, pt, fb.at(Q - 1, it)), acc[Q - 1]);
                 }
             } else {
 #pragma unroll
@@ -906,12 +1009,15 @@ struct Tile {
     // ---- switch at level l on every pair (slots in digit-reversed order); items (tau, slot, s_{>=1})
     // accumulate over t for the q values of s_0.  Results go through S so no item reads a
     // slot that another item has already rewritten.
-    static __device__ void switch_tiles(const KArgs<P> &a, C *Wt, C *S, int l)
+    template <int PM = PM_COMPUTE>
+    static __device__ void switch_tiles(const KArgs<P> &a, C *Wt, C *S, int l, float *&tb)
     {
         if constexpr (!P::is_f64 && K == KIND_GENRADON) {   // the phase whose pairs pay for their registers
-            switch_tiles_pair(a, Wt, S, l);
+            switch_tiles_pair<PM>(a, Wt, S, l, tb);
             return;
         }
+        const FT fs{tb, n_switch(a)};   // phase (th q + t_0) q + s_0 of an item
+        if constexpr (PM != PM_COMPUTE) tb += (int64_t)fs.n * PH_SWITCH;
         const int k = a.k, n = 1 << (D * k);
         const int L = a.L;
         for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
@@ -957,7 +1063,7 @@ struct Tile {
                     const C ut = u[t0 + Q * th];
 #pragma unroll
                     for (int s0 = 0; s0 < Q; ++s0)
-                        cmac(acc[s0], expphase_part<P, D, K>(a, tS[s0], PH::add(PH::part(tS[s0], e0, 0), hp[s0])), ut);
+                        cmac(acc[s0], ph<PM>(a, tS[s0], PH::add(PH::part(tS[s0], e0, 0), hp[s0]), fs.at((th * Q + t0) * Q + s0, it)), ut);
                 }
             }
             C *w = S + (tau * n + sl) * RR + sh * Q;
@@ -972,10 +1078,13 @@ struct Tile {
     // ---- the same switch with the phases evaluated two at a time (lanes of a float2):
     // targets s_0 = 2j and 2j + 1 share a pair; for odd q the last target takes two
     // consecutive t_0 in its lanes.  Each lane rounds exactly as the scalar code.
-    static __device__ void switch_tiles_pair(const KArgs<P> &a, C *Wt, C *S, int l)
+    template <int PM>
+    static __device__ void switch_tiles_pair(const KArgs<P> &a, C *Wt, C *S, int l, float *&tb)
     {
         using PH2 = Ph2<P, D, K>;
         constexpr int NPR = Q / 2, ODD = Q & 1, NT2 = NPR + ODD;
+        const FT fs{tb, n_switch(a)};   // phase (th q + t_0) q + s_0 of an item
+        if constexpr (PM != PM_COMPUTE) tb += (int64_t)fs.n * PH_SWITCH;
         const int k = a.k, n = 1 << (D * k);
         const int L = a.L;
         for (int it = threadIdx.x; it < a.T * n * QD1; it += blockDim.x) {
@@ -1029,19 +1138,23 @@ struct Tile {
                     const C ua = u[t0 + Q * th];
                     const C ub = two ? u[t0 + 1 + Q * th] : czero<C>();
                     float2 E0, E1;
+                    const int ja = (th * Q + t0) * Q, jb = ja + Q;
 #pragma unroll
                     for (int j = 0; j < NPR; ++j) {
-                        expphase_part2<P, D, K>(a, tP[j], PH2::add(PH2::part(tP[j], ea, ea, 0), hp[j]), E0, E1);
+                        ph2<PM>(a, tP[j], PH2::add(PH2::part(tP[j], ea, ea, 0), hp[j]), fs.at(ja + 2 * j, it),
+                                fs.at(ja + 2 * j + 1, it), E0, E1);
                         cmac(acc[2 * j], E0, ua);
                         cmac(acc[2 * j + 1], E1, ua);
                         if (two) {
-                            expphase_part2<P, D, K>(a, tP[j], PH2::add(PH2::part(tP[j], eb, eb, 0), hp[j]), E0, E1);
+                            ph2<PM>(a, tP[j], PH2::add(PH2::part(tP[j], eb, eb, 0), hp[j]), fs.at(jb + 2 * j, it),
+                                    fs.at(jb + 2 * j + 1, it), E0, E1);
                             cmac(acc[2 * j], E0, ub);
                             cmac(acc[2 * j + 1], E1, ub);
                         }
                     }
                     if constexpr (ODD) {
-                        expphase_part2<P, D, K>(a, tP[NPR], PH2::add(PH2::part(tP[NPR], ea, eb, 0), hp[NPR]), E0, E1);
+                        ph2<PM>(a, tP[NPR], PH2::add(PH2::part(tP[NPR], ea, eb, 0), hp[NPR]), fs.at(ja + Q - 1, it),
+                                two ? fs.at(jb + Q - 1, it) : nullptr, E0, E1);
                         cmac(acc[Q - 1], E0, ua);
                         if (two) cmac(acc[Q - 1], E1, ub);
                     }
@@ -1145,12 +1258,18 @@ struct Tile {
 
     // ---- one row-form merge level (l -> l+1) on all tiles of the CTA.  TC caches the
     // target features of the parents' nodes (T * 2^{Di} boxes x q^d nodes) for stage A.
-    static __device__ void row_level(const KArgs<P> &a, C *Wt, C *S, typename PH::T *TC, int l, int i)
+    template <int PM = PM_COMPUTE>
+    static __device__ void row_level(const KArgs<P> &a, C *Wt, C *S, typename PH::T *TC, int l, int i, float *&tb)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D;
         const int L = a.L;
         const int nbox = 1 << (D * i);
-        for (int j = threadIdx.x; j < a.T * nbox * RR; j += blockDim.x) {
+        FT fa{tb, n_row_a(a)}, fb{tb, n_row_b(a)};
+        if constexpr (PM != PM_COMPUTE) {
+            fb.p = tb + (int64_t)fa.n * PH_ROW_A;
+            tb = fb.p + (int64_t)fb.n * PH_ROW_B;
+        }
+        for (int j = threadIdx.x; PM != PM_TABLE && j < a.T * nbox * RR; j += blockDim.x) {
             const int t = j % RR, aloc = (j / RR) & (nbox - 1), tau = (j / RR) >> (D * i);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
@@ -1186,7 +1305,7 @@ struct Tile {
             for (int s0 = 0; s0 < Q; ++s0) { z[0][s0] = czero<C>(); z[1][s0] = czero<C>(); }
 #pragma unroll
             for (int t0 = 0; t0 < Q; ++t0) {
-                const C u = cjmul(expphase<P, D, K>(a, tn[t0], sc), win[t0]);
+                const C u = cjmul(phs<PM>(a, tn[t0], sc, fa.at(t0, it)), win[t0]);
 #pragma unroll
                 for (int s0 = 0; s0 < Q; ++s0) {
                     cfma2(z[0][s0], a.M2[0][t0][s0], u);
@@ -1251,7 +1370,8 @@ struct Tile {
 #pragma unroll
                         for (int c1 = 0; c1 < 2; ++c1) {
                             float2 E0, E1;
-                            expphase_part2<P, D, K>(a, tS2, PH2::add(q0, PH2::part(tS2, sc1[c1], sc1[c1], 1)), E0, E1);
+                            ph2<PM>(a, tS2, PH2::add(q0, PH2::part(tS2, sc1[c1], sc1[c1], 1)), fb.at(s1 * NC + 2 * c1, it),
+                                    fb.at(s1 * NC + 2 * c1 + 1, it), E0, E1);
                             acc[s1] = cadd(acc[s1], cmul(E0, v[2 * c1][s1]));
                             acc[s1] = cadd(acc[s1], cmul(E1, v[2 * c1 + 1][s1]));
                         }
@@ -1884,34 +2004,46 @@ struct Tile {
 // ------------------------------------------------------------------ kernels
 
 // init (l0 = 0) + k column merges + optional switch at level l0 + k
-template <int D, int Q, class P, int K>
+// PM: phase factors evaluated, or (d = 2, mixed precisions) recorded in or read from the
+// pass's reduced-phase table a.ftab (a.ftab_cta floats per CTA)
+template <int D, int Q, class P, int K, int PM = PM_COMPUTE>
 __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_col_pass(const KArgs<P> a)
 {
+    static_assert(PM == PM_COMPUTE || (D == 2 && !P::is_f64), "phase tables: d = 2, mixed precisions");
     using C = typename P::C;
     using TL = Tile<D, Q, P, K>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C *Wt = reinterpret_cast<C *>(smem_raw);
     C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
     const int rhs = blockIdx.y;
+    float *tb = nullptr;
+    if constexpr (PM != PM_COMPUTE) {
+        if (TL::table_floats(a, false) != a.ftab_cta) {   // the plan's layout disagrees: touch nothing
+            if (threadIdx.x == 0 && a.err) atomicExch(a.err, 2);
+            return;
+        }
+        tb = a.ftab + (int64_t)blockIdx.x * a.ftab_cta;
+    }
     if (a.flags & F_INIT)
         TL::init(a, Wt, rhs);
     else
         TL::load(a, Wt, rhs);
     __syncthreads();
-    for (int i = 0; i < a.k; ++i) TL::col_level(a, Wt, S, a.l0 + i, i);
+    for (int i = 0; i < a.k; ++i) TL::template col_level<PM>(a, Wt, S, a.l0 + i, i, tb);
     if (a.flags & F_SWITCH) {
         if constexpr (K == KIND_DOT || K == KIND_SEPARABLE)
             TL::template switch_sep<false>(a, Wt, S, a.l0 + a.k);
         else
-            TL::switch_tiles(a, Wt, S, a.l0 + a.k);
+            TL::template switch_tiles<PM>(a, Wt, S, a.l0 + a.k, tb);
     }
     TL::store(a, Wt, rhs);
 }
 
 // k row merges + optional final evaluation (l0 + k = L)
-template <int D, int Q, class P, int K>
+template <int D, int Q, class P, int K, int PM = PM_COMPUTE>
 __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pass(const KArgs<P> a)
 {
+    static_assert(PM == PM_COMPUTE || (D == 2 && !P::is_f64), "phase tables: d = 2, mixed precisions");
     using C = typename P::C;
     using TL = Tile<D, Q, P, K>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1919,9 +2051,17 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pa
     C *S = Wt + a.T * (1 << (D * a.k)) * TL::RR;
     const int rhs = blockIdx.y;
     typename TL::PH::T *TC = reinterpret_cast<typename TL::PH::T *>(S + 2 * a.T * (1 << (D * a.k)) * TL::RR);
+    float *tb = nullptr;
+    if constexpr (PM != PM_COMPUTE) {
+        if (TL::table_floats(a, true) != a.ftab_cta) {   // the plan's layout disagrees: touch nothing
+            if (threadIdx.x == 0 && a.err) atomicExch(a.err, 2);
+            return;
+        }
+        tb = a.ftab + (int64_t)blockIdx.x * a.ftab_cta;
+    }
     TL::load(a, Wt, rhs);
     __syncthreads();
-    for (int i = 0; i < a.k; ++i) TL::row_level(a, Wt, S, TC, a.l0 + i, i);
+    for (int i = 0; i < a.k; ++i) TL::template row_level<PM>(a, Wt, S, TC, a.l0 + i, i, tb);
     if (a.flags & F_FINAL)
         TL::final_eval(a, Wt, rhs);
     else

@@ -28,23 +28,23 @@ inline cudaError_t prepare(K kern, size_t smem, size_t *granted)
     return cudaSuccess;
 }
 
-template <int D, int Q, class P, int K>
+template <int D, int Q, class P, int K, int PM = bfk::PM_COMPUTE>
 cudaError_t launch_col(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
 {
     static size_t granted[64] = {0};
-    cudaError_t e = prepare(bfk::k_col_pass<D, Q, P, K>, smem, granted);
+    cudaError_t e = prepare(bfk::k_col_pass<D, Q, P, K, PM>, smem, granted);
     if (e != cudaSuccess) return e;
-    bfk::k_col_pass<D, Q, P, K><<<dim3(gx, gy), bfk::Cfg<D, Q, P>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    bfk::k_col_pass<D, Q, P, K, PM><<<dim3(gx, gy), bfk::Cfg<D, Q, P>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
     return cudaGetLastError();
 }
 
-template <int D, int Q, class P, int K>
+template <int D, int Q, class P, int K, int PM = bfk::PM_COMPUTE>
 cudaError_t launch_row(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
 {
     static size_t granted[64] = {0};
-    cudaError_t e = prepare(bfk::k_row_pass<D, Q, P, K>, smem, granted);
+    cudaError_t e = prepare(bfk::k_row_pass<D, Q, P, K, PM>, smem, granted);
     if (e != cudaSuccess) return e;
-    bfk::k_row_pass<D, Q, P, K><<<dim3(gx, gy), bfk::Cfg<D, Q, P>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    bfk::k_row_pass<D, Q, P, K, PM><<<dim3(gx, gy), bfk::Cfg<D, Q, P>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
     return cudaGetLastError();
 }
 
@@ -144,6 +144,8 @@ const PassFns *fns_for()
 {
     using CF = bfk::Cfg<D, Q, P>;
     if constexpr (D == 2 && !P::is_f64) {
+        // single-RHS passes with a reduced-phase table (record, read): q <= 5
+        constexpr bool TAB = Q <= 5;
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT,
                                   {launch_col_mr<Q, P, K, bfk::PM_COMPUTE>, launch_col_mr<Q, P, K, bfk::PM_BUILD>,
@@ -152,13 +154,18 @@ const PassFns *fns_for()
                                    launch_row_mr<Q, P, K, bfk::PM_TABLE>},
                                   bfk::MRMAX, bfk::CfgMR<Q>::NT,
                                   launch_batch<Q, P, K>, batch_ctas_per_sm<Q, P, K>, mr_table_occupancy<Q, P, K>,
-                                  launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
+                                  launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T),
+                                  {TAB ? launch_col<D, (TAB ? Q : 2), P, K, bfk::PM_BUILD> : nullptr,
+                                   TAB ? launch_col<D, (TAB ? Q : 2), P, K, bfk::PM_TABLE> : nullptr},
+                                  {TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_BUILD> : nullptr,
+                                   TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_TABLE> : nullptr}};
         return &f;
     } else {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, {nullptr, nullptr, nullptr},
                                   {nullptr, nullptr, nullptr}, 0, 0, nullptr, nullptr, nullptr,
-                                  launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T)};
+                                  launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T),
+                                  {nullptr, nullptr}, {nullptr, nullptr}};
         return &f;
     }
 }

@@ -26,6 +26,9 @@ struct PassFns {
     int (*mr_table_occupancy)(int row, size_t smem);   // CTAs per SM of the table-reading passes
     cudaError_t (*center_table)(const void *kargs, void *out, int levels);   // target features at box centres
     int tsize;                   // bytes of one target-feature record
+    // single-RHS passes with a reduced-phase table (d = 2, mixed, q <= 5; null if absent):
+    // [0] record the table (plan creation), [1] read it
+    pass_fn col_tab[2], row_tab[2];
 };
 
 // (d, q, precision, phase kind) -> kernels, or null if that combination is not compiled.

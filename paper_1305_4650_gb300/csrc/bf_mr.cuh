@@ -30,7 +30,6 @@ namespace bfk {
 
 constexpr int MRMAX = 16;   // right-hand sides held by one CTA
 
-enum { PM_COMPUTE = 0, PM_BUILD = 1, PM_TABLE = 2 };
 
 // ---- bulk copies (TMA engine) into shared memory, completed on an mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
