@@ -337,29 +337,37 @@ def run_ours(args, rank, world, local_rank):
         out_sfu = fsf.cpu().numpy()
         psf.close()
 
-    # ---- phase-table variant (every phase factor evaluated once at plan creation)
+    # ---- phase-table variants (every phase evaluated once at plan creation; the apply reads
+    # the reduced phases (one RHS) or the factors (several) and evaluates no Phi)
     tables = None
     if prec == "mixed" and spec.d == 2 and not args.no_tables:
-        ptb = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="mixed", phase_tables=True)
-        tinfo = ptb.table_info()
-        ftb = torch.empty_like(g)
-        for _ in range(args.warmup):
-            ptb.apply(g, ftb)
-        torch.cuda.synchronize()
-        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        c0.record(stream)
-        for _ in range(args.steps):
-            ptb.apply(g, ftb)
-        c1.record(stream)
-        torch.cuda.synchronize()
-        ms_tb = max_over_ranks(c0.elapsed_time(c1) / args.steps)
-        out_tb = ftb.cpu().numpy()
-        tables = {"value": spec.npts * nrhs * world / (ms_tb * 1e-3), "ms_per_step": round(ms_tb, 4),
-                  "table_gb": round(tinfo["bytes"] / 1e9, 3), "build_ms": round(tinfo["build_ms"], 2),
-                  "hbm_gbs": round(tinfo["bytes"] / (ms_tb * 1e-3) / 1e9, 1),
-                  "note": "plan-time phase tables (Section 1.4 precompute trade-off): the apply streams them"}
-        ptb.close()
-        del ftb
+        for tprec in ("mixed", "mixed_sfu"):
+            ptb = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=tprec, phase_tables=True)
+            tinfo = ptb.table_info()
+            ftb = torch.empty_like(g)
+            for _ in range(args.warmup):
+                ptb.apply(g, ftb)
+            torch.cuda.synchronize()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(args.steps):
+                ptb.apply(g, ftb)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            ms_tb = max_over_ranks(c0.elapsed_time(c1) / args.steps)
+            rec = {"value": spec.npts * nrhs * world / (ms_tb * 1e-3), "ms_per_step": round(ms_tb, 4),
+                   "table_gb": round(tinfo["bytes"] / 1e9, 3), "build_ms": round(tinfo["build_ms"], 2),
+                   "table_read_gbs": round(tinfo["bytes"] / (ms_tb * 1e-3) / 1e9, 1),
+                   "form": ("reduced phases (float), single-RHS kernels" if nrhs == 1
+                            else "complex factors, multi-RHS kernels (bulk copies)")}
+            if tprec == "mixed":
+                out_tb = ftb.cpu().numpy()
+                tables = rec
+                tables["note"] = "plan-time phase tables (Section 1.4 precompute trade-off); plan creation not timed"
+            else:
+                tables["sfu_sincos"] = rec
+            ptb.close()
+            del ftb
 
     # ---- end to end through the C ABI with host buffers (H2D + apply + D2H per step)
     gh = torch.from_numpy(g_np).pin_memory()

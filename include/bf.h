@@ -90,19 +90,24 @@ typedef struct {
     int32_t reserved[6];      /* must be zero                                               */
 } bf_params;
 
-/* Phase tables (phase_tables = 1; mixed precisions, d = 2): the precompute trade-off of
- * Section 1.4.  bf_plan_create evaluates every phase factor of the apply -- the 5 r
- * modulation factors per pair and level, the r x r switch matrices, init and final --
- * once into device memory (5 r L + r^2 + 2 r + 1 complex64 numbers per point: 16.2 GB at
- * d = 2, N = 1024, q = 5; BF_ERR_NOMEM if it does not fit), and every bf_apply, for any
- * nrhs, reads them instead of evaluating Phi: the apply streams the table instead of
- * being bound by instruction issue.  The factors are the ones the evaluating kernels
- * compute, so results are the same.  The apply kernels fetch each CTA's table blocks with
- * bulk copies (the TMA engine, cp.async.bulk) into two shared-memory buffers two blocks
- * ahead of use.  Needs q <= 5.  bf_plan_table_info reports the table's bytes, the time
+/* Phase tables (phase_tables = 1; mixed precisions, d = 2, q <= 5): the precompute
+ * trade-off of Section 1.4.  bf_plan_create evaluates the phase factors of the apply once,
+ * into device memory, and every bf_apply reads them instead of evaluating Phi.  Two forms:
+ *  - max_nrhs = 1: the single-RHS kernels record the reduced phase (Phi minus an integer,
+ *    one float) of every factor of the merges and of the switch -- 5 r L + r^2 floats per
+ *    point (r^2 only where the switch is not factorised): 7.9 GB at d = 2, N = 1024, q = 5.
+ *    The apply reads them with coalesced loads and evaluates only the sin/cos, so its
+ *    results equal the evaluating apply bit for bit.
+ *  - max_nrhs > 1: the multi-RHS kernels record the complex factors themselves (5 r L + r^2
+ *    + 2 r + 1 complex64 numbers per point; 16.2 GB at N = 1024) and the apply, for any
+ *    nrhs, fetches each CTA's table blocks with bulk copies (the TMA engine, cp.async.bulk)
+ *    into two shared-memory buffers two blocks ahead of use; results equal the evaluating
+ *    multi-RHS apply bit for bit.
+ * BF_ERR_NOMEM if the table does not fit.  The schedule is fixed by the table
+ * (bf_plan_autotune only times it).  bf_plan_table_info reports the table's bytes, the time
  * its construction took and (synchronising the device; timed_out may be NULL) whether a
- * wait for a copy ever gave up (results undefined then).  The adjoint and persistent
- * batches evaluate phases as without tables. */
+ * wait for a copy ever gave up, or a kernel found a table layout it did not expect (results
+ * undefined then).  The adjoint and persistent batches evaluate phases as without tables. */
 
 /* Defaults for the problem classes of Section 3: X = [0,1)^d, Y = [-N/2, N/2)^d
  * (integer frequencies), s = 1, points at the lower corner of their leaf boxes,
