@@ -46,6 +46,15 @@ TRAFFIC = {"genradon2d": {"src_sha256": "bddaf18a434a2a86878c46ad0d425de8741a07e
 TRAFFIC_SRC = ("bf_device.cuh", "bf_inst.cuh")   # the pass kernels and their launch configuration
 
 
+def measured_hbm_gbs():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (MEASURED_PEAKS.json)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
 def kernel_src_sha256():
     import hashlib
     h = hashlib.sha256()
@@ -355,9 +364,14 @@ def run_ours(args, rank, world, local_rank):
             c1.record(stream)
             torch.cuda.synchronize()
             ms_tb = max_over_ranks(c0.elapsed_time(c1) / args.steps)
+            # bytes an apply must move: the table once, the weights in and out of every pass boundary
+            moved = tinfo["bytes"] + 2 * max(len(passes) - 1, 1) * spec.npts * spec.r * 8 * nrhs
+            hbm_peak = measured_hbm_gbs()
             rec = {"value": spec.npts * nrhs * world / (ms_tb * 1e-3), "ms_per_step": round(ms_tb, 4),
                    "table_gb": round(tinfo["bytes"] / 1e9, 3), "build_ms": round(tinfo["build_ms"], 2),
                    "table_read_gbs": round(tinfo["bytes"] / (ms_tb * 1e-3) / 1e9, 1),
+                   "hbm": {"achieved_gbs": round(moved / (ms_tb * 1e-3) / 1e9, 1), "peak_gbs": hbm_peak[0],
+                           "frac": round(moved / (ms_tb * 1e-3) / 1e9 / hbm_peak[0], 3), "peak_basis": hbm_peak[1]},
                    "form": ("reduced phases (float), single-RHS kernels" if nrhs == 1
                             else "complex factors, multi-RHS kernels (bulk copies)")}
             if tprec == "mixed":

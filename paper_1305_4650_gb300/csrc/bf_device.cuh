@@ -670,6 +670,22 @@ struct Tile {
         if (!row && (a.flags & F_SWITCH) && K != KIND_DOT && K != KIND_SEPARABLE) f += (int64_t)n_switch(a) * PH_SWITCH;
         return f;
     }
+    // floats of one level's table blocks (both stages) and of the switch's
+    static __device__ __forceinline__ int64_t level_floats(const KArgs<P> &a, bool row)
+    {
+        return row ? (int64_t)n_row_a(a) * PH_ROW_A + (int64_t)n_row_b(a) * PH_ROW_B
+                   : (int64_t)n_col_a(a) * PH_COL_A + (int64_t)n_col_b(a) * PH_COL_B;
+    }
+    // ask the TMA engine to bring a table block into L2 ahead of its loads (a hint: no
+    // completion, nothing written); 16-byte aligned, a multiple of 16 bytes, 64 KB per copy
+    static __device__ __forceinline__ void prefetch_l2(const float *p, int64_t nfloats)
+    {
+        if (threadIdx.x != 0) return;
+        for (int64_t o = 0; o < nfloats; o += 16384) {
+            const unsigned bytes = (unsigned)(4 * (nfloats - o < 16384 ? nfloats - o : 16384));
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(bytes) : "memory");
+        }
+    }
     static __device__ __forceinline__ C cis(R fr)
     {
         R sn, cs;
@@ -2026,13 +2042,23 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, PM == PM_TABLE ? Cfg<D, Q, P
             return;
         }
         tb = a.ftab + (int64_t)blockIdx.x * a.ftab_cta;
+        if constexpr (PM == PM_TABLE) TL::prefetch_l2(tb, TL::level_floats(a, false));
     }
     if (a.flags & F_INIT)
         TL::init(a, Wt, rhs);
     else
         TL::load(a, Wt, rhs);
     __syncthreads();
-    for (int i = 0; i < a.k; ++i) TL::template col_level<PM>(a, Wt, S, a.l0 + i, i, tb);
+    for (int i = 0; i < a.k; ++i) {
+        if constexpr (PM == PM_TABLE) {   // the next level's blocks (or the switch's) while this level runs
+            const int64_t lf = TL::level_floats(a, false);
+            if (i + 1 < a.k)
+                TL::prefetch_l2(tb + lf, lf);
+            else if (a.flags & F_SWITCH)
+                TL::prefetch_l2(tb + lf, a.ftab_cta - (int64_t)a.k * lf);
+        }
+        TL::template col_level<PM>(a, Wt, S, a.l0 + i, i, tb);
+    }
     if (a.flags & F_SWITCH) {
         if constexpr (K == KIND_DOT || K == KIND_SEPARABLE)
             TL::template switch_sep<false>(a, Wt, S, a.l0 + a.k);
@@ -2061,10 +2087,17 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pa
             return;
         }
         tb = a.ftab + (int64_t)blockIdx.x * a.ftab_cta;
+        if constexpr (PM == PM_TABLE) TL::prefetch_l2(tb, TL::level_floats(a, true));
     }
     TL::load(a, Wt, rhs);
     __syncthreads();
-    for (int i = 0; i < a.k; ++i) TL::template row_level<PM>(a, Wt, S, TC, a.l0 + i, i, tb);
+    for (int i = 0; i < a.k; ++i) {
+        if constexpr (PM == PM_TABLE) {   // the next level's blocks while this level runs
+            const int64_t lf = TL::level_floats(a, true);
+            if (i + 1 < a.k) TL::prefetch_l2(tb + lf, lf);
+        }
+        TL::template row_level<PM>(a, Wt, S, TC, a.l0 + i, i, tb);
+    }
     if (a.flags & F_FINAL)
         TL::final_eval(a, Wt, rhs);
     else
