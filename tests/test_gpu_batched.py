@@ -105,6 +105,27 @@ def test_multi_rhs_against_oracle_beyond_one_cta_of_rhs(bf):
     plan.close()
 
 
+def test_multi_rhs_bench_size_against_restricted_oracle(bf):
+    # the benchmark's multi-RHS configuration (hyperbolic Radon N = 512, 16 right-hand sides, autotuned
+    # schedule): every right-hand side at all targets of one level-m box against the restricted oracle
+    import torch
+    spec = wl.hypradon(9)
+    nrhs = 16
+    plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="mixed")
+    plan.autotune(nrhs, reps=1)
+    g = torch.from_numpy(wl.source_values(spec, nrhs, np.complex64, seed=78)).cuda()
+    out = plan.apply(g).cpu().numpy()
+    P = oracle.Problem(**spec.oracle_kwargs())
+    lvl = spec.switch_level
+    box = (1 << (2 * lvl)) // 3
+    tg = oracle.restricted_targets(P, lvl, box)
+    gh = g.cpu().numpy().astype(np.complex128)
+    for j in (0, 7, 15):
+        ref = oracle.butterfly(P, gh[j], restrict=(lvl, box))[tg]
+        assert np.linalg.norm(out[j][tg] - ref) <= 1e-5 * np.linalg.norm(ref), j
+    plan.close()
+
+
 # ------------------------------------------------------------ persistent batch
 
 def _batch_problems():

@@ -115,3 +115,26 @@ def test_tables_refused_where_not_built(bf):
     with pytest.raises(bf.BfError) as e:
         bf.Plan.from_spec(wl.genradon3d(L=3), precision="mixed", phase_tables=True)
     assert e.value.code == 2
+
+
+def test_single_rhs_table_full_size(bf):
+    # the benchmark size (N = 1024, q = 5; a 7.9 GB table): the table apply equals the evaluating
+    # apply bit for bit, and a level-m target box matches the restricted oracle butterfly
+    import torch
+    spec = wl.genradon2d()
+    pt = bf.Plan.from_spec(spec, precision="mixed", phase_tables=True)
+    assert pt.table_info()["bytes"] == _tile_table_bytes(spec)
+    pc = bf.Plan.from_spec(spec, precision="mixed")
+    g = torch.from_numpy(wl.source_values(spec, 1, np.complex64, seed=64)).cuda()
+    ft, fc = pt.apply(g), pc.apply(g)
+    torch.cuda.synchronize()
+    assert not pt.table_info()["timed_out"]
+    assert torch.equal(ft, fc)
+    P = oracle.Problem(**spec.oracle_kwargs())
+    box = (1 << (2 * spec.switch_level)) // 5
+    tg = oracle.restricted_targets(P, spec.switch_level, box)
+    ref = oracle.butterfly(P, g[0].cpu().numpy().astype(np.complex128), restrict=(spec.switch_level, box))[tg]
+    out = ft[0].cpu().numpy()[tg]
+    assert np.linalg.norm(out - ref) <= 1e-5 * np.linalg.norm(ref)
+    pt.close()
+    pc.close()
