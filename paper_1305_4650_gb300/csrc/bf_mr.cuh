@@ -119,6 +119,22 @@ __host__ __device__ constexpr int mr_pc_extra(int q)
 // scratch entries per right-hand side (2 r per pair, plus the row scratch padding)
 __host__ __device__ constexpr int64_t mr_s_stride(int q, int64_t npr) { return 2 * npr * q * q + npr * q * mr_pad(q).rs; }
 
+// acc += M[h][t][u] v: one packed FMA where the coefficients come twice (KArgs::M2, the
+// per-pass kernels), two scalar FMAs in the persistent batch kernel (packed ones cost it
+// spills); the same roundings either way
+template <class MS> struct PackedM { static constexpr bool value = true; };
+template <class P> struct BatchArgs;
+template <class P> struct PackedM<BatchArgs<P>> { static constexpr bool value = false; };
+
+template <class MS, class C>
+__device__ __forceinline__ void mmac(C &acc, const MS &ms, int h, int t, int u, C v)
+{
+    if constexpr (PackedM<MS>::value)
+        cfma2(acc, ms.M2[h][t][u], v);
+    else
+        cfma(acc, ms.M[h][t][u], v);
+}
+
 template <int Q, class P, int K>
 struct TileMR {
     static constexpr MRPad PAD = mr_pad(Q);
@@ -400,7 +416,7 @@ struct TileMR {
                     for (int t0p = 0; t0p < Q; ++t0p) {
                         const C u = cmul(ph[cl * RR + t0p], win[t0p]);
 #pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) cfma(acc[t0], ms.M[c & 1][t0][t0p], u);
+                        for (int t0 = 0; t0 < Q; ++t0) mmac(acc[t0], ms, c & 1, t0, t0p, u);
                     }
                 }
                 C *so = S + rbl * SW + ((pA * 2 + chi) * Q + tq) * Q;
@@ -423,7 +439,7 @@ struct TileMR {
                     for (int tqp = 0; tqp < Q; ++tqp) {
                         const C v = si[tqp * Q];
 #pragma unroll
-                        for (int tq = 0; tq < Q; ++tq) cfma(acc[tq], ms.M[chi][tq][tqp], v);
+                        for (int tq = 0; tq < Q; ++tq) mmac(acc[tq], ms, chi, tq, tqp, v);
                     }
                 }
                 C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + tl;
@@ -595,8 +611,8 @@ struct TileMR {
                     const C u = cjmul(ph[t0], win[t0]);
 #pragma unroll
                     for (int s0 = 0; s0 < Q; ++s0) {
-                        cfma(z[0][s0], ms.M[0][t0][s0], u);
-                        cfma(z[1][s0], ms.M[1][t0][s0], u);
+                        mmac(z[0][s0], ms, 0, t0, s0, u);
+                        mmac(z[1][s0], ms, 1, t0, s0, u);
                     }
                 }
                 C *so = S + rbl * SW + (pin * Q + th) * SU;
@@ -624,7 +640,7 @@ struct TileMR {
                     for (int t1 = 0; t1 < Q; ++t1) {
                         const C zz = si[t1 * SU];
 #pragma unroll
-                        for (int s1 = 0; s1 < Q; ++s1) cfma(v[c][s1], ms.M[a1][t1][s1], zz);
+                        for (int s1 = 0; s1 < Q; ++s1) mmac(v[c][s1], ms, a1, t1, s1, zz);
                     }
                 }
                 C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
