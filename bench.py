@@ -301,6 +301,9 @@ def run_ours(args, rank, world, local_rank):
     roofline["measured_fma_tflops"] = {"fp32": round(bf.measure_fma_rate(False), 1),
                                        "fp32_packed_pairs": round(bf.measure_fma_rate(packed=True), 1),
                                        "fp64": round(fma64, 3)}
+    if prec != "fp64" and spec.d == 2:   # the phase ceiling: phases from registers only (bf_measure_phase_rate)
+        roofline["phase_ceiling_gphs"] = {"scalar": round(plan.phase_rate(False), 1),
+                                          "paired": round(plan.phase_rate(True), 1)}
 
     # ---- FP64 GPU butterfly on the same problem (the baseline of the speedup)
     fp64 = None
