@@ -61,7 +61,8 @@ def _tile_table_bytes(spec):
 @pytest.mark.parametrize("spec,prec", [(wl.genradon2d(L=6), "mixed"), (wl.genradon2d(L=7), "mixed_sfu"),
                                        (wl.hypradon(7), "mixed"), (wl.hypradon(5), "mixed_sfu"),
                                        (wl.genradon2d(L=3).with_(q=4), "mixed"), (wl.genradon2d(L=5).with_(q=3), "mixed"),
-                                       (wl.dft64().with_(precision="mixed"), "mixed")])
+                                       (wl.dft64().with_(precision="mixed"), "mixed"), (wl.genradon2d(L=1), "mixed"),
+                                       (wl.genradon2d(L=2).with_(q=2), "mixed"), (wl.hypradon(3), "mixed_sfu")])
 def test_single_rhs_table_equals_evaluated_phases(bf, spec, prec):
     # plans of one right-hand side record the reduced phase that the single-RHS kernels feed to
     # their sincos, so reading it gives the evaluating apply bit for bit
