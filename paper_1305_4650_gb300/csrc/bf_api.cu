@@ -219,10 +219,13 @@ size_t pass_smem(const bf_plan_s *p, const Pass &ps)
     return (size_t)3 * (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (size_t)p->r * p->csize;
 }
 
-// plus, for a row pass, the cache of the parents' node features (T 2^{d(k-1)} boxes x r nodes)
+// plus, for a row pass, the cache of the parents' node features (T 2^{d(k-1)} boxes x r nodes);
+// for a column pass, the geometry of every output pair of a level (T 2^{dk} records of the
+// centre features and four ints, rounded to 16 bytes)
 size_t row_cache_smem(const bf_plan_s *p, const Pass &ps)
 {
-    if (!ps.row || ps.k < 1) return 0;
+    if (!ps.row) return (size_t)ps.T * ((size_t)1 << (p->d * ps.k)) * (((size_t)p->fns->tsize + 16 + 15) / 16 * 16);
+    if (ps.k < 1) return 0;
     return (size_t)ps.T * ((size_t)1 << (p->d * (ps.k - 1))) * (size_t)p->r * (size_t)p->fns->tsize;
 }
 

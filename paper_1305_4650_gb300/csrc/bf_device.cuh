@@ -644,6 +644,16 @@ struct Tile {
     static constexpr int RR = ipow(Q, D);
     static constexpr int QD1 = ipow(Q, D - 1);
 
+    // geometry of one output pair of a column level, shared by all items of that pair (2q in
+    // stage A, q^{d-1} in stage B): computed once per level into shared memory
+    struct __align__(16) Geo {
+        typename PH::T tA;   // features of the target box centre
+        int cbq[DMAX];       // coordinates of the parent source box
+        int base;            // the merge block's first input slot in the tile
+    };
+    static_assert(sizeof(Geo) % 16 == 0 && sizeof(Geo) == (sizeof(typename PH::T) + 16 + 15) / 16 * 16,
+                  "Geo size (the host reserves round16(tsize + 16) bytes per pair)");
+
     // ---- reduced-phase table of a single-RHS pass (d = 2, mixed precisions).  The block of
     // one stage is [phase j of an item][item], so one phase index over a warp's items is one
     // coalesced access.  The table holds the reduced phase that the evaluating kernel feeds
@@ -813,7 +823,7 @@ struct Tile {
 
     // ---- one column-form merge level (l -> l+1) on all tiles of the CTA
     template <int PM = PM_COMPUTE>
-    static __device__ void col_level(const KArgs<P> &a, C *Wt, C *S, int l, int i, float *&tb)
+    static __device__ void col_level(const KArgs<P> &a, C *Wt, C *S, Geo *G, int l, int i, float *&tb)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D;
         const int L = a.L;
@@ -822,6 +832,24 @@ struct Tile {
             fb.p = tb + (int64_t)fa.n * PH_COL_A;
             tb = fb.p + (int64_t)fb.n * PH_COL_B;
         }
+        // the output pairs (tau, block, alpha) of this level: box centre (level l+1), parent source box
+        for (int j = threadIdx.x; j < a.T * n; j += blockDim.x) {
+            const int alpha = j & (NC - 1), beta = (j >> D) & (nblk - 1), tau = (j >> D) >> (D * (k - 1));
+            uint32_t Ap, Bstar, Apg, Bq;
+            int base;
+            tile_of(a, tau, Ap, Bstar);
+            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
+            const uint32_t Aa = (Apg << D) + alpha;
+            int ca[DMAX], cbq[DMAX];
+            morton_decode<D>(Aa, l + 1, ca);
+            morton_decode<D>(Bq, L - l - 1, cbq);
+            Geo &g = G[j];
+#pragma unroll
+            for (int q = 0; q < D; ++q) g.cbq[q] = cbq[q];
+            g.base = base;
+            if constexpr (PM != PM_TABLE) g.tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+        }
+        __syncthreads();
         // stage A: items (tau, block, alpha, c_{D-1}, t'_{D-1}): modulate and contract dims 0..D-2
         for (int it = threadIdx.x; it < a.T * nblk * NC * 2 * Q; it += blockDim.x) {
             const int tq = it % Q;
@@ -829,15 +857,12 @@ struct Tile {
             const int alpha = (it / (2 * Q)) % NC;
             const int beta = (it / (2 * Q * NC)) & (nblk - 1);
             const int tau = (it / (2 * Q * NC)) >> (D * (k - 1));
-            uint32_t Ap, Bstar, Apg, Bq;
-            int base;
-            tile_of(a, tau, Ap, Bstar);
-            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            const uint32_t Aa = (Apg << D) + alpha;                          // level l+1
-            int ca[DMAX], cbq[DMAX];
-            morton_decode<D>(Aa, l + 1, ca);
-            morton_decode<D>(Bq, L - l - 1, cbq);
-            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+            const Geo &g = G[(tau * nblk + beta) * NC + alpha];
+            const int base = g.base;
+            int cbq[DMAX];
+#pragma unroll
+            for (int q = 0; q < D; ++q) cbq[q] = g.cbq[q];
+            const typename PH::T tA = g.tA;
             const C *Wtau = Wt + tau * n * RR;
             C acc[QD1];
 #pragma unroll
@@ -961,15 +986,12 @@ struct Tile {
             const int alpha = (it / QD1) % NC;
             const int beta = (it / (QD1 * NC)) & (nblk - 1);
             const int tau = (it / (QD1 * NC)) >> (D * (k - 1));
-            uint32_t Ap, Bstar, Apg, Bq;
-            int base;
-            tile_of(a, tau, Ap, Bstar);
-            block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            const uint32_t Aa = (Apg << D) + alpha;
-            int ca[DMAX], cbq[DMAX];
-            morton_decode<D>(Aa, l + 1, ca);
-            morton_decode<D>(Bq, L - l - 1, cbq);
-            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+            const Geo &g = G[(tau * nblk + beta) * NC + alpha];
+            const int base = g.base;
+            int cbq[DMAX];
+#pragma unroll
+            for (int q = 0; q < D; ++q) cbq[q] = g.cbq[q];
+            const typename PH::T tA = g.tA;
             C acc[Q];
 #pragma unroll
             for (int j = 0; j < Q; ++j) acc[j] = czero<C>();
@@ -2049,6 +2071,7 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, PM == PM_TABLE ? Cfg<D, Q, P
     else
         TL::load(a, Wt, rhs);
     __syncthreads();
+    typename TL::Geo *G = reinterpret_cast<typename TL::Geo *>(S + 2 * a.T * (1 << (D * a.k)) * TL::RR);
     for (int i = 0; i < a.k; ++i) {
         if constexpr (PM == PM_TABLE) {   // the next level's blocks (or the switch's) while this level runs
             const int64_t lf = TL::level_floats(a, false);
@@ -2057,7 +2080,7 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, PM == PM_TABLE ? Cfg<D, Q, P
             else if (a.flags & F_SWITCH)
                 TL::prefetch_l2(tb + lf, a.ftab_cta - (int64_t)a.k * lf);
         }
-        TL::template col_level<PM>(a, Wt, S, a.l0 + i, i, tb);
+        TL::template col_level<PM>(a, Wt, S, G, a.l0 + i, i, tb);
     }
     if (a.flags & F_SWITCH) {
         if constexpr (K == KIND_DOT || K == KIND_SEPARABLE)

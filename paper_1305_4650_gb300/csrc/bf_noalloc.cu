@@ -220,6 +220,8 @@ bf_status run(int d, int L, int q, int kind, const bf_params *prm, const void *g
         size_t smem = (size_t)3 * ps[i].T * ((size_t)1 << (d * ps[i].k)) * r * sizeof(typename P::C);
         if (ps[i].row && ps[i].k >= 1)   // cache of the parents' node features in the row kernels
             smem += (size_t)ps[i].T * ((size_t)1 << (d * (ps[i].k - 1))) * r * (size_t)fns->tsize;
+        if (!ps[i].row)                  // geometry of a level's output pairs in the column kernels
+            smem += (size_t)ps[i].T * ((size_t)1 << (d * ps[i].k)) * (((size_t)fns->tsize + 16 + 15) / 16 * 16);
         cudaError_t e = (ps[i].row ? fns->row : fns->col)(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
         if (e != cudaSuccess) return BF_ERR_CUDA;
     }
