@@ -781,8 +781,24 @@ struct Tile {
         const int cX[DMAX] = {0, 0, 0};
         const int ctr[DMAX] = {Q, Q, Q};
         const typename PH::T tX = tpoint<P, D, Q, K>(a, 0, cX, ctr);   // centre of X
-        for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) {
-            const int t = it % RR, b = (it / RR) & (n - 1), tau = (it / RR) >> (D * k);
+        // the grid point of a leaf box has a non-zero Lagrange value at few nodes (one for points
+        // at box corners): zero the weights, then compute those nodes only
+        __shared__ int nzt[RR];
+        __shared__ int nnz;
+        if (threadIdx.x == 0) {
+            int c = 0;
+            for (int t = 0; t < RR; ++t) {
+                R lag = R(1);
+                for (int j = 0, tt = t; j < D; ++j, tt /= Q) lag *= a.lsrc[tt % Q];
+                if (lag != R(0)) nzt[c++] = t;
+            }
+            nnz = c;
+        }
+        for (int it = threadIdx.x; it < a.T * n * RR; it += blockDim.x) Wt[it] = czero<C>();
+        __syncthreads();
+        for (int it = threadIdx.x; it < a.T * n * nnz; it += blockDim.x) {
+            const int pr = it / nnz, t = nzt[it - pr * nnz];
+            const int b = pr & (n - 1), tau = pr >> (D * k);
             uint32_t Ap, Bstar;
             tile_of(a, tau, Ap, Bstar);
             const uint32_t B = (Bstar << (D * k)) + b;
@@ -792,20 +808,18 @@ struct Tile {
             int tk[DMAX], tt = t;
 #pragma unroll
             for (int j = 0; j < D; ++j) { tk[j] = tt % Q; tt /= Q; lag *= a.lsrc[tk[j]]; }
-            C out = czero<C>();
-            if (lag != R(0)) {
-                int64_t flat = 0;
+            int64_t flat = 0;
 #pragma unroll
-                for (int j = 0; j < D; ++j) flat = (flat << L) + cb[j];
-                const C gv = a.g[(int64_t)rhs * a.npts + flat];
-                const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
-                const C e1 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, pslot));
-                const C e0 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, tk));
-                C v = cjmul(e0, cmul(e1, gv));
-                out.x = lag * v.x;
-                out.y = lag * v.y;
-            }
-            Wt[it] = out;
+            for (int j = 0; j < D; ++j) flat = (flat << L) + cb[j];
+            const C gv = a.g[(int64_t)rhs * a.npts + flat];
+            const int pslot[DMAX] = {Q + 1, Q + 1, Q + 1};
+            const C e1 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, pslot));
+            const C e0 = expphase<P, D, K>(a, tX, spoint<P, D, Q, K>(a, 0, cb, tk));
+            C v = cjmul(e0, cmul(e1, gv));
+            C out;
+            out.x = lag * v.x;
+            out.y = lag * v.y;
+            Wt[pr * RR + t] = out;
         }
     }
 
