@@ -40,9 +40,9 @@ FP32_LANES_PER_SM = 128
 # workload, from one ncu capture of `python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-accuracy
 # --fp64-steps 0 --no-autotune --no-tables`.  They describe the kernels as built from sources with the recorded hash
 # and the recorded pass schedule; otherwise the figure is dropped (traffic: null) until captured again.
-TRAFFIC = {"genradon2d": {"src_sha256": "1228c77313e2ae4dc1bb1ed6fb6c553cf00760e8f4fa3378b2e4990a38b4b2a9",
+TRAFFIC = {"genradon2d": {"src_sha256": "9958560873e7d92ff097a72b4c149434e53aa330cfd9ea50f46377cd41d7106e",
                           "schedule": ["col2", "col3", "row2", "row3"],
-                          "bytes": [157157376, 388090112, 369864192, 216055808]}}
+                          "bytes": [157194496, 389356544, 370179584, 216019200]}}
 TRAFFIC_SRC = ("bf_device.cuh", "bf_inst.cuh")   # the pass kernels and their launch configuration
 
 

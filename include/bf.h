@@ -216,7 +216,9 @@ bf_status bf_plan_info(bf_plan plan, int *d, int64_t *N, int *q, int *m, int *fu
 bf_status bf_plan_table_info(bf_plan plan, int64_t *table_bytes, double *build_ms, int *timed_out);
 
 /* Autotuner.  Times candidate tile schedules of the apply bf_apply runs for nrhs
- * right-hand sides on this device and keeps the fastest in the plan.  Single-RHS (and
+ * right-hand sides on this device and keeps the fastest in the plan; the plan's current
+ * schedule is timed first and replaced only by a candidate at least 1% faster, so
+ * schedules of equal speed do not flip from run to run.  Single-RHS (and
  * FP64) passes: levels fused per pass (1 .. the compiled maximum) and whether the
  * short pass of a run of levels comes first or last.  Multi-RHS passes: fused levels
  * (1, 2), pairs per CTA (1 or 2 switch rounds), right-hand sides per scratch chunk

@@ -1245,6 +1245,7 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
         const int64_t ppr = p->fns->mr_nthreads / p->r;
         std::vector<Pass> keep = p->passes_mr;
         int keep_rc = p->mr_rc;
+        if (!keep.empty()) st = time_it(best);   // the incumbent: replaced only by a candidate 1% faster
         const int rcs[6] = {1, 2, 4, 5, 8, 16};
         for (int k = 1; k <= 2 && st == BF_OK; ++k)
             for (int64_t np = ppr; np <= 2 * ppr && st == BF_OK; np *= 2)
@@ -1261,7 +1262,7 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
                         p->mr_rc = rc;
                         double ms = 0.0;
                         st = time_it(ms);
-                        if (st == BF_OK && ms < best) {
+                        if (st == BF_OK && ms < 0.99 * best) {
                             best = ms;
                             keep = cand;
                             keep_rc = rc;
@@ -1270,9 +1271,11 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
         p->passes_mr = keep;
         p->mr_rc = keep_rc;
     } else if (st == BF_OK) {
-        // single-RHS tiles: fused levels per pass and where the short pass goes
+        // single-RHS tiles: fused levels per pass and where the short pass goes; the current
+        // schedule is kept unless a candidate is 1% faster (no flipping between equal schedules)
         std::vector<Pass> keep = p->passes;
         int keep_k = p->kc;
+        st = time_it(best);
         for (int k = 1; k <= p->fns->kmax && st == BF_OK; ++k)
             for (int rem = 0; rem < 2 && st == BF_OK; ++rem) {
                 std::vector<Pass> cand = schedule(p, k, p->fns->np, rem != 0);
@@ -1283,7 +1286,7 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
                 p->passes = cand;
                 double ms = 0.0;
                 st = time_it(ms);
-                if (st == BF_OK && ms < best) {
+                if (st == BF_OK && ms < 0.99 * best) {
                     best = ms;
                     keep = cand;
                     keep_k = k;
