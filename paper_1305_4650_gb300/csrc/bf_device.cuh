@@ -24,8 +24,12 @@
 // (coordinates, and sin/cos or squares of them, for box centres, Chebyshev
 // nodes and grid points), so every feature is a table read.  In the mixed
 // precision Phi is accumulated and reduced mod 1 in double-float arithmetic
-// (pairs of FP32 numbers: Dekker's product via FMA and Knuth's two-sum), then
-// the FP32 sincospif gives e^{2 pi i Phi}.  The FP64 variant uses doubles.
+// (pairs of FP32 numbers: Dekker's product via FMA and Knuth's two-sum), then a
+// quadrant-reduced FP32 sincos (or the special-function unit's) gives
+// e^{2 pi i Phi}; stages with a shared operand evaluate two phases at a time in
+// the lanes of a float2 (bf_pair.cuh).  The FP64 variant uses doubles.  With a
+// phase table (PM_TABLE) the single-RHS passes read the reduced phases recorded
+// at plan creation (PM_BUILD) instead of evaluating Phi.
 #pragma once
 
 #include <cuda_runtime.h>

@@ -12,9 +12,9 @@
 //
 // Shared memory (complex numbers, npr = pairs of the CTA):
 //   W  [nr][npr][r]       weights of every right-hand side (in place, as in Tile)
-//   S  [rc][2 npr r]      stage scratch
-//   PC [5 r npr]          phase cache of the current stage
-// Stage items, scratch layouts and the order of every accumulation follow Tile<2,...>.
+//   S  [rc][2 npr r + ..] stage scratch (row scratch units padded, mr_pad)
+//   PC [5 r npr + ..]     phase cache of the current stage (strides padded, mr_pad)
+// Stage items and the order of every accumulation follow Tile<2,...>.
 //
 // Phase tables (the precompute trade-off of Section 1.4).  A plan may keep every phase
 // factor of its apply in device memory: PM_BUILD runs the phase stages only and writes
@@ -29,7 +29,6 @@
 namespace bfk {
 
 constexpr int MRMAX = 16;   // right-hand sides held by one CTA
-
 
 // ---- bulk copies (TMA engine) into shared memory, completed on an mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
