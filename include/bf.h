@@ -52,7 +52,7 @@ typedef enum {
 } bf_status;
 
 /* Phase functions Phi (cycles; the kernel is exp(2 pi i Phi)), Section 3:
- *   BF_PHASE_DOT        Phi = s x.y                                  (Fourier, d = 1..3)
+ *   BF_PHASE_DOT        Phi = s x.y                                  (Fourier, d = 2, 3)
  *   BF_PHASE_GENRADON   Phi = s (x.y + sqrt(sum_k a_k(x)^2 y_k^2)),  generalized Radon analogue;
  *                       d=2: a_0 = (2 + sin2pi x0 sin2pi x1)/3, a_1 = (2 + cos2pi x0 cos2pi x1)/3;
  *                       d=3: a_k = (2 + sin2pi x_k cos2pi x_{k+1 mod 3})/3
