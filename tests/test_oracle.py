@@ -221,3 +221,12 @@ def test_paper_generalized_radon_accuracy():
     sup = np.abs(fb - fd).max() / np.abs(fd).max()
     lo, hi = claim["rel_sup_err_band"]
     assert lo <= sup <= hi, sup
+
+
+# ------------------------------------------------------------- phase values
+
+def test_phase_point_values():
+    # Hand-computed values of every phase formula (Sections 3.1, 3.2) at points where
+    # the trigonometric factors are 0, 1/2 or 1 and the square root is whole.
+    import phase_pins
+    assert phase_pins.failures() == []

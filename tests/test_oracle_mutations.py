@@ -24,12 +24,24 @@ MUTATIONS = {
     "final_drops_modulation": ("f[j] = kern(P, x, y0) * acc;", "f[j] = acc;"),
     "init_wrong_node": ("W[B * r + t] = conj(kern(P, x0, yt)) * lag(d, q, z, cb, wb, t, y) * src;",
                         "W[B * r + t] = conj(kern(P, x0, y)) * lag(d, q, z, cb, wb, t, y) * src;"),
+    # phase formulas (Sections 3.1, 3.2)
+    "genradon2d_a1_sin_for_cos": ("double a1 = (2.0 + cos(TWO_PI * x[0]) * cos(TWO_PI * x[1])) / 3.0;",
+                                  "double a1 = (2.0 + sin(TWO_PI * x[0]) * cos(TWO_PI * x[1])) / 3.0;"),
+    "genradon3d_wrong_neighbour": ("cos(TWO_PI * x[(k + 1) % d])", "cos(TWO_PI * x[k % d])"),
+    "genradon2d_a0_cos_for_sin": ("double a0 = (2.0 + sin(TWO_PI * x[0]) * sin(TWO_PI * x[1])) / 3.0;",
+                                  "double a0 = (2.0 + sin(TWO_PI * x[0]) * cos(TWO_PI * x[1])) / 3.0;"),
+    "genradon_drops_linear_term": ("        s = xy + sqrt(q2);", "        s = sqrt(q2);"),
+    "hypradon_wrong_slowness": ("s = x[0] * sqrt(y[0] * y[0] + y[1] * y[1] * x[1] * x[1]);",
+                                "s = x[0] * sqrt(y[0] * y[0] + y[1] * y[1] * x[0] * x[0]);"),
+    "separable_wrong_shift": ("a += sin(TWO_PI * (x[k] + (k + 1) / 7.0));", "a += sin(TWO_PI * (x[k] + k / 7.0));"),
 }
 
 
 def _pins_pass(rng) -> bool:
-    """Two whole-pipeline pins: exactness for a separable phase, DFT accuracy at q = 8."""
-    ok = True
+    """The phase point values, and two whole-pipeline pins: exactness for a separable
+    phase, DFT accuracy at q = 8."""
+    import phase_pins
+    ok = phase_pins.hold()
     P = oracle.Problem(d=2, L=4, q=3, phase="separable", tgt_off=0.25, src_off=0.3)
     g = rng.standard_normal(P.npts) + 1j * rng.standard_normal(P.npts)
     fb, fd = oracle.butterfly(P, g), oracle.direct_sum(P, g)
