@@ -33,7 +33,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "butterfly apply points*RHS/s at stated rel-err, mixed/batched vs FP64 GPU; %roof"
 UNIT = "points*RHS/s"
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each pass of the default
@@ -185,15 +184,30 @@ def phase_ops(phase: str, d: int, q: int) -> float:
     return part + (d - 1) * part / q + add + fin + sincos
 
 
+def nonzero_lagrange(q: int, node_kind: int, xi: float) -> int:
+    """Number of the q one-dimensional Lagrange values l_t(xi) = prod_{k != t} (xi - z_k) / (z_t - z_k)
+    that are non-zero in FP64, as the plan computes them (nodes on [-1/2, 1/2]:
+    cos(j pi / (q - 1)) / 2 Chebyshev-Lobatto, or cos((2j + 1) pi / 2q) / 2): the kernels skip
+    the nodes whose value is exactly zero."""
+    import math
+    z = [0.5 * math.cos(j * math.pi / (q - 1)) if node_kind == 0 else 0.5 * math.cos((2 * j + 1) * math.pi / (2 * q))
+         for j in range(q)]
+    n = 0
+    for t in range(q):
+        v = 1.0
+        for k in range(q):
+            if k != t:
+                v *= (xi - z[k]) / (z[t] - z[k])
+        n += v != 0.0
+    return n
+
+
 def pass_work(spec, ps, nrhs=1):
     """Algorithmic counts of one kernel pass: phase evaluations, complex x real MACs
     (interpolation), complex multiplies (modulation) and complex MACs (switch)."""
-    import numpy as np
-    import oracle
     d, q, r, P = spec.d, spec.q, spec.r, spec.npts
-    z = oracle.cheb_nodes(q, spec.node_kind)
-    nz_src = int(np.count_nonzero([oracle.lagrange1(z, t, spec.src_off - 0.5) for t in range(q)])) ** d
-    nz_tgt = int(np.count_nonzero([oracle.lagrange1(z, t, spec.tgt_off - 0.5) for t in range(q)])) ** d
+    nz_src = nonzero_lagrange(q, spec.node_kind, spec.src_off - 0.5) ** d
+    nz_tgt = nonzero_lagrange(q, spec.node_kind, spec.tgt_off - 0.5) ** d
     per_level_ph = (2 ** d + 1) * r
     per_level_mac = (2 ** (d + 1) - 2) * q ** (d + 1)
     w = dict(phases=0, macs=0, cmuls=0, cmacs=0)
@@ -288,8 +302,9 @@ def run_ours(args, rank, world, local_rank):
     sched = [("col" if p["kind"] == "col" else "row") + str(p["k"]) for p in passes]
     wdom = pass_work(spec, passes[dom], nrhs)
     ops = work_ops(spec, wdom)
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2.07e9 / 1e12       # FP32-pipe Tops/s at the 2070 MHz max clock
-    peak_basis = "152 SMs x 128 FP32 lanes x 2.07 GHz (derived, one FP32-pipe op per lane per clock)"
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2.07e9 / 1e12           # FP32-pipe Tops/s at the 2070 MHz max clock
+    peak_basis = f"{sms} SMs x 128 FP32 lanes x 2.07 GHz (derived, one FP32-pipe op per lane per clock)"
     fma64 = bf.measure_fma_rate(True)
     if prec == "fp64":                                        # the FP64 pipe bounds the FP64 path
         peak = fma64 / 2

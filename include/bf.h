@@ -73,8 +73,17 @@ typedef enum {
  *                      significant bits) before an FP32 polynomial sincos (error ~1e-7).
  *   BF_PREC_MIXED_SFU  as BF_PREC_MIXED but the sin/cos of the reduced phase come from the
  *                      special-function unit (error ~3.4e-7): faster, a few times the
- *                      FP32 weight rounding at the output. */
-typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1, BF_PREC_MIXED_SFU = 2 } bf_precision;
+ *                      FP32 weight rounding at the output.
+ *   BF_PREC_BF16X3     as BF_PREC_MIXED, except that an apply with several right-hand
+ *                      sides (nrhs >= 2; d = 2, q <= 5) runs the middle switch of Section
+ *                      1.4 -- per pair the complex r x r phase matrix times the r x nrhs
+ *                      weights -- as a GEMM on the tensor cores (tcgen05): every FP32
+ *                      operand split into two BF16 parts, three BF16 products accumulated
+ *                      in FP32 (relative error per product < 2^-16).  The switch is then
+ *                      its own pass (bf_pass_info kind 2).  One right-hand side, d = 3 and
+ *                      q > 5 run the BF_PREC_MIXED kernels and equal them bit for bit.  No
+ *                      phase tables (BF_ERR_UNSUPPORTED), no persistent batches. */
+typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1, BF_PREC_MIXED_SFU = 2, BF_PREC_BF16X3 = 3 } bf_precision;
 
 typedef struct {
     double x_lo[3], x_w[3];   /* target domain: prod_k [x_lo[k], x_lo[k] + x_w[k]), x_w > 0  */
@@ -107,7 +116,9 @@ typedef struct {
  * (bf_plan_autotune only times it).  bf_plan_table_info reports the table's bytes, the time
  * its construction took and (synchronising the device; timed_out may be NULL) whether a
  * wait for a copy ever gave up, or a kernel found a table layout it did not expect (results
- * undefined then).  The adjoint and persistent batches evaluate phases as without tables. */
+ * undefined then).  The adjoint and persistent batches evaluate phases as without tables.
+ * For BF_PREC_BF16X3 plans timed_out also reports a tensor-core completion wait that gave up
+ * (2 s; the switch pass then stops and its outputs are undefined). */
 
 /* Defaults for the problem classes of Section 3: X = [0,1)^d, Y = [-N/2, N/2)^d
  * (integer frequencies), s = 1, points at the lower corner of their leaf boxes,
@@ -238,7 +249,8 @@ bf_status bf_plan_autotune(bf_plan plan, int nrhs, int reps, void *stream, doubl
  * the same arguments as bf_apply; running passes 0 .. count-1 in order on one stream
  * is exactly bf_apply.  Used to time individual kernels with events recorded between
  * passes.  bf_pass_info describes pass i of the schedule for nrhs: kind (0 column
- * pass with optional init/switch, 1 row pass with optional final), first level l0,
+ * pass with optional init/switch, 1 row pass with optional final, 2 the tensor-core
+ * switch of BF_PREC_BF16X3 at level l0 with k = 0), first level l0,
  * number of fused levels k, flags (1 init, 2 switch, 4 final).  nrhs must lie in
  * 1..max_nrhs, i in 0..count-1 (else BF_ERR_INVALID_ARG). */
 bf_status bf_pass_count(bf_plan plan, int nrhs, int *count);
@@ -267,6 +279,14 @@ bf_status bf_measure_fma_rate(int fp64, double *tflops);
  * d = 3 plans. */
 bf_status bf_measure_phase_rate(bf_plan plan, int paired, double *gphases_per_s);
 bf_status bf_selfcheck_phase(bf_plan plan, int n, double *max_err_cycles);
+/* Self-check of the tensor-core GEMM blocks that BF_PREC_BF16X3 uses (operand layout in
+ * shared memory, descriptors, accumulator in tensor memory): one CTA computes a
+ * 128 x 32 x 64 product D = A B^T of fixed operands and the host compares it with the FP64
+ * product.  split = 0: small-integer operands, one BF16 product per K step (every product
+ * and sum exact: max_rel_err must be 0); split = 1: values in [-1, 1) through the BF16x3
+ * split (max_rel_err ~1e-5).  max_rel_err = max |D - D_ref| / max |D_ref|; timed_out = 1
+ * if the completion wait (2 s) gave up.  Allocates and frees a few KB, synchronises. */
+bf_status bf_selfcheck_umma(int split, double *max_rel_err, int *timed_out);
 
 /* Forward apply that allocates no device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc themselves or

@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbf_gb300.so")
 
 PHASE = {"dot": 0, "genradon": 1, "hypradon": 2, "separable": 3}
-PREC = {"fp64": 0, "mixed": 1, "mixed_sfu": 2}
+PREC = {"fp64": 0, "mixed": 1, "mixed_sfu": 2, "bf16x3": 3}
 STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_ERR_NOMEM",
           4: "BF_ERR_CUDA", 5: "BF_ERR_TIMEOUT", 6: "BF_ERR_INTERNAL"}
 
@@ -77,6 +77,7 @@ def load():
         lib.bf_selfcheck_phase.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_measure_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_measure_phase_rate.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
+        lib.bf_selfcheck_umma.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
         lib.bf_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), i32, ctypes.POINTER(vp)]
         lib.bf_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         lib.bf_batch_status.argtypes = [vp, ctypes.POINTER(i32)]
@@ -257,7 +258,7 @@ class Plan:
             kind, l0, k, fl = i32(), i32(), i32(), i32()
             _check(load().bf_pass_info(self._h, nrhs, i, ctypes.byref(kind), ctypes.byref(l0), ctypes.byref(k),
                                        ctypes.byref(fl)), "bf_pass_info")
-            out.append(dict(kind="row" if kind.value else "col", l0=l0.value, k=k.value,
+            out.append(dict(kind=("col", "row", "switch_tc")[kind.value], l0=l0.value, k=k.value,
                             init=bool(fl.value & 1), switch=bool(fl.value & 2), final=bool(fl.value & 4)))
         return out
 
@@ -305,6 +306,15 @@ def selfcheck_sincos(n: int = 1 << 22) -> float:
     e = ctypes.c_double()
     _check(load().bf_selfcheck_sincos(n, ctypes.byref(e)), "bf_selfcheck_sincos")
     return e.value
+
+
+def selfcheck_umma(split: bool = False) -> tuple[float, bool]:
+    """Tensor-core GEMM self-check (128 x 32 x 64, BF16 operands, FP32 accumulator): the
+    largest error relative to max |D| (0 expected without the split), and whether the
+    completion wait gave up."""
+    e, t = ctypes.c_double(), ctypes.c_int()
+    _check(load().bf_selfcheck_umma(1 if split else 0, ctypes.byref(e), ctypes.byref(t)), "bf_selfcheck_umma")
+    return e.value, bool(t.value)
 
 
 def measure_fma_rate(fp64: bool = False, packed: bool = False) -> float:

@@ -301,6 +301,19 @@ std::vector<Pass> schedule(const bf_plan_s *p, int kmax, int64_t np_cta, bool re
     return out;
 }
 
+// BF_PREC_BF16X3: the multi-RHS column pass that ends at the switch level stops before
+// the switch, and a tensor-core switch pass (row = 2, l0 = m) follows it
+void tc_switch_split(const bf_plan_s *p, std::vector<Pass> &sc)
+{
+    if (p->prec != BF_PREC_BF16X3 || !p->fns->switch_tc) return;
+    for (size_t i = 0; i < sc.size(); ++i)
+        if (sc[i].row == 0 && (sc[i].flags & bfk::F_SWITCH)) {
+            sc[i].flags &= ~bfk::F_SWITCH;
+            sc.insert(sc.begin() + (long)i + 1, Pass{2, p->m, 0, bfk::F_SWITCH, 1});
+            return;
+        }
+}
+
 template <class P>
 void fill_args(const bf_plan_s *p, bfk::KArgs<P> &a)
 {
@@ -365,6 +378,19 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
         a.T = ps.T;
         a.win = static_cast<const typename P::C *>(buf[i & 1]);
         a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
+        a.err = p->errflag;
+        if (ps.row == 2) {   // the switch on the tensor cores: units of two pairs, persistent CTAs
+            int dev = 0, sms = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            const int per_sm = p->fns->switch_tc_ctas_per_sm();
+            if (per_sm < 1) return BF_ERR_UNSUPPORTED;
+            int64_t grid = p->npts / 2;
+            if ((int64_t)sms * per_sm < grid) grid = (int64_t)sms * per_sm;
+            cudaError_t e = p->fns->switch_tc(&a, (unsigned)grid, (unsigned)((nrhs + 15) / 16), p->fns->switch_tc_smem, s);
+            if (e != cudaSuccess) return cuda_fail(p, e);
+            continue;
+        }
         a.ptab = p->ptab ? static_cast<typename P::C *>(p->ptab) + p->ptab_off[i] : nullptr;
         a.ptab_cta = p->ptab ? p->ptab_cta[i] : 0;
         a.err = p->errflag;
@@ -1001,7 +1027,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     if (q < 2 || q > bfk::QMAX) return BF_ERR_INVALID_ARG;
     if ((int)phase < 0 || (int)phase > 3) return BF_ERR_INVALID_ARG;
     if (phase == BF_PHASE_HYPRADON && d != 2) return BF_ERR_INVALID_ARG;
-    if (prm->precision < BF_PREC_FP64 || prm->precision > BF_PREC_MIXED_SFU) return BF_ERR_INVALID_ARG;
+    if (prm->precision < BF_PREC_FP64 || prm->precision > BF_PREC_BF16X3) return BF_ERR_INVALID_ARG;
     if (!supported_q(d, q)) return BF_ERR_UNSUPPORTED;
     if (prm->precision != BF_PREC_FP64 && phase_bound(d, (int)phase, prm) >= 2097152.0) return BF_ERR_UNSUPPORTED;
     for (int k = 0; k < d; ++k) {
@@ -1020,7 +1046,8 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     for (int i = 0; i < 6; ++i)
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
     if (prm->phase_tables != 0 && prm->phase_tables != 1) return BF_ERR_INVALID_ARG;
-    if (prm->phase_tables && (prm->precision == BF_PREC_FP64 || d != 2 || q > 5)) return BF_ERR_UNSUPPORTED;
+    if (prm->phase_tables && (prm->precision == BF_PREC_FP64 || prm->precision == BF_PREC_BF16X3 || d != 2 || q > 5))
+        return BF_ERR_UNSUPPORTED;
 
     bf_plan p = new (std::nothrow) bf_plan_s();
     if (!p) return BF_ERR_NOMEM;
@@ -1037,7 +1064,8 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     p->max_nrhs = prm->max_nrhs;
     p->prm = *prm;
     p->csize = p->prec == BF_PREC_FP64 ? 16 : 8;
-    p->fns = bfl::get_fns(d, q, (int)p->prec, (int)phase);
+    // BF16X3 evaluates its phases as BF_PREC_MIXED does and runs the same kernels but the switch
+    p->fns = bfl::get_fns(d, q, p->prec == BF_PREC_BF16X3 ? (int)BF_PREC_MIXED : (int)p->prec, (int)phase);
     if (!p->fns) {   // this combination was not compiled into the library
         delete p;
         return BF_ERR_UNSUPPORTED;
@@ -1065,6 +1093,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         const int nr = p->max_nrhs < p->fns->mr_max ? p->max_nrhs : p->fns->mr_max;
         const int64_t ppr = p->fns->mr_nthreads / p->r;
         p->passes_mr = schedule(p, kmr, ppr, true);
+        tc_switch_split(p, p->passes_mr);
         int64_t npr = 0;
         for (const Pass &ps : p->passes_mr)
             if (((int64_t)ps.T << (d * ps.k)) > npr) npr = (int64_t)ps.T << (d * ps.k);
@@ -1074,7 +1103,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         for (; rc >= 1 && !fits; --rc) {
             fits = true;
             for (const Pass &ps : p->passes_mr)
-                if (mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
+                if (ps.row != 2 && mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
             if (fits) p->mr_rc = rc;
         }
         if (!fits) p->passes_mr.clear();
@@ -1131,6 +1160,11 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
             st = BF_ERR_UNSUPPORTED;
         else
             st = p->prec == BF_PREC_MIXED_SFU ? build_phase_table<bfk::PMIXF>(p) : build_phase_table<bfk::PMIX>(p);
+    }
+    if (st == BF_OK && !p->errflag && p->prec == BF_PREC_BF16X3) {   // the tensor-core switch's bounded waits
+        cudaError_t e = cudaMalloc(&p->errflag, sizeof(int));
+        if (e == cudaSuccess) e = cudaMemset(p->errflag, 0, sizeof(int));
+        if (e != cudaSuccess) st = cuda_fail(p, e);
     }
     if (st == BF_OK) {
         const size_t wbytes = (size_t)p->max_nrhs * (size_t)p->npts * (size_t)p->r * p->csize;
@@ -1254,9 +1288,10 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
                         const int rc = rcs[ri];
                         if (rc > nr) continue;
                         std::vector<Pass> cand = schedule(p, k, np, rem != 0);
+                        tc_switch_split(p, cand);
                         bool fits = true;
                         for (const Pass &ps : cand)
-                            if (mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
+                            if (ps.row != 2 && mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
                         if (!fits) continue;
                         p->passes_mr = cand;
                         p->mr_rc = rc;
@@ -1404,7 +1439,8 @@ bf_status bf_batch_create(const bf_plan *plans, const int *nrhs, int count, bf_b
     const bf_plan p0 = plans[0];
     for (int i = 0; i < count; ++i) {
         const bf_plan p = plans[i];
-        if (p->d != 2 || p->prec == BF_PREC_FP64 || p->passes_mr.empty() || !p->fns->batch || p->points)
+        if (p->d != 2 || p->prec == BF_PREC_FP64 || p->prec == BF_PREC_BF16X3 || p->passes_mr.empty() ||
+            !p->fns->batch || p->points)
             return BF_ERR_UNSUPPORTED;
         if (p->q != p0->q || p->kind != p0->kind || p->prec != p0->prec || p->node_kind != p0->node_kind)
             return BF_ERR_UNSUPPORTED;
@@ -1517,6 +1553,12 @@ bf_status bf_selfcheck_sincos(int n, double *max_abs_err)
     if (n < 1 || !max_abs_err) return BF_ERR_INVALID_ARG;
     cudaError_t e = bfl::selfcheck_sincos(n, max_abs_err);
     return e == cudaSuccess ? BF_OK : BF_ERR_CUDA;
+}
+
+bf_status bf_selfcheck_umma(int split, double *max_rel_err, int *timed_out)
+{
+    if ((split != 0 && split != 1) || !max_rel_err || !timed_out) return BF_ERR_INVALID_ARG;
+    return bfl::selfcheck_umma(split, max_rel_err, timed_out) == cudaSuccess ? BF_OK : BF_ERR_CUDA;
 }
 
 bf_status bf_measure_fma_rate(int fp64, double *tflops)

@@ -3,6 +3,7 @@
 
 #include "bf_device.cuh"
 #include "bf_mr.cuh"
+#include "bf_tc.cuh"
 #include "bf_launch.h"
 
 namespace bfl {
@@ -129,6 +130,28 @@ int batch_ctas_per_sm(size_t smem)
     return n;
 }
 
+template <int Q, class P, int K>
+cudaError_t launch_switch_tc(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_switch_tc<Q, P, K>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_switch_tc<Q, P, K><<<dim3(gx, gy), bfk::SwTC<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    return cudaGetLastError();
+}
+
+template <int Q, class P, int K>
+int switch_tc_ctas_per_sm()
+{
+    static size_t granted[64] = {0};
+    if (prepare(bfk::k_switch_tc<Q, P, K>, bfk::SwTC<Q>::SMEM, granted) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bfk::k_switch_tc<Q, P, K>, bfk::SwTC<Q>::NT,
+                                                      bfk::SwTC<Q>::SMEM) != cudaSuccess)
+        return 0;
+    return n;
+}
+
 template <int D, int Q, class P, int K>
 cudaError_t launch_ctab(const void *kargs, void *out, int levels)
 {
@@ -146,6 +169,9 @@ const PassFns *fns_for()
     if constexpr (D == 2 && !P::is_f64) {
         // single-RHS passes with a reduced-phase table (record, read): q <= 5
         constexpr bool TAB = Q <= 5;
+        // tensor-core switch: q <= 5, polynomial sincos phases (the BF16x3 precision)
+        constexpr bool TC = Q <= 5 && !P::sfu;
+        constexpr int QT = TC ? Q : 2;
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT,
                                   {launch_col_mr<Q, P, K, bfk::PM_COMPUTE>, launch_col_mr<Q, P, K, bfk::PM_BUILD>,
@@ -158,14 +184,16 @@ const PassFns *fns_for()
                                   {TAB ? launch_col<D, (TAB ? Q : 2), P, K, bfk::PM_BUILD> : nullptr,
                                    TAB ? launch_col<D, (TAB ? Q : 2), P, K, bfk::PM_TABLE> : nullptr},
                                   {TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_BUILD> : nullptr,
-                                   TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_TABLE> : nullptr}};
+                                   TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_TABLE> : nullptr},
+                                  TC ? launch_switch_tc<QT, P, K> : nullptr,
+                                  TC ? switch_tc_ctas_per_sm<QT, P, K> : nullptr, TC ? bfk::SwTC<QT>::SMEM : 0};
         return &f;
     } else {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, {nullptr, nullptr, nullptr},
                                   {nullptr, nullptr, nullptr}, 0, 0, nullptr, nullptr, nullptr,
                                   launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T),
-                                  {nullptr, nullptr}, {nullptr, nullptr}};
+                                  {nullptr, nullptr}, {nullptr, nullptr}, nullptr, nullptr, 0};
         return &f;
     }
 }

@@ -29,6 +29,11 @@ struct PassFns {
     // single-RHS passes with a reduced-phase table (d = 2, mixed, q <= 5; null if absent):
     // [0] record the table (plan creation), [1] read it
     pass_fn col_tab[2], row_tab[2];
+    // multi-RHS switch on the tensor cores (bf_tc.cuh; d = 2, q <= 5, BF16x3 products;
+    // null if absent): grid_x CTAs take units of two pairs, grid_y blocks of 16 right-hand sides
+    pass_fn switch_tc;
+    int (*switch_tc_ctas_per_sm)();   // CTAs of switch_tc that fit on one SM
+    size_t switch_tc_smem;            // its dynamic shared memory per CTA
 };
 
 // (d, q, precision, phase kind) -> kernels, or null if that combination is not compiled.
@@ -76,5 +81,6 @@ cudaError_t selfcheck_sincos(int n, double *max_err);
 cudaError_t phase_rate(const void *kargs_mix, int sfu, int L, int q, int kind, int paired, double *gphases);
 cudaError_t selfcheck_phase(const void *kargs_mix, const void *kargs_f64, int d, int L, int q, int kind, int n,
                             double *max_err);
+cudaError_t selfcheck_umma(int split, double *max_rel_err, int *timed_out);
 
 }  // namespace bfl

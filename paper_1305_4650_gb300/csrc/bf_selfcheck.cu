@@ -3,11 +3,14 @@
 //   * the double-float Phi (mod 1) against FP64 arithmetic on the same table
 //     features (each double-float feature hi + lo taken as an FP64 number),
 //     for pseudo-random (target node, source node) pairs of a plan's tables.
+#include <cmath>
 #include <cstdint>
+#include <vector>
 
 #include "bf_device.cuh"
 #include "bf_launch.h"
 #include "bf_pair.cuh"
+#include "bf_tc.cuh"
 
 namespace {
 
@@ -186,6 +189,82 @@ __global__ void k_phase_rate(const bfk::KArgs<P> a, int L, int q, int iters, flo
     out[tid] = acc.x + acc.y;
 }
 
+// Self-check of the tensor-core building blocks with the operand layout above: one CTA
+// computes D = A B^T (M = 128, N = 32, K = 64) from row-major FP32 inputs A [128][64] and
+// B [32][64], either from the BF16 roundings of the inputs (split = 0: one product per K
+// step) or from their BF16x3 split (split = 1), and writes D [128][32] row-major.
+__global__ void __launch_bounds__(128) k_umma_selfcheck(const float *A, const float *B, float *Dout, int split, int *err)
+{
+    constexpr int M = 128, N = 32, KK = 64;
+    constexpr uint32_t LBO = 128, SBO = (KK / 8) * 128, AB = (M / 8) * SBO, BB = (N / 8) * SBO;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *Ah = smem_raw, *Al = Ah + AB, *Bh = Al + AB, *Bl = Bh + BB;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Bl + BB);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    int *sfail = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    for (int j = tid; j < M * KK / 2; j += 128) {
+        const int m = j / (KK / 2), k = 2 * (j % (KK / 2));
+        uint32_t hi, lo;
+        bfk::umma::split2(A[m * KK + k], A[m * KK + k + 1], hi, lo);
+        const uint32_t off = bfk::umma::kmajor_off(m, k, LBO, SBO);
+        *reinterpret_cast<uint32_t *>(Ah + off) = hi;
+        *reinterpret_cast<uint32_t *>(Al + off) = split ? lo : 0u;
+    }
+    for (int j = tid; j < N * KK / 2; j += 128) {
+        const int n = j / (KK / 2), k = 2 * (j % (KK / 2));
+        uint32_t hi, lo;
+        bfk::umma::split2(B[n * KK + k], B[n * KK + k + 1], hi, lo);
+        const uint32_t off = bfk::umma::kmajor_off(n, k, LBO, SBO);
+        *reinterpret_cast<uint32_t *>(Bh + off) = hi;
+        *reinterpret_cast<uint32_t *>(Bl + off) = split ? lo : 0u;
+    }
+    if (warp == 0) bfk::umma::alloc(tslot, 32);
+    if (tid == 0) {
+        bfk::mbar_init(bar, 1);
+        bfk::mbar_init_fence();
+        *sfail = 0;
+    }
+    bfk::umma::fence_smem_to_async();
+    bfk::umma::fence_before_sync();
+    __syncthreads();
+    bfk::umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    if (tid == 0) {
+        const uint32_t idesc = bfk::umma::idesc_bf16_f32(M, N);
+        for (int ks = 0; ks < KK / 16; ++ks) {
+            const uint32_t o = (uint32_t)ks * 2u * LBO;
+            const uint64_t dah = bfk::umma::desc_kmajor(bfk::umma::saddr(Ah) + o, LBO, SBO);
+            const uint64_t dal = bfk::umma::desc_kmajor(bfk::umma::saddr(Al) + o, LBO, SBO);
+            const uint64_t dbh = bfk::umma::desc_kmajor(bfk::umma::saddr(Bh) + o, LBO, SBO);
+            const uint64_t dbl = bfk::umma::desc_kmajor(bfk::umma::saddr(Bl) + o, LBO, SBO);
+            bfk::umma::mma_bf16(tmem, dah, dbh, idesc, ks > 0);
+            if (split) {
+                bfk::umma::mma_bf16(tmem, dah, dbl, idesc, 1);
+                bfk::umma::mma_bf16(tmem, dal, dbh, idesc, 1);
+            }
+        }
+        bfk::umma::commit(bar);
+        if (!bfk::mbar_wait_ns(bar, 0, bfk::TC_WAIT_NS)) {
+            atomicExch(err, 1);
+            *sfail = 1;
+            bfk::mbar_wait_ns(bar, 0, bfk::TC_WAIT_NS);
+        }
+    }
+    __syncthreads();
+    bfk::umma::fence_after_sync();
+    if (!*sfail) {
+        for (int c0 = 0; c0 < N; c0 += 8) {
+            float v[8];
+            bfk::umma::ld8(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+            for (int j = 0; j < 8; ++j) Dout[(32 * warp + lane) * N + c0 + j] = v[j];
+        }
+    }
+    bfk::umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) bfk::umma::dealloc(tmem, 32);
+}
+
 template <class P>
 cudaError_t phase_rate_t(const void *kargs, int L, int q, int kind, int paired, double *gphases)
 {
@@ -307,6 +386,58 @@ cudaError_t selfcheck_phase(const void *kargs_mix, const void *kargs_f64, int d,
     e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaMemcpy(max_err, dd, sizeof(double), cudaMemcpyDeviceToHost);
     cudaFree(dd);
+    return e;
+}
+
+// The BF16 tensor-core path on fixed operands: split = 0 uses small integers (every
+// product and sum exact, so the result must equal the FP64 product), split = 1 uniform
+// values in [-1, 1) through the BF16x3 split.  max_rel_err: largest |D - D_ref| over
+// max |D_ref|; timed_out: the completion wait gave up.
+cudaError_t selfcheck_umma(int split, double *max_rel_err, int *timed_out)
+{
+    constexpr int M = 128, N = 32, KK = 64;
+    std::vector<float> A(M * KK), B(N * KK);
+    uint32_t h = 12345u;
+    for (auto *v : {&A, &B})
+        for (float &x : *v) {
+            h = h * 1664525u + 1013904223u;
+            x = split ? (float)((int)(h >> 8) - (1 << 23)) / (float)(1 << 23) : (float)((int)((h >> 24) % 17u) - 8);
+        }
+    float *dA = nullptr, *dB = nullptr, *dD = nullptr;
+    int *derr = nullptr;
+    cudaError_t e = cudaMalloc(&dA, A.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dB, B.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&dD, (size_t)M * N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc(&derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(dA, A.data(), A.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dB, B.data(), B.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(dD, 0, (size_t)M * N * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        const size_t smem = 2 * (size_t)(M / 8) * (KK / 8) * 128 + 2 * (size_t)(N / 8) * (KK / 8) * 128 + 64;
+        k_umma_selfcheck<<<1, 128, smem>>>(dA, dB, dD, split, derr);
+        e = cudaGetLastError();
+    }
+    std::vector<float> D((size_t)M * N);
+    int terr = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(D.data(), dD, D.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&terr, derr, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        double mx = 0.0, md = 0.0;
+        for (int m = 0; m < M; ++m)
+            for (int n = 0; n < N; ++n) {
+                double ref = 0.0;
+                for (int k = 0; k < KK; ++k) ref += (double)A[m * KK + k] * (double)B[n * KK + k];
+                md = std::fmax(md, std::fabs(ref));
+                mx = std::fmax(mx, std::fabs((double)D[(size_t)m * N + n] - ref));
+            }
+        *max_rel_err = md > 0.0 ? mx / md : mx;
+        *timed_out = terr;
+    }
+    cudaFree(dA);
+    cudaFree(dB);
+    cudaFree(dD);
+    cudaFree(derr);
     return e;
 }
 

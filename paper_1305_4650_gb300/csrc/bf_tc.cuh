@@ -1,0 +1,218 @@
+// The middle switch of the butterfly (Section 1.4) on the tensor cores, for several right-
+// hand sides at once (d = 2, q <= 5, mixed-precision phases).
+//
+// At level m every pair (A, B) maps its weights through the r x r matrix
+//     E[s][t] = e^{2 pi i Phi(x_s^A, y_t^B)},      delta_s <- sum_t E[s][t] delta_t,
+// for every right-hand side: a complex (r x r) . (r x nrhs) product per pair, in which
+// each evaluated phase factor serves all right-hand sides.  Here it is a real GEMM on
+// tcgen05 tensor cores, D = A B^T with
+//     A[(s, c)][(t, c')]  rows 2s (real part of the result), 2s + 1 (imaginary part),
+//                         columns 2t (weight's real part), 2t + 1 (imaginary part):
+//                         [Re E, -Im E] in row 2s, [Im E, Re E] in row 2s + 1;
+//     B[rhs][(t, c')]     the weights of one right-hand side, as stored (re, im, re, ...),
+// so D[2s][rhs] = Re(E w)_s and D[2s + 1][rhs] = Im(E w)_s.  Two pairs share one MMA of
+// M = 128 rows (64 per pair, 2r of them used) and N = 32 columns (16 right-hand sides
+// per pair); the off-diagonal blocks of D are computed and ignored.
+//
+// Precision (BF16x3): every FP32 operand x is split into BF16 parts hi = bf16(x) and
+// lo = bf16(x - hi) (16 significant bits together), and D accumulates hi.hi + hi.lo +
+// lo.hi in FP32 in tensor memory; the dropped lo.lo term and the rounding of lo are
+// below 2^-17 relative per product.  The phase factors are those of the CUDA-core
+// multi-RHS switch, evaluated with the same code.
+#pragma once
+
+#include "bf_mr.cuh"
+#include "bf_umma.cuh"
+
+namespace bfk {
+
+// wait for phase `parity` of an mbarrier; false after limit_ns nanoseconds
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, unsigned parity, uint64_t limit_ns)
+{
+    const uint64_t t0 = globaltimer_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    return true;
+}
+
+constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // 2 s: an MMA group takes microseconds
+
+template <int Q>
+struct SwTC {
+    static constexpr int RR = Q * Q;                        // r
+    static constexpr int UP = 2;                            // pairs per MMA
+    static constexpr int ROWS = 64;                         // A rows per pair (2 r used)
+    static constexpr int NPP = 16;                          // right-hand sides (B rows) per pair
+    static constexpr int M = UP * ROWS, N = UP * NPP;       // 128 x 32 accumulator
+    static constexpr int KP = (2 * RR + 15) / 16 * 16;      // K = (t, re/im), padded to the MMA's K step
+    static constexpr int NKS = KP / 16;                     // K steps
+    static constexpr uint32_t LBO = 128;                    // core matrices along K: adjacent
+    static constexpr uint32_t SBO = (KP / 8) * 128;         // 8-row groups
+    static constexpr uint32_t A_BYTES = (M / 8) * SBO;      // one BF16 part of A
+    static constexpr uint32_t B_BYTES = (N / 8) * SBO;      // one BF16 part of B
+    static constexpr int NT = 256;                          // threads: 8 warps
+    static constexpr int TMEM_COLS = 32;
+    static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 64;
+    static_assert(2 * RR <= ROWS, "the tensor-core switch holds r <= 32");
+    static_assert(UP * RR * Q <= NT, "one phase item per thread");
+};
+
+// Switch pass: reads the level-m weights a.win ([rhs][pair][r], pair = A 2^{2(L-m)} + B),
+// writes the switched weights to a.wout in the same layout.  Right-hand sides
+// 16 blockIdx.y .. +15; units of two consecutive pairs taken blockIdx.x, + gridDim.x, ...
+// A completion wait that gives up sets *a.err, waits once more (bounded), frees the
+// tensor memory and ends the kernel (the outputs are then undefined).
+template <int Q, class P, int K>
+__global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
+{
+    using ST = SwTC<Q>;
+    using C = typename P::C;
+    using PH = Ph<P, 2, K>;
+    using PH2 = Ph2<P, 2, K>;
+    constexpr int RR = ST::RR, D = 2;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char *Ah = smem_raw, *Al = Ah + ST::A_BYTES, *Bh = Al + ST::A_BYTES, *Bl = Bh + ST::B_BYTES;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Bl + ST::B_BYTES);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    int *sfail = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // operands start at zero: the padding rows and columns are never written again
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(smem_raw);
+        const int n16 = (int)((2 * ST::A_BYTES + 2 * ST::B_BYTES) / 16);
+        for (int i = tid; i < n16; i += ST::NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (warp == 0) umma::alloc(tslot, ST::TMEM_COLS);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+        *sfail = 0;
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+
+    const int l = a.l0, L = a.L;
+    const int shB = D * (L - l);
+    const uint32_t maskB = (1u << shB) - 1u;
+    const int64_t nunits = a.npts / ST::UP;
+    const int rhs0 = (int)blockIdx.y * ST::NPP;
+    const int nr = min(ST::NPP, a.nrhs - rhs0);
+    const uint32_t idesc = umma::idesc_bf16_f32(ST::M, ST::N);
+    unsigned parity = 0;
+
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        // ---- B: the unit's weights, split into BF16 parts (rows up * 16 + rhs, K = 2t, 2t + 1)
+        for (int j = tid; j < ST::UP * ST::NPP * RR; j += ST::NT) {
+            const int t = j % RR, rb = (j / RR) % ST::NPP, up = j / (RR * ST::NPP);
+            if (rb < nr) {
+                const int64_t pair = u * ST::UP + up;
+                const C w = __ldcg(a.win + (int64_t)(rhs0 + rb) * a.wstride + pair * RR + t);
+                uint32_t hi, lo;
+                umma::split2(w.x, w.y, hi, lo);
+                const uint32_t off = umma::kmajor_off(up * ST::NPP + rb, 2 * t, ST::LBO, ST::SBO);
+                *reinterpret_cast<uint32_t *>(Bh + off) = hi;
+                *reinterpret_cast<uint32_t *>(Bl + off) = lo;
+            }
+        }
+        // ---- A: phase items (pair, s, t_1), q factors each, as the CUDA-core multi-RHS switch
+        for (int it = tid; it < ST::UP * RR * Q; it += ST::NT) {
+            const int th = it % Q, s = (it / Q) % RR, up = it / (Q * RR);
+            const uint32_t I = (uint32_t)(u * ST::UP + up);
+            int ca[DMAX], cb[DMAX];
+            morton_decode<D>(I >> shB, l, ca);
+            morton_decode<D>(I & maskB, L - l, cb);
+            const int sk[DMAX] = {s % Q, s / Q, 0};
+            const typename PH::T tS = tpoint<P, D, Q, K>(a, l, ca, sk);
+            C ev[Q];
+            const typename PH2::T tS2 = PH2::dup(tS);
+            const typename P::SE e1 = sget<P, Q>(a, 1, l, cb[1], th);
+            const typename PH2::Part hp = PH2::part(tS2, e1, e1, 1);
+#pragma unroll
+            for (int t0 = 0; t0 + 1 < Q; t0 += 2)
+                expphase_part2<P, D, K>(
+                    a, tS2, PH2::add(PH2::part(tS2, sget<P, Q>(a, 0, l, cb[0], t0), sget<P, Q>(a, 0, l, cb[0], t0 + 1), 0), hp),
+                    ev[t0], ev[t0 + 1]);
+            if constexpr (Q & 1)
+                ev[Q - 1] = expphase_part<P, D, K>(a, tS, PH::add(PH::part(tS, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0),
+                                                                 PH2::lane0(hp)));
+            const int r0 = up * ST::ROWS + 2 * s;
+#pragma unroll
+            for (int t0 = 0; t0 < Q; ++t0) {
+                const int k = 2 * (t0 + Q * th);
+                uint32_t hi, lo;
+                umma::split2(ev[t0].x, -ev[t0].y, hi, lo);
+                uint32_t off = umma::kmajor_off(r0, k, ST::LBO, ST::SBO);
+                *reinterpret_cast<uint32_t *>(Ah + off) = hi;
+                *reinterpret_cast<uint32_t *>(Al + off) = lo;
+                umma::split2(ev[t0].y, ev[t0].x, hi, lo);
+                off = umma::kmajor_off(r0 + 1, k, ST::LBO, ST::SBO);
+                *reinterpret_cast<uint32_t *>(Ah + off) = hi;
+                *reinterpret_cast<uint32_t *>(Al + off) = lo;
+            }
+        }
+        umma::fence_smem_to_async();
+        __syncthreads();
+        // ---- D = Ah Bh^T + Ah Bl^T + Al Bh^T, one thread issues; completion on the mbarrier
+        if (tid == 0) {
+            umma::fence_after_sync();
+            const uint32_t ah = umma::saddr(Ah), al = umma::saddr(Al), bh = umma::saddr(Bh), bl = umma::saddr(Bl);
+#pragma unroll
+            for (int ks = 0; ks < ST::NKS; ++ks) {
+                const uint32_t o = (uint32_t)ks * 2u * ST::LBO;
+                const uint64_t dah = umma::desc_kmajor(ah + o, ST::LBO, ST::SBO);
+                const uint64_t dal = umma::desc_kmajor(al + o, ST::LBO, ST::SBO);
+                const uint64_t dbh = umma::desc_kmajor(bh + o, ST::LBO, ST::SBO);
+                const uint64_t dbl = umma::desc_kmajor(bl + o, ST::LBO, ST::SBO);
+                umma::mma_bf16(tmem, dah, dbh, idesc, ks > 0);
+                umma::mma_bf16(tmem, dah, dbl, idesc, 1);
+                umma::mma_bf16(tmem, dal, dbh, idesc, 1);
+            }
+            umma::commit(bar);
+            if (!mbar_wait_ns(bar, parity, TC_WAIT_NS)) {
+                if (a.err) atomicExch(a.err, 1);
+                *sfail = 1;
+                mbar_wait_ns(bar, parity, TC_WAIT_NS);
+            }
+        }
+        parity ^= 1u;
+        __syncthreads();
+        if (*sfail) break;
+        umma::fence_after_sync();
+        // ---- epilogue: warp w reads lanes 32 (w % 4) .. + 31 (rows 2s + c of pair w / 2 % 2),
+        // columns of its pair's right-hand sides 8 (w / 4) .. + 7; lanes 2s and 2s + 1 swap
+        // halves so that each writes complete complex numbers
+        {
+            const int quad = warp & 3, half = warp >> 2, up = quad >> 1;
+            const int rr = 32 * (quad & 1) + lane, s = rr >> 1, c = lane & 1;
+            float v[8];
+            umma::ld8(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(up * ST::NPP + 8 * half), v);
+            float recv[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) recv[j] = __shfl_xor_sync(0xffffffffu, c ? v[j] : v[4 + j], 1);
+            if (s < RR) {
+                const int64_t pair = u * ST::UP + up;
+                C *wo = a.wout + pair * RR + s;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int rb = 8 * half + 4 * c + j;
+                    if (rb < nr) {
+                        C z;
+                        z.x = c ? recv[j] : v[j];
+                        z.y = c ? v[4 + j] : recv[j];
+                        wo[(int64_t)(rhs0 + rb) * a.wstride] = z;
+                    }
+                }
+            }
+        }
+        umma::fence_before_sync();
+        __syncthreads();
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::dealloc(tmem, ST::TMEM_COLS);
+}
+
+}  // namespace bfk

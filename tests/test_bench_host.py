@@ -77,3 +77,13 @@ def test_measured_hbm_peak_comes_from_the_pool_file():
     assert gbs > 1000.0
     if os.path.exists(os.path.join(bench.ROOT, "MEASURED_PEAKS.json")):
         assert basis.startswith("measured")
+
+
+@pytest.mark.parametrize("q,kind,off", [(5, 0, 0.0), (5, 0, 0.3), (4, 1, 0.0), (2, 0, 0.0), (3, 0, 0.5), (8, 1, 0.25)])
+def test_nonzero_lagrange_count_matches_the_oracle_basis(q, kind, off):
+    # the bench's count of non-zero Lagrange values of a grid point (it derives it from the
+    # node formula) against the oracle's basis evaluated at that point
+    import oracle
+    z = oracle.cheb_nodes(q, kind)
+    want = sum(1 for t in range(q) if oracle.lagrange1(z, t, off - 0.5) != 0.0)
+    assert bench.nonzero_lagrange(q, kind, off - 0.5) == want

@@ -1,0 +1,128 @@
+"""The switch on the tensor cores (BF_PREC_BF16X3): tcgen05 GEMM self-checks, then the
+butterfly with several right-hand sides against the FP64 oracle.
+
+Tolerance: relative l2 <= 1e-4 against the same-q oracle butterfly, per right-hand side
+(the batched-RHS split-product tolerance of the method's GPU forms).  The switch's BF16x3
+products carry a relative error below 2^-16 each (the dropped lo.lo term and the BF16
+rounding of the lo parts), ~1e-5 on a 25-term sum; every other step is the mixed path
+(a few 1e-7).  Against the all-FP32 multi-RHS apply the difference is the switch's
+error alone: 5e-5.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1305_4650_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL_ORACLE = 1e-4
+TOL_FP32 = 5e-5
+
+
+@pytest.fixture(scope="module")
+def bf():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1305_4650_gb300 import build, bf as bfmod
+    build.build()
+    return bfmod
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def test_umma_selfcheck_exact(bf):
+    # small-integer operands: every BF16 product and FP32 sum is exact
+    err, timed_out = bf.selfcheck_umma(split=False)
+    assert not timed_out
+    assert err == 0.0, err
+
+
+def test_umma_selfcheck_split(bf):
+    # values in [-1, 1) through the BF16x3 split: 64-term sums to ~2^-16 relative
+    err, timed_out = bf.selfcheck_umma(split=True)
+    assert not timed_out
+    assert err < 1e-4, err
+
+
+def _apply(bf, spec, nrhs, precision, seed, autotune=False):
+    import torch
+    plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=precision)
+    if autotune:
+        plan.autotune(nrhs, reps=1)
+    g = torch.from_numpy(wl.source_values(spec, nrhs, np.complex64, seed=seed)).cuda()
+    f = plan.apply(g)
+    torch.cuda.synchronize()
+    passes = plan.passes(nrhs)
+    timed_out = plan.table_info()["timed_out"]
+    plan.close()
+    return g.cpu().numpy(), f.cpu().numpy(), passes, timed_out
+
+
+@pytest.mark.parametrize("phase,L,q,nrhs", [("hypradon", 5, 5, 2), ("hypradon", 6, 5, 16), ("hypradon", 7, 5, 19),
+                                            ("genradon", 5, 5, 5), ("dot", 4, 5, 3), ("separable", 5, 5, 4),
+                                            ("genradon", 6, 4, 7), ("hypradon", 5, 3, 17), ("genradon", 4, 2, 3),
+                                            ("hypradon", 2, 5, 20), ("genradon", 1, 5, 3)])
+def test_bf16x3_against_oracle(bf, phase, L, q, nrhs):
+    spec = (wl.hypradon(L) if phase == "hypradon" else wl.genradon2d(L=L).with_(phase=phase)).with_(q=q)
+    g, out, passes, timed_out = _apply(bf, spec, nrhs, "bf16x3", seed=900 + L + q)
+    assert not timed_out
+    assert [p["kind"] for p in passes].count("switch_tc") == 1
+    ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.astype(np.complex128))
+    for j in range(nrhs):
+        assert rel(out[j], ref[j]) <= TOL_ORACLE, (j, rel(out[j], ref[j]))
+
+
+@pytest.mark.parametrize("m", [0, 1, 3, 4])
+def test_bf16x3_every_switch_level(bf, m):
+    spec = wl.hypradon(5).with_(m=m)
+    g, out, passes, _ = _apply(bf, spec, 6, "bf16x3", seed=950 + m)
+    sw = [p for p in passes if p["kind"] == "switch_tc"]
+    assert len(sw) == 1 and sw[0]["l0"] == m
+    ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.astype(np.complex128))
+    for j in range(6):
+        assert rel(out[j], ref[j]) <= TOL_ORACLE
+
+
+def test_bf16x3_one_rhs_is_the_mixed_apply(bf):
+    # one right-hand side runs the mixed single-RHS kernels: bit-identical
+    spec = wl.hypradon(6)
+    _, a, pa, _ = _apply(bf, spec, 1, "bf16x3", seed=5)
+    _, b, pb, _ = _apply(bf, spec, 1, "mixed", seed=5)
+    assert pa == pb
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("L,nrhs", [(7, 16), (8, 16), (9, 16), (9, 19)])
+def test_bf16x3_benchmark_sizes(bf, L, nrhs):
+    # the 48-problem batch's sizes (N = 128, 256, 512) with 16 and 19 right-hand sides,
+    # autotuned: against the FP32 multi-RHS apply everywhere and against the oracle
+    # restricted to one level-m target box (two boxes at N = 512)
+    spec = wl.hypradon(L)
+    g, out, passes, timed_out = _apply(bf, spec, nrhs, "bf16x3", seed=960 + L, autotune=True)
+    assert not timed_out
+    assert any(p["kind"] == "switch_tc" for p in passes)
+    _, f32, _, _ = _apply(bf, spec, nrhs, "mixed", seed=960 + L)
+    for j in range(nrhs):
+        assert rel(out[j], f32[j]) <= TOL_FP32, (j, rel(out[j], f32[j]))
+    P = oracle.Problem(**spec.oracle_kwargs())
+    lvl = spec.switch_level
+    boxes = [(1 << (2 * lvl)) // 3] + ([(1 << (2 * lvl)) - 5] if L == 9 else [])
+    for box in boxes:
+        tg = oracle.restricted_targets(P, lvl, box)
+        for j in (0, nrhs - 1):
+            ref = oracle.butterfly(P, g[j].astype(np.complex128), restrict=(lvl, box))
+            assert rel(out[j][tg], ref[tg]) <= TOL_ORACLE, (box, j)
+
+
+def test_bf16x3_refuses_tables_and_batches(bf):
+    spec = wl.hypradon(5)
+    with pytest.raises(bf.BfError):
+        bf.Plan.from_spec(spec, max_nrhs=4, precision="bf16x3", phase_tables=True)
+    plan = bf.Plan.from_spec(spec, max_nrhs=4, precision="bf16x3")
+    with pytest.raises(bf.BfError):
+        bf.Batch([plan], [4])
+    plan.close()
