@@ -88,6 +88,8 @@ def parse():
                     choices=["genradon2d", "genradon3d", "dft64", "hypradon512", "hypradon48", "cg1024",
                              "genradon2d_points"])
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per apply (single-problem workloads)")
+    ap.add_argument("--precision", default="", choices=["", "mixed", "mixed_sfu", "bf16x3", "fp64"],
+                    help="override the workload's precision (single-problem workloads)")
     ap.add_argument("--L", type=int, default=0, help="override log2 N of a single-problem workload (small cases)")
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -260,7 +262,7 @@ def run_ours(args, rank, world, local_rank):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
 
-    prec = spec.precision
+    prec = args.precision or spec.precision
     plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec)
     tuned = None if args.no_autotune else round(plan.autotune(nrhs, reps=3), 4)   # plan time, not timed
     passes = plan.passes(nrhs)
@@ -299,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
         for i in range(len(passes)):
             tpass[i] += evs[i].elapsed_time(evs[i + 1]) / args.steps
     dom = max(range(len(passes)), key=lambda i: tpass[i])
-    sched = [("col" if p["kind"] == "col" else "row") + str(p["k"]) for p in passes]
+    sched = [(p["kind"] if p["kind"] != "switch_tc" else "sw") + str(p["k"]) for p in passes]
     wdom = pass_work(spec, passes[dom], nrhs)
     ops = work_ops(spec, wdom)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -466,7 +468,7 @@ def run_ours(args, rank, world, local_rank):
     weight_gb = 2 * max(len(passes) - 1, 1) * spec.npts * spec.r * csize * nrhs / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64" if prec == "mixed" else "c128",
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128" if prec == "fp64" else "c64",
             "data": "synthetic",
             "config": {"workload": spec.name, "d": spec.d, "N": spec.N, "q": spec.q, "r": spec.r,
                        "phase": spec.phase, "precision": prec, "nrhs": nrhs, "switch_level": spec.switch_level,

@@ -140,16 +140,31 @@ cudaError_t launch_switch_tc(const void *kargs, unsigned gx, unsigned gy, size_t
     return cudaGetLastError();
 }
 
+// CTAs of the tensor-core switch that fit on one SM by its registers, shared memory and
+// threads (its grid is persistent, so a count above what the hardware keeps resident only
+// queues CTAs; the occupancy query is taken when it allows more)
 template <int Q, class P, int K>
 int switch_tc_ctas_per_sm()
 {
     static size_t granted[64] = {0};
     if (prepare(bfk::k_switch_tc<Q, P, K>, bfk::SwTC<Q>::SMEM, granted) != cudaSuccess) return 0;
-    int n = 0;
+    int dev = 0, n = 0;
+    cudaFuncAttributes fa{};
+    cudaDeviceProp pr{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, bfk::k_switch_tc<Q, P, K>) != cudaSuccess ||
+        cudaGetDeviceProperties(&pr, dev) != cudaSuccess)
+        return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bfk::k_switch_tc<Q, P, K>, bfk::SwTC<Q>::NT,
                                                       bfk::SwTC<Q>::SMEM) != cudaSuccess)
-        return 0;
-    return n;
+        n = 0;
+    const int warps = bfk::SwTC<Q>::NT / 32;
+    const int regs_cta = warps * ((fa.numRegs * 32 + 255) / 256 * 256);
+    const size_t smem_cta = bfk::SwTC<Q>::SMEM + fa.sharedSizeBytes + pr.reservedSharedMemPerBlock;
+    int res = pr.maxBlocksPerMultiProcessor;
+    if (regs_cta > 0 && pr.regsPerMultiprocessor / regs_cta < res) res = pr.regsPerMultiprocessor / regs_cta;
+    if ((int)(pr.sharedMemPerMultiprocessor / smem_cta) < res) res = (int)(pr.sharedMemPerMultiprocessor / smem_cta);
+    if (pr.maxThreadsPerMultiProcessor / bfk::SwTC<Q>::NT < res) res = pr.maxThreadsPerMultiProcessor / bfk::SwTC<Q>::NT;
+    return n > res ? n : res;
 }
 
 template <int D, int Q, class P, int K>

@@ -52,7 +52,10 @@ struct SwTC {
     static constexpr uint32_t B_BYTES = (N / 8) * SBO;      // one BF16 part of B
     static constexpr int NT = 256;                          // threads: 8 warps
     static constexpr int TMEM_COLS = 32;
-    static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 64;
+    static constexpr uint32_t W_BYTES = NPP * UP * RR * 8;  // a unit's weights as stored (complex64)
+    static constexpr int W_CHUNKS = W_BYTES / 16;           // 16-byte copies per unit
+    static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 2 * (size_t)W_BYTES + 64;
+    static_assert((UP * RR * 8) % 16 == 0, "a unit's weights per right-hand side are whole 16-byte pieces");
     static_assert(2 * RR <= ROWS, "the tensor-core switch holds r <= 32");
     static_assert(UP * RR * Q <= NT, "one phase item per thread");
 };
@@ -60,6 +63,9 @@ struct SwTC {
 // Switch pass: reads the level-m weights a.win ([rhs][pair][r], pair = A 2^{2(L-m)} + B),
 // writes the switched weights to a.wout in the same layout.  Right-hand sides
 // 16 blockIdx.y .. +15; units of two consecutive pairs taken blockIdx.x, + gridDim.x, ...
+// The weights of a unit (per right-hand side the two pairs' 2r complex numbers, contiguous
+// and 16-byte aligned) are copied into shared memory with cp.async one unit ahead, so the
+// loads overlap the previous unit's phase evaluation.
 // A completion wait that gives up sets *a.err, waits once more (bounded), frees the
 // tensor memory and ends the kernel (the outputs are then undefined).
 template <int Q, class P, int K>
@@ -70,9 +76,10 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
     using PH = Ph<P, 2, K>;
     using PH2 = Ph2<P, 2, K>;
     constexpr int RR = ST::RR, D = 2;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *Ah = smem_raw, *Al = Ah + ST::A_BYTES, *Bh = Al + ST::A_BYTES, *Bl = Bh + ST::B_BYTES;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Bl + ST::B_BYTES);
+    unsigned char *Wst = Bl + ST::B_BYTES;   // two buffers of a unit's weights
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Wst + 2 * ST::W_BYTES);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *sfail = reinterpret_cast<int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -103,13 +110,34 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
     const uint32_t idesc = umma::idesc_bf16_f32(ST::M, ST::N);
     unsigned parity = 0;
 
-    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+    // weights of unit v into buffer b: per right-hand side rb < nr, W_BYTES / NPP bytes in
+    // 16-byte pieces; one commit group per call (empty past the last unit)
+    auto fetch = [&](int64_t v, int b) {
+        constexpr int per_rhs = ST::W_CHUNKS / ST::NPP;
+        if (v < nunits) {
+            for (int c = tid; c < nr * per_rhs; c += ST::NT) {
+                const int rb = c / per_rhs, o = c - rb * per_rhs;
+                const char *src =
+                    reinterpret_cast<const char *>(a.win + (int64_t)(rhs0 + rb) * a.wstride + v * ST::UP * RR) + 16 * o;
+                const uint32_t dst = umma::saddr(Wst + b * ST::W_BYTES + rb * (ST::W_BYTES / ST::NPP) + 16 * o);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    fetch(blockIdx.x, 0);
+
+    int iter = 0;
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++iter) {
+        fetch(u + gridDim.x, (iter + 1) & 1);                // into the buffer read one unit ago
+        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this unit's pieces have landed
+        __syncthreads();
         // ---- B: the unit's weights, split into BF16 parts (rows up * 16 + rhs, K = 2t, 2t + 1)
+        const C *wb = reinterpret_cast<const C *>(Wst + (iter & 1) * ST::W_BYTES);
         for (int j = tid; j < ST::UP * ST::NPP * RR; j += ST::NT) {
-            const int t = j % RR, rb = (j / RR) % ST::NPP, up = j / (RR * ST::NPP);
+            const int t = j % RR, up = (j / RR) % ST::UP, rb = j / (RR * ST::UP);
             if (rb < nr) {
-                const int64_t pair = u * ST::UP + up;
-                const C w = __ldcg(a.win + (int64_t)(rhs0 + rb) * a.wstride + pair * RR + t);
+                const C w = wb[(rb * ST::UP + up) * RR + t];
                 uint32_t hi, lo;
                 umma::split2(w.x, w.y, hi, lo);
                 const uint32_t off = umma::kmajor_off(up * ST::NPP + rb, 2 * t, ST::LBO, ST::SBO);
@@ -202,7 +230,7 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
                         C z;
                         z.x = c ? recv[j] : v[j];
                         z.y = c ? v[4 + j] : recv[j];
-                        wo[(int64_t)(rhs0 + rb) * a.wstride] = z;
+                        __stcs(wo + (int64_t)(rhs0 + rb) * a.wstride, z);
                     }
                 }
             }
@@ -210,6 +238,7 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
         umma::fence_before_sync();
         __syncthreads();
     }
+    asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the kernel
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) umma::dealloc(tmem, ST::TMEM_COLS);
