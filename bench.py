@@ -96,6 +96,9 @@ def parse():
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default tile schedules")
     ap.add_argument("--no-tables", action="store_true", help="skip the phase-table variant")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="default workload: skip the 48-problem batch record (FP32, BF16x3, FP64 forms)")
+    ap.add_argument("--batch-fp64-steps", type=int, default=1, help="timed FP64 steps of that batch record")
     return ap.parse_args()
 
 
@@ -462,6 +465,13 @@ def run_ours(args, rank, world, local_rank):
         cpu = cpu_sample(spec, g_np[0])
 
     plan.close()
+
+    # ---- the 48-problem hyperbolic Radon batch (many right-hand sides, uneven N): FP32 and
+    # BF16x3 multi-RHS forms against the FP64 GPU butterfly of the same batch (default schedules)
+    batched = None
+    if args.workload == "genradon2d" and not args.L and not args.no_batched:
+        batched = batch_eval(args, rank, world, dev, min(args.steps, 5), args.warmup, False, args.batch_fp64_steps,
+                             not args.no_accuracy)
     if rank != 0:
         return None
     csize = 8 if prec != "fp64" else 16
@@ -472,125 +482,248 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic",
             "config": {"workload": spec.name, "d": spec.d, "N": spec.N, "q": spec.q, "r": spec.r,
                        "phase": spec.phase, "precision": prec, "nrhs": nrhs, "switch_level": spec.switch_level,
+                       "arithmetic": {"fp64": "complex128 weights, FP64 phase and sincos",
+                                      "mixed": "complex64 weights, FP32 interpolation; Phi in double-float FP32 (>= 44 "
+                                               "bits) reduced mod 1, polynomial FP32 sincos",
+                                      "mixed_sfu": "as mixed, sin/cos from the special-function unit",
+                                      "bf16x3": "as mixed; with several RHS the switch on the tensor cores, BF16x3 "
+                                                "products with FP32 accumulation"}[prec],
                        "passes": len(passes), "fuse_levels": plan_fuse(passes),
                        "schedule": sched,
                        "autotuned_ms": tuned,
                        "l2": (f"no flush: each step streams {weight_gb:.1f} GB of weights through the 129 MB L2"
                               if weight_gb > 0.2 else "no flush: the whole working set is L2-resident (small case)"),
                        "parallelism": f"replicas x{world}"},
-            "roofline": roofline, "fp64_gpu": fp64, "sfu_sincos": sfu, "phase_tables": tables, "accuracy": acc, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "fp64_gpu": fp64, "sfu_sincos": sfu, "phase_tables": tables, "accuracy": acc,
+            "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * len(passes), "clocks": clocks}
     return line
 
 
-def run_batched(args, rank, world, local_rank):
-    """48 hyperbolic Radon problems (16 each of N = 128, 256, 512; 1..16 RHS each, drawn from the
-    seed) applied by one persistent kernel launch per step (bf_batch_apply), captured once in a
-    CUDA graph and replayed; the same problems as one launch per pass (bf_apply_batched) are
-    timed beside it.
-    Under torchrun the problems are dealt round-robin to the ranks (independent problems,
-    no exchange); value = all ranks' points*RHS / max time."""
+def batch_eval(args, rank, world, dev, steps, warmup, autotune, fp64_steps, accuracy):
+    """The 48 hyperbolic Radon problems (16 each of N = 128, 256, 512; 1..16 RHS each, drawn
+    from the seed), q = 5, in four forms on the same inputs:
+      mixed_per_pass   FP32 multi-RHS kernels, one launch per pass of every problem (bf_apply_batched)
+      mixed_persistent the same kernels as one persistent launch per step (bf_batch_apply)
+      bf16x3_per_pass  the switch on the tensor cores (BF_PREC_BF16X3), one launch per pass
+      fp64             the plain FP64 GPU butterfly (complex128), one launch per pass
+    The first three are captured once in a CUDA graph and replayed; timed with CUDA events on
+    the launching stream (max over ranks).  Under torchrun the problems are dealt round-robin
+    to the ranks (independent problems, no exchange).  Accuracy (rank 0): the first problem of
+    each N against the FP64 oracle butterfly (all outputs at N = 128, one level-m target box
+    otherwise) and, on 32 targets of that box, against the direct sum."""
     import numpy as np
     import torch
     from paper_1305_4650_gb300 import bf, workloads as wl
     if world > 1:
         import torch.distributed as dist
-    dev = torch.device("cuda", local_rank)
-    torch.cuda.set_device(dev)
-    probs, rng = wl.hypradon_batch()
+    probs, _ = wl.hypradon_batch()
     mine = [(i, s, k) for i, (s, k) in enumerate(probs) if i % world == rank]
-    plans, gs, fs, nr = [], [], [], []
-    for i, spec, k in mine:
-        p = bf.Plan.from_spec(spec, max_nrhs=k, precision="mixed")
-        if not args.no_autotune:
-            p.autotune(k, reps=2)                            # plan time, not timed
-        g = torch.from_numpy(wl.source_values(spec, k, np.complex64, seed=spec.seed + i)).to(dev)
-        plans.append(p)
-        gs.append(g)
-        fs.append(torch.empty_like(g))
-        nr.append(k)
-    pts_rhs_local = sum(s.npts * k for _, s, k in mine)
+    nr = [k for _, _, k in mine]
+    gs = [torch.from_numpy(wl.source_values(s, k, np.complex64, seed=s.seed + i)).to(dev) for i, s, k in mine]
     pts_rhs = sum(s.npts * k for s, k in probs)
-    batch = bf.Batch(plans, nr)
-    binfo = batch.info()
     stream = torch.cuda.current_stream()
+    samples = {}                                          # N -> index into mine (first problem of each N)
+    for j, (_, s, _) in enumerate(mine):
+        samples.setdefault(s.N, j)
 
-    def timed_graph(fn):
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            for _ in range(2):                               # kernel attributes set before capture
-                fn(side)
-        torch.cuda.current_stream().wait_stream(side)
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            fn(None)
-        for _ in range(args.warmup):
-            graph.replay()
+    def max_over_ranks(t):
+        if world == 1:
+            return t
+        tt = torch.tensor([t], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        return float(tt.item())
+
+    def timed(fn, graph=True, n=steps, w=warmup):
+        if graph:
+            side = torch.cuda.Stream()
+            side.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(side):
+                for _ in range(2):                        # kernel attributes set before capture
+                    fn(side)
+            torch.cuda.current_stream().wait_stream(side)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                fn(None)
+            run = g.replay
+        else:
+            run = lambda: fn(None)
+        for _ in range(w):
+            run()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with Clocks(local_rank) as clk:
+        with Clocks(dev.index) as clk:
             if world > 1:
                 dist.barrier()
             torch.cuda.synchronize()
             e0.record(stream)
-            for _ in range(args.steps):
-                graph.replay()
+            for _ in range(n):
+                run()
             e1.record(stream)
             torch.cuda.synchronize()
             if world > 1:
                 dist.barrier()
-        t = e0.elapsed_time(e1) / args.steps
-        if world > 1:
-            tt = torch.tensor([t], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
-        return t, clk.summary()
+        return max_over_ranks(e0.elapsed_time(e1) / n), clk.summary()
 
-    # headline: one persistent launch per step; comparison: one launch per pass of every problem
-    ms, clocks = timed_graph(lambda st: batch.apply(gs, fs, stream=st))
-    timed_out = batch.status()
+    def make(prec):
+        ps = []
+        for (_, s, k) in mine:
+            p = bf.Plan.from_spec(s, max_nrhs=k, precision=prec)
+            if autotune and prec != "fp64":
+                p.autotune(k, reps=2)                     # plan time, not timed
+            ps.append(p)
+        return ps
+
+    forms, outs, launches = {}, {}, {}
+    # FP32 multi-RHS: per-pass graph and the persistent kernel
+    plans = make("mixed")
+    fs = [torch.empty_like(g) for g in gs]
+    ms, clk = timed(lambda st: bf.apply_batched(plans, gs, fs, nr, stream=st))
+    forms["mixed_per_pass"] = {"ms_per_step": round(ms, 3), "value": pts_rhs / (ms * 1e-3), "clocks": clk,
+                               "launches_per_step": sum(p.launches(k) for p, k in zip(plans, nr))}
+    outs["mixed"] = [fs[j].cpu().numpy() for j in samples.values()]
+    batch = bf.Batch(plans, nr)
+    binfo = batch.info()
+    ms, clk = timed(lambda st: batch.apply(gs, fs, stream=st))
     waits = batch.wait_stats()
-    ms_seq, _ = timed_graph(lambda st: bf.apply_batched(plans, gs, fs, nr, stream=st))
-    batch.apply(gs, fs)
-    torch.cuda.synchronize()
-    launches = 1
-    seq_launches = sum(p.launches(k) for p, k in zip(plans, nr))
-    weight_gb = sum(2 * (p.launches(k) - 1) * s.npts * s.r * 8 * k for p, (_, s, k) in zip(plans, mine)) / 1e9
-    acc = None
-    if rank == 0 and not args.no_accuracy:
-        # problem 0 (N = 128) against the oracle butterfly, all outputs, every RHS
-        import oracle
-        i0, s0, k0 = mine[0]
-        P = oracle.Problem(**s0.oracle_kwargs())
-        ref = oracle.butterfly(P, gs[0].cpu().numpy().astype(np.complex128))
-        out = fs[0].cpu().numpy()
-        acc = {"rel_l2_vs_oracle_butterfly": float(np.linalg.norm(out - ref) / np.linalg.norm(ref)),
-               "sample": f"problem {i0} (N={s0.N}, {k0} RHS), all outputs"}
+    forms["mixed_persistent"] = {"ms_per_step": round(ms, 3), "value": pts_rhs / (ms * 1e-3), "clocks": clk,
+                                 "launches_per_step": 1, "work_units": binfo["units"], "jobs": binfo["jobs"],
+                                 "ctas": binfo["grid"], "wait_timed_out": batch.status(),
+                                 "dependency_waits": waits["waits"]}
     batch.close()
+    big = max((j for j in range(len(mine)) if mine[j][1].N == 512), key=lambda j: nr[j], default=None)
     for p in plans:
         p.close()
+    # BF16x3: the switch on the tensor cores
+    plans = make("bf16x3")
+    ms, clk = timed(lambda st: bf.apply_batched(plans, gs, fs, nr, stream=st))
+    forms["bf16x3_per_pass"] = {"ms_per_step": round(ms, 3), "value": pts_rhs / (ms * 1e-3), "clocks": clk,
+                                "launches_per_step": sum(p.launches(k) for p, k in zip(plans, nr)),
+                                "tc_wait_timed_out": any(p.table_info()["timed_out"] for p in plans)}
+    outs["bf16x3"] = [fs[j].cpu().numpy() for j in samples.values()]
+    # per-pass times of the largest N = 512 problem, both precisions (events between launches)
+    roof = None
+    if big is not None:
+        roof = {}
+        for prec in ("mixed", "bf16x3"):
+            p = plans[big] if prec == "bf16x3" else bf.Plan.from_spec(mine[big][1], max_nrhs=nr[big], precision="mixed")
+            if prec == "mixed" and autotune:
+                p.autotune(nr[big], reps=2)
+            roof[prec] = pass_roofline(p, mine[big][1], nr[big], gs[big], fs[big], stream, dev, steps)
+            if prec == "mixed":
+                p.close()
+        roof["problem"] = f"N=512, {nr[big]} RHS"
+    for p in plans:
+        p.close()
+    del fs
+    # FP64 GPU butterfly of the same batch
+    if fp64_steps > 0:
+        plans = make("fp64")
+        g64 = [g.to(torch.complex128) for g in gs]
+        f64 = [torch.empty_like(g) for g in g64]
+        ms, clk = timed(lambda st: bf.apply_batched(plans, g64, f64, nr, stream=st), graph=False, n=fp64_steps, w=1)
+        forms["fp64_per_pass"] = {"ms_per_step": round(ms, 3), "value": pts_rhs / (ms * 1e-3), "clocks": clk,
+                                  "steps": fp64_steps}
+        outs["fp64"] = [f64[j].cpu().numpy() for j in samples.values()]
+        for p in plans:
+            p.close()
+        del g64, f64
+    acc = None
+    if rank == 0 and accuracy:
+        import oracle
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        acc = {}
+        for n_i, (N, j) in enumerate(samples.items()):
+            i0, s0, k0 = mine[j]
+            P = oracle.Problem(**s0.oracle_kwargs())
+            g0 = gs[j].cpu().numpy().astype(np.complex128)
+            lvl = s0.switch_level
+            box = (1 << (2 * lvl)) // 3
+            tg = np.arange(s0.npts) if N == 128 else oracle.restricted_targets(P, lvl, box)
+            rhs = list(range(k0)) if N == 128 else [0]
+            ref = [oracle.butterfly(P, g0[r]) if N == 128 else oracle.butterfly(P, g0[r], restrict=(lvl, box))
+                   for r in rhs]
+            samp = tg[:: max(1, len(tg) // 32)][:32]
+            direct = oracle.direct_sum(P, g0[0], targets=samp)
+            rec = {"problem": i0, "nrhs": k0,
+                   "compared": "all outputs, every RHS" if N == 128 else f"level-{lvl} target box {box}, RHS 0",
+                   "oracle_vs_direct_sum": rel(ref[0][samp], direct)}
+            for arm, o in outs.items():
+                out = o[n_i]
+                rec[arm] = {"rel_l2_vs_oracle_butterfly": max(rel(out[r][tg], ref[x][tg]) for x, r in enumerate(rhs)),
+                            "rel_l2_vs_direct_sum": rel(out[0][samp], direct)}
+            acc[f"N{N}"] = rec
+    fast = min(("mixed_per_pass", "mixed_persistent", "bf16x3_per_pass"), key=lambda f: forms[f]["ms_per_step"])
+    rec = {"workload": "hypradon48_q5", "problems": len(probs), "N": [128, 256, 512],
+           "nrhs_total": int(sum(k for _, k in probs)), "points_rhs": pts_rhs,
+           "value": forms[fast]["value"], "unit": UNIT, "ms_per_step": forms[fast]["ms_per_step"], "form": fast,
+           "forms": forms, "roofline": roof, "accuracy": acc,
+           "schedules": "autotuned" if autotune else "default"}
+    if "fp64_per_pass" in forms:
+        rec["speedup_over_fp64"] = round(forms["fp64_per_pass"]["ms_per_step"] / forms[fast]["ms_per_step"], 2)
+        rec["speedup_mixed_over_fp64"] = round(forms["fp64_per_pass"]["ms_per_step"] /
+                                               forms["mixed_per_pass"]["ms_per_step"], 2)
+    return rec
+
+
+def pass_roofline(plan, spec, nrhs, g, f, stream, dev, steps):
+    """Per-pass device times of one apply (events between the launches on the launching
+    stream) and the dominant pass against the FP32-lane peak: algorithmic FP32-pipe work
+    (phases, interpolation, modulation; the switch's MACs too unless they run on the tensor
+    cores) over its time."""
+    import torch
+    passes = plan.passes(nrhs)
+    sptr = stream.cuda_stream
+    for i in range(len(passes)):
+        plan.apply_pass(i, g.data_ptr(), f.data_ptr(), nrhs, sptr)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(passes) + 1)]
+    tp = [0.0] * len(passes)
+    for _ in range(steps):
+        evs[0].record(stream)
+        for i in range(len(passes)):
+            plan.apply_pass(i, g.data_ptr(), f.data_ptr(), nrhs, sptr)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        for i in range(len(passes)):
+            tp[i] += evs[i].elapsed_time(evs[i + 1]) / steps
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2.07e9 / 1e12
+
+    def alu_ops(ps):
+        w = pass_work(spec, ps, nrhs)
+        if ps["kind"] == "switch_tc":
+            w = dict(w, cmacs=0)
+        return work_ops(spec, w)
+
+    dom = max(range(len(passes)), key=lambda i: tp[i])
+    ops = alu_ops(passes[dom])
+    return {"bound": "alu", "pass_ms": [round(t, 4) for t in tp],
+            "schedule": [(p["kind"] if p["kind"] != "switch_tc" else "sw") + str(p["k"]) for p in passes],
+            "dominant": dom, "achieved": round(ops / (tp[dom] * 1e-3) / 1e12, 3), "peak": round(peak, 2),
+            "unit": "Tops/s", "frac": round(ops / (tp[dom] * 1e-3) / 1e12 / peak, 4),
+            "apply_frac": round(sum(alu_ops(p) for p in passes) / (sum(tp) * 1e-3) / 1e12 / peak, 4)}
+
+
+def run_batched(args, rank, world, local_rank):
+    """The 48-problem hyperbolic Radon batch as the line's workload (see batch_eval)."""
+    import torch
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    rec = batch_eval(args, rank, world, dev, args.steps, args.warmup, not args.no_autotune, args.fp64_steps,
+                     not args.no_accuracy)
     if rank != 0:
         return None
-    persistent = {"ms_per_step": round(ms, 3), "value": pts_rhs / (ms * 1e-3), "launches_per_step": 1,
-                  "work_units": binfo["units"], "jobs": binfo["jobs"], "ctas": binfo["grid"],
-                  "wait_timed_out": timed_out, "dependency_wait_cta_ms": round(waits["wait_ms_total"], 3),
-                  "dependency_waits": waits["waits"]}
-    per_pass = {"ms_per_step": round(ms_seq, 3), "value": pts_rhs / (ms_seq * 1e-3), "launches_per_step": seq_launches}
-    # the headline is the faster of the two launch forms; both are reported
-    best, how = (ms, "one persistent kernel per step") if ms <= ms_seq else (ms_seq, "one kernel per pass of every problem")
-    return {"metric": METRIC, "value": pts_rhs / (best * 1e-3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": round(best, 3), "higher_is_better": True, "scaling": "weak",
+    fast = rec["forms"][rec["form"]]
+    return {"metric": METRIC, "value": rec["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-            "config": {"workload": "hypradon48_q5", "problems": len(probs), "N": [128, 256, 512],
-                       "nrhs_total": int(sum(nr)) if world == 1 else None, "points_rhs": pts_rhs,
-                       "points_rhs_rank0": pts_rhs_local, "precision": "mixed",
-                       "launch": how + " (CUDA graph)",
-                       "l2": f"no flush: each step streams {weight_gb:.0f} GB of weights through the 129 MB L2",
+            "config": {"workload": "hypradon48_q5", "problems": rec["problems"], "N": rec["N"],
+                       "nrhs_total": rec["nrhs_total"], "points_rhs": rec["points_rhs"], "form": rec["form"],
+                       "precision": "bf16x3 (tensor-core switch) or mixed, the faster",
+                       "l2": "no flush: each step streams ~20 GB of weights through the 129 MB L2",
                        "parallelism": f"problems round-robin over {world} rank(s)"},
-            "persistent_launch": persistent, "per_pass_launches": per_pass,
-            "accuracy": acc, "gpu_launches": args.steps * (1 if best == ms else seq_launches), "clocks": clocks}
+            "batched": rec, "gpu_launches": args.steps * fast["launches_per_step"], "clocks": fast["clocks"]}
 
 
 def run_cg(args, rank, world, local_rank):

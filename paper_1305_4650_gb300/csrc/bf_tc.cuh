@@ -12,7 +12,10 @@
 //     B[rhs][(t, c')]     the weights of one right-hand side, as stored (re, im, re, ...),
 // so D[2s][rhs] = Re(E w)_s and D[2s + 1][rhs] = Im(E w)_s.  Two pairs share one MMA of
 // M = 128 rows (64 per pair, 2r of them used) and N = 32 columns (16 right-hand sides
-// per pair); the off-diagonal blocks of D are computed and ignored.
+// per pair); the off-diagonal blocks of D are computed and ignored.  Along K the source
+// nodes t = t_0 + q t_1 are grouped by t_1: the 2q values of digit t_1 fill a slot of 8 or
+// 16 elements (one or two 16-byte pieces of a row), so each evaluating thread writes whole
+// pieces; the rest of a slot stays zero.
 //
 // Precision (BF16x3): every FP32 operand x is split into BF16 parts hi = bf16(x) and
 // lo = bf16(x - hi) (16 significant bits together), and D accumulates hi.hi + hi.lo +
@@ -44,7 +47,9 @@ struct SwTC {
     static constexpr int ROWS = 64;                         // A rows per pair (2 r used)
     static constexpr int NPP = 16;                          // right-hand sides (B rows) per pair
     static constexpr int M = UP * ROWS, N = UP * NPP;       // 128 x 32 accumulator
-    static constexpr int KP = (2 * RR + 15) / 16 * 16;      // K = (t, re/im), padded to the MMA's K step
+    static constexpr int SLOT = 2 * Q <= 8 ? 8 : 16;        // K elements per source digit t_1
+    static constexpr int PIECES = SLOT / 8;                 // 16-byte pieces per slot and row
+    static constexpr int KP = (SLOT * Q + 15) / 16 * 16;    // K, padded to the MMA's K step
     static constexpr int NKS = KP / 16;                     // K steps
     static constexpr uint32_t LBO = 128;                    // core matrices along K: adjacent
     static constexpr uint32_t SBO = (KP / 8) * 128;         // 8-row groups
@@ -54,11 +59,24 @@ struct SwTC {
     static constexpr int TMEM_COLS = 32;
     static constexpr uint32_t W_BYTES = NPP * UP * RR * 8;  // a unit's weights as stored (complex64)
     static constexpr int W_CHUNKS = W_BYTES / 16;           // 16-byte copies per unit
-    static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + 2 * (size_t)W_BYTES + 64;
-    static_assert((UP * RR * 8) % 16 == 0, "a unit's weights per right-hand side are whole 16-byte pieces");
+    static constexpr uint32_t T_BYTES = UP * RR * 32;       // target features of the unit's nodes
+    static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + W_BYTES + T_BYTES + 64;
     static_assert(2 * RR <= ROWS, "the tensor-core switch holds r <= 32");
-    static_assert(UP * RR * Q <= NT, "one phase item per thread");
+    static_assert(UP * RR * Q <= NT && UP * NPP * Q + UP * RR <= NT, "one item per thread");
+    static_assert((UP * RR * 8) % 16 == 0, "a unit's weights per right-hand side are whole 16-byte pieces");
 };
+
+// BF16 parts of a complex number e = x + iy for the two A rows of a target node: row 2s
+// takes (x, -y), row 2s + 1 takes (y, x), packed as stored along K (first value low)
+__device__ __forceinline__ void split_rows(float x, float y, uint32_t &h0, uint32_t &l0, uint32_t &h1, uint32_t &l1)
+{
+    uint32_t h, l;
+    umma::split2(x, y, h, l);               // (x, y)
+    h0 = h ^ 0x80000000u;                   // (x, -y): negate the upper value
+    l0 = l ^ 0x80000000u;
+    h1 = __byte_perm(h, 0u, 0x1032);        // (y, x): swap the halves
+    l1 = __byte_perm(l, 0u, 0x1032);
+}
 
 // Switch pass: reads the level-m weights a.win ([rhs][pair][r], pair = A 2^{2(L-m)} + B),
 // writes the switched weights to a.wout in the same layout.  Right-hand sides
@@ -75,16 +93,19 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
     using C = typename P::C;
     using PH = Ph<P, 2, K>;
     using PH2 = Ph2<P, 2, K>;
+    using TT = typename PH::T;
+    static_assert(sizeof(TT) <= 32, "target features fit their shared-memory slot");
     constexpr int RR = ST::RR, D = 2;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *Ah = smem_raw, *Al = Ah + ST::A_BYTES, *Bh = Al + ST::A_BYTES, *Bl = Bh + ST::B_BYTES;
-    unsigned char *Wst = Bl + ST::B_BYTES;   // two buffers of a unit's weights
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Wst + 2 * ST::W_BYTES);
+    unsigned char *Wst = Bl + ST::B_BYTES;                          // the unit's weights
+    TT *Ts = reinterpret_cast<TT *>(Wst + ST::W_BYTES);             // target features, [pair][s]
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Wst + ST::W_BYTES + ST::T_BYTES);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *sfail = reinterpret_cast<int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    // operands start at zero: the padding rows and columns are never written again
+    // operands start at zero: the padding rows and slots are never written again
     {
         uint4 *z = reinterpret_cast<uint4 *>(smem_raw);
         const int n16 = (int)((2 * ST::A_BYTES + 2 * ST::B_BYTES) / 16);
@@ -110,50 +131,71 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
     const uint32_t idesc = umma::idesc_bf16_f32(ST::M, ST::N);
     unsigned parity = 0;
 
-    // weights of unit v into buffer b: per right-hand side rb < nr, W_BYTES / NPP bytes in
-    // 16-byte pieces; one commit group per call (empty past the last unit)
-    auto fetch = [&](int64_t v, int b) {
+    // weights of unit v into the staging buffer: per right-hand side rb < nr, the two pairs'
+    // 2r complex numbers in 16-byte pieces; one commit group per call
+    auto fetch = [&](int64_t v) {
         constexpr int per_rhs = ST::W_CHUNKS / ST::NPP;
         if (v < nunits) {
             for (int c = tid; c < nr * per_rhs; c += ST::NT) {
                 const int rb = c / per_rhs, o = c - rb * per_rhs;
                 const char *src =
                     reinterpret_cast<const char *>(a.win + (int64_t)(rhs0 + rb) * a.wstride + v * ST::UP * RR) + 16 * o;
-                const uint32_t dst = umma::saddr(Wst + b * ST::W_BYTES + rb * (ST::W_BYTES / ST::NPP) + 16 * o);
+                const uint32_t dst = umma::saddr(Wst + rb * (ST::W_BYTES / ST::NPP) + 16 * o);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
             }
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    fetch(blockIdx.x, 0);
+    // slot th of row `row` in a part: PIECES 16-byte pieces (2q values, then zeros)
+    auto put_slot = [&](unsigned char *base, int row, int th, const uint32_t *w) {
+#pragma unroll
+        for (int pc = 0; pc < ST::PIECES; ++pc) {
+            uint4 v;
+            v.x = 4 * pc + 0 < Q ? w[4 * pc + 0] : 0u;
+            v.y = 4 * pc + 1 < Q ? w[4 * pc + 1] : 0u;
+            v.z = 4 * pc + 2 < Q ? w[4 * pc + 2] : 0u;
+            v.w = 4 * pc + 3 < Q ? w[4 * pc + 3] : 0u;
+            *reinterpret_cast<uint4 *>(base + umma::kmajor_off(row, ST::SLOT * th + 8 * pc, ST::LBO, ST::SBO)) = v;
+        }
+    };
+    fetch(blockIdx.x);
 
-    int iter = 0;
-    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x, ++iter) {
-        fetch(u + gridDim.x, (iter + 1) & 1);                // into the buffer read one unit ago
-        asm volatile("cp.async.wait_group 1;" ::: "memory");  // this unit's pieces have landed
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        asm volatile("cp.async.wait_group 0;" ::: "memory");   // the unit's weights have landed
         __syncthreads();
-        // ---- B: the unit's weights, split into BF16 parts (rows up * 16 + rhs, K = 2t, 2t + 1)
-        const C *wb = reinterpret_cast<const C *>(Wst + (iter & 1) * ST::W_BYTES);
-        for (int j = tid; j < ST::UP * ST::NPP * RR; j += ST::NT) {
-            const int t = j % RR, up = (j / RR) % ST::UP, rb = j / (RR * ST::UP);
-            if (rb < nr) {
-                const C w = wb[(rb * ST::UP + up) * RR + t];
-                uint32_t hi, lo;
-                umma::split2(w.x, w.y, hi, lo);
-                const uint32_t off = umma::kmajor_off(up * ST::NPP + rb, 2 * t, ST::LBO, ST::SBO);
-                *reinterpret_cast<uint32_t *>(Bh + off) = hi;
-                *reinterpret_cast<uint32_t *>(Bl + off) = lo;
+        // ---- B: items (rhs, pair, t_1): q weights, split into BF16 parts, one slot each
+        {
+            const int rb = tid % ST::NPP, up = (tid / ST::NPP) % ST::UP, th = tid / (ST::NPP * ST::UP);
+            if (th < Q && rb < nr) {
+                const C *w = reinterpret_cast<const C *>(Wst) + (rb * ST::UP + up) * RR + Q * th;
+                uint32_t hi[Q], lo[Q];
+#pragma unroll
+                for (int t0 = 0; t0 < Q; ++t0) umma::split2(w[t0].x, w[t0].y, hi[t0], lo[t0]);
+                put_slot(Bh, up * ST::NPP + rb, th, hi);
+                put_slot(Bl, up * ST::NPP + rb, th, lo);
             }
         }
-        // ---- A: phase items (pair, s, t_1), q factors each, as the CUDA-core multi-RHS switch
-        for (int it = tid; it < ST::UP * RR * Q; it += ST::NT) {
-            const int th = it % Q, s = (it / Q) % RR, up = it / (Q * RR);
+        // ---- target features of the unit's nodes (pair, s), once per node, by the threads
+        // that have no weight item
+        if (tid >= ST::UP * ST::NPP * Q && tid < ST::UP * ST::NPP * Q + ST::UP * RR) {
+            const int it = tid - ST::UP * ST::NPP * Q;
+            const int s = it % RR, up = it / RR;
             const uint32_t I = (uint32_t)(u * ST::UP + up);
-            int ca[DMAX], cb[DMAX];
+            int ca[DMAX];
             morton_decode<D>(I >> shB, l, ca);
-            morton_decode<D>(I & maskB, L - l, cb);
             const int sk[DMAX] = {s % Q, s / Q, 0};
-            const typename PH::T tS = tpoint<P, D, Q, K>(a, l, ca, sk);
+            Ts[it] = tpoint<P, D, Q, K>(a, l, ca, sk);
+        }
+        __syncthreads();
+        fetch(u + gridDim.x);   // the staging buffer is free again: the next unit's copies overlap this one
+        // ---- A: items (pair, t_1, s), s fastest: q factors e^{2 pi i Phi(x_s^A, y_t^B)} each,
+        // evaluated as in the CUDA-core multi-RHS switch, split into the rows 2s, 2s + 1 of slot t_1
+        for (int it = tid; it < ST::UP * RR * Q; it += ST::NT) {
+            const int s = it % RR, th = (it / RR) % Q, up = it / (RR * Q);
+            const uint32_t I = (uint32_t)(u * ST::UP + up);
+            int cb[DMAX];
+            morton_decode<D>(I & maskB, L - l, cb);
+            const TT tS = Ts[up * RR + s];
             C ev[Q];
             const typename PH2::T tS2 = PH2::dup(tS);
             const typename P::SE e1 = sget<P, Q>(a, 1, l, cb[1], th);
@@ -166,20 +208,14 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
             if constexpr (Q & 1)
                 ev[Q - 1] = expphase_part<P, D, K>(a, tS, PH::add(PH::part(tS, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0),
                                                                  PH2::lane0(hp)));
-            const int r0 = up * ST::ROWS + 2 * s;
+            uint32_t h0[Q], l0[Q], h1[Q], l1[Q];
 #pragma unroll
-            for (int t0 = 0; t0 < Q; ++t0) {
-                const int k = 2 * (t0 + Q * th);
-                uint32_t hi, lo;
-                umma::split2(ev[t0].x, -ev[t0].y, hi, lo);
-                uint32_t off = umma::kmajor_off(r0, k, ST::LBO, ST::SBO);
-                *reinterpret_cast<uint32_t *>(Ah + off) = hi;
-                *reinterpret_cast<uint32_t *>(Al + off) = lo;
-                umma::split2(ev[t0].y, ev[t0].x, hi, lo);
-                off = umma::kmajor_off(r0 + 1, k, ST::LBO, ST::SBO);
-                *reinterpret_cast<uint32_t *>(Ah + off) = hi;
-                *reinterpret_cast<uint32_t *>(Al + off) = lo;
-            }
+            for (int t0 = 0; t0 < Q; ++t0) split_rows(ev[t0].x, ev[t0].y, h0[t0], l0[t0], h1[t0], l1[t0]);
+            const int r0 = up * ST::ROWS + 2 * s;
+            put_slot(Ah, r0, th, h0);
+            put_slot(Al, r0, th, l0);
+            put_slot(Ah, r0 + 1, th, h1);
+            put_slot(Al, r0 + 1, th, l1);
         }
         umma::fence_smem_to_async();
         __syncthreads();
@@ -235,8 +271,8 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
                 }
             }
         }
+        // the next unit's first barrier orders these tensor-memory reads before its MMAs
         umma::fence_before_sync();
-        __syncthreads();
     }
     asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the kernel
     umma::fence_before_sync();
