@@ -27,6 +27,12 @@
  *
  * Threads.  A plan owns one workspace; applies on one plan must be ordered on
  * the same stream (or otherwise serialised).  Different plans are independent.
+ * An apply (bf_apply, bf_apply_adjoint, bf_apply_host, bf_apply_pass) issued on a
+ * stream other than that of the plan's previous apply, while that apply has not
+ * completed, returns BF_ERR_UNSUPPORTED and queues nothing (the plan records an
+ * event after each apply for this check).  Applies captured into a CUDA graph are not
+ * checked: the order of the graph's launches is the caller's.  Persistent batches
+ * (bf_batch_apply) use their plans' workspaces and are not checked either.
  *
  * Errors.  Invalid arguments return BF_ERR_INVALID_ARG and write nothing.
  */
@@ -293,9 +299,12 @@ bf_status bf_selfcheck_umma(int split, double *max_rel_err, int *timed_out);
  * let a library do it -- for example a host application that hands the GPU to
  * a fixed memory pool and forbids allocations after start-up, or code running
  * where an allocation could block or fail mid-stream.  Arguments are those of
- * bf_plan_create followed by those of bf_apply; the result equals bf_apply's on
- * a plan built with the same arguments, up to the last bits of the
- * geometry tables (they are built on the device here).
+ * bf_plan_create followed by those of bf_apply.  It launches the passes of the
+ * default schedule of a plan built with the same arguments (before any
+ * bf_plan_autotune), with the single-RHS kernels for every nrhs; for nrhs = 1 the
+ * result equals that plan's bf_apply up to the last bits of the geometry tables
+ * (they are built on the device here), for nrhs >= 2 (where bf_apply runs the
+ * multi-RHS kernels) up to FP32 rounding order.  BF_PREC_BF16X3 is not accepted.
  *
  * Scratch.  The geometry tables and the two weight buffers live in one static
  * device array of BF_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the
@@ -311,7 +320,10 @@ bf_status bf_selfcheck_umma(int split, double *max_rel_err, int *timed_out);
  *
  * Set-up.  The first call on each device (with that device current) looks up
  * the array's device address with cudaGetSymbolAddress; make that first call
- * before any stream capture begins.  Asynchronous on `stream` like bf_apply. */
+ * before any stream capture begins.  The address is kept for the life of the
+ * process: it does not survive cudaDeviceReset (or anything else that destroys
+ * the device's primary context), so do not reset a device between calls.
+ * Asynchronous on `stream` like bf_apply. */
 #define BF_NOALLOC_SCRATCH_BYTES (16u << 20)
 bf_status bf_apply_noalloc(int d, int64_t N, int q, bf_phase_kind phase, const bf_params *p,
                            const void *g_dev, void *f_dev, int nrhs, void *stream);

@@ -60,6 +60,8 @@ struct bf_plan_s {
     std::vector<Pass> passes_adj;  // schedule whose reverse is the adjoint (fits the row caches)
     const bfl::PassFns *fns = nullptr;
     int last_cuda = 0;
+    cudaEvent_t busy_ev = nullptr;     // recorded after the last apply outside a stream capture
+    cudaStream_t busy_stream = nullptr;   // the stream it was recorded on
 };
 
 struct bf_batch_s {
@@ -106,6 +108,35 @@ double lagrange1(int q, const double *z, int t, double xi)
     for (int k = 0; k < q; ++k)
         if (k != t) v *= (xi - z[k]) / (z[t] - z[k]);
     return v;
+}
+
+bf_status cuda_fail(bf_plan p, cudaError_t e);
+
+// A plan owns one workspace, so an apply issued on another stream while the plan's last
+// apply is still running would race on it: that returns BF_ERR_UNSUPPORTED.  Applies
+// captured into a CUDA graph are not checked (the graph's launches are the caller's order).
+bf_status stream_guard(bf_plan p, cudaStream_t s, bool *capturing)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    *capturing = cs != cudaStreamCaptureStatusNone;
+    if (*capturing || !p->busy_ev || p->busy_stream == s) return BF_OK;
+    e = cudaEventQuery(p->busy_ev);
+    if (e == cudaErrorNotReady) return BF_ERR_UNSUPPORTED;
+    if (e != cudaSuccess) return cuda_fail(p, e);
+    return BF_OK;
+}
+
+// after an apply's launches: remember its stream and completion (outside a capture)
+void stream_mark(bf_plan p, cudaStream_t s, bool capturing)
+{
+    if (capturing) return;
+    if (!p->busy_ev && cudaEventCreateWithFlags(&p->busy_ev, cudaEventDisableTiming) != cudaSuccess) {
+        p->busy_ev = nullptr;
+        return;
+    }
+    if (cudaEventRecord(p->busy_ev, s) == cudaSuccess) p->busy_stream = s;
 }
 
 bf_status cuda_fail(bf_plan p, cudaError_t e)
@@ -1226,19 +1257,25 @@ bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
     if ((!g && !(p->points && p->nsrc == 0)) || (!f && !(p->points && p->ntgt == 0))) return BF_ERR_INVALID_ARG;
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool capturing = false;
+    bf_status st = stream_guard(p, s, &capturing);
+    if (st != BF_OK) return st;
     if (p->points) {
-        if (p->prec == BF_PREC_FP64) return run_points<bfk::PF64>(p, g, f, nrhs, s);
-        if (p->prec == BF_PREC_MIXED_SFU) return run_points<bfk::PMIXF>(p, g, f, nrhs, s);
-        return run_points<bfk::PMIX>(p, g, f, nrhs, s);
+        if (p->prec == BF_PREC_FP64) st = run_points<bfk::PF64>(p, g, f, nrhs, s);
+        else if (p->prec == BF_PREC_MIXED_SFU) st = run_points<bfk::PMIXF>(p, g, f, nrhs, s);
+        else st = run_points<bfk::PMIX>(p, g, f, nrhs, s);
+    } else {
+        const int n = (int)schedule_for(p, nrhs).size();
+        if (p->prec == BF_PREC_FP64) st = run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n);
+        else if (use_mr(p, nrhs))
+            st = p->prec == BF_PREC_MIXED_SFU ? run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, 0, n)
+                                              : run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
+        else
+            st = p->prec == BF_PREC_MIXED_SFU ? run_forward<bfk::PMIXF>(p, g, f, nrhs, s, 0, n)
+                                              : run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
     }
-    const int n = (int)schedule_for(p, nrhs).size();
-    if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n);
-    if (p->prec == BF_PREC_MIXED_SFU) {
-        if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, 0, n);
-        return run_forward<bfk::PMIXF>(p, g, f, nrhs, s, 0, n);
-    }
-    if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
-    return run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
+    stream_mark(p, s, capturing);
+    return st;
 }
 
 bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *best_ms)
@@ -1355,13 +1392,18 @@ bf_status bf_apply_pass(bf_plan p, int i, const void *g, void *f, int nrhs, void
     if (!g || !f) return BF_ERR_INVALID_ARG;
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (p->prec == BF_PREC_FP64) return run_forward<bfk::PF64>(p, g, f, nrhs, s, i, i + 1);
-    if (p->prec == BF_PREC_MIXED_SFU) {
-        if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, i, i + 1);
-        return run_forward<bfk::PMIXF>(p, g, f, nrhs, s, i, i + 1);
-    }
-    if (use_mr(p, nrhs)) return run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, i, i + 1);
-    return run_forward<bfk::PMIX>(p, g, f, nrhs, s, i, i + 1);
+    bool capturing = false;
+    bf_status st = stream_guard(p, s, &capturing);
+    if (st != BF_OK) return st;
+    if (p->prec == BF_PREC_FP64) st = run_forward<bfk::PF64>(p, g, f, nrhs, s, i, i + 1);
+    else if (use_mr(p, nrhs))
+        st = p->prec == BF_PREC_MIXED_SFU ? run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, i, i + 1)
+                                          : run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, i, i + 1);
+    else
+        st = p->prec == BF_PREC_MIXED_SFU ? run_forward<bfk::PMIXF>(p, g, f, nrhs, s, i, i + 1)
+                                          : run_forward<bfk::PMIX>(p, g, f, nrhs, s, i, i + 1);
+    stream_mark(p, s, capturing);
+    return st;
 }
 
 bf_status bf_pass_info(bf_plan p, int nrhs, int i, int *kind, int *l0, int *k, int *flags)
@@ -1387,9 +1429,14 @@ bf_status bf_apply_adjoint(bf_plan p, const void *f, void *g, int nrhs, void *st
     if (!g || !f) return BF_ERR_INVALID_ARG;
     if (((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (p->prec == BF_PREC_FP64) return run_adjoint<bfk::PF64>(p, f, g, nrhs, s);
-    if (p->prec == BF_PREC_MIXED_SFU) return run_adjoint<bfk::PMIXF>(p, f, g, nrhs, s);
-    return run_adjoint<bfk::PMIX>(p, f, g, nrhs, s);
+    bool capturing = false;
+    bf_status st = stream_guard(p, s, &capturing);
+    if (st != BF_OK) return st;
+    if (p->prec == BF_PREC_FP64) st = run_adjoint<bfk::PF64>(p, f, g, nrhs, s);
+    else if (p->prec == BF_PREC_MIXED_SFU) st = run_adjoint<bfk::PMIXF>(p, f, g, nrhs, s);
+    else st = run_adjoint<bfk::PMIX>(p, f, g, nrhs, s);
+    stream_mark(p, s, capturing);
+    return st;
 }
 
 bf_status bf_apply_host(bf_plan p, const void *g_host, void *f_host, int nrhs, void *stream)
@@ -1399,15 +1446,18 @@ bf_status bf_apply_host(bf_plan p, const void *g_host, void *f_host, int nrhs, v
     if (nrhs == 0) return BF_OK;
     if (!g_host || !f_host) return BF_ERR_INVALID_ARG;
     const int64_t ng = p->points ? p->nsrc : p->npts, nf = p->points ? p->ntgt : p->npts;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool capturing = false;
+    bf_status st = stream_guard(p, s, &capturing);   // before the staging copy into the workspace
+    if (st != BF_OK) return st;
     cudaError_t e;
     if (!p->gstage) {   // 16 bytes at least, so that empty point sets still get valid pointers
         if ((e = cudaMalloc(&p->gstage, (size_t)p->max_nrhs * ng * p->csize + 16)) != cudaSuccess) return cuda_fail(p, e);
         if ((e = cudaMalloc(&p->fstage, (size_t)p->max_nrhs * nf * p->csize + 16)) != cudaSuccess) return cuda_fail(p, e);
     }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bg = (size_t)nrhs * ng * p->csize, bfo = (size_t)nrhs * nf * p->csize;
     if (bg && (e = cudaMemcpyAsync(p->gstage, g_host, bg, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(p, e);
-    bf_status st = bf_apply(p, p->gstage, p->fstage, nrhs, stream);
+    st = bf_apply(p, p->gstage, p->fstage, nrhs, stream);
     if (st != BF_OK) return st;
     if (bfo && (e = cudaMemcpyAsync(f_host, p->fstage, bfo, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(p, e);
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(p, e);
@@ -1541,6 +1591,7 @@ bf_status bf_destroy(bf_plan p)
     if (p->ptab) cudaFree(p->ptab);
     if (p->ftab) cudaFree(p->ftab);
     if (p->errflag) cudaFree(p->errflag);
+    if (p->busy_ev) cudaEventDestroy(p->busy_ev);
     for (void *m : p->pts_mem) cudaFree(m);
     if (p->gstage) cudaFree(p->gstage);
     if (p->fstage) cudaFree(p->fstage);

@@ -183,8 +183,9 @@ bf_status run(int d, int L, int q, int kind, const bf_params *prm, const void *g
     a.g = static_cast<const typename P::C *>(g);
     a.f = static_cast<typename P::C *>(f);
 
-    // the schedule of bf_plan_create: column passes of <= kmax levels (init first,
-    // switch last), then row passes (final last)
+    // the default schedule of bf_plan_create: column passes of <= kmax levels (init first,
+    // switch last), then row passes (final last); in each run of levels the short pass
+    // (levels mod kmax) comes first
     const int m = prm->switch_level < 0 ? L / 2 : prm->switch_level;
     const int kmax = prm->fuse_levels > 0 && prm->fuse_levels < fns->kmax ? prm->fuse_levels : fns->kmax;
     NaPass ps[kMaxPasses];
@@ -194,17 +195,22 @@ bf_status run(int d, int L, int q, int kind, const bf_params *prm, const void *g
         int T = (int)(cta_pairs >> (d * k));
         ps[np++] = NaPass{row, l0, k, fl, T < 1 ? 1 : T};
     };
+    auto chunk = [&](int left, int total) {
+        const int rem = total % kmax;
+        if (rem && left == total) return rem;
+        return left < kmax ? left : kmax;
+    };
     if (m == 0) {
         add(0, 0, 0, bfk::F_INIT | bfk::F_SWITCH);
     } else {
         for (int l = 0; l < m;) {
-            const int k = (m - l) < kmax ? (m - l) : kmax;
+            const int k = chunk(m - l, m);
             add(0, l, k, (l == 0 ? bfk::F_INIT : 0) | (l + k == m ? bfk::F_SWITCH : 0));
             l += k;
         }
     }
     for (int l = m; l < L;) {
-        const int k = (L - l) < kmax ? (L - l) : kmax;
+        const int k = chunk(L - l, L - m);
         add(1, l, k, l + k == L ? bfk::F_FINAL : 0);
         l += k;
     }

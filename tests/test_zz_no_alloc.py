@@ -76,3 +76,45 @@ def test_noalloc_rejects_problems_beyond_the_static_array(bf):
     assert e.value.code == 1
     torch.cuda.synchronize()
     assert torch.all(f == 3.0)
+
+
+def test_noalloc_against_the_oracle(bf):
+    # directly against the FP64 oracle butterfly (not only through bf_apply), both sincos
+    # variants and FP64
+    import torch
+    import oracle
+    cases = ((wl.genradon2d(L=6), "mixed", np.complex64, TOL["mixed"]),
+             (wl.genradon2d(L=5), "mixed_sfu", np.complex64, TOL["mixed"]),
+             (wl.hypradon(5), "fp64", np.complex128, TOL["fp64"]))
+    for spec, prec, dt, tol in cases:
+        g = torch.from_numpy(wl.source_values(spec, 1, dt, seed=31)).cuda()
+        out = torch.full_like(g, float("nan"))
+        _call(bf, spec, prec, g, out)
+        torch.cuda.synchronize()
+        ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.cpu().numpy()[0].astype(np.complex128))
+        a = out.cpu().numpy()[0]
+        assert np.linalg.norm(a - ref) <= tol * np.linalg.norm(ref), (spec.name, prec)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "mixed_sfu"])
+def test_noalloc_several_rhs(bf, precision):
+    # three right-hand sides (the static array holds 2 x nrhs x N^d x r weights): the
+    # single-RHS kernels with grid_y = nrhs, against the plan's multi-RHS apply (FP32
+    # rounding order) and, per right-hand side, against the oracle
+    import torch
+    import oracle
+    spec = wl.genradon2d(L=6)
+    nrhs = 3
+    g = torch.from_numpy(wl.source_values(spec, nrhs, np.complex64, seed=41)).cuda()
+    plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=precision)
+    ref = plan.apply(g).cpu().numpy()
+    plan.close()
+    out = torch.full_like(g, float("nan"))
+    _call(bf, spec, precision, g, out)
+    torch.cuda.synchronize()
+    a = out.cpu().numpy()
+    P = oracle.Problem(**spec.oracle_kwargs())
+    for j in range(nrhs):
+        assert np.linalg.norm(a[j] - ref[j]) <= 2e-6 * np.linalg.norm(ref[j]), j
+        o = oracle.butterfly(P, g[j].cpu().numpy().astype(np.complex128))
+        assert np.linalg.norm(a[j] - o) <= TOL["mixed"] * np.linalg.norm(o), j
