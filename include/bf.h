@@ -147,6 +147,20 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
  * g and f must not overlap. */
 bf_status bf_apply(bf_plan plan, const void *g_dev, void *f_dev, int nrhs, void *stream);
 
+/* Sharded apply: one rank's part of f = B g when the source domain is split over G =
+ * 2^shard_g ranks (1 <= shard_g <= d; shard_g = 0 is bf_apply), following the distribution of
+ * the product space in Section 2 (Algorithms 2 and 4): rank shard_r owns the source boxes whose
+ * top shard_g Morton bits (dimension 0 in the lowest bit) equal shard_r.  Every merge below the
+ * last level combines the children of one source box, so those passes run the rank's pairs
+ * only (1/G of the work); the last pass runs on every pair with the other ranks' weights read
+ * as zero and writes f_r, this rank's contribution at every target.  Then f = sum over the
+ * ranks of f_r (one all-reduce of nrhs x N^d values), equal to bf_apply's f up to FP32 (FP64)
+ * rounding order.  g: all nrhs x N^d sources (only the rank's are read); f_r: nrhs x N^d.
+ * Each rank holds its own plan (its own GPU).  BF_ERR_UNSUPPORTED for point-set plans and
+ * plans with phase tables; BF_ERR_INVALID_ARG for shard_g > d or shard_r >= 2^shard_g. */
+bf_status bf_apply_shard(bf_plan plan, const void *g_dev, void *f_dev, int nrhs, int shard_g, int shard_r,
+                         void *stream);
+
 /* g = B^H f, the exact conjugate transpose of the approximate operator applied by
  * bf_apply (every step conjugate-transposed, levels in reverse). */
 bf_status bf_apply_adjoint(bf_plan plan, const void *f_dev, void *g_dev, int nrhs, void *stream);

@@ -78,6 +78,7 @@ def load():
         lib.bf_measure_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_measure_phase_rate.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_selfcheck_umma.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        lib.bf_apply_shard.argtypes = [vp, vp, vp, i32, i32, i32, vp]
         lib.bf_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), i32, ctypes.POINTER(vp)]
         lib.bf_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
         lib.bf_batch_status.argtypes = [vp, ctypes.POINTER(i32)]
@@ -193,6 +194,19 @@ class Plan:
         elif self._nrhs(f, self.ntgt) != n:
             raise ValueError("g and f differ in size")
         _check(load().bf_apply(self._h, g.data_ptr(), f.data_ptr(), n, _stream_ptr(stream)), "bf_apply", self._h)
+        return f
+
+    def apply_shard(self, g, shard_g: int, shard_r: int, f=None, stream=None):
+        """f_r: rank shard_r's part of B g when the sources are split over 2^shard_g ranks by the
+        top Morton bits of their leaf boxes (bf_apply_shard); the sum over ranks is B g."""
+        import torch
+        n = self._nrhs(g, self.nsrc)
+        if f is None:
+            f = torch.empty((n, self.ntgt) if g.dim() > 1 else (self.ntgt,), dtype=g.dtype, device=g.device)
+        elif self._nrhs(f, self.ntgt) != n:
+            raise ValueError("g and f differ in size")
+        _check(load().bf_apply_shard(self._h, g.data_ptr(), f.data_ptr(), n, shard_g, shard_r, _stream_ptr(stream)),
+               "bf_apply_shard", self._h)
         return f
 
     def apply_adjoint(self, f, g=None, stream=None):

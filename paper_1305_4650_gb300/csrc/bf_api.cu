@@ -383,13 +383,33 @@ void fill_args(const bf_plan_s *p, bfk::KArgs<P> &a)
     a.wstride = p->npts * p->r;
 }
 
+// Sharded apply (bf_apply_shard), rank sr of 2^sg: every pass but the last runs the rank's
+// tile groups only (mode 1), T capped so that a group never straddles two ranks' source
+// ranges; the last pass runs every tile with the other ranks' inputs read as zero (mode 2).
+// Returns the pass to launch and sets the mode and the launch's CTAs (tile groups).
+Pass shard_pass(const bf_plan_s *p, Pass ps, bool last, int sg, int *mode, int64_t *ctas)
+{
+    *mode = 0;
+    if (sg > 0 && !last) {
+        const int ls = p->d * (p->L - ps.l0 - ps.k);            // log2 of the tiles per target box
+        const int64_t tmax = (int64_t)1 << (ls - sg);
+        if (ps.T > tmax) ps.T = (int)tmax;
+        *mode = 1;
+    } else if (sg > 0) {
+        *mode = 2;
+    }
+    *ctas = ((p->npts >> (p->d * ps.k)) / ps.T) >> (*mode == 1 ? sg : 0);
+    return ps;
+}
+
 // Run passes [first, last) of the forward schedule.  Pass i reads workspace
 // buffer i % 2 (or g when it initialises) and writes buffer (i + 1) % 2 (or f
 // when it evaluates the targets).
 // Multi-RHS forward: every CTA keeps up to mr_max right-hand sides of its tiles and
 // evaluates each phase factor once for all of them.
 template <class P>
-bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last)
+bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last, int sg = 0,
+                         int sr = 0)
 {
     bfk::KArgs<P> a;
     fill_args<P>(p, a);
@@ -402,7 +422,10 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
     void *buf[2] = {p->w0, p->w1};
     const int mode = p->ptab ? bfk::PM_TABLE : bfk::PM_COMPUTE;
     for (int i = first; i < last; ++i) {
-        const Pass &ps = p->passes_mr[i];
+        int64_t ctas = 0;
+        const Pass ps = shard_pass(p, p->passes_mr[i], i + 1 == (int)p->passes_mr.size(), sg, &a.shard_mode, &ctas);
+        a.shard_g = sg;
+        a.shard_r = sr;
         a.l0 = ps.l0;
         a.k = ps.k;
         a.flags = ps.flags;
@@ -416,7 +439,7 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             const int per_sm = p->fns->switch_tc_ctas_per_sm();
             if (per_sm < 1) return BF_ERR_UNSUPPORTED;
-            int64_t grid = p->npts / 2;
+            int64_t grid = (p->npts / 2) >> (a.shard_mode == 1 ? sg : 0);
             if ((int64_t)sms * per_sm < grid) grid = (int64_t)sms * per_sm;
             cudaError_t e = p->fns->switch_tc(&a, (unsigned)grid, (unsigned)((nrhs + 15) / 16), p->fns->switch_tc_smem, s);
             if (e != cudaSuccess) return cuda_fail(p, e);
@@ -424,8 +447,6 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
         }
         a.ptab = p->ptab ? static_cast<typename P::C *>(p->ptab) + p->ptab_off[i] : nullptr;
         a.ptab_cta = p->ptab ? p->ptab_cta[i] : 0;
-        a.err = p->errflag;
-        const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
         a.ncta = (int)ctas;
         const size_t smem = p->ptab ? mr_smem_table(p, ps, nr, a.rc) : mr_smem(p, ps, nr, a.rc);
         int64_t grid = ctas;
@@ -445,7 +466,8 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
 }
 
 template <class P>
-bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last)
+bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last, int sg = 0,
+                      int sr = 0)
 {
     bfk::KArgs<P> a;
     fill_args<P>(p, a);
@@ -455,7 +477,10 @@ bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t 
     const bool tab = p->ftab && nrhs == 1;   // read the phases from the plan's table
     a.err = p->errflag;
     for (int i = first; i < last; ++i) {
-        const Pass &ps = p->passes[i];
+        int64_t ctas = 0;
+        const Pass ps = shard_pass(p, p->passes[i], i + 1 == (int)p->passes.size(), sg, &a.shard_mode, &ctas);
+        a.shard_g = sg;
+        a.shard_r = sr;
         a.l0 = ps.l0;
         a.k = ps.k;
         a.flags = ps.flags;
@@ -464,7 +489,6 @@ bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t 
         a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
         a.ftab = tab ? p->ftab + p->ftab_off[i] : nullptr;
         a.ftab_cta = tab ? p->ftab_cta[i] : 0;
-        const int64_t ctas = (p->npts >> (p->d * ps.k)) / ps.T;
         const size_t smem = pass_smem(p, ps) + row_cache_smem(p, ps);
         const bfl::pass_fn fn = tab ? (ps.row ? p->fns->row_tab : p->fns->col_tab)[1] : (ps.row ? p->fns->row : p->fns->col);
         cudaError_t e = fn(&a, (unsigned)ctas, (unsigned)nrhs, smem, s);
@@ -1274,6 +1298,30 @@ bf_status bf_apply(bf_plan p, const void *g, void *f, int nrhs, void *stream)
             st = p->prec == BF_PREC_MIXED_SFU ? run_forward<bfk::PMIXF>(p, g, f, nrhs, s, 0, n)
                                               : run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n);
     }
+    stream_mark(p, s, capturing);
+    return st;
+}
+
+bf_status bf_apply_shard(bf_plan p, const void *g, void *f, int nrhs, int shard_g, int shard_r, void *stream)
+{
+    if (!p) return BF_ERR_INVALID_ARG;
+    if (nrhs < 0 || nrhs > p->max_nrhs) return BF_ERR_INVALID_ARG;
+    if (shard_g < 0 || shard_g > p->d || shard_r < 0 || shard_r >= (1 << shard_g)) return BF_ERR_INVALID_ARG;
+    if (p->points || p->ptab || p->ftab) return BF_ERR_UNSUPPORTED;
+    if (nrhs == 0) return BF_OK;
+    if (!g || !f || ((uintptr_t)g & 15) || ((uintptr_t)f & 15)) return BF_ERR_INVALID_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool capturing = false;
+    bf_status st = stream_guard(p, s, &capturing);
+    if (st != BF_OK) return st;
+    const int n = (int)schedule_for(p, nrhs).size();
+    if (p->prec == BF_PREC_FP64) st = run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n, shard_g, shard_r);
+    else if (use_mr(p, nrhs))
+        st = p->prec == BF_PREC_MIXED_SFU ? run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, 0, n, shard_g, shard_r)
+                                          : run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, 0, n, shard_g, shard_r);
+    else
+        st = p->prec == BF_PREC_MIXED_SFU ? run_forward<bfk::PMIXF>(p, g, f, nrhs, s, 0, n, shard_g, shard_r)
+                                          : run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n, shard_g, shard_r);
     stream_mark(p, s, capturing);
     return st;
 }

@@ -248,7 +248,33 @@ struct KArgs {
     float *ftab;                      // reduced-phase table of a single-RHS pass (PM_BUILD, PM_TABLE) or null
     int64_t ftab_cta;                 // floats of that table per CTA
     int ncta;                         // CTAs (tile groups of T tiles) of the pass (multi-RHS kernels)
+    // source-domain sharding over 2^shard_g ranks (see shard_cta / shard_owned): 0 off,
+    // 1 the launch covers the rank's tiles only, 2 every tile, other ranks' inputs read as zero
+    int shard_mode, shard_g, shard_r;
 };
+
+// Sharding.  Rank r of G = 2^g owns the source boxes whose top g Morton bits equal r.  A merge
+// combines the children of one source box, so while the output source boxes still have g
+// bits every pair's inputs lie on the pair's own rank.  Mode 1 maps CTA b of a launch over
+// the rank's tile groups to the b-th tile group whose source boxes the rank owns (the host
+// makes T a divisor of the owned range, so no group straddles two ranks); mode 2 keeps the
+// CTA index and shard_owned tells which input pairs the rank holds.
+template <int D, class P>
+__device__ __forceinline__ uint32_t shard_cta(const KArgs<P> &a, uint32_t b)
+{
+    if (a.shard_mode != 1) return b;
+    const int ls = D * (a.L - a.l0 - a.k);          // log2 of the tiles per target box
+    const int lt = __ffs(a.T) - 1;                   // log2 T
+    const int lper = ls - a.shard_g - lt;            // log2 of the rank's groups per target box
+    return ((b >> lper) << (ls - lt)) | ((uint32_t)a.shard_r << lper) | (b & ((1u << lper) - 1u));
+}
+// input pair I of level a.l0 (index A 2^{D(L-l0)} + B) belongs to this rank (mode 2)
+template <int D, class P>
+__device__ __forceinline__ bool shard_owned(const KArgs<P> &a, int64_t I)
+{
+    const int lb = D * (a.L - a.l0);
+    return (int)((I & ((1LL << lb) - 1)) >> (lb - a.shard_g)) == a.shard_r;
+}
 
 // --------------------------------------------------------- index helpers
 
@@ -771,7 +797,7 @@ struct Tile {
     // (Ap, B*) of the CTA's tile tau: tile index = Ap * 2^{D(L-l0-k)} + B*
     static __device__ __forceinline__ void tile_of(const KArgs<P> &a, int tau, uint32_t &Ap, uint32_t &Bstar)
     {
-        const uint32_t tile = blockIdx.x * (uint32_t)a.T + (uint32_t)tau;   // < 2^30
+        const uint32_t tile = shard_cta<D>(a, blockIdx.x) * (uint32_t)a.T + (uint32_t)tau;   // < 2^30
         const int sh = D * (a.L - a.l0 - a.k);
         Ap = tile >> sh;
         Bstar = tile & ((1u << sh) - 1u);
@@ -2033,11 +2059,18 @@ struct Tile {
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) dst[j] = Wt[j];
     }
 
-    // ---- CTA input: T * 2^{dk} consecutive pairs (contiguous in HBM)
+    // ---- CTA input: T * 2^{dk} consecutive pairs (contiguous in HBM); with sharding mode 2
+    // the pairs of other ranks' source boxes read as zero
     static __device__ __forceinline__ void load(const KArgs<P> &a, C *Wt, int rhs)
     {
         const int cnt = a.T * (1 << (D * a.k)) * RR;
-        const C *src = a.win + (int64_t)rhs * a.wstride + (int64_t)blockIdx.x * cnt;
+        const int64_t c0 = (int64_t)shard_cta<D>(a, blockIdx.x) * cnt;
+        const C *src = a.win + (int64_t)rhs * a.wstride + c0;
+        if (a.shard_mode == 2) {
+            for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+                Wt[j] = shard_owned<D>(a, (c0 + j) / RR) ? src[j] : czero<C>();
+            return;
+        }
         for (int j = threadIdx.x; j < cnt; j += blockDim.x) Wt[j] = src[j];
     }
 

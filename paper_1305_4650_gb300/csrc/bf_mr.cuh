@@ -238,14 +238,17 @@ struct TileMR {
         for (int j = threadIdx.x; j < (n >> 1); j += NT) __stcs(d4 + j, s4[j]);
     }
 
-    // ---- CTA input: npr consecutive pairs per right-hand side
+    // ---- CTA input: npr consecutive pairs per right-hand side (sharding mode 2: the pairs of
+    // other ranks' source boxes read as zero)
     static __device__ void load(const KArgs<P> &a, const Ctx &x, C *W)
     {
         const int WS = x.npr * RR;
         const int64_t off = (int64_t)x.tile0 * ((int64_t)RR << (D * a.k));
         for (int j = threadIdx.x; j < x.nr * WS; j += NT) {
             const int rb = (j / RR) >> x.lgp, e = j - rb * WS;
-            W[j] = __ldcg(a.win + (int64_t)(x.rhs0 + rb) * a.wstride + off + e);
+            W[j] = a.shard_mode == 2 && !shard_owned<D>(a, (off + e) / RR)
+                       ? czero<C>()
+                       : __ldcg(a.win + (int64_t)(x.rhs0 + rb) * a.wstride + off + e);
         }
     }
 
@@ -722,7 +725,7 @@ struct TileMR {
     static __device__ __forceinline__ Ctx ctx(const KArgs<P> &a, int cta)
     {
         Ctx x;
-        x.tile0 = cta * a.T;
+        x.tile0 = (int)shard_cta<D>(a, (uint32_t)cta) * a.T;
         x.rhs0 = (int)blockIdx.y * MRMAX;
         x.nr = min(MRMAX, a.nrhs - x.rhs0);
         x.npr = a.T << (D * a.k);

@@ -125,7 +125,14 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
     const int l = a.l0, L = a.L;
     const int shB = D * (L - l);
     const uint32_t maskB = (1u << shB) - 1u;
-    const int64_t nunits = a.npts / ST::UP;
+    // units (two consecutive pairs); sharding mode 1: the launch covers the rank's units only
+    // (those whose source boxes carry its top bits), unit v of the launch is unit uid(v)
+    const int64_t nunits = (a.npts / ST::UP) >> (a.shard_mode == 1 ? a.shard_g : 0);
+    auto uid = [&](int64_t v) -> int64_t {
+        if (a.shard_mode != 1) return v;
+        const int lper = shB - 1 - a.shard_g;            // log2 of the rank's units per target box
+        return ((v >> lper) << (shB - 1)) | ((int64_t)a.shard_r << lper) | (v & ((1LL << lper) - 1));
+    };
     const int rhs0 = (int)blockIdx.y * ST::NPP;
     const int nr = min(ST::NPP, a.nrhs - rhs0);
     const uint32_t idesc = umma::idesc_bf16_f32(ST::M, ST::N);
@@ -139,7 +146,7 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
             for (int c = tid; c < nr * per_rhs; c += ST::NT) {
                 const int rb = c / per_rhs, o = c - rb * per_rhs;
                 const char *src =
-                    reinterpret_cast<const char *>(a.win + (int64_t)(rhs0 + rb) * a.wstride + v * ST::UP * RR) + 16 * o;
+                    reinterpret_cast<const char *>(a.win + (int64_t)(rhs0 + rb) * a.wstride + uid(v) * ST::UP * RR) + 16 * o;
                 const uint32_t dst = umma::saddr(Wst + rb * (ST::W_BYTES / ST::NPP) + 16 * o);
                 asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
             }
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
         if (tid >= ST::UP * ST::NPP * Q && tid < ST::UP * ST::NPP * Q + ST::UP * RR) {
             const int it = tid - ST::UP * ST::NPP * Q;
             const int s = it % RR, up = it / RR;
-            const uint32_t I = (uint32_t)(u * ST::UP + up);
+            const uint32_t I = (uint32_t)(uid(u) * ST::UP + up);
             int ca[DMAX];
             morton_decode<D>(I >> shB, l, ca);
             const int sk[DMAX] = {s % Q, s / Q, 0};
@@ -192,7 +199,7 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
         // evaluated as in the CUDA-core multi-RHS switch, split into the rows 2s, 2s + 1 of slot t_1
         for (int it = tid; it < ST::UP * RR * Q; it += ST::NT) {
             const int s = it % RR, th = (it / RR) % Q, up = it / (RR * Q);
-            const uint32_t I = (uint32_t)(u * ST::UP + up);
+            const uint32_t I = (uint32_t)(uid(u) * ST::UP + up);
             int cb[DMAX];
             morton_decode<D>(I & maskB, L - l, cb);
             const TT tS = Ts[up * RR + s];
@@ -257,7 +264,7 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
 #pragma unroll
             for (int j = 0; j < 4; ++j) recv[j] = __shfl_xor_sync(0xffffffffu, c ? v[j] : v[4 + j], 1);
             if (s < RR) {
-                const int64_t pair = u * ST::UP + up;
+                const int64_t pair = uid(u) * ST::UP + up;
                 C *wo = a.wout + pair * RR + s;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {

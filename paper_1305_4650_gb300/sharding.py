@@ -20,8 +20,11 @@ belongs to the rank given by the top g bits of its key.
 * At the last level the key is rev(A): ranks own target boxes by A's newest digits, the
   source bisection order bit-reversed (Section 2.2).
 
-No run here uses more than one GPU; tests/test_sharding.py checks this algebra and runs
-an exchange with world_size 2 on the CPU (gloo).
+The product path (``sharded_apply``, over ``bf_apply_shard``) keeps the local levels of
+this distribution and replaces the team exchanges of the last levels by one all-reduce of
+the targets: for G <= 2^d ranks only the last merge mixes ranks, so every rank runs the
+last pass on all pairs with the other ranks' weights read as zero and the partial target
+values are summed (N^d values per right-hand side instead of N^d r weights).
 """
 from __future__ import annotations
 
@@ -74,3 +77,30 @@ def block_ranks(d: int, L: int, g: int, level: int, Ap: int, Bp: int):
     ins = [owner(d, L, g, level, Ap, (Bp << d) + c) for c in range(1 << d)]
     outs = [owner(d, L, g, level + 1, (Ap << d) + a, Bp) for a in range(1 << d)]
     return ins, outs
+
+
+def shard_bits(world: int, d: int) -> int:
+    """g with world = 2^g ranks; one exchange (the final all-reduce) needs g <= d."""
+    g = world.bit_length() - 1
+    if world < 1 or (1 << g) != world or g > d:
+        raise ValueError(f"world size {world} must be a power of two <= 2^d = {1 << d}")
+    return g
+
+
+def sharded_apply(plan, g, group=None, stream=None, host_reduce: bool = False):
+    """f = B g over the ranks of a torch.distributed group: each rank computes its part on its
+    own GPU (bf_apply_shard with the rank's source boxes) and one all-reduce sums the parts.
+    host_reduce: reduce CPU copies (for backends without device tensors, e.g. gloo)."""
+    import torch.distributed as dist
+    world = dist.get_world_size(group)
+    rank = dist.get_rank(group)
+    f = plan.apply_shard(g, shard_bits(world, plan.d), rank, stream=stream)
+    if world == 1:
+        return f
+    if host_reduce:
+        h = f.cpu()
+        dist.all_reduce(h, op=dist.ReduceOp.SUM, group=group)
+        f.copy_(h)
+    else:
+        dist.all_reduce(f, op=dist.ReduceOp.SUM, group=group)
+    return f
