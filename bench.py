@@ -99,6 +99,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="default workload: skip the 48-problem batch record (FP32, BF16x3, FP64 forms)")
     ap.add_argument("--batch-fp64-steps", type=int, default=1, help="timed FP64 steps of that batch record")
+    ap.add_argument("--sharded", action="store_true",
+                    help="under torchrun: one problem split over the ranks (bf_apply_shard + one NCCL all-reduce "
+                         "of the targets per step, strong scaling) instead of independent replicas")
     return ap.parse_args()
 
 
@@ -273,9 +276,17 @@ def run_ours(args, rank, world, local_rank):
     g = torch.from_numpy(g_np).to(dev)
     f = torch.empty_like(g)
 
-    # ---- timed region: K applies through the C ABI (device buffers)
+    # ---- timed region: K applies through the C ABI (device buffers); with --sharded under
+    # torchrun each step is this rank's part (bf_apply_shard) and one all-reduce of the targets
+    sharded = args.sharded and world > 1
+    if sharded:
+        from paper_1305_4650_gb300 import sharding
+        shard_g = sharding.shard_bits(world, spec.d)
+        step = lambda: (plan.apply_shard(g, shard_g, rank, f=f), dist.all_reduce(f))
+    else:
+        step = lambda: plan.apply(g, f)
     for _ in range(args.warmup):
-        plan.apply(g, f)
+        step()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with Clocks(local_rank) as clk:
@@ -283,13 +294,16 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
-            plan.apply(g, f)
+            step()
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
     ms = max_over_ranks(e0.elapsed_time(e1) / args.steps)
     clocks = clk.summary()
-    value = spec.npts * nrhs * world / (ms * 1e-3)
+    value = spec.npts * nrhs * (1 if sharded else world) / (ms * 1e-3)
+    if sharded:
+        plan.apply(g, f)                                  # the rest of the line measures the whole apply
+        torch.cuda.synchronize()
     out_f = f.cpu().numpy()
 
     # ---- per-pass device times (same passes, events between launches on the same stream)
@@ -375,6 +389,29 @@ def run_ours(args, rank, world, local_rank):
                "precision": "mixed_sfu (complex64, double-float phase, SFU sin/cos)"}
         out_sfu = fsf.cpu().numpy()
         psf.close()
+
+    # ---- the sharded form on this GPU: the time of one rank's part of the apply when the
+    # sources are split over G = 2, 4 ranks (bf_apply_shard; ranks do equal work), against the
+    # whole apply; the exchange is one all-reduce of the targets (bytes stated, not timed here)
+    shard_rec = None
+    if spec.d >= 2 and not args.L and world == 1 and prec != "fp64":
+        shard_rec = {"all_reduce_bytes_per_step": spec.npts * nrhs * (16 if prec == "fp64" else 8)}
+        fs_ = torch.empty_like(g)
+        for G, sg in ((2, 1), (4, 2)):
+            for _ in range(2):
+                plan.apply_shard(g, sg, G - 1, f=fs_)
+            torch.cuda.synchronize()
+            d0, d1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            d0.record(stream)
+            for _ in range(args.steps):
+                plan.apply_shard(g, sg, G - 1, f=fs_)
+            d1.record(stream)
+            torch.cuda.synchronize()
+            t = d0.elapsed_time(d1) / args.steps
+            shard_rec[f"ranks{G}"] = {"per_rank_ms": round(t, 4), "fraction_of_apply": round(t / ms, 4)}
+        shard_rec["note"] = ("per-rank part on one GPU (rank G-1; the ranks' parts are the same size); merges below the "
+                             "last level run on the rank's pairs, the last pass on all pairs")
+        del fs_
 
     # ---- phase-table variants (every phase evaluated once at plan creation; the apply reads
     # the reduced phases (one RHS) or the factors (several) and evaluates no Phi)
@@ -478,7 +515,7 @@ def run_ours(args, rank, world, local_rank):
     weight_gb = 2 * max(len(passes) - 1, 1) * spec.npts * spec.r * csize * nrhs / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c128" if prec == "fp64" else "c64",
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "c128" if prec == "fp64" else "c64",
             "data": "synthetic",
             "config": {"workload": spec.name, "d": spec.d, "N": spec.N, "q": spec.q, "r": spec.r,
                        "phase": spec.phase, "precision": prec, "nrhs": nrhs, "switch_level": spec.switch_level,
@@ -493,9 +530,10 @@ def run_ours(args, rank, world, local_rank):
                        "autotuned_ms": tuned,
                        "l2": (f"no flush: each step streams {weight_gb:.1f} GB of weights through the 129 MB L2"
                               if weight_gb > 0.2 else "no flush: the whole working set is L2-resident (small case)"),
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": (f"one problem over {world} ranks (source-box sharding + all-reduce)"
+                                       if sharded else f"replicas x{world}")},
             "roofline": roofline, "fp64_gpu": fp64, "sfu_sincos": sfu, "phase_tables": tables, "accuracy": acc,
-            "batched": batched, "cpu_baseline": cpu, "e2e": e2e,
+            "batched": batched, "sharded": shard_rec, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * len(passes), "clocks": clocks}
     return line
 

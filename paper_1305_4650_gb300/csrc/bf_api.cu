@@ -409,8 +409,9 @@ Pass shard_pass(const bf_plan_s *p, Pass ps, bool last, int sg, int *mode, int64
 // evaluates each phase factor once for all of them.
 template <class P>
 bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last, int sg = 0,
-                         int sr = 0)
+                         int sr = 0, const std::vector<Pass> *sched = nullptr)
 {
+    const std::vector<Pass> &sc = sched ? *sched : p->passes_mr;
     bfk::KArgs<P> a;
     fill_args<P>(p, a);
     a.g = static_cast<const typename P::C *>(g);
@@ -423,7 +424,7 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
     const int mode = p->ptab ? bfk::PM_TABLE : bfk::PM_COMPUTE;
     for (int i = first; i < last; ++i) {
         int64_t ctas = 0;
-        const Pass ps = shard_pass(p, p->passes_mr[i], i + 1 == (int)p->passes_mr.size(), sg, &a.shard_mode, &ctas);
+        const Pass ps = shard_pass(p, sc[i], i + 1 == (int)sc.size(), sg, &a.shard_mode, &ctas);
         a.shard_g = sg;
         a.shard_r = sr;
         a.l0 = ps.l0;
@@ -467,8 +468,9 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
 
 template <class P>
 bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t s, int first, int last, int sg = 0,
-                      int sr = 0)
+                      int sr = 0, const std::vector<Pass> *sched = nullptr)
 {
+    const std::vector<Pass> &sc = sched ? *sched : p->passes;
     bfk::KArgs<P> a;
     fill_args<P>(p, a);
     a.g = static_cast<const typename P::C *>(g);
@@ -478,7 +480,7 @@ bf_status run_forward(bf_plan p, const void *g, void *f, int nrhs, cudaStream_t 
     a.err = p->errflag;
     for (int i = first; i < last; ++i) {
         int64_t ctas = 0;
-        const Pass ps = shard_pass(p, p->passes[i], i + 1 == (int)p->passes.size(), sg, &a.shard_mode, &ctas);
+        const Pass ps = shard_pass(p, sc[i], i + 1 == (int)sc.size(), sg, &a.shard_mode, &ctas);
         a.shard_g = sg;
         a.shard_r = sr;
         a.l0 = ps.l0;
@@ -1314,14 +1316,23 @@ bf_status bf_apply_shard(bf_plan p, const void *g, void *f, int nrhs, int shard_
     bool capturing = false;
     bf_status st = stream_guard(p, s, &capturing);
     if (st != BF_OK) return st;
-    const int n = (int)schedule_for(p, nrhs).size();
-    if (p->prec == BF_PREC_FP64) st = run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n, shard_g, shard_r);
+    // the last pass runs on every pair: keep it to one level (its other levels become a pass
+    // of their own, with the same pairs per CTA, that runs on the rank's pairs)
+    std::vector<Pass> sc = schedule_for(p, nrhs);
+    if (shard_g > 0 && sc.back().k > 1) {
+        const Pass last = sc.back();
+        const int64_t npr = (int64_t)last.T << (p->d * last.k);
+        sc.back() = Pass{last.row, last.l0, last.k - 1, last.flags & ~bfk::F_FINAL, (int)(npr >> (p->d * (last.k - 1)))};
+        sc.push_back(Pass{last.row, last.l0 + last.k - 1, 1, last.flags, (int)(npr >> p->d)});
+    }
+    const int n = (int)sc.size();
+    if (p->prec == BF_PREC_FP64) st = run_forward<bfk::PF64>(p, g, f, nrhs, s, 0, n, shard_g, shard_r, &sc);
     else if (use_mr(p, nrhs))
-        st = p->prec == BF_PREC_MIXED_SFU ? run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, 0, n, shard_g, shard_r)
-                                          : run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, 0, n, shard_g, shard_r);
+        st = p->prec == BF_PREC_MIXED_SFU ? run_forward_mr<bfk::PMIXF>(p, g, f, nrhs, s, 0, n, shard_g, shard_r, &sc)
+                                          : run_forward_mr<bfk::PMIX>(p, g, f, nrhs, s, 0, n, shard_g, shard_r, &sc);
     else
-        st = p->prec == BF_PREC_MIXED_SFU ? run_forward<bfk::PMIXF>(p, g, f, nrhs, s, 0, n, shard_g, shard_r)
-                                          : run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n, shard_g, shard_r);
+        st = p->prec == BF_PREC_MIXED_SFU ? run_forward<bfk::PMIXF>(p, g, f, nrhs, s, 0, n, shard_g, shard_r, &sc)
+                                          : run_forward<bfk::PMIX>(p, g, f, nrhs, s, 0, n, shard_g, shard_r, &sc);
     stream_mark(p, s, capturing);
     return st;
 }
