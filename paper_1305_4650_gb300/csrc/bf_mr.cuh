@@ -252,6 +252,29 @@ struct TileMR {
         }
     }
 
+    // ---- the same input by bulk copies (the TMA engine), one per right-hand side (npr r complex
+    // numbers, contiguous in HBM and 16-byte aligned), completing on *bar; issued by thread 0
+    // after the shared memory's previous generic accesses are ordered before the copies
+    static __device__ void load_async(const KArgs<P> &a, const Ctx &x, C *W, uint64_t *bar)
+    {
+        if (threadIdx.x != 0) return;
+        const unsigned bytes = (unsigned)(x.npr * RR * sizeof(C));
+        const int64_t off = (int64_t)x.tile0 * ((int64_t)RR << (D * a.k));
+        fence_proxy_async();
+        mbar_expect_tx(bar, bytes * (unsigned)x.nr);
+        for (int rb = 0; rb < x.nr; ++rb)
+            bulk_g2s(W + rb * x.npr * RR, a.win + (int64_t)(x.rhs0 + rb) * a.wstride + off, bytes, bar);
+    }
+    // every thread: wait for those copies; a wait that gives up is flagged and waited for once
+    // more, so no copy is left in flight (the results are then undefined, never a hang)
+    static __device__ void wait_input(const KArgs<P> &a, uint64_t *bar, unsigned parity)
+    {
+        if (!mbar_wait(bar, parity, TS_POLLS)) {
+            if (a.err) atomicExch(a.err, 1);
+            mbar_wait(bar, parity, TS_POLLS);
+        }
+    }
+
     // ---- CTA output: tile slots are in digit-reversed order after k merges
     static __device__ void store(const KArgs<P> &a, const Ctx &x, const C *W)
     {
@@ -338,7 +361,7 @@ struct TileMR {
     // ---- one column-form merge level (l -> l+1); ms.M holds the child->parent matrices
     template <int PM, class MS>
     static __device__ void col_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i,
-                                     TS<C> &ts)
+                                     TS<C> &ts, uint64_t *wbar = nullptr, unsigned wpar = 0)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
         if constexpr (PM == PM_TABLE) PC = ts_acquire(ts);
@@ -393,6 +416,7 @@ struct TileMR {
             PB[pA * PCB + tq * Q + tl] = expphase_part<P, D, K>(a, tA, pt);
         }
         __syncthreads();
+        if (wbar) wait_input(a, wbar, wpar);   // the weights were copied in during the phase stage
         if constexpr (PM == PM_BUILD) {   // build: store the factors; no weights are touched
             tab_store(ts.tb, PC, 5 * RR * nout);
             ts.tb += 5 * RR * nout;
@@ -539,7 +563,7 @@ struct TileMR {
     // ---- one row-form merge level (l -> l+1)
     template <int PM, class MS>
     static __device__ void row_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i,
-                                     TS<C> &ts)
+                                     TS<C> &ts, uint64_t *wbar = nullptr, unsigned wpar = 0)
     {
         const int k = a.k, n = 1 << (D * k), nblk = n >> D, L = a.L, WS = x.npr * RR, nout = x.npr;
         if constexpr (PM == PM_TABLE) PC = ts_acquire(ts);
@@ -588,6 +612,7 @@ struct TileMR {
             }
         }
         __syncthreads();
+        if (wbar) wait_input(a, wbar, wpar);   // the weights were copied in during the phase stage
         if constexpr (PM == PM_BUILD) {   // build: store the factors; no weights are touched
             tab_store(ts.tb, PC, 5 * RR * nout);
             ts.tb += 5 * RR * nout;
@@ -738,9 +763,12 @@ struct TileMR {
 // pass bodies shared by the per-pass kernels and the persistent batch kernel; ms is a
 // kernel parameter holding M, so the interpolation reads its coefficients from the
 // constant bank; ts carries the phase table (PM_BUILD, PM_TABLE)
+// wbar (per-pass kernels): the input weights come by bulk copies that overlap the first
+// level's phase stage (wpar: the mbarrier phase of this tile group); null: plain loads first
 template <int Q, class P, int K, int PM, class MS>
 __device__ __forceinline__ void col_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
-                                            unsigned char *sm, const typename P::C *g, TS<typename P::C> &ts)
+                                            unsigned char *sm, const typename P::C *g, TS<typename P::C> &ts,
+                                            uint64_t *wbar = nullptr, unsigned wpar = 0)
 {
     using C = typename P::C;
     using TM = TileMR<Q, P, K>;
@@ -748,20 +776,25 @@ __device__ __forceinline__ void col_pass_mr(const KArgs<P> &a, const MS &ms, con
     C *W = reinterpret_cast<C *>(sm);
     C *S = W + x.nr * WS;
     C *PC = S + x.rc * mr_s_stride(Q, x.npr);
+    const bool async = wbar && !(a.flags & F_INIT) && a.k > 0 && a.shard_mode != 2;
     if (a.flags & F_INIT) {
         TM::template init<PM>(a, x, W, PC, g, ts);
+    } else if (async) {
+        TM::load_async(a, x, W, wbar);
     } else if (PM != PM_BUILD) {
         TM::load(a, x, W);
         __syncthreads();
     }
-    for (int i = 0; i < a.k; ++i) TM::template col_level<PM>(a, ms, x, W, S, PC, a.l0 + i, i, ts);
+    for (int i = 0; i < a.k; ++i)
+        TM::template col_level<PM>(a, ms, x, W, S, PC, a.l0 + i, i, ts, async && i == 0 ? wbar : nullptr, wpar);
     if (a.flags & F_SWITCH) TM::template switch_tiles<PM>(a, x, W, a.l0 + a.k, ts);
     if (PM != PM_BUILD) TM::store(a, x, W);
 }
 
 template <int Q, class P, int K, int PM, class MS>
 __device__ __forceinline__ void row_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
-                                            unsigned char *sm, typename P::C *f, TS<typename P::C> &ts)
+                                            unsigned char *sm, typename P::C *f, TS<typename P::C> &ts,
+                                            uint64_t *wbar = nullptr, unsigned wpar = 0)
 {
     using C = typename P::C;
     using TM = TileMR<Q, P, K>;
@@ -769,11 +802,15 @@ __device__ __forceinline__ void row_pass_mr(const KArgs<P> &a, const MS &ms, con
     C *W = reinterpret_cast<C *>(sm);
     C *S = W + x.nr * WS;
     C *PC = S + x.rc * mr_s_stride(Q, x.npr);
-    if (PM != PM_BUILD) {
+    const bool async = wbar && a.k > 0 && a.shard_mode != 2;
+    if (async) {
+        TM::load_async(a, x, W, wbar);
+    } else if (PM != PM_BUILD) {
         TM::load(a, x, W);
         __syncthreads();
     }
-    for (int i = 0; i < a.k; ++i) TM::template row_level<PM>(a, ms, x, W, S, PC, a.l0 + i, i, ts);
+    for (int i = 0; i < a.k; ++i)
+        TM::template row_level<PM>(a, ms, x, W, S, PC, a.l0 + i, i, ts, async && i == 0 ? wbar : nullptr, wpar);
     if (a.flags & F_FINAL)
         TM::template final_eval<PM>(a, x, W, PC, f, ts);
     else if (PM != PM_BUILD)
@@ -817,11 +854,19 @@ template <int Q, class P, int K, int PM>
 __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_col_pass_mr(const KArgs<P> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t wbar;
     TS<typename P::C> ts;
     unsigned char *work = mr_setup<Q, P, K, PM>(a, TileMR<Q, P, K>::ctx(a, blockIdx.x), smem_raw, ts, false);
-    for (int c = blockIdx.x; c < a.ncta; c += gridDim.x) {
+    if (PM == PM_COMPUTE && threadIdx.x == 0) {
+        mbar_init(&wbar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    unsigned it = 0;
+    for (int c = blockIdx.x; c < a.ncta; c += gridDim.x, ++it) {
         if constexpr (PM == PM_BUILD) ts.tb = a.ptab + (int64_t)c * a.ptab_cta;
-        col_pass_mr<Q, P, K, PM>(a, a, TileMR<Q, P, K>::ctx(a, c), work, a.g, ts);
+        col_pass_mr<Q, P, K, PM>(a, a, TileMR<Q, P, K>::ctx(a, c), work, a.g, ts, PM == PM_COMPUTE ? &wbar : nullptr,
+                                 it & 1u);
         __syncthreads();
     }
 }
@@ -830,11 +875,19 @@ template <int Q, class P, int K, int PM>
 __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_row_pass_mr(const KArgs<P> a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ uint64_t wbar;
     TS<typename P::C> ts;
     unsigned char *work = mr_setup<Q, P, K, PM>(a, TileMR<Q, P, K>::ctx(a, blockIdx.x), smem_raw, ts, true);
-    for (int c = blockIdx.x; c < a.ncta; c += gridDim.x) {
+    if (PM == PM_COMPUTE && threadIdx.x == 0) {
+        mbar_init(&wbar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    unsigned it = 0;
+    for (int c = blockIdx.x; c < a.ncta; c += gridDim.x, ++it) {
         if constexpr (PM == PM_BUILD) ts.tb = a.ptab + (int64_t)c * a.ptab_cta;
-        row_pass_mr<Q, P, K, PM>(a, a, TileMR<Q, P, K>::ctx(a, c), work, a.f, ts);
+        row_pass_mr<Q, P, K, PM>(a, a, TileMR<Q, P, K>::ctx(a, c), work, a.f, ts, PM == PM_COMPUTE ? &wbar : nullptr,
+                                 it & 1u);
         __syncthreads();
     }
 }
