@@ -509,6 +509,11 @@ def run_ours(args, rank, world, local_rank):
     if args.workload == "genradon2d" and not args.L and not args.no_batched:
         batched = batch_eval(args, rank, world, dev, min(args.steps, 5), args.warmup, False, args.batch_fp64_steps,
                              not args.no_accuracy)
+    # ---- the other workloads of the method, compact (rank 0): d = 3, and the adjoint with CGLS
+    configs = None
+    if args.workload == "genradon2d" and not args.L and not args.no_batched and rank == 0:
+        configs = {"genradon3d": config3_record(min(args.steps, 10), args.warmup, not args.no_accuracy),
+                   "adjoint_cg": config5_record(min(args.steps, 10), args.warmup)}
     if rank != 0:
         return None
     csize = 8 if prec != "fp64" else 16
@@ -533,7 +538,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": (f"one problem over {world} ranks (source-box sharding + all-reduce)"
                                        if sharded else f"replicas x{world}")},
             "roofline": roofline, "fp64_gpu": fp64, "sfu_sincos": sfu, "phase_tables": tables, "accuracy": acc,
-            "batched": batched, "sharded": shard_rec, "cpu_baseline": cpu, "e2e": e2e,
+            "batched": batched, "configs": configs, "sharded": shard_rec, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * len(passes), "clocks": clocks}
     return line
 
@@ -703,6 +708,103 @@ def batch_eval(args, rank, world, dev, steps, warmup, autotune, fp64_steps, accu
         rec["speedup_mixed_over_fp64"] = round(forms["fp64_per_pass"]["ms_per_step"] /
                                                forms["mixed_per_pass"]["ms_per_step"], 2)
     return rec
+
+
+def timed_apply(fn, stream, steps, warmup):
+    """ms per call of fn() on the launching stream (CUDA events, synchronised both sides)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def config3_record(steps, warmup, accuracy):
+    """The d = 3 generalized Radon workload (N = 64, q = 4, 2^18 points): mixed and FP64 GPU
+    applies, the speedup, and both against the oracle (one level-m box) and the direct sum."""
+    import numpy as np
+    import torch
+    from paper_1305_4650_gb300 import bf, workloads as wl
+    spec = wl.genradon3d()
+    stream = torch.cuda.current_stream()
+    rec, outs = {"workload": spec.name, "points": spec.npts}, {}
+    g32 = wl.source_values(spec, 1, np.complex64)
+    for prec, n in (("mixed", steps), ("fp64", max(1, steps // 5))):
+        g_np = g32.astype(np.complex128) if prec == "fp64" else g32
+        plan = bf.Plan.from_spec(spec, precision=prec)
+        plan.autotune(1, reps=2)
+        g = torch.from_numpy(g_np).cuda()
+        f = torch.empty_like(g)
+        ms = timed_apply(lambda: plan.apply(g, f), stream, n, 2)
+        rec[prec] = {"ms_per_step": round(ms, 3), "value": spec.npts / (ms * 1e-3), "launches": plan.launches(1)}
+        outs[prec] = (g_np[0], f.cpu().numpy()[0])
+        plan.close()
+    rec["speedup_mixed_over_fp64"] = round(rec["fp64"]["ms_per_step"] / rec["mixed"]["ms_per_step"], 2)
+    if accuracy:
+        import oracle
+        rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        P = oracle.Problem(**spec.oracle_kwargs())
+        lvl, box = spec.switch_level, 300
+        tg = oracle.restricted_targets(P, lvl, box)
+        g0 = outs["mixed"][0].astype(np.complex128)
+        ref = oracle.butterfly(P, g0, restrict=(lvl, box))[tg]
+        samp = tg[:: max(1, len(tg) // 32)][:32]
+        direct = oracle.direct_sum(P, g0, targets=samp)
+        where = {int(t): i for i, t in enumerate(tg)}      # tg is in Morton order, not sorted
+        pos = np.array([where[int(t)] for t in samp])
+        for prec in ("mixed", "fp64"):
+            out = outs[prec][1]
+            rec[prec]["rel_l2_vs_oracle_butterfly"] = rel(out[tg], ref)
+            rec[prec]["rel_l2_vs_direct_sum"] = rel(out[samp], direct)
+        rec["oracle_vs_direct_sum"] = rel(ref[pos], direct)
+        rec["sample"] = f"{len(tg)} targets of level-{lvl} box {box}; direct sum on 32 (the FP64 arm's input is the mixed arm's, widened)"
+    return rec
+
+
+def config5_record(steps, warmup):
+    """The adjoint workload (d = 2 generalized Radon, N = 1024, q = 5, mixed): the adjoint apply,
+    the dot-product identity <B g, h> = <g, B^H h> at full size, and 20 CGLS iterations on
+    B^H B m = B^H d with d = B m_true (1% spikes)."""
+    import numpy as np
+    import torch
+    from paper_1305_4650_gb300 import bf, workloads as wl
+    from paper_1305_4650_gb300.autograd import cgls
+    spec = wl.genradon2d()
+    stream = torch.cuda.current_stream()
+    plan = bf.Plan.from_spec(spec, precision="mixed")
+    plan.autotune(1, reps=2)
+    g = torch.from_numpy(wl.source_values(spec, 1, np.complex64, seed=11)).cuda()
+    h = torch.from_numpy(wl.source_values(spec, 1, np.complex64, seed=12)).cuda()
+    gh = torch.empty_like(g)
+    ms_adj = timed_apply(lambda: plan.apply_adjoint(h, gh), stream, steps, warmup)
+    Bg = plan.apply(g)
+    BHh = plan.apply_adjoint(h)
+    c128 = lambda t: t.flatten().to(torch.complex128)
+    lhs, rhs = torch.vdot(c128(h), c128(Bg)), torch.vdot(c128(BHh), c128(g))
+    dot_err = (abs(lhs - rhs) / (torch.linalg.vector_norm(c128(Bg)) * torch.linalg.vector_norm(c128(h)))).item()
+    mt = torch.from_numpy(wl.sparse_spikes(spec, 0.01)).cuda()
+    d = plan.apply(mt)
+    cgls(plan, d, 2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    m, hist = cgls(plan, d, 20)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_cg = e0.elapsed_time(e1)
+    plan.close()
+    return {"workload": "cg20_" + spec.name, "adjoint_ms_per_apply": round(ms_adj, 3),
+            "adjoint_value": spec.npts / (ms_adj * 1e-3), "dot_product_identity_rel": dot_err,
+            "cg_iterations": 20, "cg_ms": round(ms_cg, 2), "cg_applies": 41,
+            "cg_points_per_s": 41 * spec.npts / (ms_cg * 1e-3),
+            "residual_history": [round(x / hist[0], 6) for x in hist[::4]] + [round(hist[-1] / hist[0], 6)],
+            "residual_monotone": all(b <= a * (1 + 1e-6) for a, b in zip(hist, hist[1:]))}
 
 
 def pass_roofline(plan, spec, nrhs, g, f, stream, dev, steps):
