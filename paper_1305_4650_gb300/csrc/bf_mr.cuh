@@ -120,7 +120,7 @@ __host__ __device__ constexpr int64_t mr_s_stride(int q, int64_t npr) { return 2
 
 // acc += M[h][t][u] v: one packed FMA where the coefficients come twice (KArgs::M2, the
 // per-pass kernels), two scalar FMAs in the persistent batch kernel (packed ones cost it
-// spills); the same roundings either way
+// spills: 112 bytes at the register budget of two CTAs per SM); the same roundings either way
 template <class MS> struct PackedM { static constexpr bool value = true; };
 template <class P> struct BatchArgs;
 template <class P> struct PackedM<BatchArgs<P>> { static constexpr bool value = false; };
@@ -766,7 +766,7 @@ struct TileMR {
 // wbar (per-pass kernels): the input weights come by bulk copies that overlap the first
 // level's phase stage (wpar: the mbarrier phase of this tile group); null: plain loads first
 template <int Q, class P, int K, int PM, class MS>
-__device__ __forceinline__ void col_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
+__device__ __forceinline__ bool col_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
                                             unsigned char *sm, const typename P::C *g, TS<typename P::C> &ts,
                                             uint64_t *wbar = nullptr, unsigned wpar = 0)
 {
@@ -789,10 +789,11 @@ __device__ __forceinline__ void col_pass_mr(const KArgs<P> &a, const MS &ms, con
         TM::template col_level<PM>(a, ms, x, W, S, PC, a.l0 + i, i, ts, async && i == 0 ? wbar : nullptr, wpar);
     if (a.flags & F_SWITCH) TM::template switch_tiles<PM>(a, x, W, a.l0 + a.k, ts);
     if (PM != PM_BUILD) TM::store(a, x, W);
+    return async;
 }
 
 template <int Q, class P, int K, int PM, class MS>
-__device__ __forceinline__ void row_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
+__device__ __forceinline__ bool row_pass_mr(const KArgs<P> &a, const MS &ms, const typename TileMR<Q, P, K>::Ctx &x,
                                             unsigned char *sm, typename P::C *f, TS<typename P::C> &ts,
                                             uint64_t *wbar = nullptr, unsigned wpar = 0)
 {
@@ -815,6 +816,7 @@ __device__ __forceinline__ void row_pass_mr(const KArgs<P> &a, const MS &ms, con
         TM::template final_eval<PM>(a, x, W, PC, f, ts);
     else if (PM != PM_BUILD)
         TM::store(a, x, W);
+    return async;
 }
 
 constexpr int TABCTL_BYTES = (int)((sizeof(TabCtl) + 15) / 16 * 16);
@@ -917,6 +919,7 @@ struct BatchJob {
 template <class P>
 struct BatchArgs {
     typename P::R M[2][QMAX][QMAX];   // child->parent matrices (the same for every problem)
+    typename P::C M2[2][QMAX][QMAX];  // the same, each value twice (operand of a packed FMA)
     const KArgs<P> *__restrict__ desc;   // per (problem, pass); g and f come from the arrays below
     const BatchJob *jobs;
     int njobs, units;
@@ -966,6 +969,13 @@ __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_batch_mr(const
     using TM = TileMR<Q, P, K>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ int s_unit, s_job, s_skip;
+    __shared__ uint64_t wbar;                                  // the units' input copies
+    if (threadIdx.x == 0) {
+        mbar_init(&wbar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    unsigned wuse = 0;                                         // phases of wbar used so far
     for (;;) {
         if (threadIdx.x == 0) {
             const int u = (int)atomicAdd(&b.ctr[b.njobs], 1u);
@@ -990,7 +1000,8 @@ __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_batch_mr(const
         if (u >= b.units) break;
         const BatchJob jb = b.jobs[s_job];
         if (!s_skip) {
-            // the pass's arguments stay in global memory (read-only for the whole launch)
+            // the pass's arguments stay in global memory (read-only for the whole launch; the
+            // kernel's shared memory is at the two-CTAs-per-SM limit)
             const KArgs<P> &a = b.desc[jb.desc];
             const int c0 = (u - jb.first) * jb.per;
             const int c1 = min(c0 + jb.per, jb.ctas);
@@ -1003,10 +1014,9 @@ __global__ void __launch_bounds__(CfgMR<Q>::NT, CfgMR<Q>::MINB) k_batch_mr(const
                 x.rc = a.rc;
                 x.lgp = __ffs(x.npr) - 1;
                 TS<typename P::C> ts{};
-                if (jb.row)
-                    row_pass_mr<Q, P, K, PM_COMPUTE>(a, b, x, smem_raw, b.f[jb.prob], ts);
-                else
-                    col_pass_mr<Q, P, K, PM_COMPUTE>(a, b, x, smem_raw, b.g[jb.prob], ts);
+                const bool used = jb.row ? row_pass_mr<Q, P, K, PM_COMPUTE>(a, b, x, smem_raw, b.f[jb.prob], ts, &wbar, wuse & 1u)
+                                         : col_pass_mr<Q, P, K, PM_COMPUTE>(a, b, x, smem_raw, b.g[jb.prob], ts, &wbar, wuse & 1u);
+                wuse += used ? 1u : 0u;
                 __syncthreads();
             }
         }
