@@ -1011,9 +1011,6 @@ bf_status batch_launch(bf_batch b, const void *const *g, void *const *f, cudaStr
     a.err = reinterpret_cast<int *>(b->ctr + b->njobs + 1);
     a.stats = static_cast<unsigned long long *>(b->state);
     std::memcpy(a.M, b->M, sizeof(a.M));
-    for (int h = 0; h < 2; ++h)
-        for (int t = 0; t < bfk::QMAX; ++t)
-            for (int u = 0; u < bfk::QMAX; ++u) a.M2[h][t][u].x = a.M2[h][t][u].y = a.M[h][t][u];
     a.wait_ns = wait_ns;
     a.dep_extra = dep_extra;
     for (int i = 0; i < b->count; ++i) {

@@ -919,7 +919,6 @@ struct BatchJob {
 template <class P>
 struct BatchArgs {
     typename P::R M[2][QMAX][QMAX];   // child->parent matrices (the same for every problem)
-    typename P::C M2[2][QMAX][QMAX];  // the same, each value twice (operand of a packed FMA)
     const KArgs<P> *__restrict__ desc;   // per (problem, pass); g and f come from the arrays below
     const BatchJob *jobs;
     int njobs, units;
