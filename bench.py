@@ -99,6 +99,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="default workload: skip the 48-problem batch record (FP32, BF16x3, FP64 forms)")
     ap.add_argument("--batch-fp64-steps", type=int, default=1, help="timed FP64 steps of that batch record")
+    ap.add_argument("--tc-levels", action="store_true",
+                    help="bf16x3: run the column merge levels on the tensor cores too (bf_params.tc_levels)")
     ap.add_argument("--sharded", action="store_true",
                     help="under torchrun: one problem split over the ranks (bf_apply_shard + one NCCL all-reduce "
                          "of the targets per step, strong scaling) instead of independent replicas")
@@ -269,7 +271,7 @@ def run_ours(args, rank, world, local_rank):
         return float(t.item())
 
     prec = args.precision or spec.precision
-    plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec)
+    plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec, tc_levels=args.tc_levels)
     tuned = None if args.no_autotune else round(plan.autotune(nrhs, reps=3), 4)   # plan time, not timed
     passes = plan.passes(nrhs)
     g_np = wl.source_values(spec, nrhs, plan.cdtype, seed=spec.seed + rank)
@@ -318,7 +320,7 @@ def run_ours(args, rank, world, local_rank):
         for i in range(len(passes)):
             tpass[i] += evs[i].elapsed_time(evs[i + 1]) / args.steps
     dom = max(range(len(passes)), key=lambda i: tpass[i])
-    sched = [(p["kind"] if p["kind"] != "switch_tc" else "sw") + str(p["k"]) for p in passes]
+    sched = [{"switch_tc": "sw", "col_tc": "ctc"}.get(p["kind"], p["kind"]) + str(p["k"]) for p in passes]
     wdom = pass_work(spec, passes[dom], nrhs)
     ops = work_ops(spec, wdom)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -832,14 +834,16 @@ def pass_roofline(plan, spec, nrhs, g, f, stream, dev, steps):
 
     def alu_ops(ps):
         w = pass_work(spec, ps, nrhs)
-        if ps["kind"] == "switch_tc":
+        if ps["kind"] == "switch_tc":                 # the switch's MACs run on the tensor cores
             w = dict(w, cmacs=0)
+        if ps["kind"] == "col_tc":                    # and so does this level's interpolation
+            w = dict(w, macs=0)
         return work_ops(spec, w)
 
     dom = max(range(len(passes)), key=lambda i: tp[i])
     ops = alu_ops(passes[dom])
     return {"bound": "alu", "pass_ms": [round(t, 4) for t in tp],
-            "schedule": [(p["kind"] if p["kind"] != "switch_tc" else "sw") + str(p["k"]) for p in passes],
+            "schedule": [{"switch_tc": "sw", "col_tc": "ctc"}.get(p["kind"], p["kind"]) + str(p["k"]) for p in passes],
             "dominant": dom, "achieved": round(ops / (tp[dom] * 1e-3) / 1e12, 3), "peak": round(peak, 2),
             "unit": "Tops/s", "frac": round(ops / (tp[dom] * 1e-3) / 1e12 / peak, 4),
             "apply_frac": round(sum(alu_ops(p) for p in passes) / (sum(tp) * 1e-3) / 1e12 / peak, 4)}

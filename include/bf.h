@@ -88,7 +88,13 @@ typedef enum {
  *                      in FP32 (relative error per product < 2^-16).  The switch is then
  *                      its own pass (bf_pass_info kind 2).  One right-hand side, d = 3 and
  *                      q > 5 run the BF_PREC_MIXED kernels and equal them bit for bit.  No
- *                      phase tables (BF_ERR_UNSUPPORTED), no persistent batches. */
+ *                      phase tables (BF_ERR_UNSUPPORTED), no persistent batches.
+ *                      With bf_params.tc_levels = 1 the column merge levels below the
+ *                      switch run on the tensor cores as well: per merge block the
+ *                      modulated inputs of its 4 source children times the constant
+ *                      Kronecker product of the child->parent interpolation matrices
+ *                      (a real 128 x 32 x 128 GEMM per block, BF16x3, FP32 accumulation),
+ *                      one level per pass (bf_pass_info kind 3). */
 typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1, BF_PREC_MIXED_SFU = 2, BF_PREC_BF16X3 = 3 } bf_precision;
 
 typedef struct {
@@ -102,7 +108,9 @@ typedef struct {
     int32_t max_nrhs;         /* largest nrhs an apply may use (>= 1)                       */
     int32_t fuse_levels;      /* levels fused per kernel pass; 0 selects the default        */
     int32_t phase_tables;     /* 1: evaluate every phase factor once, at plan creation      */
-    int32_t reserved[6];      /* must be zero                                               */
+    int32_t tc_levels;        /* BF_PREC_BF16X3: 1 also runs the column merge levels on the  */
+                              /* tensor cores (below); 0 keeps them on the CUDA cores       */
+    int32_t reserved[5];      /* must be zero                                               */
 } bf_params;
 
 /* Phase tables (phase_tables = 1; mixed precisions, d = 2, q <= 5): the precompute

@@ -40,7 +40,7 @@ class BfParams(ctypes.Structure):
                 ("phase_scale", ctypes.c_double), ("tgt_off", ctypes.c_double), ("src_off", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("switch_level", ctypes.c_int32), ("node_kind", ctypes.c_int32),
                 ("max_nrhs", ctypes.c_int32), ("fuse_levels", ctypes.c_int32), ("phase_tables", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 6)]
+                ("tc_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 _lib = None
@@ -122,7 +122,7 @@ class Plan:
     def __init__(self, d: int, N: int, q: int, phase: str, precision: str = "mixed", scale: float = 1.0,
                  x_lo=None, x_w=None, y_lo=None, y_w=None, tgt_off: float = 0.0, src_off: float = 0.0,
                  switch_level: int = -1, node_kind: int = 0, max_nrhs: int = 1, fuse_levels: int = 0,
-                 phase_tables: bool = False, sources=None, targets=None):
+                 phase_tables: bool = False, sources=None, targets=None, tc_levels: bool = False):
         lib = load()
         p = BfParams()
         _check(lib.bf_params_default(d, N, ctypes.byref(p)), "bf_params_default")
@@ -139,6 +139,7 @@ class Plan:
         p.max_nrhs = max_nrhs
         p.fuse_levels = fuse_levels
         p.phase_tables = 1 if phase_tables else 0
+        p.tc_levels = 1 if tc_levels else 0
         h = ctypes.c_void_p()
         if sources is None and targets is None:
             _check(lib.bf_plan_create(d, N, q, PHASE[phase], ctypes.byref(p), ctypes.byref(h)), "bf_plan_create")
@@ -158,12 +159,12 @@ class Plan:
 
     @classmethod
     def from_spec(cls, spec, max_nrhs: int = 1, precision: str | None = None, fuse_levels: int = 0,
-                  phase_tables: bool = False, sources=None, targets=None) -> "Plan":
+                  phase_tables: bool = False, sources=None, targets=None, tc_levels: bool = False) -> "Plan":
         """Plan for a workload spec; sources / targets ((n, d) arrays) make a point-set plan."""
         x_lo, x_w, y_lo, y_w = spec.domain()
         return cls(spec.d, spec.N, spec.q, spec.phase, precision or spec.precision, spec.scale,
                    x_lo, x_w, y_lo, y_w, spec.tgt_off, spec.src_off, spec.switch_level, spec.node_kind,
-                   max_nrhs, fuse_levels, phase_tables, sources, targets)
+                   max_nrhs, fuse_levels, phase_tables, sources, targets, tc_levels)
 
     @property
     def handle(self) -> int:
@@ -272,7 +273,7 @@ class Plan:
             kind, l0, k, fl = i32(), i32(), i32(), i32()
             _check(load().bf_pass_info(self._h, nrhs, i, ctypes.byref(kind), ctypes.byref(l0), ctypes.byref(k),
                                        ctypes.byref(fl)), "bf_pass_info")
-            out.append(dict(kind=("col", "row", "switch_tc")[kind.value], l0=l0.value, k=k.value,
+            out.append(dict(kind=("col", "row", "switch_tc", "col_tc")[kind.value], l0=l0.value, k=k.value,
                             init=bool(fl.value & 1), switch=bool(fl.value & 2), final=bool(fl.value & 4)))
         return out
 

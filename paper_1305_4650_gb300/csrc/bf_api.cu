@@ -333,16 +333,31 @@ std::vector<Pass> schedule(const bf_plan_s *p, int kmax, int64_t np_cta, bool re
 }
 
 // BF_PREC_BF16X3: the multi-RHS column pass that ends at the switch level stops before
-// the switch, and a tensor-core switch pass (row = 2, l0 = m) follows it
+// the switch, and a tensor-core switch pass (row = 2, l0 = m) follows it.  With tc_levels
+// every column merge level becomes a tensor-core pass of its own (row = 3, k = 1) and the
+// init a multi-RHS pass without levels.
 void tc_switch_split(const bf_plan_s *p, std::vector<Pass> &sc)
 {
     if (p->prec != BF_PREC_BF16X3 || !p->fns->switch_tc) return;
-    for (size_t i = 0; i < sc.size(); ++i)
-        if (sc[i].row == 0 && (sc[i].flags & bfk::F_SWITCH)) {
-            sc[i].flags &= ~bfk::F_SWITCH;
-            sc.insert(sc.begin() + (long)i + 1, Pass{2, p->m, 0, bfk::F_SWITCH, 1});
-            return;
+    std::vector<Pass> out;
+    const bool levels = p->prm.tc_levels && p->fns->col_tc;
+    for (const Pass &ps : sc) {
+        if (ps.row != 0) {
+            out.push_back(ps);
+            continue;
         }
+        if (levels) {
+            if (ps.flags & bfk::F_INIT)
+                out.push_back(make_pass(p, p->fns->mr_nthreads / p->r, 0, 0, 0, bfk::F_INIT));
+            for (int l = ps.l0; l < ps.l0 + ps.k; ++l) out.push_back(Pass{3, l, 1, 0, 1});
+        } else {
+            Pass c = ps;
+            c.flags &= ~bfk::F_SWITCH;
+            out.push_back(c);
+        }
+        if (ps.flags & bfk::F_SWITCH) out.push_back(Pass{2, p->m, 0, bfk::F_SWITCH, 1});
+    }
+    sc = out;
 }
 
 template <class P>
@@ -434,15 +449,17 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
         a.win = static_cast<const typename P::C *>(buf[i & 1]);
         a.wout = static_cast<typename P::C *>(buf[(i + 1) & 1]);
         a.err = p->errflag;
-        if (ps.row == 2) {   // the switch on the tensor cores: units of two pairs, persistent CTAs
+        if (ps.row >= 2) {   // the switch (2) or a column level (3) on the tensor cores, persistent CTAs
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const int per_sm = p->fns->switch_tc_ctas_per_sm();
+            const bool sw = ps.row == 2;
+            const int per_sm = sw ? p->fns->switch_tc_ctas_per_sm() : p->fns->col_tc_ctas_per_sm();
             if (per_sm < 1) return BF_ERR_UNSUPPORTED;
-            int64_t grid = (p->npts / 2) >> (a.shard_mode == 1 ? sg : 0);
+            int64_t grid = (p->npts / (sw ? 2 : 4)) >> (a.shard_mode == 1 ? sg : 0);
             if ((int64_t)sms * per_sm < grid) grid = (int64_t)sms * per_sm;
-            cudaError_t e = p->fns->switch_tc(&a, (unsigned)grid, (unsigned)((nrhs + 15) / 16), p->fns->switch_tc_smem, s);
+            cudaError_t e = (sw ? p->fns->switch_tc : p->fns->col_tc)(&a, (unsigned)grid, (unsigned)((nrhs + 15) / 16),
+                                                                     sw ? p->fns->switch_tc_smem : p->fns->col_tc_smem, s);
             if (e != cudaSuccess) return cuda_fail(p, e);
             continue;
         }
@@ -1100,9 +1117,10 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     if (prm->node_kind != 0 && prm->node_kind != 1) return BF_ERR_INVALID_ARG;
     if (prm->max_nrhs < 1 || prm->max_nrhs > 65535) return BF_ERR_INVALID_ARG;
     if (prm->fuse_levels < 0 || prm->fuse_levels > 8) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 6; ++i)
+    for (int i = 0; i < 5; ++i)
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
     if (prm->phase_tables != 0 && prm->phase_tables != 1) return BF_ERR_INVALID_ARG;
+    if (prm->tc_levels != 0 && prm->tc_levels != 1) return BF_ERR_INVALID_ARG;
     if (prm->phase_tables && (prm->precision == BF_PREC_FP64 || prm->precision == BF_PREC_BF16X3 || d != 2 || q > 5))
         return BF_ERR_UNSUPPORTED;
 
@@ -1160,7 +1178,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         for (; rc >= 1 && !fits; --rc) {
             fits = true;
             for (const Pass &ps : p->passes_mr)
-                if (ps.row != 2 && mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
+                if (ps.row < 2 && mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
             if (fits) p->mr_rc = rc;
         }
         if (!fits) p->passes_mr.clear();
@@ -1387,7 +1405,7 @@ bf_status bf_plan_autotune(bf_plan p, int nrhs, int reps, void *stream, double *
                         tc_switch_split(p, cand);
                         bool fits = true;
                         for (const Pass &ps : cand)
-                            if (ps.row != 2 && mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
+                            if (ps.row < 2 && mr_smem(p, ps, nr, rc) > 227 * 1024) fits = false;
                         if (!fits) continue;
                         p->passes_mr = cand;
                         p->mr_rc = rc;

@@ -167,6 +167,37 @@ int switch_tc_ctas_per_sm()
     return n > res ? n : res;
 }
 
+template <int Q, class P, int K>
+cudaError_t launch_col_tc(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
+{
+    static size_t granted[64] = {0};
+    cudaError_t e = prepare(bfk::k_col_tc<Q, P, K>, smem, granted);
+    if (e != cudaSuccess) return e;
+    bfk::k_col_tc<Q, P, K><<<dim3(gx, gy), bfk::ColTC<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    return cudaGetLastError();
+}
+
+// as switch_tc_ctas_per_sm, for the tensor-core column level
+template <int Q, class P, int K>
+int col_tc_ctas_per_sm()
+{
+    static size_t granted[64] = {0};
+    if (prepare(bfk::k_col_tc<Q, P, K>, bfk::ColTC<Q>::SMEM, granted) != cudaSuccess) return 0;
+    int dev = 0;
+    cudaFuncAttributes fa{};
+    cudaDeviceProp pr{};
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, bfk::k_col_tc<Q, P, K>) != cudaSuccess ||
+        cudaGetDeviceProperties(&pr, dev) != cudaSuccess)
+        return 0;
+    const int regs_cta = (bfk::ColTC<Q>::NT / 32) * ((fa.numRegs * 32 + 255) / 256 * 256);
+    const size_t smem_cta = bfk::ColTC<Q>::SMEM + fa.sharedSizeBytes + pr.reservedSharedMemPerBlock;
+    int res = pr.maxBlocksPerMultiProcessor;
+    if (regs_cta > 0 && pr.regsPerMultiprocessor / regs_cta < res) res = pr.regsPerMultiprocessor / regs_cta;
+    if ((int)(pr.sharedMemPerMultiprocessor / smem_cta) < res) res = (int)(pr.sharedMemPerMultiprocessor / smem_cta);
+    if (pr.maxThreadsPerMultiProcessor / bfk::ColTC<Q>::NT < res) res = pr.maxThreadsPerMultiProcessor / bfk::ColTC<Q>::NT;
+    return res;
+}
+
 template <int D, int Q, class P, int K>
 cudaError_t launch_ctab(const void *kargs, void *out, int levels)
 {
@@ -201,14 +232,16 @@ const PassFns *fns_for()
                                   {TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_BUILD> : nullptr,
                                    TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_TABLE> : nullptr},
                                   TC ? launch_switch_tc<QT, P, K> : nullptr,
-                                  TC ? switch_tc_ctas_per_sm<QT, P, K> : nullptr, TC ? bfk::SwTC<QT>::SMEM : 0};
+                                  TC ? switch_tc_ctas_per_sm<QT, P, K> : nullptr, TC ? bfk::SwTC<QT>::SMEM : 0,
+                                  TC ? launch_col_tc<QT, P, K> : nullptr,
+                                  TC ? col_tc_ctas_per_sm<QT, P, K> : nullptr, TC ? bfk::ColTC<QT>::SMEM : 0};
         return &f;
     } else {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, {nullptr, nullptr, nullptr},
                                   {nullptr, nullptr, nullptr}, 0, 0, nullptr, nullptr, nullptr,
                                   launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T),
-                                  {nullptr, nullptr}, {nullptr, nullptr}, nullptr, nullptr, 0};
+                                  {nullptr, nullptr}, {nullptr, nullptr}, nullptr, nullptr, 0, nullptr, nullptr, 0};
         return &f;
     }
 }

@@ -34,6 +34,11 @@ struct PassFns {
     pass_fn switch_tc;
     int (*switch_tc_ctas_per_sm)();   // CTAs of switch_tc that fit on one SM
     size_t switch_tc_smem;            // its dynamic shared memory per CTA
+    // one column merge level on the tensor cores (bf_tc.cuh, same conditions; null if absent):
+    // grid_x CTAs take merge blocks, grid_y blocks of 16 right-hand sides
+    pass_fn col_tc;
+    int (*col_tc_ctas_per_sm)();
+    size_t col_tc_smem;
 };
 
 // (d, q, precision, phase kind) -> kernels, or null if that combination is not compiled.

@@ -287,4 +287,225 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
     if (warp == 0) umma::dealloc(tmem, ST::TMEM_COLS);
 }
 
+// ============================================================================
+// One column-form merge level (Section 1.4) on the tensor cores, for several right-hand
+// sides: per merge block (target box A at level l, parent source box B_p at level l+1; its
+// inputs are the 4 consecutive pairs (A, B_c), its outputs the pairs (A_alpha, B_p))
+//     w_out(alpha, t) = conj(e_d(alpha, t)) sum_{c, t'} Mk[t][(c, t')] e_m(alpha, c, t') w_c(t')
+// with e_m = e^{2 pi i Phi(x0(A_alpha), y_t'^{B_c})} (modulation), e_d = e^{2 pi i Phi(x0(A_alpha),
+// y_t^{B_p})} (demodulation) and Mk the constant Kronecker product M_{c_0}(t_0, t'_0)
+// M_{c_1}(t_1, t'_1) of the child->parent matrices.  The sum is a real GEMM D = A Bt:
+//     A[(alpha, rhs, re/im)][(c, t')]  the modulated inputs u = e_m w_c, split re / im over
+//                                      rows: 4 x 16 x 2 = 128 rows (M = 128);
+//     B[t][(c, t')] = Mk               N = 32 (r <= 25 used), the same for every block;
+//     K = (c, t') in slots of 32 per child c: 128 (4 r used), 8 MMA steps.
+// BF16x3 split of both operands, FP32 accumulation in tensor memory, as in the switch.
+template <int Q>
+struct ColTC {
+    static constexpr int RR = Q * Q;
+    static constexpr int NPP = 16;                          // right-hand sides per block
+    static constexpr int KS = 32;                           // K slot per input child
+    static constexpr int M = 128, N = 32, KP = 4 * KS, NKS = KP / 16;
+    static constexpr uint32_t LBO = 128, SBO = (KP / 8) * 128;
+    static constexpr uint32_t A_BYTES = (M / 8) * SBO;      // one BF16 part of A (32 KB)
+    static constexpr uint32_t B_BYTES = (N / 8) * SBO;      // one BF16 part of B (8 KB)
+    static constexpr int NT = 256;
+    static constexpr int TMEM_COLS = 32;
+    static constexpr uint32_t W_BYTES = NPP * 4 * RR * 8;   // a block's inputs for 16 right-hand sides
+    static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + W_BYTES + 5 * 4 * RR * 8 + 64;
+    static_assert(RR <= 32 && RR <= KS, "one slot per child holds its r nodes");
+    static_assert((4 * RR * 8) % 16 == 0, "a block's inputs per right-hand side are whole 16-byte pieces");
+};
+
+// Column level l -> l+1 (a.l0 = l): reads a.win (level l), writes a.wout (level l+1), both
+// [rhs][pair][r]; right-hand sides 16 blockIdx.y .. +15; blocks taken blockIdx.x, + gridDim.x.
+// Sharding mode 1: the launch covers the blocks whose parent source box carries the rank's bits.
+template <int Q, class P, int K>
+__global__ void __launch_bounds__(ColTC<Q>::NT) k_col_tc(const KArgs<P> a)
+{
+    using ST = ColTC<Q>;
+    using C = typename P::C;
+    using PH = Ph<P, 2, K>;
+    constexpr int RR = ST::RR, D = 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *Ah = smem_raw, *Al = Ah + ST::A_BYTES, *Bh = Al + ST::A_BYTES, *Bl = Bh + ST::B_BYTES;
+    unsigned char *Wst = Bl + ST::B_BYTES;                                   // [rhs][c][t'] inputs
+    C *PM = reinterpret_cast<C *>(Wst + ST::W_BYTES);                        // [alpha][c][t'] e_m
+    C *PD = PM + 4 * 4 * RR;                                                 // [alpha][t]      e_d
+    uint64_t *bar = reinterpret_cast<uint64_t *>(PD + 4 * RR);
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
+    int *sfail = reinterpret_cast<int *>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    {
+        uint4 *z = reinterpret_cast<uint4 *>(smem_raw);
+        const int n16 = (int)((2 * ST::A_BYTES + 2 * ST::B_BYTES) / 16);
+        for (int i = tid; i < n16; i += ST::NT) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (warp == 0) umma::alloc(tslot, ST::TMEM_COLS);
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+        *sfail = 0;
+    }
+    umma::fence_before_sync();
+    __syncthreads();
+    umma::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    // B = Mk, once: items (t, c), rows t, slot c
+    for (int it = tid; it < RR * 4; it += ST::NT) {
+        const int t = it % RR, c = it / RR, t0 = t % Q, t1 = t / Q, c0 = c & 1, c1 = c >> 1;
+        for (int j = 0; j < RR; j += 2) {
+            const float m0 = a.M[c0][t0][j % Q] * a.M[c1][t1][j / Q];
+            const float m1 = j + 1 < RR ? a.M[c0][t0][(j + 1) % Q] * a.M[c1][t1][(j + 1) / Q] : 0.0f;
+            uint32_t hi, lo;
+            umma::split2(m0, m1, hi, lo);
+            const uint32_t off = umma::kmajor_off(t, ST::KS * c + j, ST::LBO, ST::SBO);
+            *reinterpret_cast<uint32_t *>(Bh + off) = hi;
+            *reinterpret_cast<uint32_t *>(Bl + off) = lo;
+        }
+    }
+
+    const int l = a.l0, L = a.L;
+    const int lbp = D * (L - l - 1);                      // log2 of the parent source boxes per target box
+    const int64_t nunits = (a.npts / 4) >> (a.shard_mode == 1 ? a.shard_g : 0);
+    auto uid = [&](int64_t v) -> int64_t {
+        if (a.shard_mode != 1) return v;
+        const int lper = lbp - a.shard_g;
+        return ((v >> lper) << lbp) | ((int64_t)a.shard_r << lper) | (v & ((1LL << lper) - 1));
+    };
+    const int rhs0 = (int)blockIdx.y * ST::NPP;
+    const int nr = min(ST::NPP, a.nrhs - rhs0);
+    const uint32_t idesc = umma::idesc_bf16_f32(ST::M, ST::N);
+    unsigned parity = 0;
+
+    auto fetch = [&](int64_t v) {
+        constexpr int per_rhs = 4 * RR * 8 / 16;
+        if (v < nunits) {
+            for (int c = tid; c < nr * per_rhs; c += ST::NT) {
+                const int rb = c / per_rhs, o = c - rb * per_rhs;
+                const char *src = reinterpret_cast<const char *>(a.win + (int64_t)(rhs0 + rb) * a.wstride + 4 * uid(v) * RR) + 16 * o;
+                const uint32_t dst = umma::saddr(Wst + rb * (4 * RR * 8) + 16 * o);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    fetch(blockIdx.x);
+
+    for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
+        const int64_t U = uid(u);                          // block: target box A, parent source box B_p
+        const uint32_t A = (uint32_t)(U >> lbp), Bp = (uint32_t)(U & ((1LL << lbp) - 1));
+        int cbq[DMAX];
+        morton_decode<D>(Bp, L - l - 1, cbq);
+        // ---- phase factors: e_m (alpha, c, t') and e_d (alpha, t)
+        for (int it = tid; it < 4 * 4 * RR + 4 * RR; it += ST::NT) {
+            const bool mod = it < 16 * RR;
+            const int jt = mod ? it : it - 16 * RR;
+            const int alpha = jt / (mod ? 4 * RR : RR), rest = jt % (mod ? 4 * RR : RR);
+            const uint32_t Aa = (A << D) + alpha;
+            int ca[DMAX];
+            morton_decode<D>(Aa, l + 1, ca);
+            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+            if (mod) {
+                const int c = rest / RR, tp = rest % RR;
+                const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, 2 * cbq[0] + (c & 1), tp % Q), 0),
+                                                     PH::part(tA, sget<P, Q>(a, 1, l, 2 * cbq[1] + (c >> 1), tp / Q), 1));
+                PM[jt] = expphase_part<P, D, K>(a, tA, pt);
+            } else {
+                const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], rest % Q), 0),
+                                                     PH::part(tA, sget<P, Q>(a, 1, l + 1, cbq[1], rest / Q), 1));
+                PD[jt] = expphase_part<P, D, K>(a, tA, pt);
+            }
+        }
+        asm volatile("cp.async.wait_group 0;" ::: "memory");   // the block's inputs have landed
+        __syncthreads();
+        // ---- A: items (rhs, c, alpha), rhs fastest: u = e_m w_c over the slot of c, rows re / im
+        {
+            const int rb = tid % ST::NPP, c = (tid / ST::NPP) % 4, alpha = tid / (4 * ST::NPP);
+            if (rb < nr) {
+                const C *w = reinterpret_cast<const C *>(Wst) + (rb * 4 + c) * RR;
+                const C *e = PM + (alpha * 4 + c) * RR;
+                const int row = 32 * alpha + 2 * rb;
+#pragma unroll
+                for (int pc = 0; pc < ST::KS / 8; ++pc) {
+                    uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const int t0 = 8 * pc + 2 * j, t1 = t0 + 1;
+                        const C u0 = t0 < RR ? cmul(e[t0], w[t0]) : czero<C>();
+                        const C u1 = t1 < RR ? cmul(e[t1], w[t1]) : czero<C>();
+                        umma::split2(u0.x, u1.x, rh[j], rl[j]);
+                        umma::split2(u0.y, u1.y, ih[j], il[j]);
+                    }
+                    const int k = ST::KS * c + 8 * pc;
+                    *reinterpret_cast<uint4 *>(Ah + umma::kmajor_off(row, k, ST::LBO, ST::SBO)) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+                    *reinterpret_cast<uint4 *>(Al + umma::kmajor_off(row, k, ST::LBO, ST::SBO)) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+                    *reinterpret_cast<uint4 *>(Ah + umma::kmajor_off(row + 1, k, ST::LBO, ST::SBO)) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+                    *reinterpret_cast<uint4 *>(Al + umma::kmajor_off(row + 1, k, ST::LBO, ST::SBO)) = make_uint4(il[0], il[1], il[2], il[3]);
+                }
+            }
+        }
+        umma::fence_smem_to_async();
+        __syncthreads();
+        fetch(u + gridDim.x);   // every A item has read the staging buffer: the next block's copies overlap the rest
+        if (tid == 0) {
+            umma::fence_after_sync();
+            const uint32_t ah = umma::saddr(Ah), al = umma::saddr(Al), bh = umma::saddr(Bh), bl = umma::saddr(Bl);
+#pragma unroll
+            for (int ks = 0; ks < ST::NKS; ++ks) {
+                const uint32_t o = (uint32_t)ks * 2u * ST::LBO;
+                const uint64_t dah = umma::desc_kmajor(ah + o, ST::LBO, ST::SBO);
+                const uint64_t dal = umma::desc_kmajor(al + o, ST::LBO, ST::SBO);
+                const uint64_t dbh = umma::desc_kmajor(bh + o, ST::LBO, ST::SBO);
+                const uint64_t dbl = umma::desc_kmajor(bl + o, ST::LBO, ST::SBO);
+                umma::mma_bf16(tmem, dah, dbh, idesc, ks > 0);
+                umma::mma_bf16(tmem, dah, dbl, idesc, 1);
+                umma::mma_bf16(tmem, dal, dbh, idesc, 1);
+            }
+            umma::commit(bar);
+            if (!mbar_wait_ns(bar, parity, TC_WAIT_NS)) {
+                if (a.err) atomicExch(a.err, 1);
+                *sfail = 1;
+                mbar_wait_ns(bar, parity, TC_WAIT_NS);
+            }
+        }
+        parity ^= 1u;
+        __syncthreads();
+        if (*sfail) break;
+        umma::fence_after_sync();
+        // ---- epilogue: warp w reads the rows of child alpha = w % 4 (lane = 2 rhs + re/im),
+        // columns t = 16 (w / 4) .. + 15; lanes 2 rhs and 2 rhs + 1 swap halves, demodulate, store
+        {
+            const int alpha = warp & 3, half = warp >> 2, rb = lane >> 1, cmp = lane & 1;
+            float v[16];
+            umma::ld8(tmem + ((uint32_t)(32 * alpha) << 16) + (uint32_t)(16 * half), v);
+            umma::ld8(tmem + ((uint32_t)(32 * alpha) << 16) + (uint32_t)(16 * half + 8), v + 8);
+            float recv[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) recv[j] = __shfl_xor_sync(0xffffffffu, cmp ? v[j] : v[8 + j], 1);
+            if (rb < nr) {
+                const int64_t outp = ((int64_t)((A << D) + alpha) << lbp) + Bp;   // pair (A_alpha, B_p) at level l+1
+                C *wo = a.wout + (int64_t)(rhs0 + rb) * a.wstride + outp * RR;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const int t = 16 * half + 8 * cmp + j;
+                    if (t < RR) {
+                        C z;
+                        z.x = cmp ? recv[j] : v[j];
+                        z.y = cmp ? v[8 + j] : recv[j];
+                        __stcs(wo + t, cjmul(PD[alpha * RR + t], z));
+                    }
+                }
+            }
+        }
+        umma::fence_before_sync();
+        __syncthreads();   // the next block's phase stage rewrites PD, its MMAs the tensor memory
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    umma::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) umma::dealloc(tmem, ST::TMEM_COLS);
+}
+
 }  // namespace bfk

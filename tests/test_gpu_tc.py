@@ -126,3 +126,59 @@ def test_bf16x3_refuses_tables_and_batches(bf):
     with pytest.raises(bf.BfError):
         bf.Batch([plan], [4])
     plan.close()
+
+
+# ---- the column merge levels on the tensor cores (bf_params.tc_levels = 1)
+
+def _apply_levels(bf, spec, nrhs, seed, autotune=False):
+    import torch
+    plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="bf16x3", tc_levels=True)
+    if autotune:
+        plan.autotune(nrhs, reps=1)
+    g = torch.from_numpy(wl.source_values(spec, nrhs, np.complex64, seed=seed)).cuda()
+    f = plan.apply(g)
+    torch.cuda.synchronize()
+    passes = plan.passes(nrhs)
+    timed_out = plan.table_info()["timed_out"]
+    plan.close()
+    return g.cpu().numpy(), f.cpu().numpy(), passes, timed_out
+
+
+@pytest.mark.parametrize("phase,L,q,nrhs", [("hypradon", 5, 5, 2), ("hypradon", 6, 5, 16), ("hypradon", 7, 5, 19),
+                                            ("genradon", 6, 5, 5), ("dot", 4, 5, 3), ("separable", 5, 5, 4),
+                                            ("genradon", 6, 4, 7), ("hypradon", 5, 3, 17), ("genradon", 4, 2, 3),
+                                            ("hypradon", 2, 5, 20), ("genradon", 1, 5, 3)])
+def test_tc_levels_against_oracle(bf, phase, L, q, nrhs):
+    spec = (wl.hypradon(L) if phase == "hypradon" else wl.genradon2d(L=L).with_(phase=phase)).with_(q=q)
+    g, out, passes, timed_out = _apply_levels(bf, spec, nrhs, seed=700 + L + q)
+    assert not timed_out
+    kinds = [p["kind"] for p in passes]
+    assert kinds.count("col_tc") == spec.switch_level and kinds.count("switch_tc") == 1 and "col" in kinds
+    ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.astype(np.complex128))
+    for j in range(nrhs):
+        assert rel(out[j], ref[j]) <= TOL_ORACLE, (j, rel(out[j], ref[j]))
+
+
+@pytest.mark.parametrize("L,nrhs", [(8, 16), (9, 16), (9, 19)])
+def test_tc_levels_benchmark_sizes(bf, L, nrhs):
+    # against the FP32 multi-RHS apply everywhere and the restricted oracle on one box
+    spec = wl.hypradon(L)
+    g, out, passes, timed_out = _apply_levels(bf, spec, nrhs, seed=760 + L, autotune=True)
+    assert not timed_out
+    _, f32, _, _ = _apply(bf, spec, nrhs, "mixed", seed=760 + L)
+    for j in range(nrhs):
+        assert rel(out[j], f32[j]) <= 2 * TOL_FP32, (j, rel(out[j], f32[j]))
+    P = oracle.Problem(**spec.oracle_kwargs())
+    lvl = spec.switch_level
+    box = (1 << (2 * lvl)) // 3
+    tg = oracle.restricted_targets(P, lvl, box)
+    ref = oracle.butterfly(P, g[0].astype(np.complex128), restrict=(lvl, box))
+    assert rel(out[0][tg], ref[tg]) <= TOL_ORACLE
+
+
+def test_tc_levels_only_with_bf16x3(bf):
+    # the option changes nothing for the other precisions' schedules
+    spec = wl.hypradon(5)
+    p = bf.Plan.from_spec(spec, max_nrhs=4, precision="mixed", tc_levels=True)
+    assert all(x["kind"] in ("col", "row") for x in p.passes(4))
+    p.close()
