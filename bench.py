@@ -180,10 +180,11 @@ def phase_ops(phase: str, d: int, q: int) -> float:
     double-float formulas with the per-dimension split of Phi: the part of source
     coordinate 0 (evaluated per phase), the parts of coordinates >= 1 (shared by the q
     phases of a node row), the sum of parts (an ordered fast two-sum where the parts are
-    non-negative), the final sqrt / mod-1 step, and 22 for the quadrant-reduced sincos
-    (setup 5, sin 5, cos 5, quadrant 7).  The frac of a double-float product costs 5
-    (two FMAs for the nearest integer and the remainder, two for the cross terms)."""
-    sincos = 22
+    non-negative), the final sqrt / mod-1 step, and 18 for the quadrant-reduced sincos
+    (setup 4, sin 4, cos 3, quadrant 7: degree-7 and degree-6 minimax polynomials in r^2 with
+    2 pi folded in).  The frac of a double-float product costs 5 (two FMAs for the nearest
+    integer and the remainder, two for the cross terms)."""
+    sincos = 18
     if phase == "dot":
         part, add, fin = 5, 1, 0
     elif phase == "genradon":
@@ -419,7 +420,7 @@ def run_ours(args, rank, world, local_rank):
     # ---- phase-table variants (every phase evaluated once at plan creation; the apply reads
     # the reduced phases (one RHS) or the factors (several) and evaluates no Phi)
     tables = None
-    if prec == "mixed" and spec.d == 2 and not args.no_tables:
+    if prec == "mixed" and (spec.d == 2 or nrhs == 1) and not args.no_tables:
         for tprec in ("mixed", "mixed_sfu"):
             ptb = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=tprec, phase_tables=True)
             tinfo = ptb.table_info()
@@ -749,6 +750,30 @@ def config3_record(steps, warmup, accuracy):
         outs[prec] = (g_np[0], f.cpu().numpy()[0])
         plan.close()
     rec["speedup_mixed_over_fp64"] = round(rec["fp64"]["ms_per_step"] / rec["mixed"]["ms_per_step"], 2)
+    # the plan-time phase table (the reduced phase of every factor, one float each) against the
+    # evaluating apply of the same schedule: time, bytes moved, and bit-identical results
+    hbm_peak = measured_hbm_gbs()
+    rec["phase_tables"] = {}
+    for tprec in ("mixed", "mixed_sfu"):
+        pt = bf.Plan.from_spec(spec, precision=tprec, phase_tables=True)
+        pe = bf.Plan.from_spec(spec, precision=tprec)
+        g = torch.from_numpy(g32).cuda()
+        ft, fe = torch.empty_like(g), torch.empty_like(g)
+        ms_t = timed_apply(lambda: pt.apply(g, ft), stream, steps, 2)
+        ms_e = timed_apply(lambda: pe.apply(g, fe), stream, steps, 2)
+        torch.cuda.synchronize()
+        info = pt.table_info()
+        moved = info["bytes"] + 2 * max(len(pt.passes(1)) - 1, 1) * spec.npts * spec.r * 8
+        rec["phase_tables"][tprec] = {
+            "ms_per_step": round(ms_t, 3), "value": spec.npts / (ms_t * 1e-3),
+            "evaluating_ms_per_step": round(ms_e, 3), "speedup_over_evaluating": round(ms_e / ms_t, 2),
+            "table_gb": round(info["bytes"] / 1e9, 3), "build_ms": round(info["build_ms"], 2),
+            "bit_identical_to_evaluating": bool(torch.equal(ft, fe)), "timed_out": bool(info["timed_out"]),
+            "hbm": {"achieved_gbs": round(moved / (ms_t * 1e-3) / 1e9, 1), "peak_gbs": hbm_peak[0],
+                    "frac": round(moved / (ms_t * 1e-3) / 1e9 / hbm_peak[0], 3), "peak_basis": hbm_peak[1]}}
+        pt.close()
+        pe.close()
+        del g, ft, fe
     if accuracy:
         import oracle
         rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))

@@ -113,15 +113,18 @@ typedef struct {
     int32_t reserved[5];      /* must be zero                                               */
 } bf_params;
 
-/* Phase tables (phase_tables = 1; mixed precisions, d = 2, q <= 5): the precompute
- * trade-off of Section 1.4.  bf_plan_create evaluates the phase factors of the apply once,
- * into device memory, and every bf_apply reads them instead of evaluating Phi.  Two forms:
+/* Phase tables (phase_tables = 1; mixed precisions; d = 2 with q <= 5, or d = 3): the
+ * precompute trade-off of Section 1.4.  bf_plan_create evaluates the phase factors of the
+ * apply once, into device memory, and every bf_apply reads them instead of evaluating Phi.
+ * Two forms:
  *  - max_nrhs = 1: the single-RHS kernels record the reduced phase (Phi minus an integer,
- *    one float) of every factor of the merges and of the switch -- 5 r L + r^2 floats per
- *    point (r^2 only where the switch is not factorised): 7.9 GB at d = 2, N = 1024, q = 5.
- *    The apply reads them with coalesced loads and evaluates only the sin/cos, so its
- *    results equal the evaluating apply bit for bit.
- *  - max_nrhs > 1: the multi-RHS kernels record the complex factors themselves (5 r L + r^2
+ *    one float) of every factor of the merges and of the switch -- (2^d + 1) r L + r^2
+ *    floats per point (r^2 only where the switch is not factorised): 7.9 GB at d = 2,
+ *    N = 1024, q = 5 and at d = 3, N = 64, q = 4.  The apply reads them with coalesced
+ *    loads and evaluates only the sin/cos, so its results equal the evaluating apply bit
+ *    for bit.
+ *  - max_nrhs > 1 (d = 2 only; BF_ERR_UNSUPPORTED at d = 3): the multi-RHS kernels record
+ *    the complex factors themselves (5 r L + r^2
  *    + 2 r + 1 complex64 numbers per point; 16.2 GB at N = 1024) and the apply, for any
  *    nrhs, fetches each CTA's table blocks with bulk copies (the TMA engine, cp.async.bulk)
  *    into two shared-memory buffers two blocks ahead of use; results equal the evaluating

@@ -849,7 +849,7 @@ bf_status build_tile_table(bf_plan p)
     p->ftab_cta.clear();
     for (const Pass &ps : p->passes) {
         const int64_t npr = (int64_t)ps.T << (p->d * ps.k), ctas = (p->npts >> (p->d * ps.k)) / ps.T;
-        int64_t per = ps.k * 5 * r * npr;
+        int64_t per = ps.k * ((1 << p->d) + 1) * r * npr;   // per pair and level: 2^d r modulations, r demodulations
         if (!ps.row && (ps.flags & bfk::F_SWITCH) && tab_switch) per += r * r * npr;
         p->ftab_off.push_back(total);
         p->ftab_cta.push_back(per);
@@ -1121,7 +1121,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
     if (prm->phase_tables != 0 && prm->phase_tables != 1) return BF_ERR_INVALID_ARG;
     if (prm->tc_levels != 0 && prm->tc_levels != 1) return BF_ERR_INVALID_ARG;
-    if (prm->phase_tables && (prm->precision == BF_PREC_FP64 || prm->precision == BF_PREC_BF16X3 || d != 2 || q > 5))
+    if (prm->phase_tables && (prm->precision == BF_PREC_FP64 || prm->precision == BF_PREC_BF16X3 || (d == 2 && q > 5)))
         return BF_ERR_UNSUPPORTED;
 
     bf_plan p = new (std::nothrow) bf_plan_s();

@@ -47,6 +47,9 @@ enum { F_INIT = 1, F_SWITCH = 2, F_FINAL = 4 };
 // in the plan's phase table (PM_BUILD, at plan creation), or read from it (PM_TABLE)
 enum { PM_COMPUTE = 0, PM_BUILD = 1, PM_TABLE = 2 };
 
+// a compile-time integer passed to a generic lambda
+template <int V> struct IntC { static constexpr int value = V; };
+
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
 // ------------------------------------------------------------ double-float
@@ -160,28 +163,29 @@ using PMIX = PMIXT<false>;
 using PMIXF = PMIXT<true>;
 
 __device__ __forceinline__ void sincos2pi(double fr, double &s, double &c) { sincospi(2.0 * fr, &s, &c); }
-// sin and cos of 2 pi f for |f| < 2^20, written from the Taylor series: quadrant
-// reduction f = j/4 + r with |r| <= 1/8, then sin a (degree 9) and cos a (degree 10)
-// for a = 2 pi r, |a| <= pi/4 (truncation error < 3e-8); the quadrant j rotates
-// (cos, sin) by j * 90 degrees.  Max abs error ~1e-7 (checked against FP64 sincospi
-// by bf_selfcheck_sincos).
+// sin and cos of 2 pi f for |f| < 2^20: quadrant reduction f = j/4 + r with |r| <= 1/8,
+// then sin(2 pi r) = r S(r^2) (degree 7) and cos(2 pi r) = C(r^2) (degree 6) with 2 pi
+// folded into the coefficients, which are minimax fits of the absolute error on
+// |r| <= 1/8 (Remez exchange, csrc/sincos_fit.py; truncation error 1.2e-9 and 3.2e-8); the quadrant j rotates
+// (cos, sin) by j * 90 degrees.  Max abs error ~1e-7 (checked against FP64 sincospi by
+// bf_selfcheck_sincos).  sincos2pi2 (bf_pair.cuh) performs the same operations per lane.
+constexpr float SC_S0 = 6.28318500518798828f, SC_S1 = -41.3416290283203125f, SC_S2 = 81.5881271362304688f,
+                SC_S3 = -75.2400665283203125f;
+constexpr float SC_C1 = -19.7391681671142578f, SC_C2 = 64.9232254028320312f, SC_C3 = -83.665924072265625f;
 __device__ __forceinline__ void sincos2pi(float f, float &s, float &c)
 {
     const float M = 12582912.0f;
     const float t = __fmaf_rn(4.0f, f, M);                 // j + 1.5 * 2^23
     const int q = __float_as_int(t);                       // low two bits: j mod 4
     const float r = __fmaf_rn(-0.25f, __fsub_rn(t, M), f);
-    const float a = __fmul_rn(r, 6.28318530717958647692f);
-    const float a2 = __fmul_rn(a, a);
-    float ps = __fmaf_rn(a2, 2.75573192e-06f, -1.98412698e-04f);
-    ps = __fmaf_rn(a2, ps, 8.33333333e-03f);
-    ps = __fmaf_rn(a2, ps, -1.66666667e-01f);
-    const float sn = __fmaf_rn(__fmul_rn(a, a2), ps, a);
-    float pc = __fmaf_rn(a2, -2.75573192e-07f, 2.48015873e-05f);
-    pc = __fmaf_rn(a2, pc, -1.38888889e-03f);
-    pc = __fmaf_rn(a2, pc, 4.16666667e-02f);
-    pc = __fmaf_rn(a2, pc, -0.5f);
-    const float cs = __fmaf_rn(a2, pc, 1.0f);
+    const float u = __fmul_rn(r, r);
+    float ps = __fmaf_rn(u, SC_S3, SC_S2);
+    ps = __fmaf_rn(u, ps, SC_S1);
+    ps = __fmaf_rn(u, ps, SC_S0);
+    const float sn = __fmul_rn(r, ps);
+    float pc = __fmaf_rn(u, SC_C3, SC_C2);
+    pc = __fmaf_rn(u, pc, SC_C1);
+    const float cs = __fmaf_rn(u, pc, 1.0f);
     const float s1 = (q & 1) ? cs : sn;
     const float c1 = (q & 1) ? sn : cs;
     s = __int_as_float(__float_as_int(s1) ^ ((q & 2) << 30));
@@ -666,6 +670,8 @@ struct Cfg {
     // the mixed-precision column pass at d = 2, q = 5 runs 3 CTAs per SM (64 registers, some
     // spills): measured 4.5% faster on its dominant pass and 9% on the init pass than 2 CTAs
     static constexpr int MINB_COL = (D == 2 && Q == 5 && !P::is_f64) ? 3 : MINB;
+    // the column pass reading a phase table (d = 2: one more CTA per SM than evaluating)
+    static constexpr int MINB_TAB = D == 2 ? MINB + 1 : MINB;
 };
 
 template <int D, int Q, class P, int K>
@@ -687,7 +693,7 @@ struct Tile {
     static_assert(sizeof(Geo) % 16 == 0 && sizeof(Geo) == (sizeof(typename PH::T) + 16 + 15) / 16 * 16,
                   "Geo size (the host reserves round16(tsize + 16) bytes per pair)");
 
-    // ---- reduced-phase table of a single-RHS pass (d = 2, mixed precisions).  The block of
+    // ---- reduced-phase table of a single-RHS pass (mixed precisions).  The block of
     // one stage is [phase j of an item][item], so one phase index over a warp's items is one
     // coalesced access.  The table holds the reduced phase that the evaluating kernel feeds
     // to its sincos, so reading it gives the evaluating kernel's results exactly.
@@ -702,7 +708,7 @@ struct Tile {
     static __device__ __forceinline__ int n_switch(const KArgs<P> &a) { return a.T * (1 << (D * a.k)) * QD1; }
     static __device__ __forceinline__ int n_row_a(const KArgs<P> &a) { return a.T * ((1 << (D * a.k)) >> D) * NC * QD1; }
     static __device__ __forceinline__ int n_row_b(const KArgs<P> &a) { return a.T * ((1 << (D * a.k)) >> D) * NC * Q; }
-    static constexpr int PH_COL_A = 2 * Q, PH_COL_B = Q, PH_SWITCH = Q * RR, PH_ROW_A = Q, PH_ROW_B = Q * NC;
+    static constexpr int PH_COL_A = (NC / 2) * QD1, PH_COL_B = Q, PH_SWITCH = Q * RR, PH_ROW_A = Q, PH_ROW_B = NC * QD1;
     // floats of the table one CTA of this pass reads (the phases of the switch of the
     // factorised kinds are evaluated, not tabled)
     static __device__ __forceinline__ int64_t table_floats(const KArgs<P> &a, bool row)
@@ -977,10 +983,10 @@ struct Tile {
 #pragma unroll
                         for (int t0p = 0; t0p + 1 < Q; t0p += 2) {
                             float2 E0, E1;
-                            expphase_part2<P, D, K>(a, tA2,
-                                                    PH2::add(PH2::part(tA2, sget<P, Q>(a, 0, l, cb[0], t0p),
-                                                                       sget<P, Q>(a, 0, l, cb[0], t0p + 1), 0), p12),
-                                                    E0, E1);
+                            ph2<PM>(a, tA2,
+                                    PH2::add(PH2::part(tA2, sget<P, Q>(a, 0, l, cb[0], t0p),
+                                                       sget<P, Q>(a, 0, l, cb[0], t0p + 1), 0), p12),
+                                    fa.at((cl * Q + t1p) * Q + t0p, it), fa.at((cl * Q + t1p) * Q + t0p + 1, it), E0, E1);
                             const C u0 = cmul(E0, wrow[t0p]), u1 = cmul(E1, wrow[t0p + 1]);
 #pragma unroll
                             for (int t0 = 0; t0 < Q; ++t0) {
@@ -990,7 +996,7 @@ struct Tile {
                         }
                         if constexpr (Q & 1) {
                             const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(p12));
-                            const C u = cmul(expphase_part<P, D, K>(a, tA, pt), wrow[Q - 1]);
+                            const C u = cmul(ph<PM>(a, tA, pt, fa.at((cl * Q + t1p) * Q + Q - 1, it)), wrow[Q - 1]);
 #pragma unroll
                             for (int t0 = 0; t0 < Q; ++t0) cfma2(tmp[t0], a.M2[c0][t0][Q - 1], u);
                         }
@@ -1403,12 +1409,19 @@ struct Tile {
         }
         __syncthreads();
         // stage B: items (tau, block, alpha, s_0): contract dims >= 1 per child c,
-        // post-modulate at the child's nodes, sum over c
-        for (int it = threadIdx.x; it < a.T * nblk * NC * Q; it += blockDim.x) {
-            const int s0 = it % Q;
-            const int alpha = (it / Q) % NC;
-            const int beta = (it / (Q * NC)) & (nblk - 1);
-            const int tau = (it / (Q * NC)) >> (D * (k - 1));
+        // post-modulate at the child's nodes, sum over c.  The bits of the output child alpha
+        // above bit 0 select the matrices M[a_1] (and M[a_2]); items are numbered with those
+        // bits outermost, so a warp's items share them (but where two ranges meet) and the body
+        // below, instantiated per value HI = alpha >> 1, indexes M with compile-time indices
+        // (a runtime index costs a constant-bank load per multiply-add).
+        const int nb = a.T * nblk * NC * Q, part = nb / (NC / 2);
+        auto stage_b = [&](auto hic, int it) {
+            constexpr int HI = decltype(hic)::value;
+            const int j = it - HI * part;
+            const int s0 = j % Q;
+            const int alpha = ((j / Q) & 1) | (HI << 1);
+            const int beta = (j / (2 * Q)) & (nblk - 1);
+            const int tau = (j / (2 * Q)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -1423,7 +1436,7 @@ struct Tile {
 #pragma unroll
             for (int j = 0; j < QD1; ++j) acc[j] = czero<C>();
             if constexpr (D == 2) {
-                const int a1 = (alpha >> 1) & 1;
+                constexpr int a1 = HI & 1;
                 C v[NC][Q];
                 typename P::SE sc0[2], sc1[2];        // children's centres per dimension
 #pragma unroll
@@ -1469,7 +1482,7 @@ struct Tile {
                     }
                 }
             } else {
-                const int a1 = (alpha >> 1) & 1, a2 = (alpha >> 2) & 1;
+                constexpr int a1 = HI & 1, a2 = (HI >> 1) & 1;
 #pragma unroll 1
                 for (int c = 0; c < NC; ++c) {
                     int cb[DMAX], ctr[DMAX] = {Q, Q, Q};
@@ -1497,13 +1510,26 @@ struct Tile {
                             for (int t1 = 0; t1 < Q; ++t1) cfma2(v, a.M2[a1][t1][s1], w[t1 * Q + s2]);
                             const int sk[DMAX] = {s0, s1, s2};
                             const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
-                            acc[s1 + Q * s2] = cadd(acc[s1 + Q * s2], cmul(expphase<P, D, K>(a, tS, sc), v));
+                            acc[s1 + Q * s2] = cadd(acc[s1 + Q * s2], cmul(phs<PM>(a, tS, sc, fb.at((s1 + Q * s2) * NC + c, it)), v));
                         }
                 }
             }
             C *wo = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
 #pragma unroll
             for (int sh = 0; sh < QD1; ++sh) wo[sh * Q] = acc[sh];
+        };
+        for (int it = threadIdx.x; it < nb; it += blockDim.x) {
+            const int hi = it / part;
+            if constexpr (D == 2) {
+                if (hi) stage_b(IntC<1>{}, it); else stage_b(IntC<0>{}, it);
+            } else {
+                switch (hi) {
+                case 0: stage_b(IntC<0>{}, it); break;
+                case 1: stage_b(IntC<1>{}, it); break;
+                case 2: stage_b(IntC<2>{}, it); break;
+                default: stage_b(IntC<3>{}, it); break;
+                }
+            }
         }
         __syncthreads();
     }
@@ -2096,15 +2122,16 @@ struct Tile {
 // ------------------------------------------------------------------ kernels
 
 // init (l0 = 0) + k column merges + optional switch at level l0 + k
-// PM: phase factors evaluated, or (d = 2, mixed precisions) recorded in or read from the
-// pass's reduced-phase table a.ftab (a.ftab_cta floats per CTA).  Reading the table, the
+// PM: phase factors evaluated, or (mixed precisions) recorded in or read from the pass's
+// reduced-phase table a.ftab (a.ftab_cta floats per CTA).  Reading the table, the d = 2
 // column pass fits one more CTA per SM (register budget cut accordingly): measured 7% faster
-// with the polynomial sincos, 19% with the SFU one; the row pass would spill.
+// with the polynomial sincos, 19% with the SFU one; the row pass would spill.  At d = 3 the
+// shared memory holds two CTAs per SM either way.
 template <int D, int Q, class P, int K, int PM = PM_COMPUTE>
-__global__ void __launch_bounds__(Cfg<D, Q, P>::NT, PM == PM_TABLE ? Cfg<D, Q, P>::MINB + 1 : Cfg<D, Q, P>::MINB_COL)
+__global__ void __launch_bounds__(Cfg<D, Q, P>::NT, PM == PM_TABLE ? Cfg<D, Q, P>::MINB_TAB : Cfg<D, Q, P>::MINB_COL)
     k_col_pass(const KArgs<P> a)
 {
-    static_assert(PM == PM_COMPUTE || (D == 2 && !P::is_f64), "phase tables: d = 2, mixed precisions");
+    static_assert(PM == PM_COMPUTE || !P::is_f64, "phase tables: mixed precisions");
     using C = typename P::C;
     using TL = Tile<D, Q, P, K>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2149,7 +2176,7 @@ __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, PM == PM_TABLE ? Cfg<D, Q, P
 template <int D, int Q, class P, int K, int PM = PM_COMPUTE>
 __global__ void __launch_bounds__(Cfg<D, Q, P>::NT, Cfg<D, Q, P>::MINB) k_row_pass(const KArgs<P> a)
 {
-    static_assert(PM == PM_COMPUTE || (D == 2 && !P::is_f64), "phase tables: d = 2, mixed precisions");
+    static_assert(PM == PM_COMPUTE || !P::is_f64, "phase tables: mixed precisions");
     using C = typename P::C;
     using TL = Tile<D, Q, P, K>;
     extern __shared__ __align__(16) unsigned char smem_raw[];

@@ -236,6 +236,16 @@ const PassFns *fns_for()
                                   TC ? launch_col_tc<QT, P, K> : nullptr,
                                   TC ? col_tc_ctas_per_sm<QT, P, K> : nullptr, TC ? bfk::ColTC<QT>::SMEM : 0};
         return &f;
+    } else if constexpr (!P::is_f64) {
+        // d = 3: single-RHS passes with a reduced-phase table; no multi-RHS kernels
+        static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
+                                  launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, {nullptr, nullptr, nullptr},
+                                  {nullptr, nullptr, nullptr}, 0, 0, nullptr, nullptr, nullptr,
+                                  launch_ctab<D, Q, P, K>, (int)sizeof(typename bfk::Ph<P, D, K>::T),
+                                  {launch_col<D, Q, P, K, bfk::PM_BUILD>, launch_col<D, Q, P, K, bfk::PM_TABLE>},
+                                  {launch_row<D, Q, P, K, bfk::PM_BUILD>, launch_row<D, Q, P, K, bfk::PM_TABLE>},
+                                  nullptr, nullptr, 0, nullptr, nullptr, 0};
+        return &f;
     } else {
         static const PassFns f = {launch_col<D, Q, P, K>, launch_row<D, Q, P, K>, launch_col_adj<D, Q, P, K>,
                                   launch_row_adj<D, Q, P, K>, CF::KMAX, CF::NP, CF::NT, {nullptr, nullptr, nullptr},

@@ -26,7 +26,7 @@ struct PassFns {
     int (*mr_table_occupancy)(int row, size_t smem);   // CTAs per SM of the table-reading passes
     cudaError_t (*center_table)(const void *kargs, void *out, int levels);   // target features at box centres
     int tsize;                   // bytes of one target-feature record
-    // single-RHS passes with a reduced-phase table (d = 2, mixed, q <= 5; null if absent):
+    // single-RHS passes with a reduced-phase table (mixed; d = 2 with q <= 5, d = 3; null if absent):
     // [0] record the table (plan creation), [1] read it
     pass_fn col_tab[2], row_tab[2];
     // multi-RHS switch on the tensor cores (bf_tc.cuh; d = 2, q <= 5, BF16x3 products;

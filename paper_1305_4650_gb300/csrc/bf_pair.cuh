@@ -94,17 +94,14 @@ __device__ __forceinline__ void sincos2pi2(float2 f, float2 &s, float2 &c)
     const float2 M = dup2(12582912.0f);
     const float2 t = fma2(dup2(4.0f), f, M);
     const float2 r = fma2(dup2(-0.25f), sub2(t, M), f);
-    const float2 a = mul2(r, dup2(6.28318530717958647692f));
-    const float2 a2 = mul2(a, a);
-    float2 ps = fma2(a2, dup2(2.75573192e-06f), dup2(-1.98412698e-04f));
-    ps = fma2(a2, ps, dup2(8.33333333e-03f));
-    ps = fma2(a2, ps, dup2(-1.66666667e-01f));
-    const float2 sn = fma2(mul2(a, a2), ps, a);
-    float2 pc = fma2(a2, dup2(-2.75573192e-07f), dup2(2.48015873e-05f));
-    pc = fma2(a2, pc, dup2(-1.38888889e-03f));
-    pc = fma2(a2, pc, dup2(4.16666667e-02f));
-    pc = fma2(a2, pc, dup2(-0.5f));
-    const float2 cs = fma2(a2, pc, dup2(1.0f));
+    const float2 u = mul2(r, r);
+    float2 ps = fma2(u, dup2(SC_S3), dup2(SC_S2));
+    ps = fma2(u, ps, dup2(SC_S1));
+    ps = fma2(u, ps, dup2(SC_S0));
+    const float2 sn = mul2(r, ps);
+    float2 pc = fma2(u, dup2(SC_C3), dup2(SC_C2));
+    pc = fma2(u, pc, dup2(SC_C1));
+    const float2 cs = fma2(u, pc, dup2(1.0f));
     const int q0 = __float_as_int(t.x), q1 = __float_as_int(t.y);
     const float s0 = (q0 & 1) ? cs.x : sn.x, c0 = (q0 & 1) ? sn.x : cs.x;
     const float s1 = (q1 & 1) ? cs.y : sn.y, c1 = (q1 & 1) ? sn.y : cs.y;

@@ -11,11 +11,11 @@ from paper_1305_4650_gb300 import workloads as wl
 
 def test_phase_ops_follow_the_formulas():
     # part of coordinate 0, the shared parts of the other coordinates (per q phases), the sum of
-    # parts, the final step and the 22-op sincos
-    assert bench.phase_ops("genradon", 2, 5) == pytest.approx(9 + 9 / 5 + 8 + 12 + 22)
-    assert bench.phase_ops("genradon", 3, 4) == pytest.approx(9 + 2 * 9 / 4 + 8 + 12 + 22)
-    assert bench.phase_ops("dot", 2, 5) == pytest.approx(5 + 5 / 5 + 1 + 0 + 22)
-    assert bench.phase_ops("hypradon", 2, 5) == pytest.approx(4 + 4 / 5 + 8 + 12 + 22)
+    # parts, the final step and the 18-op sincos
+    assert bench.phase_ops("genradon", 2, 5) == pytest.approx(9 + 9 / 5 + 8 + 12 + 18)
+    assert bench.phase_ops("genradon", 3, 4) == pytest.approx(9 + 2 * 9 / 4 + 8 + 12 + 18)
+    assert bench.phase_ops("dot", 2, 5) == pytest.approx(5 + 5 / 5 + 1 + 0 + 18)
+    assert bench.phase_ops("hypradon", 2, 5) == pytest.approx(4 + 4 / 5 + 8 + 12 + 18)
     # the Fourier phase is the cheapest, the generalized Radon phase the dearest
     ops = {k: bench.phase_ops(k, 2, 5) for k in ("dot", "genradon", "hypradon", "separable")}
     assert min(ops, key=ops.get) == "dot" and max(ops, key=ops.get) == "genradon"

@@ -17,7 +17,7 @@ def bf():
 
 
 def test_sincos_against_fp64_sincospi(bf):
-    # Taylor truncation < 3e-8 plus a few FP32 roundings of values <= 1
+    # minimax truncation < 4e-8 plus a few FP32 roundings of values <= 1
     assert bf.selfcheck_sincos(1 << 22) < 1.5e-7
 
 

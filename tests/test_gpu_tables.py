@@ -51,18 +51,29 @@ def test_tables_equal_evaluated_phases(bf, spec, nrhs, prec):
 
 
 def _tile_table_bytes(spec):
-    # single-RHS table: one float (the reduced phase) per factor, 5 r per pair and level, and
-    # r^2 per pair at the switch unless the phase is a sum over dimensions (factorised switch)
+    # single-RHS table: one float (the reduced phase) per factor, (2^d + 1) r per pair and level
+    # (2^d r modulations of the children's weights, r demodulations), and r^2 per pair at the
+    # switch unless the phase is a sum over dimensions (factorised switch)
     r, L = spec.r, spec.L
     sw = 0 if spec.phase in ("dot", "separable") else r * r
-    return 4 * spec.npts * (5 * r * L + sw)
+    return 4 * spec.npts * (((1 << spec.d) + 1) * r * L + sw)
+
+
+def _spec3(L, q, phase, **kw):
+    base = dict(x_lo=(0.0,) * 3, x_w=(1.0,) * 3)
+    base.update(kw)
+    return wl.Spec(f"t3_{L}_{q}_{phase}", 3, L, q, phase, **base)
 
 
 @pytest.mark.parametrize("spec,prec", [(wl.genradon2d(L=6), "mixed"), (wl.genradon2d(L=7), "mixed_sfu"),
                                        (wl.hypradon(7), "mixed"), (wl.hypradon(5), "mixed_sfu"),
                                        (wl.genradon2d(L=3).with_(q=4), "mixed"), (wl.genradon2d(L=5).with_(q=3), "mixed"),
                                        (wl.dft64().with_(precision="mixed"), "mixed"), (wl.genradon2d(L=1), "mixed"),
-                                       (wl.genradon2d(L=2).with_(q=2), "mixed"), (wl.hypradon(3), "mixed_sfu")])
+                                       (wl.genradon2d(L=2).with_(q=2), "mixed"), (wl.hypradon(3), "mixed_sfu"),
+                                       (wl.genradon3d(L=3), "mixed"), (wl.genradon3d(L=4), "mixed_sfu"),
+                                       (_spec3(4, 3, "genradon", tgt_off=0.3), "mixed"), (_spec3(3, 2, "genradon"), "mixed_sfu"),
+                                       (_spec3(4, 4, "dot"), "mixed"), (_spec3(3, 3, "separable", src_off=0.2), "mixed"),
+                                       (_spec3(1, 4, "genradon"), "mixed"), (_spec3(5, 2, "genradon", m=1), "mixed")])
 def test_single_rhs_table_equals_evaluated_phases(bf, spec, prec):
     # plans of one right-hand side record the reduced phase that the single-RHS kernels feed to
     # their sincos, so reading it gives the evaluating apply bit for bit
@@ -82,7 +93,7 @@ def test_single_rhs_table_equals_evaluated_phases(bf, spec, prec):
     torch.cuda.synchronize()
     assert torch.equal(ft, fc)
     ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.cpu().numpy().astype(np.complex128))
-    tol = 1e-5 if prec == "mixed" else 2e-5
+    tol = (1e-5 if prec == "mixed" else 2e-5) if spec.d == 2 else 1e-4
     assert np.linalg.norm(ft.cpu().numpy() - ref) <= tol * np.linalg.norm(ref)
     pt.close()
     pc.close()
@@ -113,8 +124,11 @@ def test_tables_refused_where_not_built(bf):
     with pytest.raises(bf.BfError) as e:
         bf.Plan.from_spec(wl.hypradon(5), precision="fp64", phase_tables=True)
     assert e.value.code == 2
+    with pytest.raises(bf.BfError) as e:     # d = 3 has no multi-RHS kernels to record factors
+        bf.Plan.from_spec(wl.genradon3d(L=3), max_nrhs=2, precision="mixed", phase_tables=True)
+    assert e.value.code == 2
     with pytest.raises(bf.BfError) as e:
-        bf.Plan.from_spec(wl.genradon3d(L=3), precision="mixed", phase_tables=True)
+        bf.Plan.from_spec(wl.genradon3d(L=3), precision="fp64", phase_tables=True)
     assert e.value.code == 2
 
 
@@ -137,5 +151,28 @@ def test_single_rhs_table_full_size(bf):
     ref = oracle.butterfly(P, g[0].cpu().numpy().astype(np.complex128), restrict=(spec.switch_level, box))[tg]
     out = ft[0].cpu().numpy()[tg]
     assert np.linalg.norm(out - ref) <= 1e-5 * np.linalg.norm(ref)
+    pt.close()
+    pc.close()
+
+
+def test_single_rhs_table_full_size_d3(bf):
+    # d = 3, N = 64, q = 4 (a 7.9 GB table): bit-identical to the evaluating apply, and a
+    # level-3 target box against the restricted oracle butterfly
+    import torch
+    spec = wl.genradon3d()
+    pt = bf.Plan.from_spec(spec, precision="mixed", phase_tables=True)
+    assert pt.table_info()["bytes"] == _tile_table_bytes(spec)
+    pc = bf.Plan.from_spec(spec, precision="mixed")
+    g = torch.from_numpy(wl.source_values(spec, 1, np.complex64, seed=65)).cuda()
+    ft, fc = pt.apply(g), pc.apply(g)
+    torch.cuda.synchronize()
+    assert not pt.table_info()["timed_out"]
+    assert torch.equal(ft, fc)
+    P = oracle.Problem(**spec.oracle_kwargs())
+    box = 300
+    tg = oracle.restricted_targets(P, spec.switch_level, box)
+    ref = oracle.butterfly(P, g[0].cpu().numpy().astype(np.complex128), restrict=(spec.switch_level, box))[tg]
+    out = ft[0].cpu().numpy()[tg]
+    assert np.linalg.norm(out - ref) <= 1e-4 * np.linalg.norm(ref)
     pt.close()
     pc.close()
