@@ -37,12 +37,13 @@ FP32_LANES_PER_SM = 128
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each pass of the default
 # workload, from one ncu capture of `python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-accuracy
-# --fp64-steps 0 --no-autotune --no-tables --no-batched` (the dominant pass writes 0.8 GB more than its
-# weights: register spills of its switch at three CTAs per SM reach DRAM).  They describe the kernels as built from sources with the recorded hash
-# and the recorded pass schedule; otherwise the figure is dropped (traffic: null) until captured again.
-TRAFFIC = {"genradon2d": {"src_sha256": "fa1afea2ce4c73946fd60c98672f5663584be66425335401a52a1340cabaa326",
+# --fp64-steps 0 --no-autotune --no-tables --no-batched` (the dominant pass writes 0.85 GB more than its
+# weights: register spills of its switch at three CTAs per SM reach DRAM).  They describe the kernels as
+# built from sources with the recorded hash and the recorded pass schedule; otherwise the figure is
+# dropped (traffic: null) until captured again.
+TRAFFIC = {"genradon2d": {"src_sha256": "208f045d60f29346696351e71ffa45cad4dc65312a8b01154ec6837d622e268e",
                           "schedule": ["col2", "col3", "row2", "row3"],
-                          "bytes": [168302848, 1213521664, 369714688, 215698688]}}
+                          "bytes": [168167424, 1273888256, 369781504, 215654912]}}
 TRAFFIC_SRC = ("bf_device.cuh", "bf_inst.cuh")   # the pass kernels and their launch configuration
 
 

@@ -47,9 +47,6 @@ enum { F_INIT = 1, F_SWITCH = 2, F_FINAL = 4 };
 // in the plan's phase table (PM_BUILD, at plan creation), or read from it (PM_TABLE)
 enum { PM_COMPUTE = 0, PM_BUILD = 1, PM_TABLE = 2 };
 
-// a compile-time integer passed to a generic lambda
-template <int V> struct IntC { static constexpr int value = V; };
-
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 
 // ------------------------------------------------------------ double-float
@@ -1409,19 +1406,12 @@ struct Tile {
         }
         __syncthreads();
         // stage B: items (tau, block, alpha, s_0): contract dims >= 1 per child c,
-        // post-modulate at the child's nodes, sum over c.  The bits of the output child alpha
-        // above bit 0 select the matrices M[a_1] (and M[a_2]); items are numbered with those
-        // bits outermost, so a warp's items share them (but where two ranges meet) and the body
-        // below, instantiated per value HI = alpha >> 1, indexes M with compile-time indices
-        // (a runtime index costs a constant-bank load per multiply-add).
-        const int nb = a.T * nblk * NC * Q, part = nb / (NC / 2);
-        auto stage_b = [&](auto hic, int it) {
-            constexpr int HI = decltype(hic)::value;
-            const int j = it - HI * part;
-            const int s0 = j % Q;
-            const int alpha = ((j / Q) & 1) | (HI << 1);
-            const int beta = (j / (2 * Q)) & (nblk - 1);
-            const int tau = (j / (2 * Q)) >> (D * (k - 1));
+        // post-modulate at the child's nodes, sum over c
+        for (int it = threadIdx.x; it < a.T * nblk * NC * Q; it += blockDim.x) {
+            const int s0 = it % Q;
+            const int alpha = (it / Q) % NC;
+            const int beta = (it / (Q * NC)) & (nblk - 1);
+            const int tau = (it / (Q * NC)) >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, tau, Ap, Bstar);
@@ -1436,7 +1426,7 @@ struct Tile {
 #pragma unroll
             for (int j = 0; j < QD1; ++j) acc[j] = czero<C>();
             if constexpr (D == 2) {
-                constexpr int a1 = HI & 1;
+                const int a1 = (alpha >> 1) & 1;
                 C v[NC][Q];
                 typename P::SE sc0[2], sc1[2];        // children's centres per dimension
 #pragma unroll
@@ -1482,7 +1472,7 @@ struct Tile {
                     }
                 }
             } else {
-                constexpr int a1 = HI & 1, a2 = (HI >> 1) & 1;
+                const int a1 = (alpha >> 1) & 1, a2 = (alpha >> 2) & 1;
 #pragma unroll 1
                 for (int c = 0; c < NC; ++c) {
                     int cb[DMAX], ctr[DMAX] = {Q, Q, Q};
@@ -1517,19 +1507,6 @@ struct Tile {
             C *wo = Wt + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
 #pragma unroll
             for (int sh = 0; sh < QD1; ++sh) wo[sh * Q] = acc[sh];
-        };
-        for (int it = threadIdx.x; it < nb; it += blockDim.x) {
-            const int hi = it / part;
-            if constexpr (D == 2) {
-                if (hi) stage_b(IntC<1>{}, it); else stage_b(IntC<0>{}, it);
-            } else {
-                switch (hi) {
-                case 0: stage_b(IntC<0>{}, it); break;
-                case 1: stage_b(IntC<1>{}, it); break;
-                case 2: stage_b(IntC<2>{}, it); break;
-                default: stage_b(IntC<3>{}, it); break;
-                }
-            }
         }
         __syncthreads();
     }

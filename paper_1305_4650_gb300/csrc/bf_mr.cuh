@@ -560,44 +560,6 @@ struct TileMR {
         if constexpr (PM == PM_BUILD) ts.tb += (int64_t)x.npr * RR * RR;
     }
 
-    // one stage-B item of a row level (right-hand side r0 + rbl, output pair pA whose child
-    // index has high bit A1, target node digit s0): v[c][s1] = sum_t1 M[A1][t1][s1] z_c[t1],
-    // then sum over c of the post-modulated v
-    template <int A1, int PRB, class MS>
-    static __device__ __forceinline__ void row_b_item(const MS &ms, const Ctx &x, C *W, const C *S, const C *PB,
-                                                      int r0, int rbl, int pA, int s0, int i, int k, int n, int nblk,
-                                                      int WS, int SW)
-    {
-        constexpr int SU = 2 * Q + PAD.rs;
-        const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
-        const int base = block_base(beta, i);
-        const int a0 = alpha & 1;
-        const C *Sblk = S + rbl * SW + (pA - alpha) * Q * SU;
-        const C *ph = PB + pA * PRB + s0;
-        C acc[Q];
-#pragma unroll
-        for (int s1 = 0; s1 < Q; ++s1) acc[s1] = czero<C>();
-        // child by child: the sums over c add in the order c = 0..3, as one per s1 would
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const C *si = Sblk + c * Q * SU + a0 * Q + s0;
-            C v[Q];
-#pragma unroll
-            for (int s1 = 0; s1 < Q; ++s1) v[s1] = czero<C>();
-#pragma unroll
-            for (int t1 = 0; t1 < Q; ++t1) {
-                const C zz = si[t1 * SU];
-#pragma unroll
-                for (int s1 = 0; s1 < Q; ++s1) mmac(v[s1], ms, A1, t1, s1, zz);
-            }
-#pragma unroll
-            for (int s1 = 0; s1 < Q; ++s1) acc[s1] = TL::cadd(acc[s1], cmul(ph[(c * Q + s1) * Q], v[s1]));
-        }
-        C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
-#pragma unroll
-        for (int s1 = 0; s1 < Q; ++s1) wo[s1 * Q] = acc[s1];
-    }
-
     // ---- one row-form merge level (l -> l+1)
     template <int PM, class MS>
     static __device__ void row_level(const KArgs<P> &a, const MS &ms, const Ctx &x, C *W, C *S, C *PC, int l, int i,
@@ -688,20 +650,35 @@ struct TileMR {
                 }
             }
             __syncthreads();
-            // stage B: items (rb, pA, s0): contract dimension 1 per child, post-modulate, sum over
-            // c.  The high bit a1 of the output child alpha selects the matrix M[a1]; items are
-            // numbered with a1 outermost, so a warp's items share it (one warp straddles) and each
-            // body indexes M with compile-time indices (a runtime index costs a constant-bank
-            // load per multiply-add).
-            const int half = (nrc * nout * Q) >> 1;
-            for (int it = threadIdx.x; it < 2 * half; it += NT) {
-                const int hi = it >= half, j = it - hi * half;
-                const int s0 = j % Q, ph2i = (j / Q) & ((nout >> 1) - 1), rbl = (j / Q) >> (x.lgp - 1);
-                const int pA = ((ph2i >> 1) << D) | (hi << 1) | (ph2i & 1);
-                if (hi)
-                    row_b_item<1, PRB>(ms, x, W, S, PB, r0, rbl, pA, s0, i, k, n, nblk, WS, SW);
-                else
-                    row_b_item<0, PRB>(ms, x, W, S, PB, r0, rbl, pA, s0, i, k, n, nblk, WS, SW);
+            // stage B: items (rb, pA, s0): contract dimension 1 per child, post-modulate, sum over c
+            for (int it = threadIdx.x; it < nrc * nout * Q; it += NT) {
+                const int s0 = it % Q, pA = (it / Q) & (nout - 1), rbl = (it / Q) >> x.lgp;
+                const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
+                const int base = block_base(beta, i);
+                const int a0 = alpha & 1, a1 = alpha >> 1;
+                const C *Sblk = S + rbl * SW + (pA - alpha) * Q * SU;
+                C v[NC][Q];
+#pragma unroll
+                for (int c = 0; c < NC; ++c) {
+                    const C *si = Sblk + c * Q * SU + a0 * Q + s0;
+#pragma unroll
+                    for (int s1 = 0; s1 < Q; ++s1) v[c][s1] = czero<C>();
+#pragma unroll
+                    for (int t1 = 0; t1 < Q; ++t1) {
+                        const C zz = si[t1 * SU];
+#pragma unroll
+                        for (int s1 = 0; s1 < Q; ++s1) mmac(v[c][s1], ms, a1, t1, s1, zz);
+                    }
+                }
+                C *wo = W + (r0 + rbl) * WS + tau * n * RR + (base + (alpha << (D * i))) * RR + s0;
+                const C *ph = PB + pA * PRB + s0;
+#pragma unroll
+                for (int s1 = 0; s1 < Q; ++s1) {
+                    C acc = czero<C>();
+#pragma unroll
+                    for (int c = 0; c < NC; ++c) acc = TL::cadd(acc, cmul(ph[(c * Q + s1) * Q], v[c][s1]));
+                    wo[s1 * Q] = acc;
+                }
             }
             __syncthreads();
         }
