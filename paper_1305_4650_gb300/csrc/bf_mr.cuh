@@ -144,6 +144,13 @@ struct TileMR {
     using PH2 = Ph2<P, 2, K>;
     using TL = Tile<2, Q, P, K>;
 
+    // geometry of one output pair of a column level, computed once per level into the
+    // scratch S (idle during the phase stage) for the stage's phase items
+    struct __align__(16) GeoC {
+        typename PH::T tA;   // target features at the centre of the pair's target box (level l+1)
+        int cbq[2];          // coordinates of the parent source box (level l+1)
+    };
+
     struct Ctx {
         int tile0;   // first tile of the CTA
         int rhs0;    // first right-hand side
@@ -369,9 +376,9 @@ struct TileMR {
         constexpr int PCA = 2 * RR + (PM == PM_COMPUTE ? PAD.ca : 0), PCB = RR + (PM == PM_COMPUTE ? PAD.cb : 0);
         C *PA = PC;                     // [pA][chi] blocks of PCA: [cl][tq][t0']  modulation of the inputs
         C *PB = PC + nout * 2 * PCA;    // [pA] blocks of PCB: [tq][tl]            demodulation of the output
-        for (int it = threadIdx.x; PM != PM_TABLE && it < nout * 4 * Q; it += NT) {
-            const int tq = it % Q, cl = (it / Q) & 1, chi = (it / (2 * Q)) & 1, pA = it / (4 * Q);
-            const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
+        GeoC *G = reinterpret_cast<GeoC *>(S);
+        for (int j = threadIdx.x; PM != PM_TABLE && j < nout; j += NT) {
+            const int alpha = j & (NC - 1), beta = (j >> D) & (nblk - 1), tau = j >> (D * k);
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, x, tau, Ap, Bstar);
@@ -380,7 +387,15 @@ struct TileMR {
             int ca[DMAX], cbq[DMAX];
             morton_decode<D>(Aa, l + 1, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
-            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+            G[j].tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+            G[j].cbq[0] = cbq[0];
+            G[j].cbq[1] = cbq[1];
+        }
+        if constexpr (PM != PM_TABLE) __syncthreads();
+        for (int it = threadIdx.x; PM != PM_TABLE && it < nout * 4 * Q; it += NT) {
+            const int tq = it % Q, cl = (it / Q) & 1, chi = (it / (2 * Q)) & 1, pA = it / (4 * Q);
+            const typename PH::T tA = G[pA].tA;
+            const int cbq[2] = {G[pA].cbq[0], G[pA].cbq[1]};
             const int c = cl | (chi << 1);
             // phases two at a time: lanes t'_0 and t'_0 + 1 (the last one alone for odd q)
             const typename PH2::T tA2 = PH2::dup(tA);
@@ -401,16 +416,8 @@ struct TileMR {
         }
         for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
             const int tl = it % Q, tq = (it / Q) % Q, pA = it / RR;
-            const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
-            uint32_t Ap, Bstar, Apg, Bq;
-            int base;
-            tile_of(a, x, tau, Ap, Bstar);
-            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            const uint32_t Aa = (Apg << D) + alpha;
-            int ca[DMAX], cbq[DMAX];
-            morton_decode<D>(Aa, l + 1, ca);
-            morton_decode<D>(Bq, L - l - 1, cbq);
-            const typename PH::T tA = tcenter<P, D, Q, K>(a, l + 1, Aa, ca);
+            const typename PH::T tA = G[pA].tA;
+            const int cbq[2] = {G[pA].cbq[0], G[pA].cbq[1]};
             const typename PH::Part pl = PH::part(tA, sget<P, Q>(a, 0, l + 1, cbq[0], tl), 0);
             const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 1, l + 1, cbq[1], tq), 1), pl);
             PB[pA * PCB + tq * Q + tl] = expphase_part<P, D, K>(a, tA, pt);
