@@ -151,6 +151,13 @@ struct TileMR {
         int cbq[2];          // coordinates of the parent source box (level l+1)
     };
 
+    // geometry of one merge block of a row level (in S during the phase stage): the parent
+    // target box (level l) and the parent source box (level l+1)
+    struct __align__(16) GeoR {
+        int ca[2];    // coordinates of the parent target box A_p
+        int cbq[2];   // coordinates of the parent source box B_q
+    };
+
     struct Ctx {
         int tile0;   // first tile of the CTA
         int rhs0;    // first right-hand side
@@ -578,32 +585,35 @@ struct TileMR {
         constexpr int PRB = 4 * RR + (PM == PM_COMPUTE ? PAD.rb : 0), SU = 2 * Q + PAD.rs;
         C *PA = PC;              // [pin][th][t0]                       pre-modulation at the parent's nodes
         C *PB = PC + nout * RR;  // [pA] blocks of PRB: [c][s1][s0]     post-modulation at the child's nodes
-        for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
-            const int t0 = it % Q, th = (it / Q) % Q, pin = it / RR;
-            const int c = pin & (NC - 1), beta = (pin >> D) & (nblk - 1), tau = pin >> (D * k);
+        // the blocks' geometry once per level, into S (idle during the phase stage)
+        GeoR *GR = reinterpret_cast<GeoR *>(S);
+        for (int j = threadIdx.x; PM != PM_TABLE && j < (nout >> D); j += NT) {
+            const int beta = j & (nblk - 1), tau = j >> (D * (k - 1));
             uint32_t Ap, Bstar, Apg, Bq;
             int base;
             tile_of(a, x, tau, Ap, Bstar);
             TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            int ca[DMAX], cbq[DMAX], cb[DMAX];
+            int ca[DMAX], cbq[DMAX];
             morton_decode<D>(Apg, l, ca);
             morton_decode<D>(Bq, L - l - 1, cbq);
-#pragma unroll
-            for (int j = 0; j < D; ++j) cb[j] = 2 * cbq[j] + ((c >> j) & 1);
+            GR[j] = GeoR{{ca[0], ca[1]}, {cbq[0], cbq[1]}};
+        }
+        if constexpr (PM != PM_TABLE) __syncthreads();
+        for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
+            const int t0 = it % Q, th = (it / Q) % Q, pin = it / RR;
+            const int c = pin & (NC - 1), b = pin >> D;
+            const int ca[DMAX] = {GR[b].ca[0], GR[b].ca[1], 0};
+            const int cb[DMAX] = {2 * GR[b].cbq[0] + (c & 1), 2 * GR[b].cbq[1] + ((c >> 1) & 1), 0};
             const int ctr[DMAX] = {Q, Q, Q};
             const int tk[DMAX] = {t0, th, 0};
             PA[it] = expphase<P, D, K>(a, tpoint<P, D, Q, K>(a, l, ca, tk), spoint<P, D, Q, K>(a, l, cb, ctr));
         }
         for (int it = threadIdx.x; PM != PM_TABLE && it < nout * RR; it += NT) {
             const int s0 = it % Q, s1 = (it / Q) % Q, pA = it / RR;
-            const int alpha = pA & (NC - 1), beta = (pA >> D) & (nblk - 1), tau = pA >> (D * k);
-            uint32_t Ap, Bstar, Apg, Bq;
-            int base;
-            tile_of(a, x, tau, Ap, Bstar);
-            TL::block_geo(Ap, Bstar, beta, i, k, Apg, Bq, base);
-            int ca[DMAX], cbq[DMAX];
-            morton_decode<D>((Apg << D) + alpha, l + 1, ca);
-            morton_decode<D>(Bq, L - l - 1, cbq);
+            const int alpha = pA & (NC - 1), b = pA >> D;
+            // the child target box (level l+1) of the block's parent box
+            const int ca[DMAX] = {2 * GR[b].ca[0] + (alpha & 1), 2 * GR[b].ca[1] + ((alpha >> 1) & 1), 0};
+            const int cbq[DMAX] = {GR[b].cbq[0], GR[b].cbq[1], 0};
             const int sk[DMAX] = {s0, s1, 0};
             const typename PH::T tS = tpoint<P, D, Q, K>(a, l + 1, ca, sk);
             // phases two at a time: lanes c_0 = 0 and 1
