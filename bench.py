@@ -90,7 +90,7 @@ def parse():
                     choices=["genradon2d", "genradon3d", "dft64", "hypradon512", "hypradon48", "cg1024",
                              "genradon2d_points"])
     ap.add_argument("--nrhs", type=int, default=1, help="right-hand sides per apply (single-problem workloads)")
-    ap.add_argument("--precision", default="", choices=["", "mixed", "mixed_sfu", "bf16x3", "fp64"],
+    ap.add_argument("--precision", default="", choices=["", "mixed", "mixed_sfu", "bf16x3", "tf32x3", "fp64"],
                     help="override the workload's precision (single-problem workloads)")
     ap.add_argument("--L", type=int, default=0, help="override log2 N of a single-problem workload (small cases)")
     ap.add_argument("--fp64-steps", type=int, default=3)
@@ -534,6 +534,8 @@ def run_ours(args, rank, world, local_rank):
                                                "bits) reduced mod 1, polynomial FP32 sincos",
                                       "mixed_sfu": "as mixed, sin/cos from the special-function unit",
                                       "bf16x3": "as mixed; with several RHS the switch on the tensor cores, BF16x3 "
+                                                "products with FP32 accumulation",
+                                      "tf32x3": "as mixed; with several RHS the switch on the tensor cores, TF32x3 "
                                                 "products with FP32 accumulation"}[prec],
                        "passes": len(passes), "fuse_levels": plan_fuse(passes),
                        "schedule": sched,
@@ -550,12 +552,13 @@ def run_ours(args, rank, world, local_rank):
 
 def batch_eval(args, rank, world, dev, steps, warmup, autotune, fp64_steps, accuracy):
     """The 48 hyperbolic Radon problems (16 each of N = 128, 256, 512; 1..16 RHS each, drawn
-    from the seed), q = 5, in four forms on the same inputs:
+    from the seed), q = 5, in five forms on the same inputs:
       mixed_per_pass   FP32 multi-RHS kernels, one launch per pass of every problem (bf_apply_batched)
       mixed_persistent the same kernels as one persistent launch per step (bf_batch_apply)
       bf16x3_per_pass  the switch on the tensor cores (BF_PREC_BF16X3), one launch per pass
+      tf32x3_per_pass  the switch on the tensor cores with TF32 parts (BF_PREC_TF32X3)
       fp64             the plain FP64 GPU butterfly (complex128), one launch per pass
-    The first three are captured once in a CUDA graph and replayed; timed with CUDA events on
+    The first four are captured once in a CUDA graph and replayed; timed with CUDA events on
     the launching stream (max over ranks).  Under torchrun the problems are dealt round-robin
     to the ranks (independent problems, no exchange).  Accuracy (rank 0): the first problem of
     each N against the FP64 oracle butterfly (all outputs at N = 128, one level-m target box
@@ -664,6 +667,15 @@ def batch_eval(args, rank, world, dev, steps, warmup, autotune, fp64_steps, accu
         roof["problem"] = f"N=512, {nr[big]} RHS"
     for p in plans:
         p.close()
+    # TF32x3: the switch on the tensor cores with TF32 parts (the accuracy of the FP32 form)
+    plans = make("tf32x3")
+    ms, clk = timed(lambda st: bf.apply_batched(plans, gs, fs, nr, stream=st))
+    forms["tf32x3_per_pass"] = {"ms_per_step": round(ms, 3), "value": pts_rhs / (ms * 1e-3), "clocks": clk,
+                                "launches_per_step": sum(p.launches(k) for p, k in zip(plans, nr)),
+                                "tc_wait_timed_out": any(p.table_info()["timed_out"] for p in plans)}
+    outs["tf32x3"] = [fs[j].cpu().numpy() for j in samples.values()]
+    for p in plans:
+        p.close()
     del fs
     # FP64 GPU butterfly of the same batch
     if fp64_steps > 0:
@@ -702,7 +714,8 @@ def batch_eval(args, rank, world, dev, steps, warmup, autotune, fp64_steps, accu
                 rec[arm] = {"rel_l2_vs_oracle_butterfly": max(rel(out[r][tg], ref[x][tg]) for x, r in enumerate(rhs)),
                             "rel_l2_vs_direct_sum": rel(out[0][samp], direct)}
             acc[f"N{N}"] = rec
-    fast = min(("mixed_per_pass", "mixed_persistent", "bf16x3_per_pass"), key=lambda f: forms[f]["ms_per_step"])
+    fast = min(("mixed_per_pass", "mixed_persistent", "bf16x3_per_pass", "tf32x3_per_pass"),
+               key=lambda f: forms[f]["ms_per_step"])
     rec = {"workload": "hypradon48_q5", "problems": len(probs), "N": [128, 256, 512],
            "nrhs_total": int(sum(k for _, k in probs)), "points_rhs": pts_rhs,
            "value": forms[fast]["value"], "unit": UNIT, "ms_per_step": forms[fast]["ms_per_step"], "form": fast,

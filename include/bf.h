@@ -94,8 +94,15 @@ typedef enum {
  *                      modulated inputs of its 4 source children times the constant
  *                      Kronecker product of the child->parent interpolation matrices
  *                      (a real 128 x 32 x 128 GEMM per block, BF16x3, FP32 accumulation),
- *                      one level per pass (bf_pass_info kind 3). */
-typedef enum { BF_PREC_FP64 = 0, BF_PREC_MIXED = 1, BF_PREC_MIXED_SFU = 2, BF_PREC_BF16X3 = 3 } bf_precision;
+ *                      one level per pass (bf_pass_info kind 3).
+ *   BF_PREC_TF32X3     as BF_PREC_BF16X3 (the switch on the tensor cores, the same
+ *                      conditions and refusals), with every FP32 operand split into two
+ *                      TF32 parts (tcgen05 kind::tf32) and three TF32 products accumulated
+ *                      in FP32: relative error per product ~2^-22, so the apply keeps the
+ *                      accuracy of BF_PREC_MIXED.  tc_levels has no effect. */
+typedef enum {
+    BF_PREC_FP64 = 0, BF_PREC_MIXED = 1, BF_PREC_MIXED_SFU = 2, BF_PREC_BF16X3 = 3, BF_PREC_TF32X3 = 4
+} bf_precision;
 
 typedef struct {
     double x_lo[3], x_w[3];   /* target domain: prod_k [x_lo[k], x_lo[k] + x_w[k]), x_w > 0  */
@@ -134,7 +141,7 @@ typedef struct {
  * its construction took and (synchronising the device; timed_out may be NULL) whether a
  * wait for a copy ever gave up, or a kernel found a table layout it did not expect (results
  * undefined then).  The adjoint and persistent batches evaluate phases as without tables.
- * For BF_PREC_BF16X3 plans timed_out also reports a tensor-core completion wait that gave up
+ * For BF_PREC_BF16X3 and BF_PREC_TF32X3 plans timed_out also reports a tensor-core completion wait that gave up
  * (2 s; the switch pass then stops and its outputs are undefined). */
 
 /* Defaults for the problem classes of Section 3: X = [0,1)^d, Y = [-N/2, N/2)^d
@@ -281,7 +288,7 @@ bf_status bf_plan_autotune(bf_plan plan, int nrhs, int reps, void *stream, doubl
  * is exactly bf_apply.  Used to time individual kernels with events recorded between
  * passes.  bf_pass_info describes pass i of the schedule for nrhs: kind (0 column
  * pass with optional init/switch, 1 row pass with optional final, 2 the tensor-core
- * switch of BF_PREC_BF16X3 at level l0 with k = 0), first level l0,
+ * switch of BF_PREC_BF16X3 or BF_PREC_TF32X3 at level l0 with k = 0), first level l0,
  * number of fused levels k, flags (1 init, 2 switch, 4 final).  nrhs must lie in
  * 1..max_nrhs, i in 0..count-1 (else BF_ERR_INVALID_ARG). */
 bf_status bf_pass_count(bf_plan plan, int nrhs, int *count);
@@ -318,6 +325,10 @@ bf_status bf_selfcheck_phase(bf_plan plan, int n, double *max_err_cycles);
  * split (max_rel_err ~1e-5).  max_rel_err = max |D - D_ref| / max |D_ref|; timed_out = 1
  * if the completion wait (2 s) gave up.  Allocates and frees a few KB, synchronises. */
 bf_status bf_selfcheck_umma(int split, double *max_rel_err, int *timed_out);
+/* The same for the TF32 blocks of BF_PREC_TF32X3 (kind::tf32, 32-bit operands, K = 32):
+ * split = 0 small integers (exact: max_rel_err 0), split = 1 the TF32x3 split of values in
+ * [-1, 1) (max_rel_err ~1e-7). */
+bf_status bf_selfcheck_umma_tf32(int split, double *max_rel_err, int *timed_out);
 
 /* Forward apply that allocates no device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot call cudaMalloc themselves or
@@ -329,7 +340,7 @@ bf_status bf_selfcheck_umma(int split, double *max_rel_err, int *timed_out);
  * bf_plan_autotune), with the single-RHS kernels for every nrhs; for nrhs = 1 the
  * result equals that plan's bf_apply up to the last bits of the geometry tables
  * (they are built on the device here), for nrhs >= 2 (where bf_apply runs the
- * multi-RHS kernels) up to FP32 rounding order.  BF_PREC_BF16X3 is not accepted.
+ * multi-RHS kernels) up to FP32 rounding order.  BF_PREC_BF16X3 and BF_PREC_TF32X3 are not accepted.
  *
  * Scratch.  The geometry tables and the two weight buffers live in one static
  * device array of BF_NOALLOC_SCRATCH_BYTES bytes that every GPU which loads the

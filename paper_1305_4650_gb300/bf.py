@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libbf_gb300.so")
 
 PHASE = {"dot": 0, "genradon": 1, "hypradon": 2, "separable": 3}
-PREC = {"fp64": 0, "mixed": 1, "mixed_sfu": 2, "bf16x3": 3}
+PREC = {"fp64": 0, "mixed": 1, "mixed_sfu": 2, "bf16x3": 3, "tf32x3": 4}
 STATUS = {0: "BF_OK", 1: "BF_ERR_INVALID_ARG", 2: "BF_ERR_UNSUPPORTED", 3: "BF_ERR_NOMEM",
           4: "BF_ERR_CUDA", 5: "BF_ERR_TIMEOUT", 6: "BF_ERR_INTERNAL"}
 
@@ -78,6 +78,7 @@ def load():
         lib.bf_measure_fma_rate.argtypes = [i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_measure_phase_rate.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double)]
         lib.bf_selfcheck_umma.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
+        lib.bf_selfcheck_umma_tf32.argtypes = [i32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32)]
         lib.bf_apply_shard.argtypes = [vp, vp, vp, i32, i32, i32, vp]
         lib.bf_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i32), i32, ctypes.POINTER(vp)]
         lib.bf_batch_apply.argtypes = [vp, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
@@ -323,12 +324,15 @@ def selfcheck_sincos(n: int = 1 << 22) -> float:
     return e.value
 
 
-def selfcheck_umma(split: bool = False) -> tuple[float, bool]:
-    """Tensor-core GEMM self-check (128 x 32 x 64, BF16 operands, FP32 accumulator): the
-    largest error relative to max |D| (0 expected without the split), and whether the
-    completion wait gave up."""
+def selfcheck_umma(split: bool = False, fmt: str = "bf16") -> tuple[float, bool]:
+    """Tensor-core GEMM self-check (128 x 32 x 64 with BF16 operands, or 128 x 32 x 32 with
+    TF32 operands (fmt="tf32"); FP32 accumulator): the largest error relative to max |D|
+    (0 expected without the split), and whether the completion wait gave up."""
     e, t = ctypes.c_double(), ctypes.c_int()
-    _check(load().bf_selfcheck_umma(1 if split else 0, ctypes.byref(e), ctypes.byref(t)), "bf_selfcheck_umma")
+    if fmt not in ("bf16", "tf32"):
+        raise ValueError(fmt)
+    fn = "bf_selfcheck_umma" if fmt == "bf16" else "bf_selfcheck_umma_tf32"
+    _check(getattr(load(), fn)(1 if split else 0, ctypes.byref(e), ctypes.byref(t)), fn)
     return e.value, bool(t.value)
 
 

@@ -332,15 +332,18 @@ std::vector<Pass> schedule(const bf_plan_s *p, int kmax, int64_t np_cta, bool re
     return out;
 }
 
-// BF_PREC_BF16X3: the multi-RHS column pass that ends at the switch level stops before
+// whether a precision runs the multi-RHS switch on the tensor cores
+bool tc_prec(int prec) { return prec == BF_PREC_BF16X3 || prec == BF_PREC_TF32X3; }
+
+// BF_PREC_BF16X3 / BF_PREC_TF32X3: the multi-RHS column pass that ends at the switch level stops before
 // the switch, and a tensor-core switch pass (row = 2, l0 = m) follows it.  With tc_levels
 // every column merge level becomes a tensor-core pass of its own (row = 3, k = 1) and the
 // init a multi-RHS pass without levels.
 void tc_switch_split(const bf_plan_s *p, std::vector<Pass> &sc)
 {
-    if (p->prec != BF_PREC_BF16X3 || !p->fns->switch_tc) return;
+    if (!tc_prec(p->prec) || !(p->prec == BF_PREC_TF32X3 ? p->fns->switch_tc32 : p->fns->switch_tc)) return;
     std::vector<Pass> out;
-    const bool levels = p->prm.tc_levels && p->fns->col_tc;
+    const bool levels = p->prec == BF_PREC_BF16X3 && p->prm.tc_levels && p->fns->col_tc;
     for (const Pass &ps : sc) {
         if (ps.row != 0) {
             out.push_back(ps);
@@ -453,13 +456,15 @@ bf_status run_forward_mr(bf_plan p, const void *g, void *f, int nrhs, cudaStream
             int dev = 0, sms = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            const bool sw = ps.row == 2;
-            const int per_sm = sw ? p->fns->switch_tc_ctas_per_sm() : p->fns->col_tc_ctas_per_sm();
+            const bool sw = ps.row == 2, t32 = p->prec == BF_PREC_TF32X3;
+            const int per_sm = sw ? (t32 ? p->fns->switch_tc32_ctas_per_sm() : p->fns->switch_tc_ctas_per_sm())
+                                  : p->fns->col_tc_ctas_per_sm();
             if (per_sm < 1) return BF_ERR_UNSUPPORTED;
             int64_t grid = (p->npts / (sw ? 2 : 4)) >> (a.shard_mode == 1 ? sg : 0);
             if ((int64_t)sms * per_sm < grid) grid = (int64_t)sms * per_sm;
-            cudaError_t e = (sw ? p->fns->switch_tc : p->fns->col_tc)(&a, (unsigned)grid, (unsigned)((nrhs + 15) / 16),
-                                                                     sw ? p->fns->switch_tc_smem : p->fns->col_tc_smem, s);
+            const bfl::pass_fn fn = sw ? (t32 ? p->fns->switch_tc32 : p->fns->switch_tc) : p->fns->col_tc;
+            const size_t smem = sw ? (t32 ? p->fns->switch_tc32_smem : p->fns->switch_tc_smem) : p->fns->col_tc_smem;
+            cudaError_t e = fn(&a, (unsigned)grid, (unsigned)((nrhs + 15) / 16), smem, s);
             if (e != cudaSuccess) return cuda_fail(p, e);
             continue;
         }
@@ -1101,7 +1106,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     if (q < 2 || q > bfk::QMAX) return BF_ERR_INVALID_ARG;
     if ((int)phase < 0 || (int)phase > 3) return BF_ERR_INVALID_ARG;
     if (phase == BF_PHASE_HYPRADON && d != 2) return BF_ERR_INVALID_ARG;
-    if (prm->precision < BF_PREC_FP64 || prm->precision > BF_PREC_BF16X3) return BF_ERR_INVALID_ARG;
+    if (prm->precision < BF_PREC_FP64 || prm->precision > BF_PREC_TF32X3) return BF_ERR_INVALID_ARG;
     if (!supported_q(d, q)) return BF_ERR_UNSUPPORTED;
     if (prm->precision != BF_PREC_FP64 && phase_bound(d, (int)phase, prm) >= 2097152.0) return BF_ERR_UNSUPPORTED;
     for (int k = 0; k < d; ++k) {
@@ -1121,7 +1126,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
     if (prm->phase_tables != 0 && prm->phase_tables != 1) return BF_ERR_INVALID_ARG;
     if (prm->tc_levels != 0 && prm->tc_levels != 1) return BF_ERR_INVALID_ARG;
-    if (prm->phase_tables && (prm->precision == BF_PREC_FP64 || prm->precision == BF_PREC_BF16X3 || (d == 2 && q > 5)))
+    if (prm->phase_tables && (prm->precision == BF_PREC_FP64 || tc_prec(prm->precision) || (d == 2 && q > 5)))
         return BF_ERR_UNSUPPORTED;
 
     bf_plan p = new (std::nothrow) bf_plan_s();
@@ -1139,8 +1144,8 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
     p->max_nrhs = prm->max_nrhs;
     p->prm = *prm;
     p->csize = p->prec == BF_PREC_FP64 ? 16 : 8;
-    // BF16X3 evaluates its phases as BF_PREC_MIXED does and runs the same kernels but the switch
-    p->fns = bfl::get_fns(d, q, p->prec == BF_PREC_BF16X3 ? (int)BF_PREC_MIXED : (int)p->prec, (int)phase);
+    // BF16X3 and TF32X3 evaluate their phases as BF_PREC_MIXED does and run the same kernels but the switch
+    p->fns = bfl::get_fns(d, q, tc_prec(p->prec) ? (int)BF_PREC_MIXED : (int)p->prec, (int)phase);
     if (!p->fns) {   // this combination was not compiled into the library
         delete p;
         return BF_ERR_UNSUPPORTED;
@@ -1236,7 +1241,7 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         else
             st = p->prec == BF_PREC_MIXED_SFU ? build_phase_table<bfk::PMIXF>(p) : build_phase_table<bfk::PMIX>(p);
     }
-    if (st == BF_OK && !p->errflag && p->prec == BF_PREC_BF16X3) {   // the tensor-core switch's bounded waits
+    if (st == BF_OK && !p->errflag && tc_prec(p->prec)) {   // the tensor-core switch's bounded waits
         cudaError_t e = cudaMalloc(&p->errflag, sizeof(int));
         if (e == cudaSuccess) e = cudaMemset(p->errflag, 0, sizeof(int));
         if (e != cudaSuccess) st = cuda_fail(p, e);
@@ -1566,7 +1571,7 @@ bf_status bf_batch_create(const bf_plan *plans, const int *nrhs, int count, bf_b
     const bf_plan p0 = plans[0];
     for (int i = 0; i < count; ++i) {
         const bf_plan p = plans[i];
-        if (p->d != 2 || p->prec == BF_PREC_FP64 || p->prec == BF_PREC_BF16X3 || p->passes_mr.empty() ||
+        if (p->d != 2 || p->prec == BF_PREC_FP64 || tc_prec(p->prec) || p->passes_mr.empty() ||
             !p->fns->batch || p->points)
             return BF_ERR_UNSUPPORTED;
         if (p->q != p0->q || p->kind != p0->kind || p->prec != p0->prec || p->node_kind != p0->node_kind)
@@ -1686,7 +1691,13 @@ bf_status bf_selfcheck_sincos(int n, double *max_abs_err)
 bf_status bf_selfcheck_umma(int split, double *max_rel_err, int *timed_out)
 {
     if ((split != 0 && split != 1) || !max_rel_err || !timed_out) return BF_ERR_INVALID_ARG;
-    return bfl::selfcheck_umma(split, max_rel_err, timed_out) == cudaSuccess ? BF_OK : BF_ERR_CUDA;
+    return bfl::selfcheck_umma(0, split, max_rel_err, timed_out) == cudaSuccess ? BF_OK : BF_ERR_CUDA;
+}
+
+bf_status bf_selfcheck_umma_tf32(int split, double *max_rel_err, int *timed_out)
+{
+    if ((split != 0 && split != 1) || !max_rel_err || !timed_out) return BF_ERR_INVALID_ARG;
+    return bfl::selfcheck_umma(1, split, max_rel_err, timed_out) == cudaSuccess ? BF_OK : BF_ERR_CUDA;
 }
 
 bf_status bf_measure_fma_rate(int fp64, double *tflops)

@@ -130,40 +130,40 @@ int batch_ctas_per_sm(size_t smem)
     return n;
 }
 
-template <int Q, class P, int K>
+template <int Q, class P, int K, int F>
 cudaError_t launch_switch_tc(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
 {
     static size_t granted[64] = {0};
-    cudaError_t e = prepare(bfk::k_switch_tc<Q, P, K>, smem, granted);
+    cudaError_t e = prepare(bfk::k_switch_tc<Q, P, K, F>, smem, granted);
     if (e != cudaSuccess) return e;
-    bfk::k_switch_tc<Q, P, K><<<dim3(gx, gy), bfk::SwTC<Q>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    bfk::k_switch_tc<Q, P, K, F><<<dim3(gx, gy), bfk::SwTC<Q, F>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
     return cudaGetLastError();
 }
 
-// CTAs of the tensor-core switch that fit on one SM by its registers, shared memory and
+// CTAs of the tensor-core switch (operand format F) that fit on one SM by its registers, shared memory and
 // threads (its grid is persistent, so a count above what the hardware keeps resident only
 // queues CTAs; the occupancy query is taken when it allows more)
-template <int Q, class P, int K>
+template <int Q, class P, int K, int F>
 int switch_tc_ctas_per_sm()
 {
     static size_t granted[64] = {0};
-    if (prepare(bfk::k_switch_tc<Q, P, K>, bfk::SwTC<Q>::SMEM, granted) != cudaSuccess) return 0;
+    if (prepare(bfk::k_switch_tc<Q, P, K, F>, bfk::SwTC<Q, F>::SMEM, granted) != cudaSuccess) return 0;
     int dev = 0, n = 0;
     cudaFuncAttributes fa{};
     cudaDeviceProp pr{};
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, bfk::k_switch_tc<Q, P, K>) != cudaSuccess ||
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, bfk::k_switch_tc<Q, P, K, F>) != cudaSuccess ||
         cudaGetDeviceProperties(&pr, dev) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bfk::k_switch_tc<Q, P, K>, bfk::SwTC<Q>::NT,
-                                                      bfk::SwTC<Q>::SMEM) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bfk::k_switch_tc<Q, P, K, F>, bfk::SwTC<Q, F>::NT,
+                                                      bfk::SwTC<Q, F>::SMEM) != cudaSuccess)
         n = 0;
-    const int warps = bfk::SwTC<Q>::NT / 32;
+    const int warps = bfk::SwTC<Q, F>::NT / 32;
     const int regs_cta = warps * ((fa.numRegs * 32 + 255) / 256 * 256);
-    const size_t smem_cta = bfk::SwTC<Q>::SMEM + fa.sharedSizeBytes + pr.reservedSharedMemPerBlock;
+    const size_t smem_cta = bfk::SwTC<Q, F>::SMEM + fa.sharedSizeBytes + pr.reservedSharedMemPerBlock;
     int res = pr.maxBlocksPerMultiProcessor;
     if (regs_cta > 0 && pr.regsPerMultiprocessor / regs_cta < res) res = pr.regsPerMultiprocessor / regs_cta;
     if ((int)(pr.sharedMemPerMultiprocessor / smem_cta) < res) res = (int)(pr.sharedMemPerMultiprocessor / smem_cta);
-    if (pr.maxThreadsPerMultiProcessor / bfk::SwTC<Q>::NT < res) res = pr.maxThreadsPerMultiProcessor / bfk::SwTC<Q>::NT;
+    if (pr.maxThreadsPerMultiProcessor / bfk::SwTC<Q, F>::NT < res) res = pr.maxThreadsPerMultiProcessor / bfk::SwTC<Q, F>::NT;
     return n > res ? n : res;
 }
 
@@ -231,10 +231,12 @@ const PassFns *fns_for()
                                    TAB ? launch_col<D, (TAB ? Q : 2), P, K, bfk::PM_TABLE> : nullptr},
                                   {TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_BUILD> : nullptr,
                                    TAB ? launch_row<D, (TAB ? Q : 2), P, K, bfk::PM_TABLE> : nullptr},
-                                  TC ? launch_switch_tc<QT, P, K> : nullptr,
-                                  TC ? switch_tc_ctas_per_sm<QT, P, K> : nullptr, TC ? bfk::SwTC<QT>::SMEM : 0,
+                                  TC ? launch_switch_tc<QT, P, K, 0> : nullptr,
+                                  TC ? switch_tc_ctas_per_sm<QT, P, K, 0> : nullptr, TC ? bfk::SwTC<QT, 0>::SMEM : 0,
                                   TC ? launch_col_tc<QT, P, K> : nullptr,
-                                  TC ? col_tc_ctas_per_sm<QT, P, K> : nullptr, TC ? bfk::ColTC<QT>::SMEM : 0};
+                                  TC ? col_tc_ctas_per_sm<QT, P, K> : nullptr, TC ? bfk::ColTC<QT>::SMEM : 0,
+                                  TC ? launch_switch_tc<QT, P, K, 1> : nullptr,
+                                  TC ? switch_tc_ctas_per_sm<QT, P, K, 1> : nullptr, TC ? bfk::SwTC<QT, 1>::SMEM : 0};
         return &f;
     } else if constexpr (!P::is_f64) {
         // d = 3: single-RHS passes with a reduced-phase table; no multi-RHS kernels

@@ -39,6 +39,11 @@ struct PassFns {
     pass_fn col_tc;
     int (*col_tc_ctas_per_sm)();
     size_t col_tc_smem;
+    // the multi-RHS switch on the tensor cores with TF32x3 products (BF_PREC_TF32X3; same
+    // conditions and grid as switch_tc)
+    pass_fn switch_tc32 = nullptr;
+    int (*switch_tc32_ctas_per_sm)() = nullptr;
+    size_t switch_tc32_smem = 0;
 };
 
 // (d, q, precision, phase kind) -> kernels, or null if that combination is not compiled.
@@ -86,6 +91,6 @@ cudaError_t selfcheck_sincos(int n, double *max_err);
 cudaError_t phase_rate(const void *kargs_mix, int sfu, int L, int q, int kind, int paired, double *gphases);
 cudaError_t selfcheck_phase(const void *kargs_mix, const void *kargs_f64, int d, int L, int q, int kind, int n,
                             double *max_err);
-cudaError_t selfcheck_umma(int split, double *max_rel_err, int *timed_out);
+cudaError_t selfcheck_umma(int fmt, int split, double *max_rel_err, int *timed_out);   // fmt 0 BF16, 1 TF32
 
 }  // namespace bfl

@@ -190,35 +190,39 @@ __global__ void k_phase_rate(const bfk::KArgs<P> a, int L, int q, int iters, flo
 }
 
 // Self-check of the tensor-core building blocks with the operand layout above: one CTA
-// computes D = A B^T (M = 128, N = 32, K = 64) from row-major FP32 inputs A [128][64] and
-// B [32][64], either from the BF16 roundings of the inputs (split = 0: one product per K
-// step) or from their BF16x3 split (split = 1), and writes D [128][32] row-major.
+// computes D = A B^T (M = 128, N = 32, K = KK) from row-major FP32 inputs A [128][KK] and
+// B [32][KK], either from the roundings of the inputs to the operand format (split = 0: one
+// product per K step) or from their split into hi + lo (split = 1: three products), and
+// writes D [128][32] row-major.  F = 0: BF16 operands (kind::f16), KK = 64; F = 1: TF32
+// operands (kind::tf32), KK = 32.
+template <int F>
 __global__ void __launch_bounds__(128) k_umma_selfcheck(const float *A, const float *B, float *Dout, int split, int *err)
 {
-    constexpr int M = 128, N = 32, KK = 64;
-    constexpr uint32_t LBO = 128, SBO = (KK / 8) * 128, AB = (M / 8) * SBO, BB = (N / 8) * SBO;
+    constexpr int M = 128, N = 32, KK = F ? 32 : 64, EPC = F ? 4 : 8;   // EPC: elements per 16-byte piece
+    constexpr uint32_t LBO = 128, SBO = (KK / EPC) * 128, AB = (M / 8) * SBO, BB = (N / 8) * SBO;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char *Ah = smem_raw, *Al = Ah + AB, *Bh = Al + AB, *Bl = Bh + BB;
     uint64_t *bar = reinterpret_cast<uint64_t *>(Bl + BB);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *sfail = reinterpret_cast<int *>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    for (int j = tid; j < M * KK / 2; j += 128) {
-        const int m = j / (KK / 2), k = 2 * (j % (KK / 2));
-        uint32_t hi, lo;
-        bfk::umma::split2(A[m * KK + k], A[m * KK + k + 1], hi, lo);
-        const uint32_t off = bfk::umma::kmajor_off(m, k, LBO, SBO);
-        *reinterpret_cast<uint32_t *>(Ah + off) = hi;
-        *reinterpret_cast<uint32_t *>(Al + off) = split ? lo : 0u;
-    }
-    for (int j = tid; j < N * KK / 2; j += 128) {
-        const int n = j / (KK / 2), k = 2 * (j % (KK / 2));
-        uint32_t hi, lo;
-        bfk::umma::split2(B[n * KK + k], B[n * KK + k + 1], hi, lo);
-        const uint32_t off = bfk::umma::kmajor_off(n, k, LBO, SBO);
-        *reinterpret_cast<uint32_t *>(Bh + off) = hi;
-        *reinterpret_cast<uint32_t *>(Bl + off) = split ? lo : 0u;
-    }
+    // one 32-bit word per item: two BF16 values or one TF32 value
+    auto put = [&](const float *X, int rows, unsigned char *hp, unsigned char *lp) {
+        constexpr int VPW = F ? 1 : 2;   // values per word
+        for (int j = tid; j < rows * KK / VPW; j += 128) {
+            const int m = j / (KK / VPW), k = VPW * (j % (KK / VPW));
+            uint32_t hi, lo;
+            if constexpr (F)
+                bfk::umma::split_tf32(X[m * KK + k], hi, lo);
+            else
+                bfk::umma::split2(X[m * KK + k], X[m * KK + k + 1], hi, lo);
+            const uint32_t off = bfk::umma::kmajor_piece_off(m, k / EPC, LBO, SBO) + (uint32_t)(k % EPC) * (F ? 4u : 2u);
+            *reinterpret_cast<uint32_t *>(hp + off) = hi;
+            *reinterpret_cast<uint32_t *>(lp + off) = split ? lo : 0u;
+        }
+    };
+    put(A, M, Ah, Al);
+    put(B, N, Bh, Bl);
     if (warp == 0) bfk::umma::alloc(tslot, 32);
     if (tid == 0) {
         bfk::mbar_init(bar, 1);
@@ -231,17 +235,23 @@ __global__ void __launch_bounds__(128) k_umma_selfcheck(const float *A, const fl
     bfk::umma::fence_after_sync();
     const uint32_t tmem = *tslot;
     if (tid == 0) {
-        const uint32_t idesc = bfk::umma::idesc_bf16_f32(M, N);
-        for (int ks = 0; ks < KK / 16; ++ks) {
+        const uint32_t idesc = F ? bfk::umma::idesc_tf32_f32(M, N) : bfk::umma::idesc_bf16_f32(M, N);
+        auto mma = [&](uint64_t da, uint64_t db, int acc) {
+            if constexpr (F)
+                bfk::umma::mma_tf32(tmem, da, db, idesc, acc);
+            else
+                bfk::umma::mma_bf16(tmem, da, db, idesc, acc);
+        };
+        for (int ks = 0; ks < KK / (2 * EPC); ++ks) {
             const uint32_t o = (uint32_t)ks * 2u * LBO;
             const uint64_t dah = bfk::umma::desc_kmajor(bfk::umma::saddr(Ah) + o, LBO, SBO);
             const uint64_t dal = bfk::umma::desc_kmajor(bfk::umma::saddr(Al) + o, LBO, SBO);
             const uint64_t dbh = bfk::umma::desc_kmajor(bfk::umma::saddr(Bh) + o, LBO, SBO);
             const uint64_t dbl = bfk::umma::desc_kmajor(bfk::umma::saddr(Bl) + o, LBO, SBO);
-            bfk::umma::mma_bf16(tmem, dah, dbh, idesc, ks > 0);
+            mma(dah, dbh, ks > 0);
             if (split) {
-                bfk::umma::mma_bf16(tmem, dah, dbl, idesc, 1);
-                bfk::umma::mma_bf16(tmem, dal, dbh, idesc, 1);
+                mma(dah, dbl, 1);
+                mma(dal, dbh, 1);
             }
         }
         bfk::umma::commit(bar);
@@ -389,14 +399,15 @@ cudaError_t selfcheck_phase(const void *kargs_mix, const void *kargs_f64, int d,
     return e;
 }
 
-// The BF16 tensor-core path on fixed operands: split = 0 uses small integers (every
-// product and sum exact, so the result must equal the FP64 product), split = 1 uniform
-// values in [-1, 1) through the BF16x3 split.  max_rel_err: largest |D - D_ref| over
-// max |D_ref|; timed_out: the completion wait gave up.
-cudaError_t selfcheck_umma(int split, double *max_rel_err, int *timed_out)
+// The tensor-core path on fixed operands (fmt 0: BF16, 1: TF32): split = 0 uses small
+// integers (every product and sum exact, so the result must equal the FP64 product),
+// split = 1 uniform values in [-1, 1) through the hi + lo split.  max_rel_err: largest
+// |D - D_ref| over max |D_ref|; timed_out: the completion wait gave up.
+cudaError_t selfcheck_umma(int fmt, int split, double *max_rel_err, int *timed_out)
 {
-    constexpr int M = 128, N = 32, KK = 64;
-    std::vector<float> A(M * KK), B(N * KK);
+    constexpr int M = 128, N = 32;
+    const int KK = fmt ? 32 : 64, EPC = fmt ? 4 : 8;
+    std::vector<float> A((size_t)M * KK), B((size_t)N * KK);
     uint32_t h = 12345u;
     for (auto *v : {&A, &B})
         for (float &x : *v) {
@@ -414,8 +425,12 @@ cudaError_t selfcheck_umma(int split, double *max_rel_err, int *timed_out)
     if (e == cudaSuccess) e = cudaMemset(dD, 0, (size_t)M * N * sizeof(float));
     if (e == cudaSuccess) e = cudaMemset(derr, 0, sizeof(int));
     if (e == cudaSuccess) {
-        const size_t smem = 2 * (size_t)(M / 8) * (KK / 8) * 128 + 2 * (size_t)(N / 8) * (KK / 8) * 128 + 64;
-        k_umma_selfcheck<<<1, 128, smem>>>(dA, dB, dD, split, derr);
+        const size_t sbo = (size_t)(KK / EPC) * 128;
+        const size_t smem = 2 * (size_t)(M / 8) * sbo + 2 * (size_t)(N / 8) * sbo + 64;   // < 48 KB
+        if (fmt)
+            k_umma_selfcheck<1><<<1, 128, smem>>>(dA, dB, dD, split, derr);
+        else
+            k_umma_selfcheck<0><<<1, 128, smem>>>(dA, dB, dD, split, derr);
         e = cudaGetLastError();
     }
     std::vector<float> D((size_t)M * N);
@@ -427,7 +442,7 @@ cudaError_t selfcheck_umma(int split, double *max_rel_err, int *timed_out)
         for (int m = 0; m < M; ++m)
             for (int n = 0; n < N; ++n) {
                 double ref = 0.0;
-                for (int k = 0; k < KK; ++k) ref += (double)A[m * KK + k] * (double)B[n * KK + k];
+                for (int k = 0; k < KK; ++k) ref += (double)A[(size_t)m * KK + k] * (double)B[(size_t)n * KK + k];
                 md = std::fmax(md, std::fabs(ref));
                 mx = std::fmax(mx, std::fabs((double)D[(size_t)m * N + n] - ref));
             }

@@ -40,21 +40,56 @@ __device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, unsigned parity, uin
 
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;   // 2 s: an MMA group takes microseconds
 
-template <int Q>
+// operand formats of the tensor-core switch.  Both split every FP32 operand x into
+// hi + lo and accumulate hi.hi + hi.lo + lo.hi in FP32 (the dropped lo.lo is below the
+// format's rounding): F = 0 BF16 parts (kind::f16, two values per 32-bit word, K = 16 per
+// MMA; ~2^-17 relative per product), F = 1 TF32 parts (kind::tf32, one value per word,
+// K = 8 per MMA; ~2^-22 relative per product, at the level of FP32 rounding).
+template <int F> struct TcFmt;
+template <> struct TcFmt<0> {
+    static constexpr int EPC = 8;      // elements per 16-byte row piece of a core matrix
+    static constexpr int KSTEP = 16;   // K of one MMA
+    static constexpr int WPC = 1;      // 32-bit words of one complex value (x, y) along K
+    // the hi and lo words of (x, y) as stored along K (first value low)
+    static __device__ __forceinline__ void split(float x, float y, uint32_t *h, uint32_t *l) { umma::split2(x, y, h[0], l[0]); }
+    // the words of (x, -y) and of (y, x) from those of (x, y)
+    static __device__ __forceinline__ void neg_y(const uint32_t *w, uint32_t *o) { o[0] = w[0] ^ 0x80000000u; }
+    static __device__ __forceinline__ void swap(const uint32_t *w, uint32_t *o) { o[0] = __byte_perm(w[0], 0u, 0x1032); }
+    static __host__ __device__ constexpr uint32_t idesc(int M, int N) { return umma::idesc_bf16_f32(M, N); }
+    static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, int acc) { umma::mma_bf16(d, a, b, id, acc); }
+};
+template <> struct TcFmt<1> {
+    static constexpr int EPC = 4;
+    static constexpr int KSTEP = 8;
+    static constexpr int WPC = 2;
+    static __device__ __forceinline__ void split(float x, float y, uint32_t *h, uint32_t *l)
+    {
+        umma::split_tf32(x, h[0], l[0]);
+        umma::split_tf32(y, h[1], l[1]);
+    }
+    static __device__ __forceinline__ void neg_y(const uint32_t *w, uint32_t *o) { o[0] = w[0]; o[1] = w[1] ^ 0x80000000u; }
+    static __device__ __forceinline__ void swap(const uint32_t *w, uint32_t *o) { o[0] = w[1]; o[1] = w[0]; }
+    static __host__ __device__ constexpr uint32_t idesc(int M, int N) { return umma::idesc_tf32_f32(M, N); }
+    static __device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, int acc) { umma::mma_tf32(d, a, b, id, acc); }
+};
+
+template <int Q, int F = 0>
 struct SwTC {
+    using FM = TcFmt<F>;
     static constexpr int RR = Q * Q;                        // r
     static constexpr int UP = 2;                            // pairs per MMA
     static constexpr int ROWS = 64;                         // A rows per pair (2 r used)
     static constexpr int NPP = 16;                          // right-hand sides (B rows) per pair
     static constexpr int M = UP * ROWS, N = UP * NPP;       // 128 x 32 accumulator
     static constexpr int SLOT = 2 * Q <= 8 ? 8 : 16;        // K elements per source digit t_1
-    static constexpr int PIECES = SLOT / 8;                 // 16-byte pieces per slot and row
-    static constexpr int KP = (SLOT * Q + 15) / 16 * 16;    // K, padded to the MMA's K step
-    static constexpr int NKS = KP / 16;                     // K steps
+    static constexpr int PIECES = SLOT / FM::EPC;           // 16-byte pieces per slot and row
+    static constexpr int NWS = Q * FM::WPC;                 // 32-bit words of a slot's 2q values
+    static constexpr int KP = (SLOT * Q + FM::KSTEP - 1) / FM::KSTEP * FM::KSTEP;   // K, padded to the MMA's K step
+    static constexpr int NKS = KP / FM::KSTEP;              // K steps
     static constexpr uint32_t LBO = 128;                    // core matrices along K: adjacent
-    static constexpr uint32_t SBO = (KP / 8) * 128;         // 8-row groups
-    static constexpr uint32_t A_BYTES = (M / 8) * SBO;      // one BF16 part of A
-    static constexpr uint32_t B_BYTES = (N / 8) * SBO;      // one BF16 part of B
+    static constexpr uint32_t SBO = (KP / FM::EPC) * 128;   // 8-row groups
+    static constexpr uint32_t A_BYTES = (M / 8) * SBO;      // one part (hi or lo) of A
+    static constexpr uint32_t B_BYTES = (N / 8) * SBO;      // one part of B
     static constexpr int NT = 256;                          // threads: 8 warps
     static constexpr int TMEM_COLS = 32;
     static constexpr uint32_t W_BYTES = NPP * UP * RR * 8;  // a unit's weights as stored (complex64)
@@ -64,19 +99,8 @@ struct SwTC {
     static_assert(2 * RR <= ROWS, "the tensor-core switch holds r <= 32");
     static_assert(UP * RR * Q <= NT && UP * NPP * Q + UP * RR <= NT, "one item per thread");
     static_assert((UP * RR * 8) % 16 == 0, "a unit's weights per right-hand side are whole 16-byte pieces");
+    static_assert(NWS <= 4 * PIECES, "a slot's values fit its pieces");
 };
-
-// BF16 parts of a complex number e = x + iy for the two A rows of a target node: row 2s
-// takes (x, -y), row 2s + 1 takes (y, x), packed as stored along K (first value low)
-__device__ __forceinline__ void split_rows(float x, float y, uint32_t &h0, uint32_t &l0, uint32_t &h1, uint32_t &l1)
-{
-    uint32_t h, l;
-    umma::split2(x, y, h, l);               // (x, y)
-    h0 = h ^ 0x80000000u;                   // (x, -y): negate the upper value
-    l0 = l ^ 0x80000000u;
-    h1 = __byte_perm(h, 0u, 0x1032);        // (y, x): swap the halves
-    l1 = __byte_perm(l, 0u, 0x1032);
-}
 
 // Switch pass: reads the level-m weights a.win ([rhs][pair][r], pair = A 2^{2(L-m)} + B),
 // writes the switched weights to a.wout in the same layout.  Right-hand sides
@@ -86,10 +110,11 @@ __device__ __forceinline__ void split_rows(float x, float y, uint32_t &h0, uint3
 // loads overlap the previous unit's phase evaluation.
 // A completion wait that gives up sets *a.err, waits once more (bounded), frees the
 // tensor memory and ends the kernel (the outputs are then undefined).
-template <int Q, class P, int K>
-__global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
+template <int Q, class P, int K, int F = 0>
+__global__ void __launch_bounds__(SwTC<Q, F>::NT) k_switch_tc(const KArgs<P> a)
 {
-    using ST = SwTC<Q>;
+    using ST = SwTC<Q, F>;
+    using FM = typename ST::FM;
     using C = typename P::C;
     using PH = Ph<P, 2, K>;
     using PH2 = Ph2<P, 2, K>;
@@ -135,7 +160,7 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
     };
     const int rhs0 = (int)blockIdx.y * ST::NPP;
     const int nr = min(ST::NPP, a.nrhs - rhs0);
-    const uint32_t idesc = umma::idesc_bf16_f32(ST::M, ST::N);
+    const uint32_t idesc = FM::idesc(ST::M, ST::N);
     unsigned parity = 0;
 
     // weights of unit v into the staging buffer: per right-hand side rb < nr, the two pairs'
@@ -153,16 +178,17 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    // slot th of row `row` in a part: PIECES 16-byte pieces (2q values, then zeros)
+    // slot th of row `row` in a part: PIECES 16-byte pieces (the NWS words of 2q values,
+    // then zeros)
     auto put_slot = [&](unsigned char *base, int row, int th, const uint32_t *w) {
 #pragma unroll
         for (int pc = 0; pc < ST::PIECES; ++pc) {
             uint4 v;
-            v.x = 4 * pc + 0 < Q ? w[4 * pc + 0] : 0u;
-            v.y = 4 * pc + 1 < Q ? w[4 * pc + 1] : 0u;
-            v.z = 4 * pc + 2 < Q ? w[4 * pc + 2] : 0u;
-            v.w = 4 * pc + 3 < Q ? w[4 * pc + 3] : 0u;
-            *reinterpret_cast<uint4 *>(base + umma::kmajor_off(row, ST::SLOT * th + 8 * pc, ST::LBO, ST::SBO)) = v;
+            v.x = 4 * pc + 0 < ST::NWS ? w[4 * pc + 0] : 0u;
+            v.y = 4 * pc + 1 < ST::NWS ? w[4 * pc + 1] : 0u;
+            v.z = 4 * pc + 2 < ST::NWS ? w[4 * pc + 2] : 0u;
+            v.w = 4 * pc + 3 < ST::NWS ? w[4 * pc + 3] : 0u;
+            *reinterpret_cast<uint4 *>(base + umma::kmajor_piece_off(row, ST::SLOT / FM::EPC * th + pc, ST::LBO, ST::SBO)) = v;
         }
     };
     fetch(blockIdx.x);
@@ -170,14 +196,14 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
     for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
         asm volatile("cp.async.wait_group 0;" ::: "memory");   // the unit's weights have landed
         __syncthreads();
-        // ---- B: items (rhs, pair, t_1): q weights, split into BF16 parts, one slot each
+        // ---- B: items (rhs, pair, t_1): q weights, split into hi and lo parts, one slot each
         {
             const int rb = tid % ST::NPP, up = (tid / ST::NPP) % ST::UP, th = tid / (ST::NPP * ST::UP);
             if (th < Q && rb < nr) {
                 const C *w = reinterpret_cast<const C *>(Wst) + (rb * ST::UP + up) * RR + Q * th;
-                uint32_t hi[Q], lo[Q];
+                uint32_t hi[ST::NWS], lo[ST::NWS];
 #pragma unroll
-                for (int t0 = 0; t0 < Q; ++t0) umma::split2(w[t0].x, w[t0].y, hi[t0], lo[t0]);
+                for (int t0 = 0; t0 < Q; ++t0) FM::split(w[t0].x, w[t0].y, hi + FM::WPC * t0, lo + FM::WPC * t0);
                 put_slot(Bh, up * ST::NPP + rb, th, hi);
                 put_slot(Bl, up * ST::NPP + rb, th, lo);
             }
@@ -215,9 +241,17 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
             if constexpr (Q & 1)
                 ev[Q - 1] = expphase_part<P, D, K>(a, tS, PH::add(PH::part(tS, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0),
                                                                  PH2::lane0(hp)));
-            uint32_t h0[Q], l0[Q], h1[Q], l1[Q];
+            // row 2s takes (x, -y), row 2s + 1 takes (y, x) of every factor x + iy
+            uint32_t h0[ST::NWS], l0[ST::NWS], h1[ST::NWS], l1[ST::NWS];
 #pragma unroll
-            for (int t0 = 0; t0 < Q; ++t0) split_rows(ev[t0].x, ev[t0].y, h0[t0], l0[t0], h1[t0], l1[t0]);
+            for (int t0 = 0; t0 < Q; ++t0) {
+                uint32_t h[FM::WPC], l[FM::WPC];
+                FM::split(ev[t0].x, ev[t0].y, h, l);
+                FM::neg_y(h, h0 + FM::WPC * t0);
+                FM::neg_y(l, l0 + FM::WPC * t0);
+                FM::swap(h, h1 + FM::WPC * t0);
+                FM::swap(l, l1 + FM::WPC * t0);
+            }
             const int r0 = up * ST::ROWS + 2 * s;
             put_slot(Ah, r0, th, h0);
             put_slot(Al, r0, th, l0);
@@ -237,9 +271,9 @@ __global__ void __launch_bounds__(SwTC<Q>::NT) k_switch_tc(const KArgs<P> a)
                 const uint64_t dal = umma::desc_kmajor(al + o, ST::LBO, ST::SBO);
                 const uint64_t dbh = umma::desc_kmajor(bh + o, ST::LBO, ST::SBO);
                 const uint64_t dbl = umma::desc_kmajor(bl + o, ST::LBO, ST::SBO);
-                umma::mma_bf16(tmem, dah, dbh, idesc, ks > 0);
-                umma::mma_bf16(tmem, dah, dbl, idesc, 1);
-                umma::mma_bf16(tmem, dal, dbh, idesc, 1);
+                FM::mma(tmem, dah, dbh, idesc, ks > 0);
+                FM::mma(tmem, dah, dbl, idesc, 1);
+                FM::mma(tmem, dal, dbh, idesc, 1);
             }
             umma::commit(bar);
             if (!mbar_wait_ns(bar, parity, TC_WAIT_NS)) {

@@ -1,7 +1,7 @@
 // Fifth-generation tensor-core (tcgen05) building blocks, as inline PTX for sm_100-family
 // GPUs (compiled for sm_103a): tensor-memory allocation, shared-memory matrix descriptors,
-// the instruction descriptor of a BF16 x BF16 -> FP32 MMA, the MMA, its completion on an
-// mbarrier and the loads of the FP32 accumulator from tensor memory.
+// the instruction descriptors of BF16 x BF16 -> FP32 and TF32 x TF32 -> FP32 MMAs, the MMAs,
+// their completion on an mbarrier and the loads of the FP32 accumulator from tensor memory.
 //
 // Operand layout (both operands K-major, no swizzle).  A matrix of 16-bit elements is
 // stored as "core matrices" of 8 rows x 16 bytes (8 elements of K), each 128 contiguous
@@ -10,7 +10,9 @@
 // where LBO (the "leading dimension byte offset") steps between core matrices along K and
 // SBO (the "stride dimension byte offset") between groups of 8 rows.  One MMA of
 // kind::f16 consumes K = 16, i.e. two core matrices along K; the next K step starts
-// 2 LBO further on.
+// 2 LBO further on.  With 32-bit elements (TF32) a core matrix holds 8 rows x 4 elements
+// of K, element (row, k) at start + (row / 8) * SBO + (k / 4) * LBO + (row % 8) * 16 +
+// (k % 4) * 4, and one MMA of kind::tf32 consumes K = 8: again two core matrices.
 //
 // Accumulator layout (cta_group::1, M = 128): row i of D is tensor-memory lane i, column j
 // is column base + j, one FP32 value per (lane, column).  A warp can read only the lane
@@ -41,6 +43,21 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N)
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// instruction descriptor of tcgen05.mma kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
+// (bits 7-9 and 10-12 = 2), no negation, both K-major, N / 8 in bits 17-22, M / 16 in bits
+// 24-28
+__host__ __device__ constexpr uint32_t idesc_tf32_f32(int M, int N)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// byte offset of the 16-byte piece `piece` along K (elements k = piece * (16 / element
+// size) ...) of row `row` in a K-major, unswizzled operand
+__host__ __device__ constexpr uint32_t kmajor_piece_off(int row, int piece, uint32_t lbo, uint32_t sbo)
+{
+    return (uint32_t)(row >> 3) * sbo + (uint32_t)piece * lbo + (uint32_t)(row & 7) * 16u;
+}
+
 // byte offset of element (row, k) in a K-major, unswizzled operand (see above)
 __host__ __device__ constexpr uint32_t kmajor_off(int row, int k, uint32_t lbo, uint32_t sbo)
 {
@@ -53,6 +70,16 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// D (+)= A B^T over one K step of 8 TF32 elements; issued by one thread
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
         ::"r"(tmem_d), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
         : "memory");
 }
@@ -115,6 +142,18 @@ __device__ __forceinline__ void split2(float x0, float x1, uint32_t &hi, uint32_
     const float h0 = __uint_as_float(h << 16), h1 = __uint_as_float(h & 0xFFFF0000u);
     uint32_t l;
     asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(l) : "f"(__fsub_rn(x1, h1)), "f"(__fsub_rn(x0, h0)));
+    hi = h;
+    lo = l;
+}
+
+// split x into TF32 parts: hi = x rounded to TF32 (10 stored mantissa bits), lo = (x - hi)
+// (exact in FP32) rounded to TF32, so that hi + lo carries 22 significant bits; each part
+// as the 32-bit word the tensor core reads
+__device__ __forceinline__ void split_tf32(float x, uint32_t &hi, uint32_t &lo)
+{
+    uint32_t h, l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(__fsub_rn(x, __uint_as_float(h))));
     hi = h;
     lo = l;
 }

@@ -1,4 +1,4 @@
-"""The switch on the tensor cores (BF_PREC_BF16X3): tcgen05 GEMM self-checks, then the
+"""The switch on the tensor cores (BF_PREC_BF16X3, BF_PREC_TF32X3): tcgen05 GEMM self-checks, then the
 butterfly with several right-hand sides against the FP64 oracle.
 
 Tolerance: relative l2 <= 1e-4 against the same-q oracle butterfly, per right-hand side
@@ -181,4 +181,79 @@ def test_tc_levels_only_with_bf16x3(bf):
     spec = wl.hypradon(5)
     p = bf.Plan.from_spec(spec, max_nrhs=4, precision="mixed", tc_levels=True)
     assert all(x["kind"] in ("col", "row") for x in p.passes(4))
+    p.close()
+
+
+# ---- TF32x3 (BF_PREC_TF32X3): the same switch with TF32 parts, kind::tf32
+
+def test_umma_tf32_selfcheck_exact(bf):
+    err, timed_out = bf.selfcheck_umma(split=False, fmt="tf32")
+    assert not timed_out
+    assert err == 0.0, err
+
+
+def test_umma_tf32_selfcheck_split(bf):
+    # values in [-1, 1) through the TF32x3 split: 32-term sums to ~2^-21 relative
+    err, timed_out = bf.selfcheck_umma(split=True, fmt="tf32")
+    assert not timed_out
+    assert err < 1e-6, err
+
+
+TOL_TF32_ORACLE = 1e-5      # the mixed tolerance: the TF32x3 products are at FP32 rounding
+
+
+@pytest.mark.parametrize("phase,L,q,nrhs", [("hypradon", 5, 5, 2), ("hypradon", 6, 5, 16), ("hypradon", 7, 5, 19),
+                                            ("genradon", 5, 5, 5), ("dot", 4, 5, 3), ("separable", 5, 5, 4),
+                                            ("genradon", 6, 4, 7), ("hypradon", 5, 3, 17), ("genradon", 4, 2, 3),
+                                            ("hypradon", 2, 5, 20), ("genradon", 1, 5, 3)])
+def test_tf32x3_against_oracle(bf, phase, L, q, nrhs):
+    spec = (wl.hypradon(L) if phase == "hypradon" else wl.genradon2d(L=L).with_(phase=phase)).with_(q=q)
+    g, out, passes, timed_out = _apply(bf, spec, nrhs, "tf32x3", seed=1900 + L + q)
+    assert not timed_out
+    assert [p["kind"] for p in passes].count("switch_tc") == 1
+    ref = oracle.butterfly(oracle.Problem(**spec.oracle_kwargs()), g.astype(np.complex128))
+    for j in range(nrhs):
+        assert rel(out[j], ref[j]) <= TOL_TF32_ORACLE, (j, rel(out[j], ref[j]))
+
+
+def test_tf32x3_one_rhs_is_the_mixed_apply(bf):
+    spec = wl.hypradon(6)
+    _, a, pa, _ = _apply(bf, spec, 1, "tf32x3", seed=15)
+    _, b, pb, _ = _apply(bf, spec, 1, "mixed", seed=15)
+    assert pa == pb
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("L,nrhs", [(8, 16), (9, 16), (9, 19)])
+def test_tf32x3_benchmark_sizes(bf, L, nrhs):
+    # against the FP32 multi-RHS apply (the switch's products differ by ~2^-22) and the
+    # restricted oracle on one level-m box; BF16x3 of the same input is ~10x further off
+    spec = wl.hypradon(L)
+    g, out, passes, timed_out = _apply(bf, spec, nrhs, "tf32x3", seed=1960 + L, autotune=True)
+    assert not timed_out
+    assert any(p["kind"] == "switch_tc" for p in passes)
+    _, f32, _, _ = _apply(bf, spec, nrhs, "mixed", seed=1960 + L)
+    _, b16, _, _ = _apply(bf, spec, nrhs, "bf16x3", seed=1960 + L)
+    e32 = [rel(out[j], f32[j]) for j in range(nrhs)]
+    e16 = [rel(b16[j], f32[j]) for j in range(nrhs)]
+    assert max(e32) <= 2e-6, max(e32)
+    assert max(e32) < 0.5 * min(e16), (max(e32), min(e16))
+    P = oracle.Problem(**spec.oracle_kwargs())
+    lvl = spec.switch_level
+    box = (1 << (2 * lvl)) // 3
+    tg = oracle.restricted_targets(P, lvl, box)
+    ref = oracle.butterfly(P, g[0].astype(np.complex128), restrict=(lvl, box))
+    assert rel(out[0][tg], ref[tg]) <= TOL_TF32_ORACLE
+
+
+def test_tf32x3_refuses_tables_and_batches_and_ignores_tc_levels(bf):
+    spec = wl.hypradon(5)
+    with pytest.raises(bf.BfError):
+        bf.Plan.from_spec(spec, max_nrhs=4, precision="tf32x3", phase_tables=True)
+    plan = bf.Plan.from_spec(spec, max_nrhs=4, precision="tf32x3")
+    with pytest.raises(bf.BfError):
+        bf.Batch([plan], [4])
+    plan.close()
+    p = bf.Plan.from_spec(spec, max_nrhs=4, precision="tf32x3", tc_levels=True)
+    assert [x["kind"] for x in p.passes(4)].count("col_tc") == 0
     p.close()
