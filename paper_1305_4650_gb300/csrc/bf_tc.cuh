@@ -14,14 +14,16 @@
 // M = 128 rows (64 per pair, 2r of them used) and N = 32 columns (16 right-hand sides
 // per pair); the off-diagonal blocks of D are computed and ignored.  Along K the source
 // nodes t = t_0 + q t_1 are grouped by t_1: the 2q values of digit t_1 fill a slot of 8 or
-// 16 elements (one or two 16-byte pieces of a row), so each evaluating thread writes whole
+// 16 elements (whole 16-byte pieces of a row), so each evaluating thread writes whole
 // pieces; the rest of a slot stays zero.
 //
 // Precision (BF16x3): every FP32 operand x is split into BF16 parts hi = bf16(x) and
 // lo = bf16(x - hi) (16 significant bits together), and D accumulates hi.hi + hi.lo +
 // lo.hi in FP32 in tensor memory; the dropped lo.lo term and the rounding of lo are
-// below 2^-17 relative per product.  The phase factors are those of the CUDA-core
-// multi-RHS switch, evaluated with the same code.
+// below 2^-17 relative per product.  TF32x3 does the same with TF32 parts (22 significant
+// bits together, kind::tf32, one value per 32-bit word): ~2^-22 relative per product.
+// The phase factors are those of the CUDA-core multi-RHS switch, evaluated with the same
+// code.  The column merge level on the tensor cores (ColTC, below) uses BF16x3 only.
 #pragma once
 
 #include "bf_mr.cuh"
