@@ -25,7 +25,7 @@ EXPORTS = ["bf_params_default", "bf_plan_create", "bf_apply", "bf_apply_adjoint"
            "bf_apply_pass", "bf_pass_info", "bf_pass_count", "bf_selfcheck_sincos", "bf_selfcheck_phase", "bf_measure_fma_rate",
            "bf_measure_phase_rate", "bf_batch_create", "bf_batch_apply", "bf_batch_status",
            "bf_batch_selftest_timeout", "bf_batch_info", "bf_batch_wait_stats", "bf_batch_destroy", "bf_plan_autotune",
-           "bf_plan_table_info", "bf_plan_create_points", "bf_plan_points_info"]
+           "bf_plan_table_info", "bf_plan_create_points", "bf_plan_points_info", "bf_plan_tc_info"]
 
 
 class BfError(RuntimeError):
@@ -40,7 +40,7 @@ class BfParams(ctypes.Structure):
                 ("phase_scale", ctypes.c_double), ("tgt_off", ctypes.c_double), ("src_off", ctypes.c_double),
                 ("precision", ctypes.c_int32), ("switch_level", ctypes.c_int32), ("node_kind", ctypes.c_int32),
                 ("max_nrhs", ctypes.c_int32), ("fuse_levels", ctypes.c_int32), ("phase_tables", ctypes.c_int32),
-                ("tc_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("tc_levels", ctypes.c_int32), ("tc_cpasync", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
 
 
 _lib = None
@@ -91,6 +91,7 @@ def load():
         lib.bf_plan_create_points.argtypes = [i32, i64, i32, i32, ctypes.POINTER(BfParams), i64, vp, i64, vp,
                                               ctypes.POINTER(vp)]
         lib.bf_plan_points_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.bf_plan_tc_info.argtypes = [vp, ctypes.POINTER(i32)]
         lib.bf_plan_table_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(i32)]
         lib.bf_batch_wait_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i64)]
@@ -123,7 +124,8 @@ class Plan:
     def __init__(self, d: int, N: int, q: int, phase: str, precision: str = "mixed", scale: float = 1.0,
                  x_lo=None, x_w=None, y_lo=None, y_w=None, tgt_off: float = 0.0, src_off: float = 0.0,
                  switch_level: int = -1, node_kind: int = 0, max_nrhs: int = 1, fuse_levels: int = 0,
-                 phase_tables: bool = False, sources=None, targets=None, tc_levels: bool = False):
+                 phase_tables: bool = False, sources=None, targets=None, tc_levels: bool = False,
+                 tc_cpasync: bool = False):
         lib = load()
         p = BfParams()
         _check(lib.bf_params_default(d, N, ctypes.byref(p)), "bf_params_default")
@@ -141,6 +143,7 @@ class Plan:
         p.fuse_levels = fuse_levels
         p.phase_tables = 1 if phase_tables else 0
         p.tc_levels = 1 if tc_levels else 0
+        p.tc_cpasync = 1 if tc_cpasync else 0
         h = ctypes.c_void_p()
         if sources is None and targets is None:
             _check(lib.bf_plan_create(d, N, q, PHASE[phase], ctypes.byref(p), ctypes.byref(h)), "bf_plan_create")
@@ -160,12 +163,13 @@ class Plan:
 
     @classmethod
     def from_spec(cls, spec, max_nrhs: int = 1, precision: str | None = None, fuse_levels: int = 0,
-                  phase_tables: bool = False, sources=None, targets=None, tc_levels: bool = False) -> "Plan":
+                  phase_tables: bool = False, sources=None, targets=None, tc_levels: bool = False,
+                  tc_cpasync: bool = False) -> "Plan":
         """Plan for a workload spec; sources / targets ((n, d) arrays) make a point-set plan."""
         x_lo, x_w, y_lo, y_w = spec.domain()
         return cls(spec.d, spec.N, spec.q, spec.phase, precision or spec.precision, spec.scale,
                    x_lo, x_w, y_lo, y_w, spec.tgt_off, spec.src_off, spec.switch_level, spec.node_kind,
-                   max_nrhs, fuse_levels, phase_tables, sources, targets, tc_levels)
+                   max_nrhs, fuse_levels, phase_tables, sources, targets, tc_levels, tc_cpasync)
 
     @property
     def handle(self) -> int:
@@ -252,6 +256,12 @@ class Plan:
         _check(load().bf_plan_table_info(self._h, ctypes.byref(b), ctypes.byref(ms), ctypes.byref(t)),
                "bf_plan_table_info")
         return dict(bytes=b.value, build_ms=ms.value, timed_out=bool(t.value))
+
+    def tc_info(self) -> dict:
+        """Whether the tensor-core switch stages its weights by tiled bulk copies (TMA)."""
+        t = ctypes.c_int()
+        _check(load().bf_plan_tc_info(self._h, ctypes.byref(t)), "bf_plan_tc_info")
+        return dict(tiled_copies=bool(t.value))
 
     def autotune(self, nrhs: int = 1, reps: int = 3, stream=None) -> float:
         """Time candidate tile schedules for nrhs right-hand sides, keep the fastest; ms per apply."""

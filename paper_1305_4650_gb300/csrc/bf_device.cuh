@@ -252,6 +252,9 @@ struct KArgs {
     // source-domain sharding over 2^shard_g ranks (see shard_cta / shard_owned): 0 off,
     // 1 the launch covers the rank's tiles only, 2 every tile, other ranks' inputs read as zero
     int shard_mode, shard_g, shard_r;
+    // tensor map (a CUtensorMap in device memory) of a.win viewed as [rhs][complex number]
+    // for tiled bulk copies, or null (the tensor-core switch)
+    const void *wmap;
 };
 
 // Sharding.  Rank r of G = 2^g owns the source boxes whose top g Morton bits equal r.  A merge

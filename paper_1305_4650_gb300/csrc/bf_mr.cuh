@@ -47,6 +47,15 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned by
                  ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
+// tiled bulk copy (TMA) of the 2-D box at element coordinates (x, y) of the tensor that
+// `map` describes (a CUtensorMap in global memory) into shared memory, completed on bar;
+// the box's rows land contiguously (x times the element size must be a multiple of 16 bytes)
+__device__ __forceinline__ void bulk_tensor_2d_g2s(void *dst, const void *map, int x, int y, uint64_t *bar)
+{
+    asm volatile("cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+                 ::"r"(smem_u32(dst)), "l"(map), "r"(x), "r"(y), "r"(smem_u32(bar))
+                 : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned parity)
 {
     uint32_t ok;

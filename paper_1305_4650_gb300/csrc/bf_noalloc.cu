@@ -261,9 +261,9 @@ extern "C" bf_status bf_apply_noalloc(int d, int64_t N, int q, bf_phase_kind pha
     if (prm->switch_level < -1 || prm->switch_level >= L) return BF_ERR_INVALID_ARG;
     if (prm->node_kind != 0 && prm->node_kind != 1) return BF_ERR_INVALID_ARG;
     if (prm->fuse_levels < 0 || prm->fuse_levels > 8) return BF_ERR_INVALID_ARG;
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i < 4; ++i)
         if (prm->reserved[i]) return BF_ERR_INVALID_ARG;
-    if (prm->tc_levels) return BF_ERR_INVALID_ARG;        // a BF_PREC_BF16X3 option
+    if (prm->tc_levels || prm->tc_cpasync) return BF_ERR_INVALID_ARG;   // BF_PREC_BF16X3 options
     if (prm->phase_tables) return BF_ERR_INVALID_ARG;   // a table would need device memory
     if (nrhs < 0 || nrhs > 65535) return BF_ERR_INVALID_ARG;
     const int prec = prm->precision;

@@ -130,7 +130,11 @@ __global__ void __launch_bounds__(SwTC<Q, F>::NT) k_switch_tc(const KArgs<P> a)
     uint64_t *bar = reinterpret_cast<uint64_t *>(Wst + ST::W_BYTES + ST::T_BYTES);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(bar + 1);
     int *sfail = reinterpret_cast<int *>(tslot + 1);
+    uint64_t *wbar = reinterpret_cast<uint64_t *>(sfail + 1);       // the tiled copies of the weights
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // a unit's weights arrive by one tiled bulk copy when the plan has a tensor map of the
+    // input (the staging buffer is 128-byte aligned), else by 16-byte cp.async copies
+    const bool use_tma = a.wmap != nullptr && (umma::saddr(Wst) & 127u) == 0u;
 
     // operands start at zero: the padding rows and slots are never written again
     {
@@ -141,6 +145,7 @@ __global__ void __launch_bounds__(SwTC<Q, F>::NT) k_switch_tc(const KArgs<P> a)
     if (warp == 0) umma::alloc(tslot, ST::TMEM_COLS);
     if (tid == 0) {
         mbar_init(bar, 1);
+        mbar_init(wbar, 1);
         mbar_init_fence();
         *sfail = 0;
     }
@@ -166,8 +171,24 @@ __global__ void __launch_bounds__(SwTC<Q, F>::NT) k_switch_tc(const KArgs<P> a)
     unsigned parity = 0;
 
     // weights of unit v into the staging buffer: per right-hand side rb < nr, the two pairs'
-    // 2r complex numbers in 16-byte pieces; one commit group per call
+    // 2r complex numbers.  Tiled: one copy of the box (2r complex numbers x 16 right-hand
+    // sides) at (unit offset, first right-hand side), rows past the last right-hand side read
+    // as zero; its phase of wbar completes when the bytes have landed.  Else 16-byte pieces,
+    // one commit group per call.
+    unsigned wpar = 0;       // phase of wbar the next wait expects
+    bool inflight = false;   // a tiled copy was issued and not yet waited for
     auto fetch = [&](int64_t v) {
+        if (use_tma) {
+            if (v < nunits) {
+                if (tid == 0) {
+                    fence_proxy_async();   // the generic reads of the staging buffer come first
+                    mbar_expect_tx(wbar, ST::W_BYTES);
+                    bulk_tensor_2d_g2s(Wst, a.wmap, (int)(uid(v) * ST::UP * RR), rhs0, wbar);
+                }
+                inflight = true;
+            }
+            return;
+        }
         constexpr int per_rhs = ST::W_CHUNKS / ST::NPP;
         if (v < nunits) {
             for (int c = tid; c < nr * per_rhs; c += ST::NT) {
@@ -196,8 +217,18 @@ __global__ void __launch_bounds__(SwTC<Q, F>::NT) k_switch_tc(const KArgs<P> a)
     fetch(blockIdx.x);
 
     for (int64_t u = blockIdx.x; u < nunits; u += gridDim.x) {
-        asm volatile("cp.async.wait_group 0;" ::: "memory");   // the unit's weights have landed
+        if (use_tma) {   // every thread waits for the unit's weights (bounded)
+            if (!mbar_wait_ns(wbar, wpar, TC_WAIT_NS)) {
+                if (a.err) atomicExch(a.err, 1);
+                *sfail = 1;
+            }
+            wpar ^= 1u;
+            inflight = false;
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");   // the unit's weights have landed
+        }
         __syncthreads();
+        if (*sfail) break;
         // ---- B: items (rhs, pair, t_1): q weights, split into hi and lo parts, one slot each
         {
             const int rb = tid % ST::NPP, up = (tid / ST::NPP) % ST::UP, th = tid / (ST::NPP * ST::UP);
@@ -318,6 +349,7 @@ __global__ void __launch_bounds__(SwTC<Q, F>::NT) k_switch_tc(const KArgs<P> a)
         umma::fence_before_sync();
     }
     asm volatile("cp.async.wait_all;" ::: "memory");   // no copy outlives the kernel
+    if (use_tma && inflight && tid == 0) mbar_wait_ns(wbar, wpar, TC_WAIT_NS);
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) umma::dealloc(tmem, ST::TMEM_COLS);

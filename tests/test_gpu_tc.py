@@ -257,3 +257,50 @@ def test_tf32x3_refuses_tables_and_batches_and_ignores_tc_levels(bf):
     p = bf.Plan.from_spec(spec, max_nrhs=4, precision="tf32x3", tc_levels=True)
     assert [x["kind"] for x in p.passes(4)].count("col_tc") == 0
     p.close()
+
+
+# ---- staging of the switch's weights: one tiled bulk copy (TMA) per unit, or cp.async
+
+@pytest.mark.parametrize("L,nrhs", [(6, 2), (7, 16), (8, 19)])
+def test_bf16x3_tiled_and_cpasync_staging_agree(bf, L, nrhs):
+    # the same arithmetic on the same staged bytes: bit-identical; 19 right-hand sides make
+    # a second block of 16 whose last 13 rows lie past max_nrhs (read as zero, unused)
+    import torch
+    spec = wl.hypradon(L)
+    g = torch.from_numpy(wl.source_values(spec, nrhs, np.complex64, seed=2100 + L)).cuda()
+    outs, tiled = [], []
+    for cp in (False, True):
+        plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="bf16x3", tc_cpasync=cp)
+        tiled.append(plan.tc_info()["tiled_copies"])
+        outs.append(plan.apply(g))
+        torch.cuda.synchronize()
+        assert not plan.table_info()["timed_out"]
+        plan.close()
+    assert tiled == [True, False]
+    assert torch.equal(outs[0], outs[1])
+
+
+def test_staging_reported_per_precision(bf):
+    spec = wl.hypradon(5)
+    for prec, expect in (("bf16x3", True), ("tf32x3", False), ("mixed", False)):
+        p = bf.Plan.from_spec(spec, max_nrhs=4, precision=prec)
+        assert p.tc_info()["tiled_copies"] == expect, prec
+        p.close()
+    p = bf.Plan.from_spec(spec, max_nrhs=1, precision="bf16x3")    # one right-hand side: no switch pass
+    assert p.tc_info()["tiled_copies"] is False
+    p.close()
+
+
+def test_tiled_staging_autotuned_benchmark_size(bf):
+    # the autotuned schedule of the N = 512 problem with 16 right-hand sides, both stagings
+    import torch
+    spec = wl.hypradon(9)
+    g = torch.from_numpy(wl.source_values(spec, 16, np.complex64, seed=2200)).cuda()
+    outs = []
+    for cp in (False, True):
+        plan = bf.Plan.from_spec(spec, max_nrhs=16, precision="bf16x3", tc_cpasync=cp)
+        plan.autotune(16, reps=1)
+        outs.append(plan.apply(g))
+        torch.cuda.synchronize()
+        plan.close()
+    assert torch.equal(outs[0], outs[1])
