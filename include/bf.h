@@ -117,7 +117,7 @@ typedef struct {
     int32_t phase_tables;     /* 1: evaluate every phase factor once, at plan creation      */
     int32_t tc_levels;        /* BF_PREC_BF16X3: 1 also runs the column merge levels on the  */
                               /* tensor cores (below); 0 keeps them on the CUDA cores       */
-    int32_t tc_cpasync;       /* BF_PREC_BF16X3: 1 stages the switch's weights with 16-byte  */
+    int32_t tc_cpasync;       /* BF16X3, TF32X3: 1 stages the switch's weights with 16-byte  */
                               /* cp.async copies instead of one tiled bulk copy (TMA) per   */
                               /* unit (same results; bf_plan_tc_info)                       */
     int32_t reserved[4];      /* must be zero                                               */
@@ -268,8 +268,8 @@ bf_status bf_plan_info(bf_plan plan, int *d, int64_t *N, int *q, int *m, int *fu
 bf_status bf_plan_table_info(bf_plan plan, int64_t *table_bytes, double *build_ms, int *timed_out);
 /* Staging of the tensor-core switch: *tiled_copies = 1 when its weights arrive by one tiled
  * bulk copy (cp.async.bulk.tensor, a tensor map of each weight buffer built at plan
- * creation) per unit of two pairs, 0 when by cp.async copies (BF_PREC_TF32X3, tc_cpasync = 1,
- * or a driver without the tensor-map encoder) or when the plan has no tensor-core switch. */
+ * creation) per unit of two pairs, 0 when by cp.async copies (tc_cpasync = 1, or a driver
+ * without the tensor-map encoder) or when the plan has no tensor-core switch. */
 bf_status bf_plan_tc_info(bf_plan plan, int *tiled_copies);
 
 /* Autotuner.  Times candidate tile schedules of the apply bf_apply runs for nrhs

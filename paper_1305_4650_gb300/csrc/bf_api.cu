@@ -1297,9 +1297,8 @@ bf_status bf_plan_create(int d, int64_t N, int q, bf_phase_kind phase, const bf_
         if (e != cudaSuccess) st = cuda_fail(p, e);
         if (st == BF_OK && tile_table)
             st = p->prec == BF_PREC_MIXED_SFU ? build_tile_table<bfk::PMIXF>(p) : build_tile_table<bfk::PMIX>(p);
-        // tiled copies for the BF16x3 switch (measured 5% faster than cp.async there; slower
-        // with the TF32x3 operands, which keep cp.async)
-        if (st == BF_OK && p->prec == BF_PREC_BF16X3 && !prm->tc_cpasync && p->max_nrhs >= 2 && p->fns->switch_tc)
+        // tiled copies for the tensor-core switch (measured faster than cp.async in both formats)
+        if (st == BF_OK && tc_prec(p->prec) && !prm->tc_cpasync && p->max_nrhs >= 2 && p->fns->switch_tc)
             build_weight_maps(p);
         p->ws_bytes = (int64_t)(2 * wbytes) + p->ptab_bytes;
     }

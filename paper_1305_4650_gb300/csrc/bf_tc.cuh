@@ -112,8 +112,10 @@ struct SwTC {
 // loads overlap the previous unit's phase evaluation.
 // A completion wait that gives up sets *a.err, waits once more (bounded), frees the
 // tensor memory and ends the kernel (the outputs are then undefined).
+// Register budget: 64 for BF16 (three CTAs fit an SM by shared memory), up to 128 for
+// TF32, whose shared memory admits two CTAs (with 64 its staging code spilled).
 template <int Q, class P, int K, int F = 0>
-__global__ void __launch_bounds__(SwTC<Q, F>::NT) k_switch_tc(const KArgs<P> a)
+__global__ void __launch_bounds__(SwTC<Q, F>::NT, F ? 2 : 4) k_switch_tc(const KArgs<P> a)
 {
     using ST = SwTC<Q, F>;
     using FM = typename ST::FM;

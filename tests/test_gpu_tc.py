@@ -261,8 +261,9 @@ def test_tf32x3_refuses_tables_and_batches_and_ignores_tc_levels(bf):
 
 # ---- staging of the switch's weights: one tiled bulk copy (TMA) per unit, or cp.async
 
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("L,nrhs", [(6, 2), (7, 16), (8, 19)])
-def test_bf16x3_tiled_and_cpasync_staging_agree(bf, L, nrhs):
+def test_tiled_and_cpasync_staging_agree(bf, prec, L, nrhs):
     # the same arithmetic on the same staged bytes: bit-identical; 19 right-hand sides make
     # a second block of 16 whose last 13 rows lie past max_nrhs (read as zero, unused)
     import torch
@@ -270,7 +271,7 @@ def test_bf16x3_tiled_and_cpasync_staging_agree(bf, L, nrhs):
     g = torch.from_numpy(wl.source_values(spec, nrhs, np.complex64, seed=2100 + L)).cuda()
     outs, tiled = [], []
     for cp in (False, True):
-        plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision="bf16x3", tc_cpasync=cp)
+        plan = bf.Plan.from_spec(spec, max_nrhs=nrhs, precision=prec, tc_cpasync=cp)
         tiled.append(plan.tc_info()["tiled_copies"])
         outs.append(plan.apply(g))
         torch.cuda.synchronize()
@@ -282,7 +283,7 @@ def test_bf16x3_tiled_and_cpasync_staging_agree(bf, L, nrhs):
 
 def test_staging_reported_per_precision(bf):
     spec = wl.hypradon(5)
-    for prec, expect in (("bf16x3", True), ("tf32x3", False), ("mixed", False)):
+    for prec, expect in (("bf16x3", True), ("tf32x3", True), ("mixed", False)):
         p = bf.Plan.from_spec(spec, max_nrhs=4, precision=prec)
         assert p.tc_info()["tiled_copies"] == expect, prec
         p.close()
