@@ -130,13 +130,18 @@ int batch_ctas_per_sm(size_t smem)
     return n;
 }
 
+// the switch kernel of operand format F (0 BF16, 1 TF32)
+template <int Q, class P, int K, int F> struct KSW;
+template <int Q, class P, int K> struct KSW<Q, P, K, 0> { static constexpr auto fn = bfk::k_switch_tc<Q, P, K>; };
+template <int Q, class P, int K> struct KSW<Q, P, K, 1> { static constexpr auto fn = bfk::k_switch_tc32<Q, P, K>; };
+
 template <int Q, class P, int K, int F>
 cudaError_t launch_switch_tc(const void *kargs, unsigned gx, unsigned gy, size_t smem, cudaStream_t s)
 {
     static size_t granted[64] = {0};
-    cudaError_t e = prepare(bfk::k_switch_tc<Q, P, K, F>, smem, granted);
+    cudaError_t e = prepare(KSW<Q, P, K, F>::fn, smem, granted);
     if (e != cudaSuccess) return e;
-    bfk::k_switch_tc<Q, P, K, F><<<dim3(gx, gy), bfk::SwTC<Q, F>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
+    KSW<Q, P, K, F>::fn<<<dim3(gx, gy), bfk::SwTC<Q, F>::NT, smem, s>>>(*static_cast<const bfk::KArgs<P> *>(kargs));
     return cudaGetLastError();
 }
 
@@ -147,14 +152,14 @@ template <int Q, class P, int K, int F>
 int switch_tc_ctas_per_sm()
 {
     static size_t granted[64] = {0};
-    if (prepare(bfk::k_switch_tc<Q, P, K, F>, bfk::SwTC<Q, F>::SMEM, granted) != cudaSuccess) return 0;
+    if (prepare(KSW<Q, P, K, F>::fn, bfk::SwTC<Q, F>::SMEM, granted) != cudaSuccess) return 0;
     int dev = 0, n = 0;
     cudaFuncAttributes fa{};
     cudaDeviceProp pr{};
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, bfk::k_switch_tc<Q, P, K, F>) != cudaSuccess ||
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaFuncGetAttributes(&fa, KSW<Q, P, K, F>::fn) != cudaSuccess ||
         cudaGetDeviceProperties(&pr, dev) != cudaSuccess)
         return 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, bfk::k_switch_tc<Q, P, K, F>, bfk::SwTC<Q, F>::NT,
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, KSW<Q, P, K, F>::fn, bfk::SwTC<Q, F>::NT,
                                                       bfk::SwTC<Q, F>::SMEM) != cudaSuccess)
         n = 0;
     const int warps = bfk::SwTC<Q, F>::NT / 32;

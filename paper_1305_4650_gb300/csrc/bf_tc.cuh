@@ -112,10 +112,8 @@ struct SwTC {
 // loads overlap the previous unit's phase evaluation.
 // A completion wait that gives up sets *a.err, waits once more (bounded), frees the
 // tensor memory and ends the kernel (the outputs are then undefined).
-// Register budget: 64 for BF16 (three CTAs fit an SM by shared memory), up to 128 for
-// TF32, whose shared memory admits two CTAs (with 64 its staging code spilled).
-template <int Q, class P, int K, int F = 0>
-__global__ void __launch_bounds__(SwTC<Q, F>::NT, F ? 2 : 4) k_switch_tc(const KArgs<P> a)
+template <int Q, class P, int K, int F>
+__device__ __forceinline__ void switch_tc_body(const KArgs<P> &a)
 {
     using ST = SwTC<Q, F>;
     using FM = typename ST::FM;
@@ -355,6 +353,21 @@ __global__ void __launch_bounds__(SwTC<Q, F>::NT, F ? 2 : 4) k_switch_tc(const K
     umma::fence_before_sync();
     __syncthreads();
     if (warp == 0) umma::dealloc(tmem, ST::TMEM_COLS);
+}
+
+// The switch kernels of the two operand formats.  BF16 keeps the compiler's default register
+// target (64 registers; three CTAs fit an SM by shared memory; an explicit bound measured
+// 8% slower), TF32 is compiled for two CTAs per SM, which its shared memory admits (88
+// registers; with 64 its staging code spilled).
+template <int Q, class P, int K>
+__global__ void __launch_bounds__(SwTC<Q, 0>::NT) k_switch_tc(const KArgs<P> a)
+{
+    switch_tc_body<Q, P, K, 0>(a);
+}
+template <int Q, class P, int K>
+__global__ void __launch_bounds__(SwTC<Q, 1>::NT, 2) k_switch_tc32(const KArgs<P> a)
+{
+    switch_tc_body<Q, P, K, 1>(a);
 }
 
 // ============================================================================
