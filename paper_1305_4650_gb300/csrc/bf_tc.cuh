@@ -80,9 +80,19 @@ struct SwTC {
     using FM = TcFmt<F>;
     static constexpr int RR = Q * Q;                        // r
     static constexpr int UP = 2;                            // pairs per MMA
-    static constexpr int ROWS = 64;                         // A rows per pair (2 r used)
+    static constexpr int ROWS = 64;                         // MMA rows per pair
     static constexpr int NPP = 16;                          // right-hand sides (B rows) per pair
     static constexpr int M = UP * ROWS, N = UP * NPP;       // 128 x 32 accumulator
+    // BF16 parts: the 2r rows of pair 1 start at row PS (the first 8-row group after pair
+    // 0's), so one part of A holds A_GROUPS groups; the MMA reads M rows, and the rows past
+    // the part (the start of the next parts: lo of A, then B) only reach accumulator rows
+    // that nothing reads.  Where those rows would reach past B, a part keeps all M rows.
+    // At q = 5 this takes the shared memory from 59 to 54 KB: four CTAs per SM instead of
+    // three (switch 0.91 -> 0.88 ms at N = 512, 16 right-hand sides).  TF32 parts keep
+    // 64-row blocks: two CTAs per SM either way, and the compact form measured 2% slower.
+    static constexpr int PS = F == 0 ? (2 * RR + 7) / 8 * 8 : ROWS;
+    static constexpr int A_USED = (PS + 2 * RR + 7) / 8;
+    static constexpr int A_GROUPS = M / 8 - A_USED <= 2 * (N / 8) ? A_USED : M / 8;
     static constexpr int SLOT = 2 * Q <= 8 ? 8 : 16;        // K elements per source digit t_1
     static constexpr int PIECES = SLOT / FM::EPC;           // 16-byte pieces per slot and row
     static constexpr int NWS = Q * FM::WPC;                 // 32-bit words of a slot's 2q values
@@ -90,7 +100,7 @@ struct SwTC {
     static constexpr int NKS = KP / FM::KSTEP;              // K steps
     static constexpr uint32_t LBO = 128;                    // core matrices along K: adjacent
     static constexpr uint32_t SBO = (KP / FM::EPC) * 128;   // 8-row groups
-    static constexpr uint32_t A_BYTES = (M / 8) * SBO;      // one part (hi or lo) of A
+    static constexpr uint32_t A_BYTES = A_GROUPS * SBO;     // one part (hi or lo) of A
     static constexpr uint32_t B_BYTES = (N / 8) * SBO;      // one part of B
     static constexpr int NT = 256;                          // threads: 8 warps
     static constexpr int TMEM_COLS = 32;
@@ -99,6 +109,8 @@ struct SwTC {
     static constexpr uint32_t T_BYTES = UP * RR * 32;       // target features of the unit's nodes
     static constexpr size_t SMEM = 2 * (size_t)A_BYTES + 2 * (size_t)B_BYTES + W_BYTES + T_BYTES + 64;
     static_assert(2 * RR <= ROWS, "the tensor-core switch holds r <= 32");
+    static_assert(PS + 2 * RR <= M && A_GROUPS <= M / 8, "both pairs' rows lie in the M rows of the MMA");
+    static_assert((M / 8 - A_GROUPS) * SBO <= 2 * B_BYTES, "the rows the MMA reads past a part lie in the next parts");
     static_assert(UP * RR * Q <= NT && UP * NPP * Q + UP * RR <= NT, "one item per thread");
     static_assert((UP * RR * 8) % 16 == 0, "a unit's weights per right-hand side are whole 16-byte pieces");
     static_assert(NWS <= 4 * PIECES, "a slot's values fit its pieces");
@@ -285,7 +297,7 @@ __device__ __forceinline__ void switch_tc_body(const KArgs<P> &a)
                 FM::swap(h, h1 + FM::WPC * t0);
                 FM::swap(l, l1 + FM::WPC * t0);
             }
-            const int r0 = up * ST::ROWS + 2 * s;
+            const int r0 = up * ST::PS + 2 * s;
             put_slot(Ah, r0, th, h0);
             put_slot(Al, r0, th, l0);
             put_slot(Ah, r0 + 1, th, h1);
@@ -319,14 +331,27 @@ __device__ __forceinline__ void switch_tc_body(const KArgs<P> &a)
         __syncthreads();
         if (*sfail) break;
         umma::fence_after_sync();
-        // ---- epilogue: warp w reads lanes 32 (w % 4) .. + 31 (rows 2s + c of pair w / 2 % 2),
-        // columns of its pair's right-hand sides 8 (w / 4) .. + 7; lanes 2s and 2s + 1 swap
-        // halves so that each writes complete complex numbers
+        // ---- epilogue: warp w reads lanes 32 (w % 4) .. + 31 (row 32 (w % 4) + lane: rows
+        // 2s + c of pair 0, or of pair 1 from row PS on), columns of the lane's pair's right-
+        // hand sides 8 (w / 4) .. + 7 (a quarter that holds rows of both pairs reads both
+        // column blocks); lanes 2s and 2s + 1 swap halves so that each writes complete
+        // complex numbers
         {
-            const int quad = warp & 3, half = warp >> 2, up = quad >> 1;
-            const int rr = 32 * (quad & 1) + lane, s = rr >> 1, c = lane & 1;
+            const int quad = warp & 3, half = warp >> 2;
+            const int row = 32 * quad + lane, up = row >= ST::PS ? 1 : 0, loc = row - up * ST::PS;
+            const int s = loc >> 1, c = lane & 1;
+            const int pa = 32 * quad >= ST::PS ? 1 : 0, pb = 32 * quad + 31 >= ST::PS ? 1 : 0;   // warp-uniform
+            const uint32_t lanes = (uint32_t)(32 * quad) << 16;
             float v[8];
-            umma::ld8(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(up * ST::NPP + 8 * half), v);
+            umma::ld8(tmem + lanes + (uint32_t)(pa * ST::NPP + 8 * half), v);
+            if (pb != pa) {
+                float w[8];
+                umma::ld8(tmem + lanes + (uint32_t)(pb * ST::NPP + 8 * half), w);
+                if (up == pb) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = w[j];
+                }
+            }
             float recv[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) recv[j] = __shfl_xor_sync(0xffffffffu, c ? v[j] : v[4 + j], 1);
