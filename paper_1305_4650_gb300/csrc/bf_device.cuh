@@ -874,6 +874,18 @@ struct Tile {
         Bq = (Bstar << (D * (k - i - 1))) + bp;
     }
 
+    // acc += M[h][t][u] v in the column levels.  d = 2: two scalar FMAs, the coefficient a
+    // kernel-parameter operand (a packed FMA needs the duplicated pair M2 in registers first;
+    // 1% faster on the column passes at N = 1024, q = 5); d = 3 and the row levels keep the
+    // packed form, which measured 0.5-1% faster there.  The same roundings either way.
+    static __device__ __forceinline__ void colmac(C &acc, const KArgs<P> &a, int h, int t, int u, C v)
+    {
+        if constexpr (D == 2)
+            cfma(acc, a.M[h][t][u], v);
+        else
+            cfma2(acc, a.M2[h][t][u], v);
+    }
+
     // ---- one column-form merge level (l -> l+1) on all tiles of the CTA
     template <int PM = PM_COMPUTE>
     static __device__ void col_level(const KArgs<P> &a, C *Wt, C *S, Geo *G, int l, int i, float *&tb)
@@ -945,15 +957,15 @@ struct Tile {
                         const C u0 = cmul(E0, win[t0p + Q * tq]), u1 = cmul(E1, win[t0p + 1 + Q * tq]);
 #pragma unroll
                         for (int t0 = 0; t0 < Q; ++t0) {
-                            cfma2(acc[t0], a.M2[c0][t0][t0p], u0);
-                            cfma2(acc[t0], a.M2[c0][t0][t0p + 1], u1);
+                            colmac(acc[t0], a, c0, t0, t0p, u0);
+                            colmac(acc[t0], a, c0, t0, t0p + 1, u1);
                         }
                     }
                     if constexpr (Q & 1) {
                         const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(p1));
                         const C u = cmul(ph<PM>(a, tA, pt, fa.at(cl * Q + Q - 1, it)), win[Q - 1 + Q * tq]);
 #pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0], a.M2[c0][t0][Q - 1], u);
+                        for (int t0 = 0; t0 < Q; ++t0) colmac(acc[t0], a, c0, t0, Q - 1, u);
                     }
                 } else if constexpr (D == 2) {
                     const int c0 = c & 1;
@@ -963,7 +975,7 @@ struct Tile {
                         const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], t0p), 0), p1);
                         const C u = cmul(expphase_part<P, D, K>(a, tA, pt), win[t0p + Q * tq]);
 #pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0], a.M2[c0][t0][t0p], u);
+                        for (int t0 = 0; t0 < Q; ++t0) colmac(acc[t0], a, c0, t0, t0p, u);
                     }
                 } else if constexpr (!P::is_f64) {
                     // d = 3: the parts of coordinates 2 and 1 hoisted, phases two at a time over t'_0
@@ -990,20 +1002,20 @@ struct Tile {
                             const C u0 = cmul(E0, wrow[t0p]), u1 = cmul(E1, wrow[t0p + 1]);
 #pragma unroll
                             for (int t0 = 0; t0 < Q; ++t0) {
-                                cfma2(tmp[t0], a.M2[c0][t0][t0p], u0);
-                                cfma2(tmp[t0], a.M2[c0][t0][t0p + 1], u1);
+                                colmac(tmp[t0], a, c0, t0, t0p, u0);
+                                colmac(tmp[t0], a, c0, t0, t0p + 1, u1);
                             }
                         }
                         if constexpr (Q & 1) {
                             const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(p12));
                             const C u = cmul(ph<PM>(a, tA, pt, fa.at((cl * Q + t1p) * Q + Q - 1, it)), wrow[Q - 1]);
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) cfma2(tmp[t0], a.M2[c0][t0][Q - 1], u);
+                            for (int t0 = 0; t0 < Q; ++t0) colmac(tmp[t0], a, c0, t0, Q - 1, u);
                         }
 #pragma unroll
                         for (int t1 = 0; t1 < Q; ++t1)
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0 + Q * t1], a.M2[c1][t1][t1p], tmp[t0]);
+                            for (int t0 = 0; t0 < Q; ++t0) colmac(acc[t0 + Q * t1], a, c1, t1, t1p, tmp[t0]);
                     }
                 } else {
                     const int c0 = c & 1, c1 = (c >> 1) & 1;
@@ -1018,12 +1030,12 @@ struct Tile {
                             PH::src1(sp, 0, sget<P, Q>(a, 0, l, cb[0], t0p));
                             const C u = cmul(expphase<P, D, K>(a, tA, sp), win[t0p + Q * t1p + Q * Q * tq]);
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) cfma2(tmp[t0], a.M2[c0][t0][t0p], u);
+                            for (int t0 = 0; t0 < Q; ++t0) colmac(tmp[t0], a, c0, t0, t0p, u);
                         }
 #pragma unroll
                         for (int t1 = 0; t1 < Q; ++t1)
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) cfma2(acc[t0 + Q * t1], a.M2[c1][t1][t1p], tmp[t0]);
+                            for (int t0 = 0; t0 < Q; ++t0) colmac(acc[t0 + Q * t1], a, c1, t1, t1p, tmp[t0]);
                     }
                 }
             }
@@ -1055,7 +1067,7 @@ struct Tile {
                 for (int tqp = 0; tqp < Q; ++tqp) {
                     const C v = si[tqp * QD1];
 #pragma unroll
-                    for (int tq = 0; tq < Q; ++tq) cfma2(acc[tq], a.M2[chi][tq][tqp], v);
+                    for (int tq = 0; tq < Q; ++tq) colmac(acc[tq], a, chi, tq, tqp, v);
                 }
             }
             int tk[DMAX];

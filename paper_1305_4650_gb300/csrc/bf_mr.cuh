@@ -127,20 +127,15 @@ __host__ __device__ constexpr int mr_pc_extra(int q)
 // scratch entries per right-hand side (2 r per pair, plus the row scratch padding)
 __host__ __device__ constexpr int64_t mr_s_stride(int q, int64_t npr) { return 2 * npr * q * q + npr * q * mr_pad(q).rs; }
 
-// acc += M[h][t][u] v: one packed FMA where the coefficients come twice (KArgs::M2, the
-// per-pass kernels), two scalar FMAs in the persistent batch kernel (packed ones cost it
-// spills: 112 bytes at the register budget of two CTAs per SM); the same roundings either way
-template <class MS> struct PackedM { static constexpr bool value = true; };
-template <class P> struct BatchArgs;
-template <class P> struct PackedM<BatchArgs<P>> { static constexpr bool value = false; };
-
+// acc += M[h][t][u] v: two scalar FMAs, the coefficient an operand from the kernel
+// parameters (constant bank).  One packed FMA with the coefficient duplicated (KArgs::M2)
+// needs that pair loaded into registers first: measured 1% slower per apply at N = 512
+// with 16 right-hand sides (the same roundings either way; in the persistent batch kernel
+// the packed form also spilled)
 template <class MS, class C>
 __device__ __forceinline__ void mmac(C &acc, const MS &ms, int h, int t, int u, C v)
 {
-    if constexpr (PackedM<MS>::value)
-        cfma2(acc, ms.M2[h][t][u], v);
-    else
-        cfma(acc, ms.M[h][t][u], v);
+    cfma(acc, ms.M[h][t][u], v);
 }
 
 template <int Q, class P, int K>
