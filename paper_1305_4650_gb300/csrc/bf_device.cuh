@@ -874,11 +874,13 @@ struct Tile {
         Bq = (Bstar << (D * (k - i - 1))) + bp;
     }
 
-    // acc += M[h][t][u] v in the column levels.  d = 2: two scalar FMAs, the coefficient a
-    // kernel-parameter operand (a packed FMA needs the duplicated pair M2 in registers first;
-    // 1% faster on the column passes at N = 1024, q = 5); d = 3 and the row levels keep the
-    // packed form, which measured 0.5-1% faster there.  The same roundings either way.
-    static __device__ __forceinline__ void colmac(C &acc, const KArgs<P> &a, int h, int t, int u, C v)
+    // acc += M[h][t][u] v in the column levels and the first stage of the row levels.  d = 2:
+    // two scalar FMAs, the coefficient a kernel-parameter operand (a packed FMA needs the
+    // duplicated pair M2 in registers first; at N = 1024, q = 5 the column passes 1% and the
+    // row passes 1% faster); d = 3 and the row levels' second stage, whose coefficient index
+    // is not a compile-time constant, keep the packed form, which measured 0.5-2% faster
+    // there.  The same roundings either way.
+    static __device__ __forceinline__ void imac(C &acc, const KArgs<P> &a, int h, int t, int u, C v)
     {
         if constexpr (D == 2)
             cfma(acc, a.M[h][t][u], v);
@@ -957,15 +959,15 @@ struct Tile {
                         const C u0 = cmul(E0, win[t0p + Q * tq]), u1 = cmul(E1, win[t0p + 1 + Q * tq]);
 #pragma unroll
                         for (int t0 = 0; t0 < Q; ++t0) {
-                            colmac(acc[t0], a, c0, t0, t0p, u0);
-                            colmac(acc[t0], a, c0, t0, t0p + 1, u1);
+                            imac(acc[t0], a, c0, t0, t0p, u0);
+                            imac(acc[t0], a, c0, t0, t0p + 1, u1);
                         }
                     }
                     if constexpr (Q & 1) {
                         const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(p1));
                         const C u = cmul(ph<PM>(a, tA, pt, fa.at(cl * Q + Q - 1, it)), win[Q - 1 + Q * tq]);
 #pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) colmac(acc[t0], a, c0, t0, Q - 1, u);
+                        for (int t0 = 0; t0 < Q; ++t0) imac(acc[t0], a, c0, t0, Q - 1, u);
                     }
                 } else if constexpr (D == 2) {
                     const int c0 = c & 1;
@@ -975,7 +977,7 @@ struct Tile {
                         const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], t0p), 0), p1);
                         const C u = cmul(expphase_part<P, D, K>(a, tA, pt), win[t0p + Q * tq]);
 #pragma unroll
-                        for (int t0 = 0; t0 < Q; ++t0) colmac(acc[t0], a, c0, t0, t0p, u);
+                        for (int t0 = 0; t0 < Q; ++t0) imac(acc[t0], a, c0, t0, t0p, u);
                     }
                 } else if constexpr (!P::is_f64) {
                     // d = 3: the parts of coordinates 2 and 1 hoisted, phases two at a time over t'_0
@@ -1002,20 +1004,20 @@ struct Tile {
                             const C u0 = cmul(E0, wrow[t0p]), u1 = cmul(E1, wrow[t0p + 1]);
 #pragma unroll
                             for (int t0 = 0; t0 < Q; ++t0) {
-                                colmac(tmp[t0], a, c0, t0, t0p, u0);
-                                colmac(tmp[t0], a, c0, t0, t0p + 1, u1);
+                                imac(tmp[t0], a, c0, t0, t0p, u0);
+                                imac(tmp[t0], a, c0, t0, t0p + 1, u1);
                             }
                         }
                         if constexpr (Q & 1) {
                             const typename PH::Part pt = PH::add(PH::part(tA, sget<P, Q>(a, 0, l, cb[0], Q - 1), 0), PH2::lane0(p12));
                             const C u = cmul(ph<PM>(a, tA, pt, fa.at((cl * Q + t1p) * Q + Q - 1, it)), wrow[Q - 1]);
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) colmac(tmp[t0], a, c0, t0, Q - 1, u);
+                            for (int t0 = 0; t0 < Q; ++t0) imac(tmp[t0], a, c0, t0, Q - 1, u);
                         }
 #pragma unroll
                         for (int t1 = 0; t1 < Q; ++t1)
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) colmac(acc[t0 + Q * t1], a, c1, t1, t1p, tmp[t0]);
+                            for (int t0 = 0; t0 < Q; ++t0) imac(acc[t0 + Q * t1], a, c1, t1, t1p, tmp[t0]);
                     }
                 } else {
                     const int c0 = c & 1, c1 = (c >> 1) & 1;
@@ -1030,12 +1032,12 @@ struct Tile {
                             PH::src1(sp, 0, sget<P, Q>(a, 0, l, cb[0], t0p));
                             const C u = cmul(expphase<P, D, K>(a, tA, sp), win[t0p + Q * t1p + Q * Q * tq]);
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) colmac(tmp[t0], a, c0, t0, t0p, u);
+                            for (int t0 = 0; t0 < Q; ++t0) imac(tmp[t0], a, c0, t0, t0p, u);
                         }
 #pragma unroll
                         for (int t1 = 0; t1 < Q; ++t1)
 #pragma unroll
-                            for (int t0 = 0; t0 < Q; ++t0) colmac(acc[t0 + Q * t1], a, c1, t1, t1p, tmp[t0]);
+                            for (int t0 = 0; t0 < Q; ++t0) imac(acc[t0 + Q * t1], a, c1, t1, t1p, tmp[t0]);
                     }
                 }
             }
@@ -1067,7 +1069,7 @@ struct Tile {
                 for (int tqp = 0; tqp < Q; ++tqp) {
                     const C v = si[tqp * QD1];
 #pragma unroll
-                    for (int tq = 0; tq < Q; ++tq) colmac(acc[tq], a, chi, tq, tqp, v);
+                    for (int tq = 0; tq < Q; ++tq) imac(acc[tq], a, chi, tq, tqp, v);
                 }
             }
             int tk[DMAX];
@@ -1411,8 +1413,8 @@ struct Tile {
                 const C u = cjmul(phs<PM>(a, tn[t0], sc, fa.at(t0, it)), win[t0]);
 #pragma unroll
                 for (int s0 = 0; s0 < Q; ++s0) {
-                    cfma2(z[0][s0], a.M2[0][t0][s0], u);
-                    cfma2(z[1][s0], a.M2[1][t0][s0], u);
+                    imac(z[0][s0], a, 0, t0, s0, u);
+                    imac(z[1][s0], a, 1, t0, s0, u);
                 }
             }
             C *so = S + (((tau * nblk + beta) * NC + c) * QD1 + th) * 2 * Q;
