@@ -382,7 +382,7 @@ __device__ __forceinline__ void switch_tc_body(const KArgs<P> &a)
 
 // The switch kernels of the two operand formats.  BF16 keeps the compiler's default register
 // target (64 registers; three CTAs fit an SM by shared memory; an explicit bound measured
-// 8% slower), TF32 is compiled for two CTAs per SM, which its shared memory admits (88
+// 8% slower), TF32 is compiled for two CTAs per SM, which its shared memory admits (89
 // registers; with 64 its staging code spilled).
 template <int Q, class P, int K>
 __global__ void __launch_bounds__(SwTC<Q, 0>::NT) k_switch_tc(const KArgs<P> a)
